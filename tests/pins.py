@@ -1,0 +1,114 @@
+"""Independent mathematics the oracle is pinned to (test-side only).
+
+Nothing here calls the oracle or the CUDA path.  The discrete problem is the
+5-point Dirichlet problem on an n x n interior with h = 1/(n+1), scaled by h^2:
+
+    4 u_ij - (u_N + u_S + u_W + u_E) = h^2 f_ij      (boundary values on the ring)
+
+written as  A x = b  with the boundary moved to the right side.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.fft
+
+
+def interior_index(n):
+    return np.arange(n * n).reshape(n, n)
+
+
+def dense_system(u0, f=None):
+    """Dense A (n^2 x n^2, natural row-major ordering) and b for the grid u0."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    A = np.zeros((n * n, n * n))
+    b = np.zeros(n * n)
+    idx = interior_index(n)
+    for i in range(1, n + 1):
+        for j in range(1, n + 1):
+            r = idx[i - 1, j - 1]
+            A[r, r] = 4.0
+            b[r] = h2 * f[i - 1, j - 1] if f is not None else 0.0
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                ii, jj = i + di, j + dj
+                if 1 <= ii <= n and 1 <= jj <= n:
+                    A[r, idx[ii - 1, jj - 1]] = -1.0
+                else:
+                    b[r] += u0[ii, jj]
+    return A, b
+
+
+def dense_solve(u0, f=None):
+    """Exact discrete solution on the full (n+2)^2 array (LAPACK)."""
+    n = u0.shape[0] - 2
+    A, b = dense_system(u0, f)
+    x = np.linalg.solve(A, b)
+    u = u0.copy()
+    u[1:-1, 1:-1] = x.reshape(n, n)
+    return u
+
+
+def dst_solve(u0, f=None):
+    """Exact discrete solution by the type-I discrete sine transform, which
+    diagonalises the 5-point Dirichlet operator: eigenvalues
+    (2 - 2cos(p pi/(n+1))) + (2 - 2cos(q pi/(n+1)))."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    b = np.zeros((n, n)) if f is None else h2 * np.asarray(f, dtype=np.float64).copy()
+    b[0, :] += u0[0, 1:-1]
+    b[-1, :] += u0[-1, 1:-1]
+    b[:, 0] += u0[1:-1, 0]
+    b[:, -1] += u0[1:-1, -1]
+    k = np.arange(1, n + 1)
+    lam = 2.0 - 2.0 * np.cos(k * np.pi / (n + 1))
+    bh = scipy.fft.dstn(b, type=1)
+    uh = bh / (lam[:, None] + lam[None, :])
+    x = scipy.fft.idstn(uh, type=1)
+    u = u0.copy()
+    u[1:-1, 1:-1] = x
+    return u
+
+
+def red_black_iteration(u0, omega, iters, f=None):
+    """Red-black SOR written as a matrix splitting (not as a sweep): with the
+    unknowns ordered red first, A = D - L - U (D = 4I, L strictly lower, U
+    strictly upper in that ordering), x_{k+1} = (D - wL)^{-1}[((1-w)D + wU) x_k + w b].
+    Returns the list of full arrays u_1..u_iters."""
+    n = u0.shape[0] - 2
+    A, b = dense_system(u0, f)
+    ii, jj = np.meshgrid(np.arange(1, n + 1), np.arange(1, n + 1), indexing="ij")
+    red = ((ii + jj) % 2 == 0).ravel()
+    order = np.concatenate([np.nonzero(red)[0], np.nonzero(~red)[0]])
+    P = A[np.ix_(order, order)]
+    bp = b[order]
+    D = np.diag(np.diag(P))
+    L = -np.tril(P, -1)
+    U = -np.triu(P, 1)
+    lhs = D - omega * L
+    M = np.linalg.solve(lhs, (1.0 - omega) * D + omega * U)
+    c = np.linalg.solve(lhs, omega * bp)
+    x = u0[1:-1, 1:-1].ravel()[order].copy()
+    out = []
+    for _ in range(iters):
+        x = M @ x + c
+        full = np.empty(n * n)
+        full[order] = x
+        u = u0.copy()
+        u[1:-1, 1:-1] = full.reshape(n, n)
+        out.append(u)
+    return out
+
+
+def young_rate(omega, n):
+    """Asymptotic SOR convergence factor for a consistently ordered matrix
+    with Jacobi spectral radius mu = cos(pi h), for omega <= omega_opt."""
+    mu = np.cos(np.pi / (n + 1))
+    disc = omega * omega * mu * mu - 4.0 * (omega - 1.0)
+    return ((omega * mu + np.sqrt(disc)) / 2.0) ** 2
+
+
+def rel_err(a, b):
+    """Normwise relative difference over the interior: max|a-b| / max|b|."""
+    a, b = np.asarray(a)[1:-1, 1:-1], np.asarray(b)[1:-1, 1:-1]
+    s = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
