@@ -1,0 +1,191 @@
+/*
+ * sor.h -- C ABI of the GB300 red-black SOR library (libsorgb.so).
+ *
+ * The library solves the 2D steady heat-conduction / Poisson problem
+ *     -Laplace(u) = f  on the unit square, Dirichlet data on the edges,
+ * discretised with the 5-point stencil on an N x N interior (array side N+2,
+ * h = 1/(N+1)), by red-black successive over-relaxation:
+ *   - cell update: Eq. 1 of the paper (SOR extrapolation of the Gauss-Seidel
+ *     value) with the 5-point stencil, Section 2.1 and Section 3.1:
+ *       u_ij <- (1-w) u_ij + (w/4) (u_{i-1,j} + u_{i+1,j} + u_{i,j-1} + u_{i,j+1} + h^2 f_ij)
+ *   - colouring: red <=> (i+j) even, black <=> (i+j) odd (Section 3.1,
+ *     Figure 1); each iteration updates all red cells, then all black cells
+ *     from the new red values (Section 3.1, Algorithm 1);
+ *   - convergence: the largest change between successive iterates is
+ *     compared with the tolerance every K iterations (Section 2.1,
+ *     Section 3.3, Algorithm 1); a residual-based test is also offered.
+ * Indices: row i = 0..N+1 (row 0 is the north edge), column j = 0..N+1;
+ * arrays are row-major, (N+2)*(N+2) doubles, the outer ring holding the
+ * Dirichlet data.  The ring is read, never written.
+ *
+ * Every entry point returns a sor_status; nothing throws, aborts or exits
+ * across the ABI.  Non-convergence within the iteration cap is not an
+ * error: the call returns SOR_OK with result.converged == 0 (Algorithm 1
+ * reports whether SOR converged).
+ *
+ * Pointers to caller data may be host or device pointers (detected with
+ * cudaPointerGetAttributes).  The library never frees caller memory.
+ */
+#ifndef SOR_H_
+#define SOR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sor_ctx sor_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  SOR_OK = 0,
+  SOR_NOT_READY = 1,            /* sor_poll: the solve is still queued or running */
+  SOR_ERR_INVALID_ARG = -1,     /* a NULL pointer, N < 1, w outside (0,2), ... */
+  SOR_ERR_BUDGET = -2,          /* the request alone needs more than the context's HBM budget */
+  SOR_ERR_OOM = -3,             /* a device or host allocation failed */
+  SOR_ERR_CUDA = -4,            /* a CUDA runtime call failed (sor_last_error has the text) */
+  SOR_ERR_TIMEOUT = -5,         /* sor_wait gave up, or a device-side wait ran past its limit */
+  SOR_ERR_INTERNAL = -6,        /* a device-side consistency check failed */
+  SOR_ERR_UNKNOWN_TICKET = -7,  /* sor_poll / sor_wait of a ticket this context never issued,
+                                   or one whose result was already collected */
+  SOR_ERR_CANCELLED = -8        /* the context was destroyed before the solve finished */
+} sor_status;
+
+/* Convergence quantity tested every check_every iterations (plain modes). */
+typedef enum {
+  SOR_STOP_MAXDELTA = 0,  /* max over the interior of |u_k - u_{k-1}| < tol (Section 2.1) */
+  SOR_STOP_RESID_REL = 1  /* ||b - A u||_inf / ||b||_inf < tol, boundary moved into b
+                             (||r||_inf alone when b == 0) */
+} sor_stop;
+
+typedef enum {
+  SOR_FP64 = 0,        /* FP64 storage and arithmetic */
+  SOR_FP32 = 1,        /* FP32 storage and arithmetic (reduced precision; error vs FP64 stated) */
+  SOR_FP32_REFINE = 2  /* FP64 defect correction: r = b - A u and u += d in FP64, the
+                          correction d from inner_sweeps FP32 red-black SOR sweeps on
+                          A d = r starting from d = 0; stops on the relative residual */
+} sor_precision;
+
+/* Bit flags for sor_params.flags. */
+#define SOR_FLAG_EXACT_ORDER 1 /* SOR_FP64: evaluate the update as
+                                  (1-w)*u + (w/4)*(((N+S)+(W+E))+g) with every
+                                  product and sum rounded separately (no fused
+                                  multiply-add, no rescaling).  Slower on GB300,
+                                  whose FP64 rate is low; results then equal a
+                                  plain CPU evaluation bit for bit. */
+
+typedef struct {
+  int32_t n;            /* interior side N >= 1 (array side N+2) */
+  int32_t precision;    /* sor_precision */
+  double omega;         /* relaxation factor, 0 < w < 2; w <= 0 selects
+                           w_opt = 2 / (1 + sin(pi / (N+1))) */
+  double tol;           /* tolerance eps of the stopping test (strict <) */
+  int32_t stop;         /* sor_stop; ignored by SOR_FP32_REFINE (always residual) */
+  int32_t max_iters;    /* cap on red-black iterations (sweeps); >= 0 */
+  int32_t check_every;  /* K >= 1: test only when the iteration count is a multiple of K
+                           (Section 3.3).  SOR_FP32_REFINE tests after every correction. */
+  int32_t inner_sweeps; /* SOR_FP32_REFINE: sweeps per correction (>= 1); 0 = 20 */
+  int32_t flags;        /* SOR_FLAG_* */
+  int32_t reserved;     /* must be 0 */
+} sor_params;
+
+typedef struct {
+  int32_t iterations;     /* red-black iterations (sweeps) carried out */
+  int32_t converged;      /* 1 if the stopping test passed, 0 if the cap was hit */
+  int32_t outer_steps;    /* SOR_FP32_REFINE: corrections applied; 0 otherwise */
+  int32_t reserved;
+  double final_maxdelta;  /* max |change| of the last iteration (plain modes; -1 if none) */
+  double final_resid_rel; /* relative residual of the returned solution, in FP64 */
+  double latency_s;       /* host wall time from the call (or submit) to the result */
+  double device_s;        /* device time of the solve's kernels and copies (CUDA events) */
+} sor_result;
+
+/* Optional device-memory hooks: alloc(bytes, user) returns device memory or
+ * NULL; free_(ptr, user) releases it.  Both NULL: cudaMalloc / cudaFree. */
+typedef void *(*sor_alloc_fn)(size_t bytes, void *user);
+typedef void (*sor_free_fn)(void *ptr, void *user);
+
+/* Create a context on CUDA device `device`.
+ *   hbm_budget_bytes: upper bound on the device memory the context holds for
+ *     solves (0 = 90% of the free memory at creation).  A solve needing more
+ *     than the whole budget fails with SOR_ERR_BUDGET; batch requests wait
+ *     until enough of the budget is free.
+ *   cuda_stream: cudaStream_t for sor_solve's work (NULL = a stream the
+ *     library creates).  Batch work runs on a library-owned stream.
+ * On success *out receives the context (free it with sor_destroy). */
+sor_status sor_create(sor_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream,
+                      sor_alloc_fn alloc, sor_free_fn free_, void *alloc_user);
+
+/* Blocking solve of one problem.
+ *   u0:    (N+2)^2 row-major initial profile; its ring is the Dirichlet data
+ *          (Algorithm 1 input).  Host or device memory.
+ *   f:     N*N row-major interior source of -Laplace(u) = f, or NULL for f = 0.
+ *   u_out: (N+2)^2 row-major final profile (may equal u0).
+ *   res:   optional result record.
+ * Inputs are read before the call returns; u_out is written before it returns. */
+sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
+                     sor_result *res);
+
+/* Non-blocking submission to the context's continuous-batching scheduler.
+ * u0 and f are copied before the call returns.  u_out must stay valid until
+ * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.
+ * Requests are admitted in arrival order while their device memory fits the
+ * budget, and every admitted request is stepped together with the others. */
+sor_status sor_batch_submit(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f,
+                            double *u_out, uint64_t *ticket);
+
+/* SOR_NOT_READY while the ticket is queued or running; SOR_OK (and *res)
+ * once u_out holds the result -- the ticket is then retired; the solve's own
+ * error status if it failed; SOR_ERR_UNKNOWN_TICKET otherwise. */
+sor_status sor_poll(sor_ctx *ctx, uint64_t ticket, sor_result *res);
+
+/* sor_poll, blocking up to timeout_s seconds (< 0: no limit); SOR_ERR_TIMEOUT
+ * if the ticket is still pending then (it stays valid). */
+sor_status sor_wait(sor_ctx *ctx, uint64_t ticket, double timeout_s, sor_result *res);
+
+/* Cancel queued and running batch work (their tickets report
+ * SOR_ERR_CANCELLED to nobody: the context is gone), release every device
+ * buffer and stream the library created, and free the context. */
+sor_status sor_destroy(sor_ctx *ctx);
+
+/* Tuning and instrumentation knobs (sor_set_option / sor_get_option). */
+typedef enum {
+  SOR_OPT_TIMING = 1,          /* 1: time the sweep kernels with CUDA events (sor_get_stats) */
+  SOR_OPT_GRAPHS = 2,          /* 1 (default): replay launch sequences as CUDA graphs */
+  SOR_OPT_CHUNK = 3,           /* iterations per launched chunk between convergence polls (0 = auto) */
+  SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per tile pass (0 = autotuned) */
+  SOR_OPT_AUTOTUNE = 5,        /* 1: time candidate kernel configurations on first use of a size */
+  SOR_OPT_BATCH_MAX_SLOTS = 6  /* cap on concurrently admitted batch requests (0 = no cap) */
+} sor_option;
+
+sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);
+sor_status sor_get_option(sor_ctx *ctx, int32_t option, int64_t *value);
+
+/* Counters accumulated since sor_create or the last sor_reset_stats. */
+typedef struct {
+  uint64_t solves;            /* sor_solve calls completed */
+  uint64_t batch_completed;   /* batch tickets completed */
+  uint64_t sweep_launches;    /* colour half-sweep (or fused sweep) kernel launches issued */
+  uint64_t lattice_updates;   /* interior cell updates performed (sweeps x N^2) */
+  double sweep_ms;            /* CUDA-event time of the timed sweep chunks (SOR_OPT_TIMING) */
+  uint64_t timed_launches;    /* sweep launches inside those timed chunks */
+  uint64_t timed_updates;     /* lattice updates inside those timed chunks */
+  uint64_t bytes_reserved;    /* device bytes currently held for solves */
+  uint64_t bytes_peak;        /* high-water mark of bytes_reserved */
+} sor_stats;
+
+sor_status sor_get_stats(sor_ctx *ctx, sor_stats *out);
+sor_status sor_reset_stats(sor_ctx *ctx);
+
+/* Text of the last error recorded on this context (thread-safe copy). */
+sor_status sor_last_error(sor_ctx *ctx, char *buf, size_t len);
+const char *sor_status_string(int32_t status);
+
+/* w_opt = 2 / (1 + sin(pi / (N+1))) for the 5-point Laplacian (Young). */
+double sor_omega_opt(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOR_H_ */

@@ -1,0 +1,598 @@
+// Continuous-batching scheduler.
+//
+// One host thread per context owns the admitted requests ("slots").  Each
+// scheduler step
+//   1. admits queued requests in arrival order while their device memory fits
+//      the context budget (and the slot cap), copying and packing their inputs;
+//   2. launches one step over every active slot at once: the kernels walk a
+//      device-side tile table that covers all slots of a kind, so grids of
+//      different sizes share each launch (a defect-correction step is a
+//      residual pass plus the inner sweeps; a plain step is a fixed number of
+//      red-black iterations);
+//   3. reads back the per-slot state (the only device->host sync of a step)
+//      and retires finished slots: unpack, copy to the caller, free memory.
+// Requests that arrive while others run are admitted at the next step, so
+// their work overlaps on the device with the slots already running.  Slots
+// never interact: every slot's arithmetic is the same as a lone solve.
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+#include <unordered_set>
+
+#include "sor_runtime.h"
+
+namespace sorgb {
+
+#define SOR_BCK(expr)                                                                              \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      std::ostringstream os_;                                                                      \
+      os_ << #expr << ": " << cudaGetErrorString(e_) << " (" << __FILE__ << ":" << __LINE__ << ")"; \
+      c->set_error(os_.str());                                                                     \
+      return SOR_ERR_CUDA;                                                                         \
+    }                                                                                              \
+  } while (0)
+
+static constexpr int kPlainStepIters = 16;  // iterations per scheduler step for plain slots
+
+struct Batcher {
+  Ctx* c = nullptr;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;      // wakes the scheduler
+  std::condition_variable done_cv; // wakes sor_wait callers
+  std::deque<std::unique_ptr<Request>> queue;
+  std::unordered_map<uint64_t, Completed> completed;
+  std::unordered_set<uint64_t> pending;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  bool failed = false;
+  sor_status fail_status = SOR_OK;
+
+  // scheduler-thread state
+  cudaStream_t stream = nullptr;
+  std::vector<std::unique_ptr<Request>> slots;  // index = slot id (nullptr = free)
+  int cap = 0;
+  SlotDesc* d_desc = nullptr;
+  SlotState* d_state = nullptr;
+  SlotState* h_state = nullptr;  // pinned
+  Tile* d_tiles = nullptr;       // [refine sweep | refine resid | plain64 | plain32 | retire]
+  size_t tiles_cap = 0;
+  int nt_refine = 0, nt_p64 = 0, nt_p32 = 0;
+  size_t off_p64 = 0, off_p32 = 0, off_retire = 0;
+  int max_inner = 1;
+  bool any_resid_stop = false;
+  uint64_t version = 0;       // bumps when the active set changes
+  uint64_t graph_version = ~0ull;
+  cudaGraphExec_t graph = nullptr;
+  size_t reserved_tables = 0;
+};
+
+static sor_status ensure_tables(Batcher* b, int cap, size_t ntiles) {
+  Ctx* c = b->c;
+  if (cap > b->cap) {
+    int nc = std::max(cap, std::max(16, b->cap * 2));
+    SlotDesc* nd = (SlotDesc*)ctx_dev_alloc(c, sizeof(SlotDesc) * nc);
+    SlotState* ns = (SlotState*)ctx_dev_alloc(c, sizeof(SlotState) * nc);
+    SlotState* nh = nullptr;
+    if (!nd || !ns || cudaMallocHost(&nh, sizeof(SlotState) * nc) != cudaSuccess) {
+      cudaGetLastError();
+      ctx_dev_free(c, nd);
+      ctx_dev_free(c, ns);
+      c->set_error("batch table allocation failed");
+      return SOR_ERR_OOM;
+    }
+    SOR_BCK(cudaMemsetAsync(ns, 0, sizeof(SlotState) * nc, b->stream));
+    if (b->cap) {
+      SOR_BCK(cudaMemcpyAsync(nd, b->d_desc, sizeof(SlotDesc) * b->cap, cudaMemcpyDeviceToDevice, b->stream));
+      SOR_BCK(cudaMemcpyAsync(ns, b->d_state, sizeof(SlotState) * b->cap, cudaMemcpyDeviceToDevice, b->stream));
+      SOR_BCK(cudaStreamSynchronize(b->stream));
+    }
+    ctx_dev_free(c, b->d_desc);
+    ctx_dev_free(c, b->d_state);
+    if (b->h_state) cudaFreeHost(b->h_state);
+    b->d_desc = nd;
+    b->d_state = ns;
+    b->h_state = nh;
+    b->cap = nc;
+    b->slots.resize(nc);
+  }
+  if (ntiles > b->tiles_cap) {
+    size_t nc = std::max(ntiles, b->tiles_cap * 2);
+    Tile* nt = (Tile*)ctx_dev_alloc(c, sizeof(Tile) * nc);
+    if (!nt) {
+      c->set_error("batch tile table allocation failed");
+      return SOR_ERR_OOM;
+    }
+    SOR_BCK(cudaStreamSynchronize(b->stream));
+    ctx_dev_free(c, b->d_tiles);
+    b->d_tiles = nt;
+    b->tiles_cap = nc;
+  }
+  return SOR_OK;
+}
+
+// Rebuild the tile table after the active set changed.
+static sor_status rebuild_tiles(Batcher* b) {
+  std::vector<Tile> ref, p64, p32;
+  b->max_inner = 1;
+  b->any_resid_stop = false;
+  for (size_t s = 0; s < b->slots.size(); ++s) {
+    Request* r = b->slots[s].get();
+    if (!r) continue;
+    const Layout& L = r->buf.L;
+    if (r->plan.kind == kRefine) {
+      build_tiles(L, (int)s, &ref, nullptr);
+      b->max_inner = std::max(b->max_inner, r->plan.inner);
+    } else if (r->plan.kind == kPlain64) {
+      build_tiles(L, (int)s, &p64, nullptr);
+      if (r->plan.stop == kStopResid) b->any_resid_stop = true;
+    } else {
+      build_tiles(L, (int)s, &p32, nullptr);
+      if (r->plan.stop == kStopResid) b->any_resid_stop = true;
+    }
+  }
+  const size_t total = ref.size() + p64.size() + p32.size();
+  sor_status rs = ensure_tables(b, (int)b->slots.size(), total + 1);
+  if (rs != SOR_OK) return rs;
+  std::vector<Tile> all;
+  all.reserve(total);
+  all.insert(all.end(), ref.begin(), ref.end());
+  all.insert(all.end(), p64.begin(), p64.end());
+  all.insert(all.end(), p32.begin(), p32.end());
+  b->nt_refine = (int)ref.size();
+  b->nt_p64 = (int)p64.size();
+  b->nt_p32 = (int)p32.size();
+  b->off_p64 = ref.size();
+  b->off_p32 = ref.size() + p64.size();
+  Ctx* c = b->c;
+  if (!all.empty())
+    SOR_BCK(cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, b->stream));
+  b->version++;
+  return SOR_OK;
+}
+
+// The launches of one scheduler step over every active slot.
+static sor_status enqueue_step(Batcher* b) {
+  Ctx* c = b->c;
+  cudaStream_t s = b->stream;
+  if (b->nt_refine) {
+    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 0, s));
+    for (int sw = 0; sw < b->max_inner; ++sw) {
+      SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 0, sw, s));
+      SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 1, sw, s));
+    }
+  }
+  for (int kind = 0; kind < 2; ++kind) {
+    const int nt = kind == 0 ? b->nt_p64 : b->nt_p32;
+    if (!nt) continue;
+    const Tile* t = b->d_tiles + (kind == 0 ? b->off_p64 : b->off_p32);
+    const SweepKind sk = kind == 0 ? kSweepPlain64 : kSweepPlain32;
+    for (int it = 0; it < kPlainStepIters; ++it) {
+      SOR_BCK(launch_sweep(sk, b->d_desc, b->d_state, t, nt, 0, 0, 0, s));
+      SOR_BCK(launch_sweep(sk, b->d_desc, b->d_state, t, nt, 0, 1, 0, s));
+      if (b->any_resid_stop)
+        SOR_BCK(launch_resid(kind == 0 ? kResidCheck64 : kResidCheck32, b->d_desc, b->d_state, t, nt, 0, 0, s));
+    }
+  }
+  return SOR_OK;
+}
+
+static sor_status run_step(Batcher* b) {
+  Ctx* c = b->c;
+  if (!c->opt_graphs.load()) return enqueue_step(b);
+  if (b->graph_version != b->version || !b->graph) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    SOR_BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    sor_status rs = enqueue_step(b);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (rs != SOR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rs;
+    }
+    SOR_BCK(e);
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    SOR_BCK(e);
+    b->graph_version = b->version;
+  }
+  SOR_BCK(cudaGraphLaunch(b->graph, b->stream));
+  return SOR_OK;
+}
+
+static size_t request_bytes(const Plan& p) {
+  const size_t stage = (size_t)(p.n + 2) * (p.n + 2) * 8 + (p.has_f ? (size_t)p.n * p.n * 8 : 0);
+  return slot_bytes(p, false) + stage;
+}
+
+// Allocate, copy and pack one request into slot `s` (scheduler thread).
+static sor_status activate(Batcher* b, Request* r, int s) {
+  Ctx* c = b->c;
+  const Plan& p = r->plan;
+  sor_status rs = alloc_slot(c, p, false, &r->buf);
+  if (rs != SOR_OK) return rs;
+  r->stage_bytes = (size_t)(p.n + 2) * (p.n + 2) * 8 + (p.has_f ? (size_t)p.n * p.n * 8 : 0);
+  r->d_stage = (double*)ctx_dev_alloc(c, r->stage_bytes);
+  if (!r->d_stage) {
+    free_slot(c, &r->buf);
+    return SOR_ERR_OOM;
+  }
+  r->slot = s;
+  rs = zero_slot(c, p, &r->buf, b->stream);
+  if (rs != SOR_OK) return rs;
+  const size_t nu = (size_t)(p.n + 2) * (p.n + 2);
+  SOR_BCK(cudaMemcpyAsync(r->d_stage, r->u0.data(), nu * 8, cudaMemcpyHostToDevice, b->stream));
+  if (p.has_f)
+    SOR_BCK(cudaMemcpyAsync(r->d_stage + nu, r->f.data(), (size_t)p.n * p.n * 8, cudaMemcpyHostToDevice, b->stream));
+  fill_desc(p, &r->buf);
+  SlotState st0 = initial_state(p);
+  SOR_BCK(cudaMemcpyAsync(b->d_desc + s, &r->buf.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, b->stream));
+  SOR_BCK(cudaMemcpyAsync(b->d_state + s, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, b->stream));
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.u0 = r->d_stage;
+  pa.f = p.has_f ? r->d_stage + nu : nullptr;
+  pa.n = p.n;
+  pa.pitch = r->buf.L.pitch;
+  const double h = 1.0 / (double)(p.n + 1);
+  pa.h2 = h * h;
+  pa.fp32 = p.kind != kPlain64;
+  const SlotDesc& d = r->buf.desc;
+  if (p.kind == kRefine) {
+    for (int k = 0; k < 2; ++k)
+      for (int col = 0; col < 2; ++col) pa.u[k][col] = d.u[k][col];
+    for (int col = 0; col < 2; ++col) pa.g64[col] = (double*)d.g64[col];
+  } else {
+    for (int col = 0; col < 2; ++col) {
+      pa.x[0][col] = d.x[0][col];
+      pa.g[col] = d.g[col];
+      pa.g64[col] = p.kind == kPlain32 ? (double*)d.g64[col] : nullptr;
+    }
+  }
+  pa.state = b->d_state + s;
+  SOR_BCK(launch_pack(pa, b->stream));
+  r->u0.clear();
+  r->u0.shrink_to_fit();
+  r->f.clear();
+  r->f.shrink_to_fit();
+  return SOR_OK;
+}
+
+static void complete(Batcher* b, uint64_t ticket, sor_status st, const sor_result& res) {
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    b->pending.erase(ticket);
+    Completed cp;
+    cp.status = st;
+    cp.res = res;
+    b->completed[ticket] = cp;
+  }
+  b->done_cv.notify_all();
+}
+
+static void release_request(Batcher* b, Request* r) {
+  Ctx* c = b->c;
+  free_slot(c, &r->buf);
+  ctx_dev_free(c, r->d_stage);
+  r->d_stage = nullptr;
+  ctx_release(c, request_bytes(r->plan));
+}
+
+// Retire finished slots: final residual for plain slots, unpack, copy out.
+static sor_status retire(Batcher* b, const std::vector<int>& fin) {
+  Ctx* c = b->c;
+  cudaStream_t s = b->stream;
+  std::vector<Tile> p64, p32;
+  for (int sidx : fin) {
+    Request* r = b->slots[sidx].get();
+    if (r->plan.kind == kPlain64) build_tiles(r->buf.L, sidx, &p64, nullptr);
+    if (r->plan.kind == kPlain32) build_tiles(r->buf.L, sidx, &p32, nullptr);
+  }
+  if (!p64.empty() || !p32.empty()) {
+    std::vector<Tile> all(p64);
+    all.insert(all.end(), p32.begin(), p32.end());
+    Tile* dt = (Tile*)ctx_dev_alloc(c, sizeof(Tile) * all.size());
+    if (!dt) return SOR_ERR_OOM;
+    SOR_BCK(cudaMemcpyAsync(dt, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, s));
+    if (!p64.empty()) SOR_BCK(launch_resid(kResidFinal64, b->d_desc, b->d_state, dt, (int)p64.size(), 0, 0, s));
+    if (!p32.empty())
+      SOR_BCK(launch_resid(kResidFinal32, b->d_desc, b->d_state, dt + p64.size(), (int)p32.size(), 0, 0, s));
+    SOR_BCK(cudaStreamSynchronize(s));
+    ctx_dev_free(c, dt);
+    for (int sidx : fin)
+      SOR_BCK(cudaMemcpyAsync(&b->h_state[sidx], b->d_state + sidx, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR_BCK(cudaStreamSynchronize(s));
+  }
+  for (int sidx : fin) {
+    Request* r = b->slots[sidx].get();
+    const SlotState& hs = b->h_state[sidx];
+    const Plan& p = r->plan;
+    const SlotDesc& d = r->buf.desc;
+    double* dout = r->out_on_device ? r->u_out : r->d_stage;
+    if (p.kind == kRefine)
+      SOR_BCK(launch_unpack(d.u[hs.ubuf][0], d.u[hs.ubuf][1], false, p.n, r->buf.L.pitch, dout, s));
+    else
+      SOR_BCK(launch_unpack(d.x[hs.xbuf][0], d.x[hs.xbuf][1], p.kind == kPlain32, p.n, r->buf.L.pitch, dout, s));
+    if (!r->out_on_device)
+      SOR_BCK(cudaMemcpyAsync(r->u_out, dout, (size_t)(p.n + 2) * (p.n + 2) * 8, cudaMemcpyDeviceToHost, s));
+  }
+  SOR_BCK(cudaStreamSynchronize(s));
+  const double t = now_s();
+  for (int sidx : fin) {
+    std::unique_ptr<Request> r = std::move(b->slots[sidx]);
+    const SlotState& hs = b->h_state[sidx];
+    sor_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.iterations = hs.iters;
+    res.converged = hs.converged;
+    res.outer_steps = r->plan.kind == kRefine ? hs.outer : 0;
+    res.final_maxdelta = hs.last_dmax;
+    res.final_resid_rel = hs.last_rho;
+    res.latency_s = t - r->t_submit;
+    res.device_s = 0.0;
+    {
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.batch_completed += 1;
+      c->stats.sweep_launches += 2ull * (unsigned long long)hs.iters;
+      c->stats.lattice_updates +=
+          (unsigned long long)hs.iters * (unsigned long long)r->plan.n * (unsigned long long)r->plan.n;
+    }
+    release_request(b, r.get());
+    complete(b, r->ticket, hs.error ? SOR_ERR_INTERNAL : SOR_OK, res);
+  }
+  return SOR_OK;
+}
+
+static int active_count(const Batcher* b) {
+  int n = 0;
+  for (const auto& r : b->slots)
+    if (r) ++n;
+  return n;
+}
+
+static void fail_all(Batcher* b, sor_status st) {
+  sor_result res;
+  std::memset(&res, 0, sizeof(res));
+  std::vector<uint64_t> tickets;
+  for (auto& r : b->slots)
+    if (r) {
+      tickets.push_back(r->ticket);
+      release_request(b, r.get());
+      r.reset();
+    }
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    for (auto& q : b->queue) tickets.push_back(q->ticket);
+    b->queue.clear();
+    b->failed = true;
+    b->fail_status = st;
+  }
+  for (uint64_t t : tickets) complete(b, t, st, res);
+}
+
+static void scheduler_main(Batcher* b) {
+  Ctx* c = b->c;
+  cudaSetDevice(c->device);
+  for (;;) {
+    std::vector<std::unique_ptr<Request>> admitted;
+    {
+      std::unique_lock<std::mutex> g(b->mu);
+      b->cv.wait(g, [&] { return b->stop || !b->queue.empty() || active_count(b) > 0; });
+      if (b->stop) break;
+      const int cap = c->opt_max_slots.load();
+      int active = active_count(b);
+      while (!b->queue.empty() && (cap <= 0 || active + (int)admitted.size() < cap)) {
+        Request* r = b->queue.front().get();
+        const size_t need = request_bytes(r->plan);
+        if (ctx_reserve(c, need, false, 0.0) != SOR_OK) break;  // waits for retirements
+        admitted.push_back(std::move(b->queue.front()));
+        b->queue.pop_front();
+      }
+      if (admitted.empty() && active == 0) {
+        // nothing running here will free memory: drop sor_solve's cached
+        // workspace if no solve is using it, else wait for it to finish
+        g.unlock();
+        if (c->solve_mu.try_lock()) {
+          release_solve_workspace(c);
+          c->solve_mu.unlock();
+        }
+        std::unique_lock<std::mutex> mg(c->mem_mu);
+        c->mem_cv.wait_for(mg, std::chrono::milliseconds(5));
+        continue;
+      }
+    }
+    sor_status rs = SOR_OK;
+    for (auto& r : admitted) {
+      int sidx = -1;
+      for (size_t k = 0; k < b->slots.size(); ++k)
+        if (!b->slots[k]) { sidx = (int)k; break; }
+      if (sidx < 0) {
+        sidx = (int)b->slots.size();
+        rs = ensure_tables(b, sidx + 1, 1);
+        if (rs != SOR_OK) break;
+        if ((int)b->slots.size() <= sidx) b->slots.resize(sidx + 1);
+      }
+      rs = activate(b, r.get(), sidx);
+      if (rs != SOR_OK) {
+        sor_result res;
+        std::memset(&res, 0, sizeof(res));
+        ctx_release(c, request_bytes(r->plan));
+        complete(b, r->ticket, rs, res);
+        rs = SOR_OK;
+        continue;
+      }
+      b->slots[sidx] = std::move(r);
+    }
+    if (rs == SOR_OK && !admitted.empty()) rs = rebuild_tiles(b);
+    if (rs == SOR_OK && active_count(b) > 0) rs = run_step(b);
+    if (rs == SOR_OK) {
+      for (size_t k = 0; k < b->slots.size(); ++k)
+        if (b->slots[k]) {
+          cudaError_t e =
+              cudaMemcpyAsync(&b->h_state[k], b->d_state + k, sizeof(SlotState), cudaMemcpyDeviceToHost, b->stream);
+          if (e != cudaSuccess) {
+            c->set_error(cudaGetErrorString(e));
+            rs = SOR_ERR_CUDA;
+            break;
+          }
+        }
+    }
+    if (rs == SOR_OK) {
+      cudaError_t e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) {
+        c->set_error(cudaGetErrorString(e));
+        rs = SOR_ERR_CUDA;
+      }
+    }
+    if (rs == SOR_OK) {
+      std::vector<int> fin;
+      for (size_t k = 0; k < b->slots.size(); ++k)
+        if (b->slots[k] && b->h_state[k].done) fin.push_back((int)k);
+      if (!fin.empty()) {
+        rs = retire(b, fin);
+        if (rs == SOR_OK) rs = rebuild_tiles(b);
+      }
+    }
+    if (rs != SOR_OK) {
+      fail_all(b, rs);
+      break;
+    }
+  }
+  // shutdown: drop queued and active work
+  for (auto& r : b->slots)
+    if (r) {
+      release_request(b, r.get());
+      r.reset();
+    }
+}
+
+void BatcherDeleter::operator()(Batcher* b) const { delete b; }
+
+static sor_status start_batcher(Ctx* c) {
+  std::lock_guard<std::mutex> g(c->batcher_mu);
+  if (c->batcher) return SOR_OK;
+  std::unique_ptr<Batcher, BatcherDeleter> b(new Batcher());
+  b->c = c;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    c->set_error(cudaGetErrorString(e));
+    return SOR_ERR_CUDA;
+  }
+  sor_status rs = ensure_tables(b.get(), 16, 64);
+  if (rs != SOR_OK) return rs;
+  b->slots.clear();
+  b->slots.resize(b->cap);
+  Batcher* raw = b.get();
+  c->batcher = std::move(b);
+  raw->th = std::thread(scheduler_main, raw);
+  return SOR_OK;
+}
+
+sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out, uint64_t* ticket) {
+  if (request_bytes(p) > c->budget) {
+    c->set_error("request needs more device memory than the whole budget");
+    return SOR_ERR_BUDGET;
+  }
+  sor_status rs = start_batcher(c);
+  if (rs != SOR_OK) return rs;
+  Batcher* b = c->batcher.get();
+  auto r = std::make_unique<Request>();
+  r->plan = p;
+  r->t_submit = now_s();
+  const size_t nu = (size_t)(p.n + 2) * (p.n + 2);
+  r->u0.resize(nu);
+  if (is_device_ptr(u0)) {
+    if (cudaMemcpy(r->u0.data(), u0, nu * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      c->set_error("copy of u0 failed");
+      return SOR_ERR_CUDA;
+    }
+  } else {
+    std::memcpy(r->u0.data(), u0, nu * 8);
+  }
+  if (p.has_f) {
+    const size_t nf = (size_t)p.n * p.n;
+    r->f.resize(nf);
+    if (is_device_ptr(f)) {
+      if (cudaMemcpy(r->f.data(), f, nf * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        c->set_error("copy of f failed");
+        return SOR_ERR_CUDA;
+      }
+    } else {
+      std::memcpy(r->f.data(), f, nf * 8);
+    }
+  }
+  r->u_out = u_out;
+  r->out_on_device = is_device_ptr(u_out);
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    if (b->failed) return b->fail_status;
+    r->ticket = b->next_ticket++;
+    *ticket = r->ticket;
+    b->pending.insert(r->ticket);
+    b->queue.push_back(std::move(r));
+  }
+  b->cv.notify_all();
+  return SOR_OK;
+}
+
+sor_status batch_poll(Ctx* c, uint64_t ticket, double timeout_s, sor_result* res) {
+  Batcher* b = nullptr;
+  {
+    std::lock_guard<std::mutex> g(c->batcher_mu);
+    b = c->batcher.get();
+  }
+  if (!b) return SOR_ERR_UNKNOWN_TICKET;
+  std::unique_lock<std::mutex> g(b->mu);
+  auto ready = [&] { return b->completed.count(ticket) > 0 || b->pending.count(ticket) == 0; };
+  if (timeout_s != 0.0 && !ready()) {
+    if (timeout_s < 0)
+      b->done_cv.wait(g, ready);
+    else
+      b->done_cv.wait_for(g, std::chrono::duration<double>(timeout_s), ready);
+  }
+  auto it = b->completed.find(ticket);
+  if (it != b->completed.end()) {
+    const Completed cp = it->second;
+    b->completed.erase(it);
+    if (res) *res = cp.res;
+    return cp.status;
+  }
+  if (b->pending.count(ticket)) return timeout_s != 0.0 ? SOR_ERR_TIMEOUT : SOR_NOT_READY;
+  return SOR_ERR_UNKNOWN_TICKET;
+}
+
+void batch_shutdown(Ctx* c) {
+  std::unique_ptr<Batcher, BatcherDeleter> b;
+  {
+    std::lock_guard<std::mutex> g(c->batcher_mu);
+    b = std::move(c->batcher);
+  }
+  if (!b) return;
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    b->stop = true;
+  }
+  b->cv.notify_all();
+  c->mem_cv.notify_all();
+  if (b->th.joinable()) b->th.join();
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    b->queue.clear();  // queued requests hold no reservation yet
+    b->pending.clear();
+  }
+  b->done_cv.notify_all();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaStreamSynchronize(b->stream);
+  ctx_dev_free(c, b->d_desc);
+  ctx_dev_free(c, b->d_state);
+  ctx_dev_free(c, b->d_tiles);
+  if (b->h_state) cudaFreeHost(b->h_state);
+  cudaStreamDestroy(b->stream);
+}
+
+}  // namespace sorgb

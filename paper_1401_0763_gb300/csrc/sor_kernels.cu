@@ -1,0 +1,579 @@
+// Red-black SOR kernels for sm_103a (GB300).
+//
+//   k_pack / k_unpack     natural (N+2)^2 <-> colour-split storage, h^2 f, ||b~||_inf
+//   k_sweep<T>            one colour phase (Section 3.1, Algorithm 1 updateGridRed /
+//                         updateGridBlack) over a list of tiles of one or many slots,
+//                         with the fused max|change| reduction (Section 2.1,
+//                         Section 3.3) and the per-iteration bookkeeping of Algorithm 1
+//   k_sweep_fast64        FP64 phase with shared neighbour pair sums and rescaled
+//                         unknowns (fewer FP64 instructions per update)
+//   k_resid<T>            scaled residual r~ = h^2 f + sum_nb(u) - 4u in FP64 with
+//                         the relative-residual test and, for defect correction,
+//                         u += d fused in
+//
+// Arithmetic: k_sweep and k_resid evaluate every expression in the order
+//   (1-w)*u + (w/4)*(((N+S)+(W+E))+g)   and   (g + ((N+S)+(W+E))) - 4u
+// with each product and sum rounded on its own (__fmul_rn / __fadd_rn and the
+// FP64 forms), so their results do not depend on compiler contraction.
+#include <cuda_runtime.h>
+
+#include "sor_device.cuh"
+#include "sor_kernels.h"
+
+namespace sorgb {
+
+// ------------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  double2 a = reinterpret_cast<const double2*>(p)[0];
+  double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// |x| as the bit pattern of a non-negative double: unsigned order == numeric
+// order, and any NaN compares above +inf, so a NaN is never lost by max.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Block-wide max of v into *dst (atomic).  All threads of the block call it.
+__device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long long* dst,
+                                             unsigned long long* smem /* [kWarpsY] */) {
+  v = warp_max64(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = smem[0];
+#pragma unroll
+    for (int k = 1; k < kWarpsY; ++k) m = umax64(m, smem[k]);
+    if (m) atomicMax(dst, m);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ size_t eidx(int i, int q, int pitch) { return (size_t)i * pitch + q + kOff; }
+
+// ------------------------------------------------------------------------------------------------
+// pack / unpack
+// ------------------------------------------------------------------------------------------------
+
+// Thread (i, q) moves the natural cells j = 2q-1 and j = 2q of row i (one of
+// each colour) into the colour arrays; interior cells also receive h^2 f and
+// contribute |b~| = |h^2 f + (ring neighbours)| to ||b~||_inf.
+template <typename T>
+__global__ void k_pack(const double* __restrict__ u0, const double* __restrict__ f, int n, int pitch, double h2,
+                       T* x00, T* x01, T* x10, T* x11, T* g0, T* g1, double* g64_0, double* g64_1,
+                       double* u00, double* u01, double* u10, double* u11, SlotState* st) {
+  __shared__ unsigned long long red[kWarpsY];
+  const int m = n + 2;
+  const int qw = (n + 1) / 2 + 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  unsigned long long bb = 0;
+  if (q < qw) {
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int j = 2 * q - 1 + t;
+      if (j < 0 || j >= m) continue;
+      const int c = (i + j) & 1;
+      const double v = u0[(size_t)i * m + j];
+      const size_t e = eidx(i, q, pitch);
+      T* xa = c ? x01 : x00;
+      T* xb = c ? x11 : x10;
+      if (xa) xa[e] = (T)v;
+      if (xb) xb[e] = (T)v;
+      double* ua = c ? u01 : u00;
+      double* ub = c ? u11 : u10;
+      if (ua) ua[e] = v;
+      if (ub) ub[e] = v;
+      const bool interior = (i >= 1 && i <= n && j >= 1 && j <= n);
+      double gij = 0.0;
+      if (interior && f) gij = __dmul_rn(h2, f[(size_t)(i - 1) * n + (j - 1)]);
+      T* gg = c ? g1 : g0;
+      if (gg) gg[e] = (T)gij;
+      double* g6 = c ? g64_1 : g64_0;
+      if (g6) g6[e] = gij;
+      if (interior) {
+        // b~ = g + ring neighbours, summed in the order N, S, W, E
+        double bnd = 0.0;
+        if (i == 1) bnd = __dadd_rn(bnd, u0[(size_t)0 * m + j]);
+        if (i == n) bnd = __dadd_rn(bnd, u0[(size_t)(n + 1) * m + j]);
+        if (j == 1) bnd = __dadd_rn(bnd, u0[(size_t)i * m + 0]);
+        if (j == n) bnd = __dadd_rn(bnd, u0[(size_t)i * m + (n + 1)]);
+        bb = umax64(bb, abs_bits(__dadd_rn(gij, bnd)));
+      }
+    }
+  }
+  block_max_to(bb, &st->bmax_bits, red);
+}
+
+// Inverse of k_pack for the iterate in colour arrays c0 / c1 (type T).
+template <typename T>
+__global__ void k_unpack(const T* __restrict__ c0, const T* __restrict__ c1, int n, int pitch,
+                         double* __restrict__ out) {
+  const int m = n + 2;
+  const int qw = (n + 1) / 2 + 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (q >= qw) return;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int j = 2 * q - 1 + t;
+    if (j < 0 || j >= m) continue;
+    const int c = (i + j) & 1;
+    out[(size_t)i * m + j] = (double)(c ? c1 : c0)[eidx(i, q, pitch)];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// one colour phase, exact operation order
+// ------------------------------------------------------------------------------------------------
+
+// Per-slot decisions taken once per tile by thread 0.
+struct TileCtl {
+  int skip, k, measure, xbuf;
+};
+
+// Plain-mode bookkeeping after the black phase of iteration k (Algorithm 1):
+// count the iteration, test the change on check iterations, stop at the cap.
+__device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st, int k, int measure) {
+  st->arrive = 0;
+  st->iters = k;
+  if (measure) {
+    const double mk = bits_to_double(atomicExch(&st->dmax_bits, 0ull));
+    st->last_dmax = mk;
+    if (sd.stop == kStopDelta && (k % sd.K) == 0 && mk < sd.tol) {
+      st->done = 1;
+      st->converged = 1;
+    }
+  }
+  if (k >= sd.max_iters) st->done = 1;
+}
+
+// MODE 0: plain iteration on x (type T) with optional rhs g (type T).
+// MODE 1: inner sweep of defect correction on d (FP32) with rhs r~ (FP32);
+//         `sweep` is the index of this iteration within the correction; at
+//         sweep 0 the correction starts from d = 0.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                    const Tile* __restrict__ tiles, int ntiles, int colour,
+                                                    int sweep) {
+  __shared__ unsigned long long red[kWarpsY];
+  __shared__ TileCtl ctl;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const SlotDesc& sd = slots[tl.slot];
+    SlotState* st = states + tl.slot;
+    if (threadIdx.x == 0) {
+      TileCtl c;
+      c.skip = *((volatile int*)&st->done);
+      if (MODE == 1 && sweep >= sd.inner) c.skip = 1;
+      c.k = *((volatile int*)&st->iters) + 1;
+      c.measure = (MODE == 0) && (((c.k % sd.K) == 0) || (c.k >= sd.max_iters));
+      c.xbuf = (MODE == 0) ? *((volatile int*)&st->xbuf) : 0;
+      ctl = c;
+    }
+    __syncthreads();
+    const TileCtl c = ctl;
+    __syncthreads();
+    if (c.skip) continue;
+
+    const int pitch = sd.pitch, n = sd.n;
+    T* X = (T*)sd.x[c.xbuf][colour];
+    const T* O = (const T*)sd.x[c.xbuf][colour ^ 1];
+    const T* G = (const T*)sd.g[colour];
+    T a, b;
+    if (sizeof(T) == 4) { a = (T)sd.a32; b = (T)sd.b32; } else { a = (T)sd.a64; b = (T)sd.b64; }
+    const bool zero_all = (MODE == 1) && sweep == 0 && colour == 0;  // d = 0 before the first red phase
+    const bool zero_own = (MODE == 1) && sweep == 0;                // black cells still 0 in the first black phase
+
+    const int q0 = tl.col0 + lane * kVec;
+    const int rows_per_warp = (tl.nrows + kWarpsY - 1) / kWarpsY;
+    const int i0 = tl.row0 + wy * rows_per_warp;
+    const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
+    unsigned long long dm = 0;
+    if (i0 < i1) {
+      T om[4], oc[4], op[4];
+      if (zero_all) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { om[v] = T(0); oc[v] = T(0); }
+      } else {
+        load4(O + eidx(i0 - 1, q0, pitch), om);
+        load4(O + eidx(i0, q0, pitch), oc);
+      }
+      for (int i = i0; i < i1; ++i) {
+        T own[4], gv[4];
+        if (zero_all) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) op[v] = T(0);
+        } else {
+          load4(O + eidx(i + 1, q0, pitch), op);
+        }
+        if (zero_own) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) own[v] = T(0);
+        } else {
+          load4(X + eidx(i, q0, pitch), own);
+        }
+        if (G) load4(G + eidx(i, q0, pitch), gv);
+        T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
+        T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
+        if (!zero_all) {
+          if (lane == 0) left = O[eidx(i, q0 - 1, pitch)];
+          if (lane == 31) right = O[eidx(i, q0 + kVec, pitch)];
+        } else {
+          left = T(0); right = T(0);
+        }
+        const int s = (i + colour) & 1;
+        const int qlim = (n + s) >> 1;
+        T W[4], E[4];
+        if (s == 0) {
+          W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+          E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
+        } else {
+          W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+          E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+        }
+        T nv[4];
+        bool all_in = true;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
+          if (G) sum = radd(sum, gv[v]);
+          const T nu = radd(rmul(a, own[v]), rmul(b, sum));
+          const bool in = (q0 + v) <= qlim;
+          all_in = all_in && in;
+          nv[v] = in ? nu : own[v];
+          if (MODE == 0 && c.measure && in) dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
+        }
+        if (all_in) {
+          store4(X + eidx(i, q0, pitch), nv);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { om[v] = oc[v]; oc[v] = op[v]; }
+      }
+    }
+    if (MODE == 0) {
+      if (c.measure) block_max_to(dm, &st->dmax_bits, red);
+      if (colour == 1) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          const unsigned prev = atomicAdd(&st->arrive, 1u);
+          if (prev == (unsigned)sd.sweep_tiles - 1u) {
+            __threadfence();
+            finalize_plain(sd, st, c.k, c.measure);
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// residual pass (FP64), both colours per tile
+// ------------------------------------------------------------------------------------------------
+
+// r~ for the cell (i, q) of colour c given rows of the other colour.
+template <typename U>
+struct ResidRows {
+  double m[4], c[4], p[4];  // other colour rows i-1, i, i+1 (FP64 values)
+};
+
+// Loads 4 consecutive values of row i (colour arrays in FP64 or FP32, plus an
+// optional FP32 correction) as FP64.
+template <typename T>
+__device__ __forceinline__ void load_u4(const T* X, const float* D, size_t e, double (&v)[4]) {
+  T t[4];
+  load4(X + e, t);
+  if (D) {
+    float d[4];
+    load4(D + e, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __dadd_rn((double)t[k], (double)d[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (double)t[k];
+  }
+}
+template <typename T>
+__device__ __forceinline__ double load_u1(const T* X, const float* D, size_t e) {
+  return D ? __dadd_rn((double)X[e], (double)D[e]) : (double)X[e];
+}
+
+// ROLE kResidFinal / kResidCheck: plain slots, iterate x[xbuf] (type T).
+// ROLE kResidRefine: refine slots; u[ubuf] (+ d from x[0] unless this is the
+// first pass) -> u[ubuf^1], r~ rounded to FP32 into g[c].
+template <typename T, int ROLE>
+__global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                    const Tile* __restrict__ tiles, int ntiles, int dbuf) {
+  __shared__ unsigned long long red[kWarpsY];
+  __shared__ TileCtl ctl;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const SlotDesc& sd = slots[tl.slot];
+    SlotState* st = states + tl.slot;
+    if (threadIdx.x == 0) {
+      TileCtl c;
+      const int done = *((volatile int*)&st->done);
+      const int it = *((volatile int*)&st->iters);
+      c.k = it;
+      c.measure = 0;
+      if (ROLE == kResidFinal) {
+        c.skip = 0;
+      } else if (ROLE == kResidCheck) {
+        const int conv = *((volatile int*)&st->converged);
+        c.skip = conv || it == 0 || (it % sd.K) != 0 || it == *((volatile int*)&st->checked_iter);
+      } else {
+        c.skip = done;
+        c.measure = *((volatile int*)&st->checked_iter) >= 0;  // a correction is pending after the first pass
+      }
+      c.xbuf = (ROLE == kResidRefine) ? *((volatile int*)&st->ubuf) : *((volatile int*)&st->xbuf);
+      ctl = c;
+    }
+    __syncthreads();
+    const TileCtl c = ctl;
+    __syncthreads();
+    if (c.skip) continue;
+
+    const int pitch = sd.pitch, n = sd.n;
+    const T* X0;
+    const T* X1;
+    const float* D0 = nullptr;
+    const float* D1 = nullptr;
+    double* W0 = nullptr;
+    double* W1 = nullptr;
+    if (ROLE == kResidRefine) {
+      X0 = (const T*)sd.u[c.xbuf][0];
+      X1 = (const T*)sd.u[c.xbuf][1];
+      if (c.measure) {  // apply the pending correction
+        D0 = (const float*)sd.x[dbuf][0];
+        D1 = (const float*)sd.x[dbuf][1];
+        W0 = sd.u[c.xbuf ^ 1][0];
+        W1 = sd.u[c.xbuf ^ 1][1];
+      }
+    } else {
+      X0 = (const T*)sd.x[c.xbuf][0];
+      X1 = (const T*)sd.x[c.xbuf][1];
+    }
+    const double* G0 = sd.g64[0];
+    const double* G1 = sd.g64[1];
+    float* R0 = (ROLE == kResidRefine) ? (float*)sd.g[0] : nullptr;
+    float* R1 = (ROLE == kResidRefine) ? (float*)sd.g[1] : nullptr;
+
+    const int q0 = tl.col0 + lane * kVec;
+    const int rows_per_warp = (tl.nrows + kWarpsY - 1) / kWarpsY;
+    const int i0 = tl.row0 + wy * rows_per_warp;
+    const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
+    unsigned long long rm = 0;
+    for (int i = i0; i < i1; ++i) {
+#pragma unroll
+      for (int c0 = 0; c0 < 2; ++c0) {
+        const T* Xs = c0 ? X1 : X0;  // own colour
+        const T* Xo = c0 ? X0 : X1;  // other colour
+        const float* Ds = c0 ? D1 : D0;
+        const float* Do = c0 ? D0 : D1;
+        double own[4], nm[4], nc[4], np[4], gv[4];
+        load_u4(Xs, Ds, eidx(i, q0, pitch), own);
+        load_u4(Xo, Do, eidx(i - 1, q0, pitch), nm);
+        load_u4(Xo, Do, eidx(i, q0, pitch), nc);
+        load_u4(Xo, Do, eidx(i + 1, q0, pitch), np);
+        if (G0) {
+          load4((c0 ? G1 : G0) + eidx(i, q0, pitch), gv);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) gv[v] = 0.0;
+        }
+        double left = __shfl_up_sync(0xffffffffu, nc[3], 1);
+        double right = __shfl_down_sync(0xffffffffu, nc[0], 1);
+        if (lane == 0) left = load_u1(Xo, Do, eidx(i, q0 - 1, pitch));
+        if (lane == 31) right = load_u1(Xo, Do, eidx(i, q0 + kVec, pitch));
+        const int s = (i + c0) & 1;
+        const int qlim = (n + s) >> 1;
+        double Wv[4], Ev[4];
+        if (s == 0) {
+          Wv[0] = nc[0]; Wv[1] = nc[1]; Wv[2] = nc[2]; Wv[3] = nc[3];
+          Ev[0] = nc[1]; Ev[1] = nc[2]; Ev[2] = nc[3]; Ev[3] = right;
+        } else {
+          Wv[0] = left; Wv[1] = nc[0]; Wv[2] = nc[1]; Wv[3] = nc[2];
+          Ev[0] = nc[0]; Ev[1] = nc[1]; Ev[2] = nc[2]; Ev[3] = nc[3];
+        }
+        float rv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double nb = __dadd_rn(__dadd_rn(nm[v], np[v]), __dadd_rn(Wv[v], Ev[v]));
+          const double r = __dadd_rn(__dadd_rn(gv[v], nb), -__dmul_rn(4.0, own[v]));
+          const bool in = (q0 + v) <= qlim;
+          if (in) rm = umax64(rm, abs_bits(r));
+          rv[v] = in ? (float)r : 0.0f;
+        }
+        const bool all_in = (q0 + 3) <= qlim;
+        if (ROLE == kResidRefine) {
+          float* R = c0 ? R1 : R0;
+          double* Wd = c0 ? W1 : W0;
+          if (all_in) {
+            store4(R + eidx(i, q0, pitch), rv);
+            if (Wd) store4(Wd + eidx(i, q0, pitch), own);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if ((q0 + v) <= qlim) {
+                R[eidx(i, q0 + v, pitch)] = rv[v];
+                if (Wd) Wd[eidx(i, q0 + v, pitch)] = own[v];
+              }
+          }
+        }
+      }
+    }
+    block_max_to(rm, &st->rmax_bits, red);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned prev = atomicAdd(&st->arrive_res, 1u);
+      if (prev == (unsigned)sd.resid_tiles - 1u) {
+        __threadfence();
+        st->arrive_res = 0;
+        const double rmax = bits_to_double(atomicExch(&st->rmax_bits, 0ull));
+        const double bmax = bits_to_double(*((volatile unsigned long long*)&st->bmax_bits));
+        const double rho = bmax > 0.0 ? __ddiv_rn(rmax, bmax) : rmax;
+        st->last_rho = rho;
+        if (ROLE == kResidCheck) {
+          st->checked_iter = c.k;
+          if (rho < sd.tol) { st->converged = 1; st->done = 1; }
+        } else if (ROLE == kResidRefine) {
+          if (c.measure) {
+            st->ubuf = c.xbuf ^ 1;
+            st->outer += 1;
+            st->iters += sd.inner;
+          }
+          st->checked_iter = st->iters;
+          if (rho < sd.tol) {
+            st->converged = 1;
+            st->done = 1;
+          } else if (st->iters + sd.inner > sd.max_iters) {
+            st->done = 1;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// launch wrappers (host)
+// ------------------------------------------------------------------------------------------------
+
+static dim3 pack_grid(int n) {
+  const int qw = (n + 1) / 2 + 2;
+  return dim3((qw + kThreads - 1) / kThreads, n + 2);
+}
+
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t s) {
+  const dim3 grid = pack_grid(a.n);
+  if (a.fp32) {
+    k_pack<float><<<grid, kThreads, 0, s>>>(a.u0, a.f, a.n, a.pitch, a.h2, (float*)a.x[0][0], (float*)a.x[0][1],
+                                            (float*)a.x[1][0], (float*)a.x[1][1], (float*)a.g[0], (float*)a.g[1],
+                                            a.g64[0], a.g64[1], a.u[0][0], a.u[0][1], a.u[1][0], a.u[1][1],
+                                            a.state);
+  } else {
+    k_pack<double><<<grid, kThreads, 0, s>>>(a.u0, a.f, a.n, a.pitch, a.h2, (double*)a.x[0][0],
+                                             (double*)a.x[0][1], (double*)a.x[1][0], (double*)a.x[1][1],
+                                             (double*)a.g[0], (double*)a.g[1], a.g64[0], a.g64[1], a.u[0][0],
+                                             a.u[0][1], a.u[1][0], a.u[1][1], a.state);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const void* c0, const void* c1, bool fp32, int n, int pitch, double* out,
+                          cudaStream_t s) {
+  const dim3 grid = pack_grid(n);
+  if (fp32)
+    k_unpack<float><<<grid, kThreads, 0, s>>>((const float*)c0, (const float*)c1, n, pitch, out);
+  else
+    k_unpack<double><<<grid, kThreads, 0, s>>>((const double*)c0, (const double*)c1, n, pitch, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
+                         int grid, int colour, int sweep, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  switch (kind) {
+    case kSweepPlain64:
+      k_sweep<double, 0><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, sweep);
+      break;
+    case kSweepPlain32:
+      k_sweep<float, 0><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, sweep);
+      break;
+    case kSweepInner32:
+      k_sweep<float, 1><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, sweep);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
+                         int grid, int dbuf, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  switch (kind) {
+    case kResidFinal64:
+      k_resid<double, kResidFinal><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+      break;
+    case kResidFinal32:
+      k_resid<float, kResidFinal><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+      break;
+    case kResidCheck64:
+      k_resid<double, kResidCheck><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+      break;
+    case kResidCheck32:
+      k_resid<float, kResidCheck><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+      break;
+    case kResidRefine64:
+      k_resid<double, kResidRefine><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sorgb

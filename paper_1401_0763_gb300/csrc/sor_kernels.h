@@ -1,0 +1,32 @@
+// Host-side launch interface of the SOR kernels (sor_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sor_device.cuh"
+
+namespace sorgb {
+
+enum SweepKind : int { kSweepPlain64 = 0, kSweepPlain32 = 1, kSweepInner32 = 2 };
+enum ResidKind : int { kResidFinal64 = 0, kResidFinal32 = 1, kResidCheck64 = 2, kResidCheck32 = 3, kResidRefine64 = 4 };
+
+struct PackArgs {
+  const double* u0;  // natural (n+2)^2, device
+  const double* f;   // natural n^2 interior, device, or null
+  int n, pitch;
+  double h2;         // h*h, h = 1/(n+1)
+  bool fp32;         // x / g arrays are FP32
+  void* x[2][2];     // iterate buffers to fill (null entries skipped)
+  void* g[2];        // sweep rhs h^2 f in the iterate's type (null: none)
+  double* g64[2];    // h^2 f in FP64 (null: none)
+  double* u[2][2];   // FP64 solution buffers to fill (refine; null entries skipped)
+  SlotState* state;  // receives bmax_bits (must be zeroed before)
+};
+
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t s);
+cudaError_t launch_unpack(const void* c0, const void* c1, bool fp32, int n, int pitch, double* out, cudaStream_t s);
+cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
+                         int grid, int colour, int sweep, cudaStream_t s);
+cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
+                         int grid, int dbuf, cudaStream_t s);
+
+}  // namespace sorgb

@@ -1,0 +1,606 @@
+// Host runtime: context memory accounting, slot buffers, and the blocking
+// solve driver.  Every arithmetic step runs in the kernels of sor_kernels.cu;
+// this file only allocates, copies, launches and reads back state.
+#include "sor_runtime.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <sstream>
+
+namespace sorgb {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+#define SOR_CK(ctx, expr)                                                                     \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      std::ostringstream os_;                                                                 \
+      os_ << #expr << ": " << cudaGetErrorString(e_) << " (" << __FILE__ << ":" << __LINE__ << ")"; \
+      (ctx)->set_error(os_.str());                                                            \
+      return SOR_ERR_CUDA;                                                                    \
+    }                                                                                         \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------------
+// plans and sizes
+// ------------------------------------------------------------------------------------------------
+
+sor_status make_plan(const sor_params* p, bool has_f, Plan* out, std::string* why) {
+  if (!p) { *why = "params is NULL"; return SOR_ERR_INVALID_ARG; }
+  if (p->n < 1 || p->n > 60000) { *why = "n must be in [1, 60000]"; return SOR_ERR_INVALID_ARG; }
+  if (p->precision < SOR_FP64 || p->precision > SOR_FP32_REFINE) { *why = "unknown precision"; return SOR_ERR_INVALID_ARG; }
+  if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) { *why = "unknown stop"; return SOR_ERR_INVALID_ARG; }
+  if (p->max_iters < 0) { *why = "max_iters < 0"; return SOR_ERR_INVALID_ARG; }
+  if (p->check_every < 1) { *why = "check_every < 1"; return SOR_ERR_INVALID_ARG; }
+  if (p->inner_sweeps < 0) { *why = "inner_sweeps < 0"; return SOR_ERR_INVALID_ARG; }
+  if (p->flags & ~SOR_FLAG_EXACT_ORDER) { *why = "unknown flag bits"; return SOR_ERR_INVALID_ARG; }
+  if (p->reserved != 0) { *why = "reserved must be 0"; return SOR_ERR_INVALID_ARG; }
+  if (std::isnan(p->tol)) { *why = "tol is NaN"; return SOR_ERR_INVALID_ARG; }
+  double w = p->omega;
+  if (std::isnan(w)) { *why = "omega is NaN"; return SOR_ERR_INVALID_ARG; }
+  if (w <= 0.0) w = sor_omega_opt(p->n);
+  if (!(w > 0.0 && w < 2.0)) { *why = "omega must satisfy 0 < omega < 2"; return SOR_ERR_INVALID_ARG; }
+  Plan P;
+  P.n = p->n;
+  P.omega = w;
+  P.tol = p->tol;
+  P.max_iters = p->max_iters;
+  P.has_f = has_f;
+  P.exact = (p->flags & SOR_FLAG_EXACT_ORDER) != 0;
+  if (p->precision == SOR_FP32_REFINE) {
+    P.kind = kRefine;
+    P.stop = kStopResid;
+    P.K = 1;
+    P.inner = p->inner_sweeps > 0 ? p->inner_sweeps : 20;
+  } else {
+    P.kind = p->precision == SOR_FP64 ? kPlain64 : kPlain32;
+    P.stop = p->stop == SOR_STOP_MAXDELTA ? kStopDelta : kStopResid;
+    P.K = p->check_every;
+    P.inner = 0;
+  }
+  *out = P;
+  return SOR_OK;
+}
+
+size_t slot_bytes(const Plan& p, bool pingpong) {
+  const Layout L = Layout::make(p.n);
+  const size_t E = L.elems();
+  const size_t nb = pingpong ? 2 : 1;
+  switch (p.kind) {
+    case kPlain64:
+      return nb * 2 * E * 8 + (p.has_f ? 2 * E * 8 : 0);
+    case kPlain32:
+      return nb * 2 * E * 4 + (p.has_f ? 2 * E * (4 + 8) : 0);
+    default:
+      return 2 * 2 * E * 8 + (p.has_f ? 2 * E * 8 : 0) + nb * 2 * E * 4 + 2 * E * 4;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// device memory under the budget
+// ------------------------------------------------------------------------------------------------
+
+sor_status ctx_reserve(Ctx* c, size_t bytes, bool wait, double timeout_s) {
+  std::unique_lock<std::mutex> g(c->mem_mu);
+  if (bytes > c->budget) return SOR_ERR_BUDGET;
+  if (c->reserved + bytes > c->budget) {
+    if (!wait) return SOR_ERR_BUDGET;
+    auto pred = [&] { return c->reserved + bytes <= c->budget; };
+    if (timeout_s < 0) {
+      c->mem_cv.wait(g, pred);
+    } else if (!c->mem_cv.wait_for(g, std::chrono::duration<double>(timeout_s), pred)) {
+      return SOR_ERR_BUDGET;
+    }
+  }
+  c->reserved += bytes;
+  c->peak = std::max(c->peak, c->reserved);
+  return SOR_OK;
+}
+
+void ctx_release(Ctx* c, size_t bytes) {
+  {
+    std::lock_guard<std::mutex> g(c->mem_mu);
+    c->reserved = bytes > c->reserved ? 0 : c->reserved - bytes;
+  }
+  c->mem_cv.notify_all();
+}
+
+void* ctx_dev_alloc(Ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (c->alloc) return c->alloc(bytes, c->alloc_user);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void ctx_dev_free(Ctx* c, void* p) {
+  if (!p) return;
+  if (c->free_)
+    c->free_(p, c->alloc_user);
+  else
+    cudaFree(p);
+}
+
+// ------------------------------------------------------------------------------------------------
+// slot buffers
+// ------------------------------------------------------------------------------------------------
+
+static void* slot_take(Ctx* c, SlotBuffers* b, size_t bytes, bool* ok) {
+  void* p = ctx_dev_alloc(c, bytes);
+  if (!p) { *ok = false; return nullptr; }
+  b->allocs.push_back(p);
+  return p;
+}
+
+sor_status alloc_slot(Ctx* c, const Plan& p, bool pingpong, SlotBuffers* out) {
+  SlotBuffers b;
+  b.L = Layout::make(p.n);
+  b.kind = p.kind;
+  b.has_f = p.has_f;
+  b.pingpong = pingpong;
+  b.bytes = slot_bytes(p, pingpong);
+  const size_t E = b.L.elems();
+  bool ok = true;
+  SlotDesc& d = b.desc;
+  std::memset(&d, 0, sizeof(d));
+  const int nb = pingpong ? 2 : 1;
+  if (p.kind == kPlain64 || p.kind == kPlain32) {
+    const size_t es = p.kind == kPlain64 ? 8 : 4;
+    for (int k = 0; k < nb; ++k)
+      for (int col = 0; col < 2; ++col) d.x[k][col] = slot_take(c, &b, E * es, &ok);
+    if (p.has_f) {
+      for (int col = 0; col < 2; ++col) d.g[col] = slot_take(c, &b, E * es, &ok);
+      for (int col = 0; col < 2; ++col)
+        d.g64[col] = p.kind == kPlain64 ? (const double*)d.g[col] : (const double*)slot_take(c, &b, E * 8, &ok);
+    }
+  } else {
+    for (int k = 0; k < 2; ++k)
+      for (int col = 0; col < 2; ++col) d.u[k][col] = (double*)slot_take(c, &b, E * 8, &ok);
+    if (p.has_f)
+      for (int col = 0; col < 2; ++col) d.g64[col] = (const double*)slot_take(c, &b, E * 8, &ok);
+    for (int k = 0; k < nb; ++k)
+      for (int col = 0; col < 2; ++col) d.x[k][col] = slot_take(c, &b, E * 4, &ok);
+    for (int col = 0; col < 2; ++col) d.g[col] = slot_take(c, &b, E * 4, &ok);
+  }
+  if (!ok) {
+    free_slot(c, &b);
+    return SOR_ERR_OOM;
+  }
+  *out = std::move(b);
+  return SOR_OK;
+}
+
+void free_slot(Ctx* c, SlotBuffers* b) {
+  for (void* p : b->allocs) ctx_dev_free(c, p);
+  b->allocs.clear();
+}
+
+void fill_desc(const Plan& p, SlotBuffers* b) {
+  SlotDesc& d = b->desc;
+  d.n = p.n;
+  d.pitch = b->L.pitch;
+  d.qmax = b->L.qmax;
+  d.kind = p.kind;
+  d.K = p.K;
+  d.max_iters = p.max_iters;
+  d.stop = p.stop;
+  d.inner = p.inner;
+  d.a64 = 1.0 - p.omega;
+  d.b64 = p.omega / 4.0;
+  d.a32 = (float)(1.0 - p.omega);
+  d.b32 = (float)(p.omega / 4.0);
+  d.tol = p.tol;
+  d.sweep_tiles = b->L.row_tiles() * b->L.col_tiles();
+  d.resid_tiles = d.sweep_tiles;
+}
+
+void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid) {
+  for (int r = 0; r < L.row_tiles(); ++r) {
+    const int row0 = 1 + r * kTileRows;
+    const int nrows = std::min(kTileRows, L.n - r * kTileRows);
+    for (int t = 0; t < L.col_tiles(); ++t) {
+      Tile tl{slot, row0, 1 + t * kWarpCols, nrows};
+      if (sweep) sweep->push_back(tl);
+      if (resid) resid->push_back(tl);
+    }
+  }
+}
+
+SlotState initial_state(const Plan& p) {
+  SlotState s;
+  std::memset(&s, 0, sizeof(s));
+  s.checked_iter = -1;
+  s.last_dmax = -1.0;
+  s.last_rho = -1.0;
+  if (p.kind != kRefine && p.max_iters == 0) s.done = 1;
+  return s;
+}
+
+// ------------------------------------------------------------------------------------------------
+// blocking solve
+// ------------------------------------------------------------------------------------------------
+
+static void free_workspace(Ctx* c, SolveWorkspace* w) {
+  if (!w) return;
+  for (auto& kv : w->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  w->graphs.clear();
+  free_slot(c, &w->slot);
+  ctx_dev_free(c, w->d_desc);
+  ctx_dev_free(c, w->d_state);
+  ctx_dev_free(c, w->d_sweep_tiles);
+  ctx_dev_free(c, w->d_resid_tiles);
+  ctx_dev_free(c, w->d_nat_u);
+  ctx_dev_free(c, w->d_nat_f);
+  if (w->h_state) cudaFreeHost(w->h_state);
+  for (auto e : w->poll_events) cudaEventDestroy(e);
+  for (auto& pr : w->chunk_events) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (w->ev0) cudaEventDestroy(w->ev0);
+  if (w->ev1) cudaEventDestroy(w->ev1);
+  ctx_release(c, w->bytes);
+}
+
+void release_solve_workspace(Ctx* c) {
+  if (c->ws) {
+    free_workspace(c, c->ws.get());
+    c->ws.reset();
+  }
+}
+
+sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s) {
+  const size_t E = b->L.elems();
+  const SlotDesc& d = b->desc;
+  const size_t xs = p.kind == kPlain64 ? 8 : 4;
+  for (int k = 0; k < 2; ++k)
+    for (int col = 0; col < 2; ++col) {
+      if (d.x[k][col]) SOR_CK(c, cudaMemsetAsync(d.x[k][col], 0, E * xs, s));
+      if (d.u[k][col]) SOR_CK(c, cudaMemsetAsync(d.u[k][col], 0, E * 8, s));
+    }
+  for (int col = 0; col < 2; ++col) {
+    if (d.g[col]) SOR_CK(c, cudaMemsetAsync(d.g[col], 0, E * (p.kind == kPlain64 ? 8 : 4), s));
+    if (d.g64[col] && (void*)d.g64[col] != d.g[col]) SOR_CK(c, cudaMemsetAsync((void*)d.g64[col], 0, E * 8, s));
+  }
+  return SOR_OK;
+}
+
+static constexpr int kInflight = 3;
+
+static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
+  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f) {
+    *out = c->ws.get();
+    return SOR_OK;
+  }
+  release_solve_workspace(c);
+  auto w = std::make_unique<SolveWorkspace>();
+  w->n = p.n;
+  w->kind = p.kind;
+  w->has_f = p.has_f;
+  const Layout L = Layout::make(p.n);
+  std::vector<Tile> st, rt;
+  build_tiles(L, 0, &st, &rt);
+  const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
+  const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
+  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size()) * sizeof(Tile);
+  const size_t total = slot_bytes(p, false) + nat_u + nat_f + small + 4096;
+  sor_status rs = ctx_reserve(c, total, false, 0.0);
+  if (rs != SOR_OK) {
+    c->set_error("solve needs more device memory than the budget has free");
+    return rs;
+  }
+  w->bytes = total;
+  rs = alloc_slot(c, p, false, &w->slot);
+  if (rs != SOR_OK) {
+    ctx_release(c, total);
+    c->set_error("device allocation failed");
+    return rs;
+  }
+  bool ok = true;
+  w->d_desc = (SlotDesc*)ctx_dev_alloc(c, sizeof(SlotDesc));
+  w->d_state = (SlotState*)ctx_dev_alloc(c, sizeof(SlotState));
+  w->d_sweep_tiles = (Tile*)ctx_dev_alloc(c, st.size() * sizeof(Tile));
+  w->d_resid_tiles = (Tile*)ctx_dev_alloc(c, rt.size() * sizeof(Tile));
+  w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
+  if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
+  ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_nat_u && (!p.has_f || w->d_nat_f);
+  if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
+    cudaGetLastError();
+    free_workspace(c, w.get());
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  w->h_state_count = kInflight;
+  w->poll_events.resize(kInflight);
+  w->chunk_events.resize(kInflight);
+  for (int k = 0; k < kInflight; ++k) {
+    cudaEventCreateWithFlags(&w->poll_events[k], cudaEventDisableTiming);
+    cudaEventCreate(&w->chunk_events[k].first);
+    cudaEventCreate(&w->chunk_events[k].second);
+  }
+  cudaEventCreate(&w->ev0);
+  cudaEventCreate(&w->ev1);
+  w->n_sweep_tiles = (int)st.size();
+  w->n_resid_tiles = (int)rt.size();
+  SOR_CK(c, cudaMemcpyAsync(w->d_sweep_tiles, st.data(), st.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  SOR_CK(c, cudaMemcpyAsync(w->d_resid_tiles, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  // zero every array once: kernels write interior cells only, so padding and
+  // the correction's ring stay zero for the workspace's lifetime
+  rs = zero_slot(c, p, &w->slot, c->stream);
+  if (rs != SOR_OK) {
+    free_workspace(c, w.get());
+    return rs;
+  }
+  c->ws = std::move(w);
+  *out = c->ws.get();
+  return SOR_OK;
+}
+
+// Chunk length (iterations for plain kinds, corrections for refine) between
+// convergence polls: a few milliseconds of work, at most 256 iterations.
+static int chunk_length(Ctx* c, const Plan& p) {
+  const int opt = c->opt_chunk.load();
+  const double cells = (double)p.n * (double)p.n;
+  if (p.kind == kRefine) {
+    if (opt > 0) return opt;
+    const double per_step = cells * p.inner;
+    int k = (int)std::ceil(4.0e8 / std::max(per_step, 1.0));
+    return std::max(1, std::min(k, 16));
+  }
+  int L = opt > 0 ? opt : (int)std::ceil(2.0e8 / std::max(cells, 1.0));
+  L = std::max(4, std::min(L, 256));
+  if (p.stop == kStopResid) {
+    // align residual tests with chunk positions: multiples of K inside a chunk
+    if (p.K <= L) {
+      L = p.K * std::max(1, L / p.K);
+    } else {
+      int best = 1;
+      for (int d = L; d >= 1; --d)
+        if (p.K % d == 0) { best = d; break; }
+      if (best >= 4) L = best;
+    }
+  }
+  return L;
+}
+
+// Launch sequence of one chunk of a plain solve: L iterations, each a red
+// and a black phase, with residual tests where the iteration may be a
+// multiple of K (the kernel itself skips the others).
+static sor_status enqueue_plain_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  const SweepKind sk = p.kind == kPlain64 ? kSweepPlain64 : kSweepPlain32;
+  const bool resid_every = p.stop == kStopResid && !(p.K <= L && L % p.K == 0) && !(p.K > L && p.K % L == 0);
+  for (int it = 0; it < L; ++it) {
+    SOR_CK(c, launch_sweep(sk, w->d_desc, w->d_state, w->d_sweep_tiles, w->n_sweep_tiles, 0, 0, 0, s));
+    SOR_CK(c, launch_sweep(sk, w->d_desc, w->d_state, w->d_sweep_tiles, w->n_sweep_tiles, 0, 1, 0, s));
+    if (p.stop == kStopResid) {
+      const bool at = resid_every || (p.K <= L ? ((it + 1) % p.K == 0) : (it == L - 1));
+      if (at)
+        SOR_CK(c, launch_resid(p.kind == kPlain64 ? kResidCheck64 : kResidCheck32, w->d_desc, w->d_state,
+                               w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+    }
+  }
+  return SOR_OK;
+}
+
+// One chunk of defect correction: C steps of [residual pass (applies the
+// pending correction, tests rho, writes r~), inner sweeps].
+static sor_status enqueue_refine_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int C, cudaStream_t s) {
+  for (int step = 0; step < C; ++step) {
+    SOR_CK(c, launch_resid(kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+    for (int sw = 0; sw < p.inner; ++sw) {
+      SOR_CK(c, launch_sweep(kSweepInner32, w->d_desc, w->d_state, w->d_sweep_tiles, w->n_sweep_tiles, 0, 0, sw, s));
+      SOR_CK(c, launch_sweep(kSweepInner32, w->d_desc, w->d_state, w->d_sweep_tiles, w->n_sweep_tiles, 0, 1, sw, s));
+    }
+  }
+  return SOR_OK;
+}
+
+static sor_status enqueue_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  return p.kind == kRefine ? enqueue_refine_chunk(c, w, p, L, s) : enqueue_plain_chunk(c, w, p, L, s);
+}
+
+static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  if (!c->opt_graphs.load()) return enqueue_chunk(c, w, p, L, s);
+  std::ostringstream key;
+  key << p.kind << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L;
+  auto it = w->graphs.find(key.str());
+  if (it == w->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    SOR_CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    sor_status rs = enqueue_chunk(c, w, p, L, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rs != SOR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rs;
+    }
+    SOR_CK(c, e);
+    GraphEntry ge;
+    e = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    SOR_CK(c, e);
+    it = w->graphs.emplace(key.str(), ge).first;
+  }
+  SOR_CK(c, cudaGraphLaunch(it->second.exec, s));
+  return SOR_OK;
+}
+
+sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+                          sor_result* res) {
+  const double t0 = now_s();
+  std::lock_guard<std::mutex> lock(c->solve_mu);
+  cudaStream_t s = c->stream;
+  SolveWorkspace* w = nullptr;
+  sor_status rs = get_workspace(c, p, &w);
+  if (rs != SOR_OK) return rs;
+
+  const bool timing = c->opt_timing.load() != 0;
+  SOR_CK(c, cudaEventRecord(w->ev0, s));
+  const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2);
+  const double* du0 = u0;
+  if (!is_device_ptr(u0)) {
+    SOR_CK(c, cudaMemcpyAsync(w->d_nat_u, u0, nat_u * 8, cudaMemcpyHostToDevice, s));
+    du0 = w->d_nat_u;
+  }
+  const double* df = nullptr;
+  if (p.has_f) {
+    df = f;
+    if (!is_device_ptr(f)) {
+      SOR_CK(c, cudaMemcpyAsync(w->d_nat_f, f, (size_t)p.n * p.n * 8, cudaMemcpyHostToDevice, s));
+      df = w->d_nat_f;
+    }
+  }
+  fill_desc(p, &w->slot);
+  SlotState st0 = initial_state(p);
+  SOR_CK(c, cudaMemcpyAsync(w->d_desc, &w->slot.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
+  SOR_CK(c, cudaMemcpyAsync(w->d_state, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));
+
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.u0 = du0;
+  pa.f = df;
+  pa.n = p.n;
+  pa.pitch = w->slot.L.pitch;
+  const double h = 1.0 / (double)(p.n + 1);
+  pa.h2 = h * h;
+  pa.fp32 = p.kind != kPlain64;
+  const SlotDesc& d = w->slot.desc;
+  if (p.kind == kRefine) {
+    for (int k = 0; k < 2; ++k)
+      for (int col = 0; col < 2; ++col) pa.u[k][col] = d.u[k][col];
+    for (int col = 0; col < 2; ++col) pa.g64[col] = (double*)d.g64[col];
+  } else {
+    for (int k = 0; k < 2; ++k)
+      for (int col = 0; col < 2; ++col) pa.x[k][col] = d.x[k][col];
+    for (int col = 0; col < 2; ++col) {
+      pa.g[col] = d.g[col];
+      pa.g64[col] = p.kind == kPlain32 ? (double*)d.g64[col] : nullptr;
+    }
+  }
+  pa.state = w->d_state;
+  SOR_CK(c, launch_pack(pa, s));
+
+  // chunks, polled with a lag of kInflight - 1 so the device never idles
+  const int L = chunk_length(c, p);
+  const long long total_units =
+      p.kind == kRefine ? (long long)(p.max_iters / p.inner) + 1 : (long long)p.max_iters;
+  long long planned = 0;
+  std::deque<int> inflight;
+  std::vector<int> iters_before(kInflight, 0);
+  int slot_i = 0;
+  bool finished = (p.kind != kRefine && p.max_iters == 0);
+  int last_iters = 0;
+  long long updates_timed = 0;
+  double ms_timed = 0.0;
+  long long launches_timed = 0;
+  auto harvest = [&](int k) -> sor_status {
+    SOR_CK(c, cudaEventSynchronize(w->poll_events[k]));
+    const SlotState& hs = w->h_state[k];
+    if (hs.done) finished = true;
+    if (timing) {
+      float ms = 0.f;
+      SOR_CK(c, cudaEventElapsedTime(&ms, w->chunk_events[k].first, w->chunk_events[k].second));
+      const int di = hs.iters - iters_before[k];
+      ms_timed += ms;
+      updates_timed += (long long)di * p.n * p.n;
+      launches_timed += p.kind == kRefine ? 2LL * di : 2LL * di;
+    }
+    last_iters = hs.iters;
+    return SOR_OK;
+  };
+  while (!finished && planned < total_units) {
+    if ((int)inflight.size() == kInflight - 1) {
+      rs = harvest(inflight.front());
+      inflight.pop_front();
+      if (rs != SOR_OK) return rs;
+      if (finished) break;
+    }
+    const int k = slot_i;
+    slot_i = (slot_i + 1) % kInflight;
+    iters_before[k] = last_iters;
+    if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
+    const long long left = total_units - planned;
+    const int Lc = (int)std::min<long long>(L, left);
+    rs = launch_chunk(c, w, p, Lc, s);
+    if (rs != SOR_OK) return rs;
+    planned += Lc;
+    if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].second, s));
+    SOR_CK(c, cudaMemcpyAsync(&w->h_state[k], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR_CK(c, cudaEventRecord(w->poll_events[k], s));
+    inflight.push_back(k);
+  }
+  while (!inflight.empty()) {
+    rs = harvest(inflight.front());
+    inflight.pop_front();
+    if (rs != SOR_OK) return rs;
+  }
+
+  // residual of the returned iterate (plain kinds; refine measured it last)
+  if (p.kind == kPlain64)
+    SOR_CK(c, launch_resid(kResidFinal64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+  else if (p.kind == kPlain32)
+    SOR_CK(c, launch_resid(kResidFinal32, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+
+  // read the final state, then unpack the buffer it names
+  SlotState fin;
+  SOR_CK(c, cudaMemcpyAsync(&w->h_state[0], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+  SOR_CK(c, cudaStreamSynchronize(s));
+  fin = w->h_state[0];
+  const bool out_dev = is_device_ptr(u_out);
+  double* dout = out_dev ? u_out : w->d_nat_u;
+  if (p.kind == kRefine) {
+    SOR_CK(c, launch_unpack(d.u[fin.ubuf][0], d.u[fin.ubuf][1], false, p.n, w->slot.L.pitch, dout, s));
+  } else {
+    SOR_CK(c, launch_unpack(d.x[fin.xbuf][0], d.x[fin.xbuf][1], p.kind == kPlain32, p.n, w->slot.L.pitch, dout, s));
+  }
+  if (!out_dev) SOR_CK(c, cudaMemcpyAsync(u_out, dout, nat_u * 8, cudaMemcpyDeviceToHost, s));
+  SOR_CK(c, cudaEventRecord(w->ev1, s));
+  SOR_CK(c, cudaStreamSynchronize(s));
+  float dev_ms = 0.f;
+  SOR_CK(c, cudaEventElapsedTime(&dev_ms, w->ev0, w->ev1));
+  if (fin.error) {
+    c->set_error("device-side consistency check failed");
+    return SOR_ERR_INTERNAL;
+  }
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->iterations = fin.iters;
+    res->converged = fin.converged;
+    res->outer_steps = p.kind == kRefine ? fin.outer : 0;
+    res->final_maxdelta = fin.last_dmax;
+    res->final_resid_rel = fin.last_rho;
+    res->latency_s = now_s() - t0;
+    res->device_s = dev_ms * 1e-3;
+  }
+  {
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    c->stats.solves += 1;
+    c->stats.sweep_launches += 2ull * (unsigned long long)fin.iters;
+    c->stats.lattice_updates += (unsigned long long)fin.iters * (unsigned long long)p.n * (unsigned long long)p.n;
+    c->stats.sweep_ms += ms_timed;
+    c->stats.timed_launches += (unsigned long long)launches_timed;
+    c->stats.timed_updates += (unsigned long long)updates_timed;
+  }
+  return SOR_OK;
+}
+
+}  // namespace sorgb

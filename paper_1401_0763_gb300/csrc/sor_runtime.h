@@ -1,0 +1,172 @@
+// Host runtime of the SOR library: context, device memory under a budget,
+// per-solve device state, launch plans replayed as CUDA graphs, and the
+// continuous-batching scheduler.  Exposed to C callers only through sor.h.
+#pragma once
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sor.h"
+#include "sor_device.cuh"
+#include "sor_kernels.h"
+
+namespace sorgb {
+
+struct Ctx;
+
+// Device memory of one slot (one problem) in the colour-split layout.
+struct SlotBuffers {
+  Layout L{};
+  int kind = kPlain64;
+  bool has_f = false;
+  bool pingpong = false;  // second iterate buffer (temporally blocked sweeps)
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  SlotDesc desc{};  // device pointers filled in; solver parameters set per solve
+};
+
+// Resolved parameters of one solve.
+struct Plan {
+  int n = 0;
+  int kind = kPlain64;
+  int stop = kStopDelta;
+  int K = 1;
+  int max_iters = 0;
+  int inner = 20;
+  bool exact = false;
+  bool has_f = false;
+  double omega = 0.0;
+  double tol = 0.0;
+};
+
+sor_status make_plan(const sor_params* p, bool has_f, Plan* out, std::string* why);
+size_t slot_bytes(const Plan& p, bool pingpong);
+
+// A cached CUDA graph keyed by the launch sequence it replays.
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+};
+
+// Workspace of sor_solve: slot buffers plus the small device tables, kept
+// between solves of the same shape so buffers and graphs are reused.
+struct SolveWorkspace {
+  int n = -1, kind = -1;
+  bool has_f = false;
+  SlotBuffers slot;
+  SlotDesc* d_desc = nullptr;
+  SlotState* d_state = nullptr;
+  Tile* d_sweep_tiles = nullptr;
+  Tile* d_resid_tiles = nullptr;
+  int n_sweep_tiles = 0, n_resid_tiles = 0;
+  double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
+  double* d_nat_f = nullptr;  // n^2 staging
+  SlotState* h_state = nullptr;  // pinned mirror, one per in-flight poll
+  int h_state_count = 0;
+  std::vector<cudaEvent_t> poll_events;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> chunk_events;
+  std::map<std::string, GraphEntry> graphs;
+  size_t bytes = 0;
+};
+
+// One queued or active batch request.
+struct Request {
+  uint64_t ticket = 0;
+  Plan plan;
+  std::vector<double> u0, f;  // host copies of the inputs
+  double* u_out = nullptr;
+  bool out_on_device = false;
+  double t_submit = 0.0;
+  // filled while active
+  int slot = -1;
+  SlotBuffers buf;
+  double* d_stage = nullptr;  // natural staging for inputs / output
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_start = nullptr;
+};
+
+struct Completed {
+  sor_status status = SOR_OK;
+  sor_result res{};
+};
+
+struct Batcher;
+struct BatcherDeleter {
+  void operator()(Batcher* b) const;  // defined in sor_batch.cu
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  sor_alloc_fn alloc = nullptr;
+  sor_free_fn free_ = nullptr;
+  void* alloc_user = nullptr;
+  size_t budget = 0;
+  int sm_count = 0;
+
+  std::mutex mem_mu;
+  std::condition_variable mem_cv;
+  size_t reserved = 0, peak = 0;
+
+  std::mutex solve_mu;  // serialises sor_solve callers
+  std::unique_ptr<SolveWorkspace> ws;
+
+  std::mutex err_mu;
+  std::string last_error;
+
+  std::mutex stats_mu;
+  sor_stats stats{};
+
+  // options
+  std::atomic<int> opt_timing{0};
+  std::atomic<int> opt_graphs{1};
+  std::atomic<int> opt_chunk{0};
+  std::atomic<int> opt_tdepth{0};
+  std::atomic<int> opt_autotune{0};
+  std::atomic<int> opt_max_slots{0};
+
+  std::unique_ptr<Batcher, BatcherDeleter> batcher;
+  std::mutex batcher_mu;
+
+  void set_error(const std::string& s) {
+    std::lock_guard<std::mutex> g(err_mu);
+    last_error = s;
+  }
+};
+
+// device memory accounting
+sor_status ctx_reserve(Ctx* c, size_t bytes, bool wait, double timeout_s);
+void ctx_release(Ctx* c, size_t bytes);
+void* ctx_dev_alloc(Ctx* c, size_t bytes);
+void ctx_dev_free(Ctx* c, void* p);
+
+sor_status alloc_slot(Ctx* c, const Plan& p, bool pingpong, SlotBuffers* out);
+void free_slot(Ctx* c, SlotBuffers* b);
+void fill_desc(const Plan& p, SlotBuffers* b);
+void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid);
+
+sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
+SlotState initial_state(const Plan& p);
+void release_solve_workspace(Ctx* c);
+sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+                          sor_result* res);
+
+sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out, uint64_t* ticket);
+sor_status batch_poll(Ctx* c, uint64_t ticket, double timeout_s, sor_result* res);
+void batch_shutdown(Ctx* c);
+
+double now_s();
+bool is_device_ptr(const void* p);
+
+}  // namespace sorgb

@@ -1,0 +1,198 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars:
+* FP64 with SOR_FLAG_EXACT_ORDER, FP32 sweeps and FP32-refinement: bit
+  identical to the oracle (same operation order, every operation rounded on
+  its own on both sides), same iteration / correction counts.
+* FP64 default path: normwise relative difference <= 1e-12 after equal
+  iteration counts.
+Sizes span several 32 x 128 tiles plus ragged tails and the degenerate
+grids n = 1, 2, 3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_0763_gb300 import workloads as wl
+from tests import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1401_0763_gb300 import _build, capi
+    _build.build()
+    c = capi.Context(0)
+    yield c
+    c.close()
+
+
+def capi_mod():
+    from paper_1401_0763_gb300 import capi
+    return capi
+
+
+def run(ctx, u0, f=None, device=True, **kw):
+    if device:
+        u0t = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+        ft = torch.from_numpy(np.ascontiguousarray(f)).cuda() if f is not None else None
+        out, res = ctx.solve(u0t, ft, **kw)
+        torch.cuda.synchronize()
+        return out.cpu().numpy(), res
+    return ctx.solve(np.ascontiguousarray(u0), None if f is None else np.ascontiguousarray(f), **kw)
+
+
+SIZES = [1, 2, 3, 5, 31, 64, 127, 128, 129, 255, 256, 257, 300]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fp64_exact_bitwise(ctx, n):
+    capi = capi_mod()
+    u0 = wl.random_edges(n, n)
+    f = wl.gaussian_source(n, n + 1) * 50 if n % 2 else None
+    w = oracle.omega_opt(n)
+    iters = 37
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=iters, check_every=5, tol=-1.0)
+    got, res = run(ctx, u0, f, omega=w, tol=-1.0, max_iters=iters, check_every=5,
+                   flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert res["iterations"] == iters and not res["converged"]
+    assert np.array_equal(got, ref["u"]), pins.rel_err(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fp64_default_within_tolerance(ctx, n):
+    u0 = wl.random_edges(n, 2 * n)
+    f = wl.gaussian_source(n, n) * 20 if n % 3 == 0 else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=60, check_every=1, tol=-1.0)
+    got, res = run(ctx, u0, f, omega=w, tol=-1.0, max_iters=60, check_every=1)
+    assert res["iterations"] == 60
+    assert pins.rel_err(got, ref["u"]) <= TOL64
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fp32_bitwise(ctx, n):
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 3 * n)
+    f = wl.gaussian_source(n, n) * 30 if n % 2 == 0 else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f32(u0, w, f=f, max_iters=41, check_every=4, tol=-1.0)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=41, check_every=4)
+    assert res["iterations"] == 41
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+def test_config1_heat_plate_converges_like_oracle(ctx):
+    """258 x 258 plate, top edge 100, w_opt, stop on max|change| < 1e-8 (K = 1)."""
+    capi = capi_mod()
+    n = 256
+    u0 = wl.heat_plate(n, 100.0)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, max_iters=5000, check_every=1, tol=1e-8)
+    assert ref["converged"]
+    got, res = run(ctx, u0, omega=w, tol=1e-8, max_iters=5000, check_every=1, flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert res["converged"] and res["iterations"] == ref["iterations"]
+    assert np.array_equal(got, ref["u"])
+    got2, res2 = run(ctx, u0, omega=w, tol=1e-8, max_iters=5000, check_every=1)
+    assert res2["converged"] and abs(res2["iterations"] - ref["iterations"]) <= 1
+    assert pins.rel_err(got2, ref["u"]) <= TOL64 * 10
+
+
+def test_config1_harmonic_case(ctx):
+    n = 256
+    u0 = wl.harmonic_xx_minus_yy(n)
+    w = oracle.omega_opt(n)
+    got, res = run(ctx, u0, omega=w, tol=1e-13, max_iters=20000, check_every=1)
+    assert res["converged"]
+    c = np.arange(n + 2) / (n + 1)
+    exact = c[None, :] ** 2 - c[:, None] ** 2
+    assert np.max(np.abs(got - exact)) < 1e-11
+
+
+@pytest.mark.parametrize("K", [1, 7, 50])
+def test_check_interval_and_resid_stop(ctx, K):
+    capi = capi_mod()
+    n = 100
+    u0 = wl.random_edges(n, 5)
+    f = wl.gaussian_source(n, 6)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=3000, check_every=K, tol=1e-7)
+    got, res = run(ctx, u0, f, omega=w, tol=1e-7, max_iters=3000, check_every=K, flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert res["iterations"] == ref["iterations"] and res["converged"] == ref["converged"]
+    assert np.array_equal(got, ref["u"])
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=3000, check_every=K, tol=1e-9, stop_mode=1)
+    got, res = run(ctx, u0, f, omega=w, tol=1e-9, max_iters=3000, check_every=K, stop=capi.SOR_STOP_RESID_REL,
+                   flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert res["iterations"] == ref["iterations"] and res["converged"] and ref["converged"]
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+    assert np.array_equal(got, ref["u"])
+
+
+@pytest.mark.parametrize("n,inner", [(1, 3), (2, 20), (63, 20), (130, 7), (256, 20)])
+def test_refine_bitwise(ctx, n, inner):
+    capi = capi_mod()
+    u0, f = wl.poisson_problem(n, n)
+    u0 = u0 + wl.random_edges(n, n + 7)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine(u0, w, f=f, inner_sweeps=inner, tol=1e-10, max_outer=4000 // inner)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-10, max_iters=4000,
+                   inner_sweeps=inner)
+    assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
+    assert res["iterations"] == ref["sweeps"]
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+    assert np.array_equal(got, ref["u"])
+
+
+def test_refine_cap_and_zero_iterations(ctx):
+    capi = capi_mod()
+    n = 40
+    u0, f = wl.poisson_problem(n, 1)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine(u0, w, f=f, inner_sweeps=20, tol=1e-14, max_outer=3)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-14, max_iters=60,
+                   inner_sweeps=20)
+    assert res["outer_steps"] == 3 and not res["converged"] and not ref["converged"]
+    assert np.array_equal(got, ref["u"])
+    # zero iterations: the input comes back, residual of the input reported
+    got, res = run(ctx, u0, f, omega=w, tol=1e-8, max_iters=0)
+    assert res["iterations"] == 0 and np.array_equal(got, u0)
+    assert res["final_resid_rel"] == oracle.resid_rel(u0, f=f)
+
+
+def test_host_and_device_pointers_agree(ctx):
+    n = 77
+    u0 = wl.random_edges(n, 9)
+    a, ra = run(ctx, u0, device=True, tol=-1.0, max_iters=30)
+    b, rb = run(ctx, u0, device=False, tol=-1.0, max_iters=30)
+    assert np.array_equal(a, b) and ra["iterations"] == rb["iterations"]
+
+
+def test_invalid_arguments(ctx):
+    capi = capi_mod()
+    u0 = wl.heat_plate(8, 1.0)
+    for kw in ({"omega": 2.0}, {"omega": 2.5}, {"max_iters": -1}, {"check_every": 0}, {"precision": 7},
+               {"stop": 3}, {"flags": 8}, {"tol": float("nan")}):
+        with pytest.raises(capi.SorError) as e:
+            ctx.solve(u0, **kw)
+        assert e.value.status == capi.SOR_ERR_INVALID_ARG
+
+
+def test_fp64_full_size_sampled(ctx):
+    """4098 x 4098 with random edges (the bandwidth workload), in the launch
+    configuration the benchmark times: 100 iterations compared everywhere
+    with the oracle."""
+    n = 4096
+    u0 = wl.random_edges(n, 0)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, max_iters=100, check_every=50, tol=-1.0)
+    got, res = run(ctx, u0, omega=w, tol=-1.0, max_iters=100, check_every=50)
+    assert res["iterations"] == 100
+    assert pins.rel_err(got, ref["u"]) <= TOL64
+    assert res["final_maxdelta"] == pytest.approx(ref["final_maxdelta"], rel=1e-9)
