@@ -172,7 +172,7 @@ def run_ours(args, ws, rank, local):
         st, res = ctx.solve_raw(capi.make_params(N, precision=precision, **kw), src.data_ptr(), None, dst.data_ptr())
         if st != capi.SOR_OK:
             raise capi.SorError(st, ctx.last_error())
-        return res
+        return res.as_dict()
 
     # ---- device-resident FP64 (the headline) --------------------------------------------------------------
     for _ in range(args.warmup):

@@ -503,6 +503,9 @@ sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f
   Batcher* b = c->batcher.get();
   auto r = std::make_unique<Request>();
   r->plan = p;
+  // batched FP64 slots share launches with slots at other iteration counts, so
+  // they use the exact-order phases (no per-chunk rescaling)
+  if (r->plan.kind == kPlain64) r->plan.exact = true;
   r->t_submit = now_s();
   const size_t nu = (size_t)(p.n + 2) * (p.n + 2);
   r->u0.resize(nu);

@@ -305,6 +305,196 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__
 }
 
 // ------------------------------------------------------------------------------------------------
+// one colour phase in FP64 with fewer FP64 instructions per update
+// ------------------------------------------------------------------------------------------------
+//
+// GB300 issues FP64 at about 1/64 of its FP32 rate, so this phase is bound by
+// FP64 instruction issue, not by HBM.  Two reformulations of the same update
+// cut the FP64 instructions from 6 to about 3.1 per cell (no sources):
+//
+// (a) Shared pair sums.  With s = (i + c) & 1 the four neighbours of (i, q)
+//     split into an upper-left pair DU(i,q) = N + W and a lower-right pair
+//     DL(i,q) = E + S, and DU(i+1, q) = DL(i, q + s_i - 1): walking down a
+//     column strip, each pair sum is formed once and used by two cells, so the
+//     neighbour sum costs 2 additions instead of 3.
+// (b) Rescaled unknowns inside a chunk of L iterations.  Red values after the
+//     red phase of iteration t of the chunk are carried as a_t * u with
+//     a_t = (w/4)^-(2t-1), black values as b_t * u with b_t = (w/4)^-2t.  Then
+//     both phases read  X' = alpha * X + (sum of the four neighbours)  with
+//     alpha = (1-w)/(w/4)^2 (one FMA), and the sources enter as gamma * g.
+//     The first red phase starts from unscaled values and the last iteration
+//     of the chunk returns to unscaled values (X' = alpha X + beta Sigma),
+//     so between chunks -- where convergence is tested, max|change| measured
+//     and the result read -- the arrays hold u itself.
+// Every cell's expression depends only on its own neighbours and the launch
+// constants, never on the tiling, so results are reproducible bit for bit
+// across tile shapes and batch compositions.
+struct FastPhase {
+  double alpha, beta, gamma, dscale;
+  double bscale;  // scale the neighbour colour is carried at in this phase; Dirichlet ring values
+                  // (never updated, so always unscaled) are multiplied by it when read
+  int last;       // this phase belongs to the last iteration of its chunk (values unscaled after it)
+};
+
+// Multiplies the entries of a loaded neighbour vector (row r, packed columns
+// q..q+3 of the neighbour colour) that are not interior cells by bs.
+__device__ __forceinline__ void scale_ring4(double (&v)[4], int r, int q, int n, int ocol, double bs, bool edge) {
+  if (r == 0 || r == n + 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __dmul_rn(v[k], bs);
+  } else if (edge) {
+    const int lim = (n + ((r + ocol) & 1)) >> 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (q + k < 1 || q + k > lim) v[k] = __dmul_rn(v[k], bs);
+  }
+}
+__device__ __forceinline__ double scale_ring1(double v, int r, int q, int n, int ocol, double bs) {
+  const int lim = (n + ((r + ocol) & 1)) >> 1;
+  return (r == 0 || r == n + 1 || q < 1 || q > lim) ? __dmul_rn(v, bs) : v;
+}
+
+template <bool UNIT_BETA, bool HAS_G>
+__global__ void __launch_bounds__(kThreads) k_sweep_fast(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                         const Tile* __restrict__ tiles, int ntiles, int colour,
+                                                         FastPhase ph) {
+  __shared__ unsigned long long red[kWarpsY];
+  __shared__ TileCtl ctl;
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const SlotDesc& sd = slots[tl.slot];
+    SlotState* st = states + tl.slot;
+    if (threadIdx.x == 0) {
+      TileCtl c;
+      c.skip = *((volatile int*)&st->done);
+      c.k = *((volatile int*)&st->iters) + 1;
+      c.measure = ((c.k % sd.K) == 0) || (c.k >= sd.max_iters);
+      c.xbuf = *((volatile int*)&st->xbuf);
+      if (!c.skip && c.measure && !ph.last) {  // the host plan must end chunks at measured iterations
+        st->error = 1;
+        st->done = 1;
+        c.skip = 1;
+      }
+      ctl = c;
+    }
+    __syncthreads();
+    const TileCtl c = ctl;
+    __syncthreads();
+    if (c.skip) continue;
+
+    const int pitch = sd.pitch, n = sd.n;
+    double* X = (double*)sd.x[c.xbuf][colour];
+    const double* O = (const double*)sd.x[c.xbuf][colour ^ 1];
+    const double* G = (const double*)sd.g[colour];
+    const int q0 = tl.col0 + lane * kVec;
+    const int rows_per_warp = (tl.nrows + kWarpsY - 1) / kWarpsY;
+    const int i0 = tl.row0 + wy * rows_per_warp;
+    const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
+    unsigned long long dm = 0;
+    // ring values need rescaling only when the neighbour colour is scaled, and
+    // only rows 0 / n+1 and tiles touching the first or last packed columns hold them
+    const bool rescale = ph.bscale != 1.0;
+    const bool edge = rescale && (tl.col0 == 1 || tl.col0 + kWarpCols > (n >> 1));
+    const int ocol = colour ^ 1;
+    if (i0 < i1) {
+      double om[4], oc[4], op[4], dlp[4];
+      load4(O + eidx(i0 - 1, q0, pitch), om);
+      load4(O + eidx(i0, q0, pitch), oc);
+      if (rescale) {
+        scale_ring4(om, i0 - 1, q0, n, ocol, ph.bscale, edge);
+        scale_ring4(oc, i0, q0, n, ocol, ph.bscale, edge);
+      }
+      int s_prev = -1;
+      for (int i = i0; i < i1; ++i) {
+        double own[4], gv[4];
+        load4(O + eidx(i + 1, q0, pitch), op);
+        if (rescale) scale_ring4(op, i + 1, q0, n, ocol, ph.bscale, edge);
+        load4(X + eidx(i, q0, pitch), own);
+        if (HAS_G) load4(G + eidx(i, q0, pitch), gv);
+        double left = __shfl_up_sync(0xffffffffu, oc[3], 1);
+        double right = __shfl_down_sync(0xffffffffu, oc[0], 1);
+        if (lane == 0) {
+          left = O[eidx(i, q0 - 1, pitch)];
+          if (edge) left = scale_ring1(left, i, q0 - 1, n, ocol, ph.bscale);
+        }
+        if (lane == 31) {
+          right = O[eidx(i, q0 + kVec, pitch)];
+          if (edge) right = scale_ring1(right, i, q0 + kVec, n, ocol, ph.bscale);
+        }
+        const int s = (i + colour) & 1;
+        const int qlim = (n + s) >> 1;
+        double W[4], E[4];
+        if (s == 0) {
+          W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+          E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
+        } else {
+          W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+          E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+        }
+        double DL[4], DU[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) DL[v] = __dadd_rn(E[v], op[v]);
+        if (s_prev < 0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(om[v], W[v]);
+        } else if (s_prev == 1) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) DU[v] = dlp[v];
+        } else {
+          double d0 = __shfl_up_sync(0xffffffffu, dlp[3], 1);
+          if (lane == 0) d0 = __dadd_rn(om[0], left);  // the pair of the column left of this strip
+          DU[0] = d0; DU[1] = dlp[0]; DU[2] = dlp[1]; DU[3] = dlp[2];
+        }
+        double nv[4];
+        bool all_in = true;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const double sum = __dadd_rn(DU[v], DL[v]);
+          double t2;
+          if (UNIT_BETA)
+            t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], sum) : sum;
+          else
+            t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
+          const double nu = __fma_rn(ph.alpha, own[v], t2);
+          const bool in = (q0 + v) <= qlim;
+          all_in = all_in && in;
+          nv[v] = in ? nu : own[v];
+          if (c.measure && in) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
+        }
+        if (all_in) {
+          store4(X + eidx(i, q0, pitch), nv);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          dlp[v] = DL[v];
+          om[v] = oc[v];
+          oc[v] = op[v];
+        }
+        s_prev = s;
+      }
+    }
+    if (c.measure) block_max_to(dm, &st->dmax_bits, red);
+    if (colour == 1) {
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        if (prev == (unsigned)sd.sweep_tiles - 1u) {
+          __threadfence();
+          finalize_plain(sd, st, c.k, c.measure);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // residual pass (FP64), both colours per tile
 // ------------------------------------------------------------------------------------------------
 
@@ -547,6 +737,23 @@ cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* state
     default:
       return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
+                                int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.bscale, a.last};
+  const bool unit = a.beta == 1.0;
+  if (unit && !has_g)
+    k_sweep_fast<true, false><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+  else if (unit && has_g)
+    k_sweep_fast<true, true><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+  else if (!has_g)
+    k_sweep_fast<false, false><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+  else
+    k_sweep_fast<false, true><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
   return cudaGetLastError();
 }
 

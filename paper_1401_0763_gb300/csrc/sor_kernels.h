@@ -26,6 +26,16 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t s);
 cudaError_t launch_unpack(const void* c0, const void* c1, bool fp32, int n, int pitch, double* out, cudaStream_t s);
 cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int colour, int sweep, cudaStream_t s);
+// Constants of one FP64 colour phase of the rescaled formulation:
+//   X' = alpha * X + beta * (pair-sum of neighbours) + gamma * g,
+// with |change| measured as |X' - dscale * X| (last iteration of a chunk only)
+// and Dirichlet ring values read as bscale * value.
+struct FastPhaseArgs {
+  double alpha, beta, gamma, dscale, bscale;
+  int last;
+};
+cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
+                                int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int dbuf, cudaStream_t s);
 

@@ -211,12 +211,15 @@ void fill_desc(const Plan& p, SlotBuffers* b) {
   d.tol = p.tol;
   d.sweep_tiles = b->L.row_tiles() * b->L.col_tiles();
   d.resid_tiles = d.sweep_tiles;
+  if (p.kind == kPlain64 && !p.exact)
+    d.sweep_tiles = ((p.n + kFastTileRows - 1) / kFastTileRows) * b->L.col_tiles();
 }
 
-void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid) {
-  for (int r = 0; r < L.row_tiles(); ++r) {
-    const int row0 = 1 + r * kTileRows;
-    const int nrows = std::min(kTileRows, L.n - r * kTileRows);
+void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid, int tile_rows) {
+  const int row_tiles = (L.n + tile_rows - 1) / tile_rows;
+  for (int r = 0; r < row_tiles; ++r) {
+    const int row0 = 1 + r * tile_rows;
+    const int nrows = std::min(tile_rows, L.n - r * tile_rows);
     for (int t = 0; t < L.col_tiles(); ++t) {
       Tile tl{slot, row0, 1 + t * kWarpCols, nrows};
       if (sweep) sweep->push_back(tl);
@@ -249,6 +252,7 @@ static void free_workspace(Ctx* c, SolveWorkspace* w) {
   ctx_dev_free(c, w->d_state);
   ctx_dev_free(c, w->d_sweep_tiles);
   ctx_dev_free(c, w->d_resid_tiles);
+  ctx_dev_free(c, w->d_fast_tiles);
   ctx_dev_free(c, w->d_nat_u);
   ctx_dev_free(c, w->d_nat_f);
   if (w->h_state) cudaFreeHost(w->h_state);
@@ -298,11 +302,12 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->kind = p.kind;
   w->has_f = p.has_f;
   const Layout L = Layout::make(p.n);
-  std::vector<Tile> st, rt;
-  build_tiles(L, 0, &st, &rt);
+  std::vector<Tile> st, rt, ft;
+  build_tiles(L, 0, &st, &rt, kTileRows);
+  build_tiles(L, 0, &ft, nullptr, kFastTileRows);
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
-  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size()) * sizeof(Tile);
+  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size() + ft.size()) * sizeof(Tile);
   const size_t total = slot_bytes(p, false) + nat_u + nat_f + small + 4096;
   sor_status rs = ctx_reserve(c, total, false, 0.0);
   if (rs != SOR_OK) {
@@ -321,9 +326,11 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_state = (SlotState*)ctx_dev_alloc(c, sizeof(SlotState));
   w->d_sweep_tiles = (Tile*)ctx_dev_alloc(c, st.size() * sizeof(Tile));
   w->d_resid_tiles = (Tile*)ctx_dev_alloc(c, rt.size() * sizeof(Tile));
+  w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
-  ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_nat_u && (!p.has_f || w->d_nat_f);
+  ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_nat_u &&
+       (!p.has_f || w->d_nat_f);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
     cudaGetLastError();
     free_workspace(c, w.get());
@@ -342,8 +349,10 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   cudaEventCreate(&w->ev1);
   w->n_sweep_tiles = (int)st.size();
   w->n_resid_tiles = (int)rt.size();
+  w->n_fast_tiles = (int)ft.size();
   SOR_CK(c, cudaMemcpyAsync(w->d_sweep_tiles, st.data(), st.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_resid_tiles, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  SOR_CK(c, cudaMemcpyAsync(w->d_fast_tiles, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   // zero every array once: kernels write interior cells only, so padding and
   // the correction's ring stay zero for the workspace's lifetime
   rs = zero_slot(c, p, &w->slot, c->stream);
@@ -415,14 +424,98 @@ static sor_status enqueue_refine_chunk(Ctx* c, SolveWorkspace* w, const Plan& p,
   return SOR_OK;
 }
 
+// Longest chunk for the rescaled FP64 phases: the carried scale grows by
+// (4/w)^2 per iteration; keep it below 2^400 so values stay far from overflow.
+static int fast_lmax(double omega) {
+  const double bits = 2.0 * std::log2(4.0 / omega);
+  const int L = bits > 0.0 ? (int)std::floor(400.0 / bits) : 256;
+  return std::max(1, std::min(L, 256));
+}
+
+// Iterations in the next chunk of a plain solve that has planned k0 so far.
+// The rescaled FP64 phases must end a chunk wherever |change| is measured
+// (multiples of K and the cap), since only chunk ends hold unscaled values.
+static int next_chunk(Ctx* c, const Plan& p, long long k0, int L) {
+  if (p.kind == kPlain64 && !p.exact) {
+    const long long to_check = p.K - (k0 % p.K);
+    const long long to_cap = (long long)p.max_iters - k0;
+    long long Lc = std::min<long long>(fast_lmax(p.omega), std::min(to_check, to_cap));
+    (void)c;
+    (void)L;
+    return (int)std::max<long long>(1, Lc);
+  }
+  return L;
+}
+
+static FastPhaseArgs fast_phase(const Plan& p, int t, int L, int colour) {
+  const double w4 = p.omega / 4.0, omc = 1.0 - p.omega;
+  FastPhaseArgs a;
+  // scale of the neighbour colour during this phase: red reads black at
+  // b_{t-1} (1 at t = 1), black reads red at a_t (1 at t = L)
+  if (colour == 0)
+    a.bscale = t == 1 ? 1.0 : std::pow(w4, -(2 * t - 2));
+  else
+    a.bscale = t == L ? 1.0 : std::pow(w4, -(2 * t - 1));
+  if (colour == 0) {
+    if (t == L) {  // back to unscaled values
+      const double inv_a = t == 1 ? 1.0 : std::pow(w4, 2 * t - 3);  // 1 / a_{t-1}
+      const double inv_b = t == 1 ? 1.0 : std::pow(w4, 2 * t - 2);  // 1 / b_{t-1}
+      a.alpha = omc * inv_a;
+      a.beta = w4 * inv_b;
+      a.gamma = w4;
+      a.dscale = inv_a;
+      a.last = 1;
+    } else {
+      a.alpha = t == 1 ? omc / w4 : omc / (w4 * w4);
+      a.beta = 1.0;
+      a.gamma = std::pow(w4, -(2 * t - 2));
+      a.dscale = 0.0;
+      a.last = 0;
+    }
+  } else {
+    if (t == L) {
+      const double inv_b = t == 1 ? 1.0 : std::pow(w4, 2 * t - 2);
+      a.alpha = omc * inv_b;
+      a.beta = w4;
+      a.gamma = w4;
+      a.dscale = inv_b;
+      a.last = 1;
+    } else {
+      a.alpha = omc / (w4 * w4);
+      a.beta = 1.0;
+      a.gamma = std::pow(w4, -(2 * t - 1));
+      a.dscale = 0.0;
+      a.last = 0;
+    }
+  }
+  return a;
+}
+
+// L iterations of the rescaled FP64 phases (one chunk).
+static sor_status enqueue_fast_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  for (int t = 1; t <= L; ++t) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const FastPhaseArgs a = fast_phase(p, t, L, colour);
+      SOR_CK(c, launch_sweep_fast64(w->d_desc, w->d_state, w->d_fast_tiles, w->n_fast_tiles, 0, colour, a, p.has_f,
+                                    s));
+    }
+  }
+  if (p.stop == kStopResid)
+    SOR_CK(c, launch_resid(kResidCheck64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+  return SOR_OK;
+}
+
 static sor_status enqueue_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
-  return p.kind == kRefine ? enqueue_refine_chunk(c, w, p, L, s) : enqueue_plain_chunk(c, w, p, L, s);
+  if (p.kind == kRefine) return enqueue_refine_chunk(c, w, p, L, s);
+  if (p.kind == kPlain64 && !p.exact) return enqueue_fast_chunk(c, w, p, L, s);
+  return enqueue_plain_chunk(c, w, p, L, s);
 }
 
 static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
   if (!c->opt_graphs.load()) return enqueue_chunk(c, w, p, L, s);
   std::ostringstream key;
-  key << p.kind << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L;
+  key << p.kind << ":" << p.exact << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L << ":" << p.has_f
+      << ":" << p.omega;
   auto it = w->graphs.find(key.str());
   if (it == w->graphs.end()) {
     cudaGraph_t g = nullptr;
@@ -505,10 +598,9 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
       p.kind == kRefine ? (long long)(p.max_iters / p.inner) + 1 : (long long)p.max_iters;
   long long planned = 0;
   std::deque<int> inflight;
-  std::vector<int> iters_before(kInflight, 0);
   int slot_i = 0;
   bool finished = (p.kind != kRefine && p.max_iters == 0);
-  int last_iters = 0;
+  int last_iters = 0;  // device iteration count after the last harvested chunk (chunks harvest in order)
   long long updates_timed = 0;
   double ms_timed = 0.0;
   long long launches_timed = 0;
@@ -519,7 +611,7 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
     if (timing) {
       float ms = 0.f;
       SOR_CK(c, cudaEventElapsedTime(&ms, w->chunk_events[k].first, w->chunk_events[k].second));
-      const int di = hs.iters - iters_before[k];
+      const int di = hs.iters - last_iters;
       ms_timed += ms;
       updates_timed += (long long)di * p.n * p.n;
       launches_timed += p.kind == kRefine ? 2LL * di : 2LL * di;
@@ -536,10 +628,9 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
     }
     const int k = slot_i;
     slot_i = (slot_i + 1) % kInflight;
-    iters_before[k] = last_iters;
     if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
     const long long left = total_units - planned;
-    const int Lc = (int)std::min<long long>(L, left);
+    const int Lc = (int)std::min<long long>(next_chunk(c, p, planned, L), left);
     rs = launch_chunk(c, w, p, Lc, s);
     if (rs != SOR_OK) return rs;
     planned += Lc;

@@ -67,7 +67,8 @@ struct SolveWorkspace {
   SlotState* d_state = nullptr;
   Tile* d_sweep_tiles = nullptr;
   Tile* d_resid_tiles = nullptr;
-  int n_sweep_tiles = 0, n_resid_tiles = 0;
+  Tile* d_fast_tiles = nullptr;  // taller tiles of the rescaled FP64 phases
+  int n_sweep_tiles = 0, n_resid_tiles = 0, n_fast_tiles = 0;
   double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
   double* d_nat_f = nullptr;  // n^2 staging
   SlotState* h_state = nullptr;  // pinned mirror, one per in-flight poll
@@ -154,7 +155,8 @@ void ctx_dev_free(Ctx* c, void* p);
 sor_status alloc_slot(Ctx* c, const Plan& p, bool pingpong, SlotBuffers* out);
 void free_slot(Ctx* c, SlotBuffers* b);
 void fill_desc(const Plan& p, SlotBuffers* b);
-void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid);
+void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid,
+                 int tile_rows = kTileRows);
 
 sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
 SlotState initial_state(const Plan& p);

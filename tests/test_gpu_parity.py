@@ -196,3 +196,37 @@ def test_fp64_full_size_sampled(ctx):
     assert res["iterations"] == 100
     assert pins.rel_err(got, ref["u"]) <= TOL64
     assert res["final_maxdelta"] == pytest.approx(ref["final_maxdelta"], rel=1e-9)
+
+
+@pytest.mark.parametrize("n,omega,K,iters,with_f", [
+    (256, None, 1, 40, False),     # chunk of one iteration: every phase unscaled
+    (256, None, 50, 1000, False),  # the benchmark's check interval
+    (200, None, 7, 123, True),     # cap not a multiple of K, Poisson source
+    (300, 0.376, 4000, 700, False),  # the paper's under-relaxation: shorter chunks (scale growth)
+    (129, 1.0, 3, 90, True),       # Gauss-Seidel: alpha = 0
+    (5, 1.9, 2, 31, True),
+])
+def test_fp64_rescaled_phases(ctx, n, omega, K, iters, with_f):
+    w = oracle.omega_opt(n) if omega is None else omega
+    u0 = wl.random_edges(n, n + K)
+    f = wl.gaussian_source(n, K) * 100 if with_f else None
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=iters, check_every=K, tol=-1.0)
+    got, res = run(ctx, u0, f, omega=w, tol=-1.0, max_iters=iters, check_every=K)
+    assert res["iterations"] == iters
+    assert pins.rel_err(got, ref["u"]) <= TOL64
+    assert res["final_maxdelta"] == pytest.approx(ref["final_maxdelta"], rel=1e-8, abs=1e-13)
+
+
+def test_fp64_rescaled_converges_like_oracle(ctx):
+    n = 180
+    u0 = wl.random_edges(n, 44)
+    w = oracle.omega_opt(n)
+    for K in (1, 10):
+        ref = oracle.sor_f64(u0, w, max_iters=5000, check_every=K, tol=1e-9)
+        got, res = run(ctx, u0, omega=w, tol=1e-9, max_iters=5000, check_every=K)
+        assert res["converged"] and ref["converged"]
+        assert abs(res["iterations"] - ref["iterations"]) <= K  # m_k near tol may cross one check apart
+        assert pins.rel_err(got, ref["u"]) <= 1e-11
+        refr = oracle.sor_f64(u0, w, max_iters=5000, check_every=K, tol=1e-9, stop_mode=1)
+        got, res = run(ctx, u0, omega=w, tol=1e-9, max_iters=5000, check_every=K, stop=1)
+        assert res["converged"] and abs(res["iterations"] - refr["iterations"]) <= K
