@@ -185,6 +185,36 @@ const char *sor_status_string(int32_t status);
 /* w_opt = 2 / (1 + sin(pi / (N+1))) for the 5-point Laplacian (Young). */
 double sor_omega_opt(int32_t n);
 
+/* Blocking FP64 solve that allocates no memory (no counterpart in the paper:
+ * it exists for library integration only).
+ *
+ * For callers that must not allocate device memory while they run: hosts
+ * with a fixed memory plan (real-time or embedded code that reserves every
+ * buffer up front), plug-ins whose framework owns the device allocator, and
+ * code that may not call cudaMalloc at all.  sor_solve allocates its working
+ * buffers; this call instead keeps them in one fixed array of about 4.8 MB of
+ * device memory built into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ *   params: as for sor_solve, restricted to precision SOR_FP64 and
+ *           1 <= n <= 512; larger grids or other precisions return
+ *           SOR_ERR_INVALID_ARG.  The update is evaluated in exact order
+ *           (the SOR_FLAG_EXACT_ORDER path of sor_solve, whose results it
+ *           equals bit for bit) whatever the flag says.
+ *   u0, f, u_out: DEVICE pointers on the current device (f may be NULL);
+ *           host pointers return SOR_ERR_INVALID_ARG.
+ *   res:    optional; device_s is 0 (no events are created).
+ *   cuda_stream: stream for the work (NULL = the legacy default stream).
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array and it keeps the previous call's contents, so each call
+ * clears what it reads first.  Calls that overlapped on the GPU would race on
+ * the array: the library serialises callers and each call returns only after
+ * its work on the stream has finished.  Allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library call. */
+sor_status sor_solve_static(const sor_params *params, const double *u0, const double *f, double *u_out,
+                            sor_result *res, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsorgb.so")
-SOURCES = ["sor_kernels.cu", "sor_runtime.cu", "sor_batch.cu", "sor_capi.cu"]
+SOURCES = ["sor_kernels.cu", "sor_runtime.cu", "sor_batch.cu", "sor_capi.cu", "sor_static.cu"]
 HEADERS = ["sor_device.cuh", "sor_kernels.h", "sor_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

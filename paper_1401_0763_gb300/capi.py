@@ -47,7 +47,7 @@ SOR_OPT_BATCH_MAX_SLOTS = 6
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
-            "sor_status_string", "sor_omega_opt")
+            "sor_status_string", "sor_omega_opt", "sor_solve_static")
 
 
 class sor_params(ctypes.Structure):
@@ -118,6 +118,8 @@ def load(build_if_missing: bool = False):
         lib.sor_last_error.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t]
         lib.sor_status_string.argtypes = [ctypes.c_int32]
         lib.sor_status_string.restype = ctypes.c_char_p
+        lib.sor_solve_static.argtypes = [P(sor_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         P(sor_result), ctypes.c_void_p]
         lib.sor_omega_opt.argtypes = [ctypes.c_int32]
         lib.sor_omega_opt.restype = ctypes.c_double
         for name in EXPORTED:
