@@ -24,7 +24,6 @@ constexpr int kWarpCols = 32 * kVec;   // 128 packed columns per warp / tile
 constexpr int kWarpsY = 4;             // warps per block, stacked in rows
 constexpr int kThreads = 32 * kWarpsY; // 128 threads per block
 constexpr int kTileRows = 32;          // rows per sweep tile (8 per warp)
-constexpr int kFastTileRows = 64;      // rows per tile of the rescaled FP64 phases (16 per warp)
 
 struct Layout {
   int n;      // interior side

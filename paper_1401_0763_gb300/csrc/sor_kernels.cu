@@ -354,144 +354,235 @@ __device__ __forceinline__ double scale_ring1(double v, int r, int q, int n, int
   return (r == 0 || r == n + 1 || q < 1 || q > lim) ? __dmul_rn(v, bs) : v;
 }
 
+// Register state of one warp walking down a strip of rows: the neighbour-colour
+// rows i-1 and i, and the lower-right pair sums of the previous row.
+struct FastWalk {
+  double om[4], oc[4], dlp[4];
+};
+
+// One row of a strip.  S = (i + colour) & 1 is known at compile time, which
+// fixes where W / E come from and how the upper-left pair sum of this row is
+// obtained from the previous row's lower-right ones: S == 0 -> the same
+// columns; S == 1 -> one column to the left (a shuffle; lane 0 forms the
+// strip-edge pair itself).  FIRST: no previous row, form the pair directly.
+// EDGE: this strip touches the first or last packed column, so Dirichlet ring
+// values may be among the loaded neighbours and are rescaled by ph.bscale.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST>
+__device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, const double* __restrict__ O,
+                                         double* __restrict__ X, const double* __restrict__ G, int pitch, int n,
+                                         int ocol, int q0, int lane, const FastPhase& ph, unsigned long long& dm) {
+  double op[4], own[4], gv[4];
+  load4(O + eidx(i + 1, q0, pitch), op);
+  if (ring_below) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) op[v] = __dmul_rn(op[v], ph.bscale);
+  } else if (EDGE) {
+    scale_ring4(op, i + 1, q0, n, ocol, ph.bscale, true);
+  }
+  load4(X + eidx(i, q0, pitch), own);
+  if (HAS_G) load4(G + eidx(i, q0, pitch), gv);
+  double left = __shfl_up_sync(0xffffffffu, w.oc[3], 1);
+  double right = __shfl_down_sync(0xffffffffu, w.oc[0], 1);
+  if (lane == 0) {
+    left = O[eidx(i, q0 - 1, pitch)];
+    if (EDGE) left = scale_ring1(left, i, q0 - 1, n, ocol, ph.bscale);
+  }
+  if (lane == 31) {
+    right = O[eidx(i, q0 + kVec, pitch)];
+    if (EDGE) right = scale_ring1(right, i, q0 + kVec, n, ocol, ph.bscale);
+  }
+  double W[4], E[4];
+  if (S == 0) {
+    W[0] = w.oc[0]; W[1] = w.oc[1]; W[2] = w.oc[2]; W[3] = w.oc[3];
+    E[0] = w.oc[1]; E[1] = w.oc[2]; E[2] = w.oc[3]; E[3] = right;
+  } else {
+    W[0] = left; W[1] = w.oc[0]; W[2] = w.oc[1]; W[3] = w.oc[2];
+    E[0] = w.oc[0]; E[1] = w.oc[1]; E[2] = w.oc[2]; E[3] = w.oc[3];
+  }
+  double DL[4], DU[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) DL[v] = __dadd_rn(E[v], op[v]);
+  if (FIRST) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(w.om[v], W[v]);
+  } else if (S == 0) {  // previous row had s = 1: same columns
+#pragma unroll
+    for (int v = 0; v < 4; ++v) DU[v] = w.dlp[v];
+  } else {  // previous row had s = 0: one column to the left
+    double d0 = __shfl_up_sync(0xffffffffu, w.dlp[3], 1);
+    if (lane == 0) d0 = __dadd_rn(w.om[0], left);
+    DU[0] = d0; DU[1] = w.dlp[0]; DU[2] = w.dlp[1]; DU[3] = w.dlp[2];
+  }
+  const int qlim = (n + S) >> 1;
+  double nv[4];
+  bool all_in = true;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const double sum = __dadd_rn(DU[v], DL[v]);
+    double t2;
+    if (UNIT_BETA)
+      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], sum) : sum;
+    else
+      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
+    const double nu = __fma_rn(ph.alpha, own[v], t2);
+    const bool in = (q0 + v) <= qlim;
+    all_in = all_in && in;
+    nv[v] = in ? nu : own[v];
+    if (MEASURE && in) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
+  }
+  if (all_in) {
+    store4(X + eidx(i, q0, pitch), nv);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    w.dlp[v] = DL[v];
+    w.om[v] = w.oc[v];
+    w.oc[v] = op[v];
+  }
+}
+
+// Rows [i0, i1) of one strip; rows alternate parity, so the body is unrolled
+// by two with the parity of each half fixed at compile time.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE>
+__device__ __forceinline__ unsigned long long fast_walk(const double* __restrict__ O, double* __restrict__ X,
+                                                        const double* __restrict__ G, int pitch, int n, int colour,
+                                                        int q0, int i0, int i1, int lane, const FastPhase& ph,
+                                                        bool rescale) {
+  const int ocol = colour ^ 1;
+  FastWalk w;
+  load4(O + eidx(i0 - 1, q0, pitch), w.om);
+  load4(O + eidx(i0, q0, pitch), w.oc);
+  if (rescale) {
+    scale_ring4(w.om, i0 - 1, q0, n, ocol, ph.bscale, EDGE);
+    if (EDGE) scale_ring4(w.oc, i0, q0, n, ocol, ph.bscale, true);
+  }
+  unsigned long long dm = 0;
+  // the last grid row reads the south ring; give it its own call
+  const int iend = (rescale && i1 == n + 1) ? n : i1;
+  int i = i0;
+  const int s0 = (i0 + colour) & 1;
+  if (i < iend) {
+    if (s0 == 0)
+      fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, true>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+    else
+      fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, true>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+    ++i;
+    if (s0 == 0) {
+      for (; i + 1 < iend; i += 2) {
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i + 1, false, O, X, G, pitch, n, ocol, q0, lane, ph,
+                                                            dm);
+      }
+      if (i < iend) {
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        ++i;
+      }
+    } else {
+      for (; i + 1 < iend; i += 2) {
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i + 1, false, O, X, G, pitch, n, ocol, q0, lane, ph,
+                                                            dm);
+      }
+      if (i < iend) {
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        ++i;
+      }
+    }
+  }
+  if (i < i1) {  // row n with the south ring below (only when rescaling)
+    const bool first = (i == i0);
+    const int s = (i + colour) & 1;
+    if (first) {
+      if (s == 0)
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, true>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+      else
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, true>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+    } else {
+      if (s == 0)
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+      else
+        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+    }
+  }
+  return dm;
+}
+
+// Warp-per-strip kernel: each warp walks one strip (slot, first row, first
+// packed column, rows) of 128 packed columns; a persistent grid strides over
+// a strip table cut so that every warp gets the same number of rows.
 template <bool UNIT_BETA, bool HAS_G>
 __global__ void __launch_bounds__(kThreads) k_sweep_fast(const SlotDesc* __restrict__ slots, SlotState* states,
-                                                         const Tile* __restrict__ tiles, int ntiles, int colour,
+                                                         const Tile* __restrict__ strips, int nstrips, int colour,
                                                          FastPhase ph) {
-  __shared__ unsigned long long red[kWarpsY];
-  __shared__ TileCtl ctl;
-  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
+  const int lane = threadIdx.x & 31;
+  const int warp = blockIdx.x * kWarpsY + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * kWarpsY;
+  for (int t = warp; t < nstrips; t += nwarps) {
+    const Tile tl = strips[t];
     const SlotDesc& sd = slots[tl.slot];
     SlotState* st = states + tl.slot;
-    if (threadIdx.x == 0) {
-      TileCtl c;
-      c.skip = *((volatile int*)&st->done);
-      c.k = *((volatile int*)&st->iters) + 1;
-      c.measure = ((c.k % sd.K) == 0) || (c.k >= sd.max_iters);
-      c.xbuf = *((volatile int*)&st->xbuf);
-      if (!c.skip && c.measure && !ph.last) {  // the host plan must end chunks at measured iterations
+    int skip = 0, k = 0, measure = 0, xbuf = 0;
+    if (lane == 0) {
+      skip = *((volatile int*)&st->done);
+      k = *((volatile int*)&st->iters) + 1;
+      measure = ((k % sd.K) == 0) || (k >= sd.max_iters);
+      xbuf = *((volatile int*)&st->xbuf);
+      if (!skip && measure && !ph.last) {  // the host plan must end chunks at measured iterations
         st->error = 1;
         st->done = 1;
-        c.skip = 1;
+        skip = 1;
       }
-      ctl = c;
     }
-    __syncthreads();
-    const TileCtl c = ctl;
-    __syncthreads();
-    if (c.skip) continue;
+    skip = __shfl_sync(0xffffffffu, skip, 0);
+    if (skip) continue;
+    k = __shfl_sync(0xffffffffu, k, 0);
+    measure = __shfl_sync(0xffffffffu, measure, 0);
+    xbuf = __shfl_sync(0xffffffffu, xbuf, 0);
 
     const int pitch = sd.pitch, n = sd.n;
-    double* X = (double*)sd.x[c.xbuf][colour];
-    const double* O = (const double*)sd.x[c.xbuf][colour ^ 1];
+    double* X = (double*)sd.x[xbuf][colour];
+    const double* O = (const double*)sd.x[xbuf][colour ^ 1];
     const double* G = (const double*)sd.g[colour];
     const int q0 = tl.col0 + lane * kVec;
-    const int rows_per_warp = (tl.nrows + kWarpsY - 1) / kWarpsY;
-    const int i0 = tl.row0 + wy * rows_per_warp;
-    const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
-    unsigned long long dm = 0;
-    // ring values need rescaling only when the neighbour colour is scaled, and
-    // only rows 0 / n+1 and tiles touching the first or last packed columns hold them
+    const int i0 = tl.row0, i1 = tl.row0 + tl.nrows;
     const bool rescale = ph.bscale != 1.0;
     const bool edge = rescale && (tl.col0 == 1 || tl.col0 + kWarpCols > (n >> 1));
-    const int ocol = colour ^ 1;
-    if (i0 < i1) {
-      double om[4], oc[4], op[4], dlp[4];
-      load4(O + eidx(i0 - 1, q0, pitch), om);
-      load4(O + eidx(i0, q0, pitch), oc);
-      if (rescale) {
-        scale_ring4(om, i0 - 1, q0, n, ocol, ph.bscale, edge);
-        scale_ring4(oc, i0, q0, n, ocol, ph.bscale, edge);
-      }
-      int s_prev = -1;
-      for (int i = i0; i < i1; ++i) {
-        double own[4], gv[4];
-        load4(O + eidx(i + 1, q0, pitch), op);
-        if (rescale) scale_ring4(op, i + 1, q0, n, ocol, ph.bscale, edge);
-        load4(X + eidx(i, q0, pitch), own);
-        if (HAS_G) load4(G + eidx(i, q0, pitch), gv);
-        double left = __shfl_up_sync(0xffffffffu, oc[3], 1);
-        double right = __shfl_down_sync(0xffffffffu, oc[0], 1);
-        if (lane == 0) {
-          left = O[eidx(i, q0 - 1, pitch)];
-          if (edge) left = scale_ring1(left, i, q0 - 1, n, ocol, ph.bscale);
-        }
-        if (lane == 31) {
-          right = O[eidx(i, q0 + kVec, pitch)];
-          if (edge) right = scale_ring1(right, i, q0 + kVec, n, ocol, ph.bscale);
-        }
-        const int s = (i + colour) & 1;
-        const int qlim = (n + s) >> 1;
-        double W[4], E[4];
-        if (s == 0) {
-          W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
-          E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
-        } else {
-          W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
-          E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
-        }
-        double DL[4], DU[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) DL[v] = __dadd_rn(E[v], op[v]);
-        if (s_prev < 0) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(om[v], W[v]);
-        } else if (s_prev == 1) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) DU[v] = dlp[v];
-        } else {
-          double d0 = __shfl_up_sync(0xffffffffu, dlp[3], 1);
-          if (lane == 0) d0 = __dadd_rn(om[0], left);  // the pair of the column left of this strip
-          DU[0] = d0; DU[1] = dlp[0]; DU[2] = dlp[1]; DU[3] = dlp[2];
-        }
-        double nv[4];
-        bool all_in = true;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const double sum = __dadd_rn(DU[v], DL[v]);
-          double t2;
-          if (UNIT_BETA)
-            t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], sum) : sum;
-          else
-            t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
-          const double nu = __fma_rn(ph.alpha, own[v], t2);
-          const bool in = (q0 + v) <= qlim;
-          all_in = all_in && in;
-          nv[v] = in ? nu : own[v];
-          if (c.measure && in) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
-        }
-        if (all_in) {
-          store4(X + eidx(i, q0, pitch), nv);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          dlp[v] = DL[v];
-          om[v] = oc[v];
-          oc[v] = op[v];
-        }
-        s_prev = s;
-      }
+    unsigned long long dm;
+    if (measure) {
+      dm = edge ? fast_walk<UNIT_BETA, HAS_G, true, true>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale)
+                : fast_walk<UNIT_BETA, HAS_G, true, false>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale);
+      dm = warp_max64(dm);
+      if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+    } else {
+      dm = edge ? fast_walk<UNIT_BETA, HAS_G, false, true>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale)
+                : fast_walk<UNIT_BETA, HAS_G, false, false>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale);
     }
-    if (c.measure) block_max_to(dm, &st->dmax_bits, red);
     if (colour == 1) {
       __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      __syncwarp();
+      if (lane == 0) {
         const unsigned prev = atomicAdd(&st->arrive, 1u);
         if (prev == (unsigned)sd.sweep_tiles - 1u) {
           __threadfence();
-          finalize_plain(sd, st, c.k, c.measure);
+          finalize_plain(sd, st, k, measure);
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
+}
+
+int fast_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_fast<true, false>, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 4;
+  }
+  return nb > 0 ? nb : 1;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -743,7 +834,8 @@ cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* state
 cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
                                 int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
-  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  const int need = (ntiles + kWarpsY - 1) / kWarpsY;  // one warp per strip
+  if (grid <= 0 || grid > need) grid = need;
   FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.bscale, a.last};
   const bool unit = a.beta == 1.0;
   if (unit && !has_g)

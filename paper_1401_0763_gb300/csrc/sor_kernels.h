@@ -34,6 +34,9 @@ struct FastPhaseArgs {
   double alpha, beta, gamma, dscale, bscale;
   int last;
 };
+// Resident blocks per SM of the FP64 phase kernel (sizes its persistent grid).
+int fast_blocks_per_sm();
+// ntiles counts warp strips (one warp each); grid <= 0: one warp per strip.
 cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
                                 int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,

@@ -211,8 +211,6 @@ void fill_desc(const Plan& p, SlotBuffers* b) {
   d.tol = p.tol;
   d.sweep_tiles = b->L.row_tiles() * b->L.col_tiles();
   d.resid_tiles = d.sweep_tiles;
-  if (p.kind == kPlain64 && !p.exact)
-    d.sweep_tiles = ((p.n + kFastTileRows - 1) / kFastTileRows) * b->L.col_tiles();
 }
 
 void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid, int tile_rows) {
@@ -226,6 +224,21 @@ void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vecto
       if (resid) resid->push_back(tl);
     }
   }
+}
+
+// Warp strips for the FP64 phase kernel: each 128-column tile is cut into m
+// row ranges of (nearly) equal length so that the warps of a persistent grid
+// of `warps` warps each get one strip of the same size.
+void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out) {
+  const int ct = L.col_tiles();
+  int m = std::max(1, warps / std::max(1, ct));
+  m = std::min(m, std::max(1, L.n / 8));  // at least 8 rows per strip
+  for (int t = 0; t < ct; ++t)
+    for (int r = 0; r < m; ++r) {
+      const int a = 1 + (int)((long long)r * L.n / m);
+      const int b = 1 + (int)((long long)(r + 1) * L.n / m);
+      if (b > a) out->push_back(Tile{slot, a, 1 + t * kWarpCols, b - a});
+    }
 }
 
 SlotState initial_state(const Plan& p) {
@@ -304,7 +317,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   const Layout L = Layout::make(p.n);
   std::vector<Tile> st, rt, ft;
   build_tiles(L, 0, &st, &rt, kTileRows);
-  build_tiles(L, 0, &ft, nullptr, kFastTileRows);
+  build_strips(L, 0, c->sm_count * fast_blocks_per_sm() * kWarpsY, &ft);
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
   const size_t small = sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size() + ft.size()) * sizeof(Tile);
@@ -563,6 +576,7 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
     }
   }
   fill_desc(p, &w->slot);
+  if (p.kind == kPlain64 && !p.exact) w->slot.desc.sweep_tiles = w->n_fast_tiles;  // warp strips
   SlotState st0 = initial_state(p);
   SOR_CK(c, cudaMemcpyAsync(w->d_desc, &w->slot.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
   SOR_CK(c, cudaMemcpyAsync(w->d_state, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));

@@ -67,7 +67,7 @@ struct SolveWorkspace {
   SlotState* d_state = nullptr;
   Tile* d_sweep_tiles = nullptr;
   Tile* d_resid_tiles = nullptr;
-  Tile* d_fast_tiles = nullptr;  // taller tiles of the rescaled FP64 phases
+  Tile* d_fast_tiles = nullptr;  // warp strips of the rescaled FP64 phases
   int n_sweep_tiles = 0, n_resid_tiles = 0, n_fast_tiles = 0;
   double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
   double* d_nat_f = nullptr;  // n^2 staging
@@ -158,6 +158,7 @@ void fill_desc(const Plan& p, SlotBuffers* b);
 void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid,
                  int tile_rows = kTileRows);
 
+void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out);
 sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
 SlotState initial_state(const Plan& p);
 void release_solve_workspace(Ctx* c);
