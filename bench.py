@@ -155,6 +155,7 @@ def run_ours(args, ws, rank, local):
     stream = torch.cuda.Stream(device=dev)
     ctx = capi.Context(local, 0, stream)
     ctx.set_option(capi.SOR_OPT_TIMING, 1)
+    ctx.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, args.tdepth)
 
     u0_np = wl.random_edges(N, rank)
     w = capi.sor_omega_opt(N)
@@ -296,6 +297,7 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=150)
     ap.add_argument("--ref-iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tdepth", type=int, default=0, help="FP32 iterations fused per tile pass (0 = library default)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

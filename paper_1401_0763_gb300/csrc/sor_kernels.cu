@@ -586,6 +586,216 @@ int fast_blocks_per_sm() {
 }
 
 // ------------------------------------------------------------------------------------------------
+// FP32 colour phases fused over several iterations per tile (temporal blocking)
+// ------------------------------------------------------------------------------------------------
+//
+// A tile of kTbRows x kTbCols packed cells of both colours is staged in
+// shared memory together with a halo of 2T rows and HQ >= T+1 packed columns
+// (a cell's value after t red-black iterations depends on cells at most 2t
+// rows and t packed columns away), then T iterations -- red phase, black
+// phase, each the exact update of k_sweep -- run on the staged copy.  After
+// each phase the cells within 1 of the staged border are stale, the stale
+// band growing inward; the centre tile stays exact and is written to the
+// other buffer of the ping-pong pair, so neighbouring tiles keep reading the
+// previous iterate.  HBM traffic per cell: one read and one write per T
+// iterations (plus the halo re-reads, mostly served by L2).
+
+template <int T>
+struct TbGeom {
+  static constexpr int HR = 2 * T;                  // halo rows
+  static constexpr int HQ = ((T + 1 + 3) / 4) * 4;  // halo packed columns, a multiple of 4 (16-byte rows)
+  static constexpr int R = kTbRows + 2 * HR;
+  static constexpr int C = kTbCols + 2 * HQ;
+  static constexpr int G = C / 4;                   // float4 groups per staged row
+  static constexpr size_t smem = 2ull * R * C * sizeof(float);
+};
+
+__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 16 : 0;  // src-size 0 fills the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(valid ? gsrc : nullptr), "r"(n));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// MODE 0: plain FP32 iterations on x (rhs g optional), src buffer from the
+//         slot state; the last iteration of the launch may be a measured one.
+// MODE 1: inner sweeps of defect correction on d with rhs r~; `src` is the
+//         buffer holding d (the first launch of a correction, sweep0 == 0,
+//         starts from d = 0 and reads nothing).
+template <int T, int MODE>
+__global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                         const Tile* __restrict__ tiles, int ntiles, int nt_req,
+                                                         int src_param, int sweep0) {
+  using Gm = TbGeom<T>;
+  extern __shared__ __align__(16) float tb_smem[];
+  float* const S0 = tb_smem;
+  float* const S1 = tb_smem + Gm::R * Gm::C;
+  __shared__ unsigned long long red[kTbThreads / 32];
+  __shared__ int ctl[5];  // skip, nt, k_end, measure, src
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const SlotDesc& sd = slots[tl.slot];
+    SlotState* st = states + tl.slot;
+    if (threadIdx.x == 0) {
+      int skip = *((volatile int*)&st->done);
+      int nt = 0, k_end = 0, measure = 0, src = 0;
+      if (MODE == 0) {
+        const int k0 = *((volatile int*)&st->iters);
+        nt = min(nt_req, sd.max_iters - k0);
+        k_end = k0 + nt;
+        measure = (k_end % sd.K) == 0 || k_end >= sd.max_iters;
+        src = *((volatile int*)&st->xbuf);
+        for (int j = k0 + 1; j < k_end && !skip; ++j)  // the host plan ends launches at measured iterations
+          if ((j % sd.K) == 0) {
+            st->error = 1;
+            st->done = 1;
+            skip = 1;
+          }
+        if (nt <= 0) skip = 1;
+      } else {
+        nt = min(nt_req, sd.inner - sweep0);
+        if (nt <= 0) skip = 1;
+        src = src_param;
+      }
+      ctl[0] = skip; ctl[1] = nt; ctl[2] = k_end; ctl[3] = measure; ctl[4] = src;
+    }
+    __syncthreads();
+    const int skip = ctl[0], nt = ctl[1], k_end = ctl[2], measure = ctl[3], src = ctl[4];
+    __syncthreads();
+    if (skip) continue;
+
+    const int pitch = sd.pitch, n = sd.n;
+    const int base_r = tl.row0 - Gm::HR;
+    const int base_q = tl.col0 - Gm::HQ;
+    const int base_e = base_q + kOff;  // element index of staged column 0 (a multiple of 4)
+    const bool zero_start = (MODE == 1) && sweep0 == 0;
+    // stage both colours (rows outside the array and columns outside the row read as 0)
+    for (int idx = threadIdx.x; idx < 2 * Gm::R * Gm::G; idx += blockDim.x) {
+      const int c = idx / (Gm::R * Gm::G);
+      const int rem = idx - c * (Gm::R * Gm::G);
+      const int r = rem / Gm::G;
+      const int g = rem - r * Gm::G;
+      const int i = base_r + r;
+      const int e = base_e + 4 * g;
+      const bool valid = !zero_start && i >= 0 && i <= n + 1 && e >= 0 && e + 4 <= pitch;
+      const float* gp = valid ? (const float*)sd.x[src][c] + (size_t)i * pitch + e : nullptr;
+      cp_async16((c ? S1 : S0) + r * Gm::C + 4 * g, gp, valid);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const float a = sd.a32, b = sd.b32;
+    unsigned long long dm = 0;
+    for (int it = 0; it < nt; ++it) {
+      const bool last = it == nt - 1;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float* Sc = c ? S1 : S0;
+        const float* So = c ? S0 : S1;
+        const float* Gc = (const float*)sd.g[c];
+        for (int idx = threadIdx.x; idx < (Gm::R - 2) * Gm::G; idx += blockDim.x) {
+          const int r = 1 + idx / Gm::G;
+          const int g = idx - (r - 1) * Gm::G;
+          const int i = base_r + r;
+          if (i < 1 || i > n) continue;
+          const int s = (i + c) & 1;
+          const int qlim = (n + s) >> 1;
+          const int qf = base_q + 4 * g;
+          if (qf + 3 < 1 || qf > qlim) continue;  // no interior cell in this group
+          float own[4], nm[4], np[4], oc[4], gv[4];
+          load4(Sc + r * Gm::C + 4 * g, own);
+          load4(So + (r - 1) * Gm::C + 4 * g, nm);
+          load4(So + (r + 1) * Gm::C + 4 * g, np);
+          load4(So + r * Gm::C + 4 * g, oc);
+          const float left = g > 0 ? So[r * Gm::C + 4 * g - 1] : 0.0f;
+          const float right = g + 1 < Gm::G ? So[r * Gm::C + 4 * g + 4] : 0.0f;
+          if (Gc) {
+            load4(Gc + (size_t)i * pitch + qf + kOff, gv);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
+          }
+          float W[4], E[4];
+          if (s == 0) {
+            W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+            E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
+          } else {
+            W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+            E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+          }
+          const bool out_row = r >= Gm::HR && r < Gm::HR + tl.nrows;
+          float nv[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int q = qf + v;
+            const int col = 4 * g + v;
+            float sum = radd(radd(nm[v], np[v]), radd(W[v], E[v]));
+            if (Gc) sum = radd(sum, gv[v]);
+            const float nu = radd(rmul(a, own[v]), rmul(b, sum));
+            const bool in = q >= 1 && q <= qlim && col >= 1 && col <= Gm::C - 2;
+            nv[v] = in ? nu : own[v];
+            if (MODE == 0 && measure && last && in && out_row && col >= Gm::HQ && col < Gm::HQ + kTbCols)
+              dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
+          }
+          store4(Sc + r * Gm::C + 4 * g, nv);
+        }
+        __syncthreads();
+      }
+    }
+    // write the centre tile to the other buffer
+    const int dst = src ^ 1;
+    for (int idx = threadIdx.x; idx < 2 * kTbRows * (kTbCols / 4); idx += blockDim.x) {
+      const int c = idx / (kTbRows * (kTbCols / 4));
+      const int rem = idx - c * (kTbRows * (kTbCols / 4));
+      const int r = rem / (kTbCols / 4);
+      const int g = rem - r * (kTbCols / 4);
+      if (r >= tl.nrows) continue;
+      const int i = tl.row0 + r;
+      const int s = (i + c) & 1;
+      const int qlim = (n + s) >> 1;
+      const int qf = tl.col0 + 4 * g;
+      if (qf > qlim) continue;
+      float v4[4];
+      load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + Gm::HQ + 4 * g, v4);
+      float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
+      if (qf + 3 <= qlim) {
+        store4(Xd, v4);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if (qf + v <= qlim) Xd[v] = v4[v];
+      }
+    }
+    if (MODE == 0) {
+      if (measure) {
+        dm = warp_max64(dm);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          unsigned long long m = 0;
+          for (int k = 0; k < kTbThreads / 32; ++k) m = umax64(m, red[k]);
+          if (m) atomicMax(&st->dmax_bits, m);
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        if (prev == (unsigned)sd.sweep_tiles - 1u) {
+          __threadfence();
+          st->xbuf = src ^ 1;
+          finalize_plain(sd, st, k_end, measure);
+        }
+      }
+    }
+    __syncthreads();  // the next tile reuses the staged arrays
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // residual pass (FP64), both colours per tile
 // ------------------------------------------------------------------------------------------------
 
@@ -847,6 +1057,42 @@ cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const 
   else
     k_sweep_fast<false, true><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
   return cudaGetLastError();
+}
+
+template <int T, int MODE>
+static cudaError_t launch_tb_t(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
+                               int nt, int src, int sweep0, cudaStream_t s) {
+  static bool attr_set = false;  // benign race: setting the attribute twice is harmless
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TbGeom<T>::smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  k_sweep_tb<T, MODE><<<grid, kTbThreads, TbGeom<T>::smem, s>>>(slots, states, tiles, ntiles, nt, src, sweep0);
+  return cudaGetLastError();
+}
+
+bool tb_depth_supported(int T) { return T == 2 || T == 3 || T == 4 || T == 6 || T == 8; }
+
+cudaError_t launch_sweep_tb(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
+                            int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  if (nt < 1 || nt > T) return cudaErrorInvalidValue;
+  switch (T) {
+    case 2: return inner ? launch_tb_t<2, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                         : launch_tb_t<2, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    case 3: return inner ? launch_tb_t<3, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                         : launch_tb_t<3, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    case 4: return inner ? launch_tb_t<4, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                         : launch_tb_t<4, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    case 6: return inner ? launch_tb_t<6, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                         : launch_tb_t<6, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    case 8: return inner ? launch_tb_t<8, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                         : launch_tb_t<8, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,

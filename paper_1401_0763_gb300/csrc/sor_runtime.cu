@@ -266,6 +266,7 @@ static void free_workspace(Ctx* c, SolveWorkspace* w) {
   ctx_dev_free(c, w->d_sweep_tiles);
   ctx_dev_free(c, w->d_resid_tiles);
   ctx_dev_free(c, w->d_fast_tiles);
+  ctx_dev_free(c, w->d_tb_tiles);
   ctx_dev_free(c, w->d_nat_u);
   ctx_dev_free(c, w->d_nat_f);
   if (w->h_state) cudaFreeHost(w->h_state);
@@ -304,8 +305,20 @@ sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s) {
 
 static constexpr int kInflight = 3;
 
+// Iterations fused per tile pass for the FP32 sweeps: the SOR_OPT_TEMPORAL_DEPTH
+// option, 0 = the default depth 4; depths the kernel is not built for round
+// down to the next built one.
+int resolve_tdepth(Ctx* c, const Plan& p) {
+  if (p.kind == kPlain64) return 1;
+  int t = c->opt_tdepth.load();
+  if (t == 0) t = 4;
+  while (t > 1 && !tb_depth_supported(t)) --t;
+  return std::max(1, t);
+}
+
 static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
-  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f) {
+  const bool pingpong = p.tdepth > 1;
+  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f && c->ws->pingpong == pingpong) {
     *out = c->ws.get();
     return SOR_OK;
   }
@@ -314,21 +327,24 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->n = p.n;
   w->kind = p.kind;
   w->has_f = p.has_f;
+  w->pingpong = pingpong;
   const Layout L = Layout::make(p.n);
-  std::vector<Tile> st, rt, ft;
+  std::vector<Tile> st, rt, ft, tt;
   build_tiles(L, 0, &st, &rt, kTileRows);
   build_strips(L, 0, c->sm_count * fast_blocks_per_sm() * kWarpsY, &ft);
+  build_tiles(L, 0, &tt, nullptr, kTbRows);
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
-  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size() + ft.size()) * sizeof(Tile);
-  const size_t total = slot_bytes(p, false) + nat_u + nat_f + small + 4096;
+  const size_t small =
+      sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size() + ft.size() + tt.size()) * sizeof(Tile);
+  const size_t total = slot_bytes(p, pingpong) + nat_u + nat_f + small + 4096;
   sor_status rs = ctx_reserve(c, total, false, 0.0);
   if (rs != SOR_OK) {
     c->set_error("solve needs more device memory than the budget has free");
     return rs;
   }
   w->bytes = total;
-  rs = alloc_slot(c, p, false, &w->slot);
+  rs = alloc_slot(c, p, pingpong, &w->slot);
   if (rs != SOR_OK) {
     ctx_release(c, total);
     c->set_error("device allocation failed");
@@ -340,9 +356,11 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_sweep_tiles = (Tile*)ctx_dev_alloc(c, st.size() * sizeof(Tile));
   w->d_resid_tiles = (Tile*)ctx_dev_alloc(c, rt.size() * sizeof(Tile));
   w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
+  w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, tt.size() * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
-  ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_nat_u &&
+  ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
+       w->d_nat_u &&
        (!p.has_f || w->d_nat_f);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
     cudaGetLastError();
@@ -363,6 +381,8 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->n_sweep_tiles = (int)st.size();
   w->n_resid_tiles = (int)rt.size();
   w->n_fast_tiles = (int)ft.size();
+  w->n_tb_tiles = (int)tt.size();
+  SOR_CK(c, cudaMemcpyAsync(w->d_tb_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_sweep_tiles, st.data(), st.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_resid_tiles, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_fast_tiles, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
@@ -409,6 +429,19 @@ static int chunk_length(Ctx* c, const Plan& p) {
 // and a black phase, with residual tests where the iteration may be a
 // multiple of K (the kernel itself skips the others).
 static sor_status enqueue_plain_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  if (p.kind == kPlain32 && p.tdepth > 1) {
+    // launches of tdepth fused iterations; the chunk ends where |change| or
+    // the residual is tested, so no launch spans a tested iteration
+    for (int done = 0; done < L;) {
+      const int nt = std::min(p.tdepth, L - done);
+      SOR_CK(c, launch_sweep_tb(false, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt, 0, 0,
+                                s));
+      done += nt;
+    }
+    if (p.stop == kStopResid)
+      SOR_CK(c, launch_resid(kResidCheck32, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+    return SOR_OK;
+  }
   const SweepKind sk = p.kind == kPlain64 ? kSweepPlain64 : kSweepPlain32;
   const bool resid_every = p.stop == kStopResid && !(p.K <= L && L % p.K == 0) && !(p.K > L && p.K % L == 0);
   for (int it = 0; it < L; ++it) {
@@ -426,7 +459,28 @@ static sor_status enqueue_plain_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, 
 
 // One chunk of defect correction: C steps of [residual pass (applies the
 // pending correction, tests rho, writes r~), inner sweeps].
+// Buffer holding the correction after a correction's launches: launch j of
+// the temporally blocked sweeps reads buffer (j even ? 1 : 0) -- the first
+// one reads nothing, d starting from 0 -- and writes the other one.
+int refine_dbuf(const Plan& p) {
+  if (p.tdepth <= 1) return 0;
+  const int launches = (p.inner + p.tdepth - 1) / p.tdepth;
+  return ((launches - 1) % 2 == 0) ? 0 : 1;
+}
+
 static sor_status enqueue_refine_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int C, cudaStream_t s) {
+  if (p.tdepth > 1) {
+    const int dbuf = refine_dbuf(p);
+    for (int step = 0; step < C; ++step) {
+      SOR_CK(c, launch_resid(kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, dbuf, s));
+      for (int j = 0, sw = 0; sw < p.inner; ++j, sw += p.tdepth) {
+        const int nt = std::min(p.tdepth, p.inner - sw);
+        SOR_CK(c, launch_sweep_tb(true, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt,
+                                  (j % 2 == 0) ? 1 : 0, sw, s));
+      }
+    }
+    return SOR_OK;
+  }
   for (int step = 0; step < C; ++step) {
     SOR_CK(c, launch_resid(kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
     for (int sw = 0; sw < p.inner; ++sw) {
@@ -449,6 +503,11 @@ static int fast_lmax(double omega) {
 // The rescaled FP64 phases must end a chunk wherever |change| is measured
 // (multiples of K and the cap), since only chunk ends hold unscaled values.
 static int next_chunk(Ctx* c, const Plan& p, long long k0, int L) {
+  if (p.kind == kPlain32 && p.tdepth > 1) {
+    const long long to_check = p.K - (k0 % p.K);
+    const long long to_cap = (long long)p.max_iters - k0;
+    return (int)std::max<long long>(1, std::min<long long>(std::max(L, p.tdepth), std::min(to_check, to_cap)));
+  }
   if (p.kind == kPlain64 && !p.exact) {
     const long long to_check = p.K - (k0 % p.K);
     const long long to_cap = (long long)p.max_iters - k0;
@@ -528,7 +587,7 @@ static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, 
   if (!c->opt_graphs.load()) return enqueue_chunk(c, w, p, L, s);
   std::ostringstream key;
   key << p.kind << ":" << p.exact << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L << ":" << p.has_f
-      << ":" << p.omega;
+      << ":" << p.omega << ":" << p.tdepth;
   auto it = w->graphs.find(key.str());
   if (it == w->graphs.end()) {
     cudaGraph_t g = nullptr;
@@ -550,10 +609,12 @@ static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, 
   return SOR_OK;
 }
 
-sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+sor_status solve_blocking(Ctx* c, const Plan& plan_in, const double* u0, const double* f, double* u_out,
                           sor_result* res) {
   const double t0 = now_s();
   std::lock_guard<std::mutex> lock(c->solve_mu);
+  Plan p = plan_in;
+  p.tdepth = resolve_tdepth(c, p);
   cudaStream_t s = c->stream;
   SolveWorkspace* w = nullptr;
   sor_status rs = get_workspace(c, p, &w);
@@ -577,6 +638,7 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
   }
   fill_desc(p, &w->slot);
   if (p.kind == kPlain64 && !p.exact) w->slot.desc.sweep_tiles = w->n_fast_tiles;  // warp strips
+  if (p.kind == kPlain32 && p.tdepth > 1) w->slot.desc.sweep_tiles = w->n_tb_tiles;  // fused-iteration tiles
   SlotState st0 = initial_state(p);
   SOR_CK(c, cudaMemcpyAsync(w->d_desc, &w->slot.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
   SOR_CK(c, cudaMemcpyAsync(w->d_state, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, s));

@@ -45,6 +45,7 @@ struct Plan {
   int inner = 20;
   bool exact = false;
   bool has_f = false;
+  int tdepth = 1;  // FP32 sweeps: iterations fused per tile pass (1 = one launch per colour phase)
   double omega = 0.0;
   double tol = 0.0;
 };
@@ -62,13 +63,15 @@ struct GraphEntry {
 struct SolveWorkspace {
   int n = -1, kind = -1;
   bool has_f = false;
+  bool pingpong = false;
   SlotBuffers slot;
   SlotDesc* d_desc = nullptr;
   SlotState* d_state = nullptr;
   Tile* d_sweep_tiles = nullptr;
   Tile* d_resid_tiles = nullptr;
   Tile* d_fast_tiles = nullptr;  // warp strips of the rescaled FP64 phases
-  int n_sweep_tiles = 0, n_resid_tiles = 0, n_fast_tiles = 0;
+  Tile* d_tb_tiles = nullptr;    // tiles of the temporally blocked FP32 phases
+  int n_sweep_tiles = 0, n_resid_tiles = 0, n_fast_tiles = 0, n_tb_tiles = 0;
   double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
   double* d_nat_f = nullptr;  // n^2 staging
   SlotState* h_state = nullptr;  // pinned mirror, one per in-flight poll
@@ -162,6 +165,8 @@ void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out);
 sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
 SlotState initial_state(const Plan& p);
 void release_solve_workspace(Ctx* c);
+int resolve_tdepth(Ctx* c, const Plan& p);
+int refine_dbuf(const Plan& p);
 sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
                           sor_result* res);
 

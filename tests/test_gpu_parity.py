@@ -230,3 +230,77 @@ def test_fp64_rescaled_converges_like_oracle(ctx):
         refr = oracle.sor_f64(u0, w, max_iters=5000, check_every=K, tol=1e-9, stop_mode=1)
         got, res = run(ctx, u0, omega=w, tol=1e-9, max_iters=5000, check_every=K, stop=1)
         assert res["converged"] and abs(res["iterations"] - refr["iterations"]) <= K
+
+
+@pytest.fixture(scope="module")
+def ctx_depth():
+    """Contexts with each temporal depth of the FP32 sweeps (1 = unfused)."""
+    from paper_1401_0763_gb300 import _build, capi
+    _build.build()
+    made = {}
+
+    def get(depth):
+        if depth not in made:
+            c = capi.Context(0)
+            c.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, depth)
+            made[depth] = c
+        return made[depth]
+    yield get
+    for c in made.values():
+        c.close()
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("n,K,iters,with_f", [(1, 1, 9, True), (2, 3, 17, False), (63, 5, 43, True),
+                                               (130, 50, 200, False), (257, 7, 61, True)])
+def test_fp32_fused_iterations_bitwise(ctx_depth, depth, n, K, iters, with_f):
+    capi = capi_mod()
+    ctx = ctx_depth(depth)
+    u0 = wl.random_edges(n, n + depth)
+    f = wl.gaussian_source(n, K) * 25 if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f32(u0, w, f=f, max_iters=iters, check_every=K, tol=-1.0)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=iters, check_every=K)
+    assert res["iterations"] == iters
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+@pytest.mark.parametrize("depth", [1, 3, 4, 8])
+def test_fp32_fused_converges_like_oracle(ctx_depth, depth):
+    capi = capi_mod()
+    ctx = ctx_depth(depth)
+    n = 150
+    u0 = wl.heat_plate(n, 100.0)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f32(u0, w, max_iters=4000, check_every=10, tol=1e-3)
+    got, res = run(ctx, u0, precision=capi.SOR_FP32, omega=w, tol=1e-3, max_iters=4000, check_every=10)
+    assert res["converged"] == ref["converged"] and res["iterations"] == ref["iterations"]
+    assert np.array_equal(got, ref["u"])
+
+
+@pytest.mark.parametrize("depth", [1, 2, 4, 6, 8])
+@pytest.mark.parametrize("n,inner", [(2, 20), (63, 20), (200, 7), (129, 1)])
+def test_refine_fused_bitwise(ctx_depth, depth, n, inner):
+    capi = capi_mod()
+    ctx = ctx_depth(depth)
+    u0, f = wl.poisson_problem(n, n + depth)
+    u0 = u0 + wl.random_edges(n, n)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine(u0, w, f=f, inner_sweeps=inner, tol=1e-10, max_outer=6000 // inner)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-10, max_iters=6000,
+                   inner_sweeps=inner)
+    assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
+    assert np.array_equal(got, ref["u"])
+
+
+def test_fp32_fused_full_size(ctx_depth):
+    """4098^2 FP32 plate at the default depth, 100 iterations, against the oracle."""
+    capi = capi_mod()
+    ctx = ctx_depth(4)
+    n = 4096
+    u0 = wl.random_edges(n, 1)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f32(u0, w, max_iters=100, check_every=50, tol=-1.0)
+    got, res = run(ctx, u0, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=100, check_every=50)
+    assert np.array_equal(got, ref["u"]) and res["final_maxdelta"] == ref["final_maxdelta"]
