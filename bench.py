@@ -288,6 +288,188 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------------------------------------------
+# other workloads (one JSON line each; not the driver's default line)
+# ---------------------------------------------------------------------------------------------------------------
+
+def _pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def workload_plate256(args, ctx, capi, wl):
+    """258x258 plate, top edge 100, w_opt, stop on max|change| < 1e-8 checked every iteration."""
+    import numpy as np
+    n = 256
+    u0 = np.ascontiguousarray(wl.heat_plate(n, 100.0))
+    out = np.empty_like(u0)
+    lines = {}
+    for name, flags in (("fp64", 0), ("fp64_exact_order", capi.SOR_FLAG_EXACT_ORDER)):
+        kw = dict(omega=capi.sor_omega_opt(n), tol=1e-8, max_iters=5000, check_every=1, flags=flags)
+        for _ in range(args.warmup):
+            ctx.solve(u0, out=out, **kw)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, res = ctx.solve(u0, out=out, **kw)
+        dt = (time.perf_counter() - t0) / args.steps
+        lines[name] = {"solve_ms": 1e3 * dt, "solves_per_s": 1.0 / dt, "iterations": res["iterations"],
+                       "glups": n * n * res["iterations"] / dt / 1e9, "converged": res["converged"]}
+    return {"metric": "time to solution, 258x258 heat plate to max|change| < 1e-8", "value": lines["fp64"]["solve_ms"],
+            "unit": "ms", "higher_is_better": False, "detail": lines,
+            "config": {"workload": "258x258 plate, top 100, w_opt, K=1, cap 5000, host buffers"}}
+
+
+def workload_poisson4096(args, ctx, capi, wl):
+    """4098^2 Poisson, 8-Gaussian source, zero edges: FP32 sweeps + FP64 defect correction to
+    ||f-Au||/||f|| < 1e-10 versus plain FP64 SOR with the residual test every 20 iterations."""
+    import numpy as np
+    import torch
+    n = 4096
+    u0_np, f_np = wl.poisson_problem(n, args.seed)
+    u0 = torch.from_numpy(u0_np).cuda()
+    f = torch.from_numpy(f_np).cuda()
+    out = torch.empty_like(u0)
+    w = capi.sor_omega_opt(n)
+    runs = {"fp32_refine": dict(precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-10, max_iters=400000, inner_sweeps=20),
+            "fp64_plain": dict(precision=capi.SOR_FP64, omega=w, tol=1e-10, max_iters=400000, check_every=20,
+                               stop=capi.SOR_STOP_RESID_REL)}
+    detail = {}
+    sol = {}
+    for name, kw in runs.items():
+        ctx.solve(u0, f, out=out, **dict(kw, max_iters=200))  # warm-up: workspace, graphs
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(1, args.steps // 2)):
+            t0 = time.perf_counter()
+            _, res = ctx.solve(u0, f, out=out, **kw)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        dt = min(ts)
+        sol[name] = out.cpu().numpy()
+        detail[name] = {"time_to_solution_s": dt, "sweeps": res["iterations"], "outer_steps": res["outer_steps"],
+                        "final_resid_rel": res["final_resid_rel"], "converged": res["converged"],
+                        "glups": float(n) * n * res["iterations"] / dt / 1e9}
+    if args.check:
+        from tests import pins  # the DST-I exact discrete solution (test-side mathematics)
+        exact = pins.dst_solve(u0_np, f_np)
+        for name in sol:
+            detail[name]["rel_err_vs_exact"] = pins.rel_err(sol[name], exact)
+    speed = detail["fp64_plain"]["time_to_solution_s"] / detail["fp32_refine"]["time_to_solution_s"]
+    return {"metric": "time to 1e-10 relative residual, 4098^2 Poisson (8 Gaussians)",
+            "value": detail["fp32_refine"]["time_to_solution_s"], "unit": "s", "higher_is_better": False,
+            "speedup_vs_plain_fp64": speed, "detail": detail,
+            "config": {"workload": "4098^2, zero edges, f = 8-Gaussian sum (seeded), w_opt, inner 20 FP32 sweeps"}}
+
+
+def workload_batch512(args, ctx, capi, wl):
+    """512 heat plates, interior side log-uniform in [64, 1024], random edges, FP32 sweeps + FP64 defect
+    correction to a 1e-10 relative residual, all submitted at once to the batching scheduler."""
+    import numpy as np
+    count = args.count or 512
+    sizes = wl.batch_sizes(count, args.seed)
+    reqs = []
+    for k, n in enumerate(sizes):
+        n = int(n)
+        u0 = np.ascontiguousarray(wl.random_edges(n, args.seed * 1000 + k))
+        reqs.append((n, u0, np.empty_like(u0)))
+    kw = dict(precision=capi.SOR_FP32_REFINE, tol=1e-10, max_iters=1000000, inner_sweeps=20)
+    best = None
+    for rep in range(max(1, args.steps // 2) + 1):  # first repetition warms up
+        t0 = time.perf_counter()
+        tickets = [ctx.submit(u0, None, out=o, omega=capi.sor_omega_opt(n), **kw)[0] for n, u0, o in reqs]
+        lat, sweeps, conv = [], 0, 0
+        for (n, _, _), t in zip(reqs, tickets):
+            st, res = ctx.wait(t, 600.0)
+            if st != capi.SOR_OK:
+                raise capi.SorError(st, ctx.last_error())
+            lat.append(res["latency_s"])
+            sweeps += res["iterations"] * n * n
+            conv += res["converged"]
+        dt = time.perf_counter() - t0
+        if rep > 0 and (best is None or dt < best[0]):
+            best = (dt, lat, sweeps, conv)
+    dt, lat, lups, conv = best
+    return {"metric": "solves/s, 512 heat plates (N log-uniform 64..1024) to 1e-10 relative residual",
+            "value": count / dt, "unit": "solves/s", "higher_is_better": True,
+            "detail": {"makespan_s": dt, "converged": conv, "count": count, "glups": lups / dt / 1e9,
+                       "latency_p50_s": _pct(lat, 50), "latency_p99_s": _pct(lat, 99)},
+            "config": {"workload": f"{count} plates, seed {args.seed}, FP32 sweeps + FP64 correction, inner 20"}}
+
+
+def workload_serve(args, ctx, capi, wl):
+    """Poisson arrivals of solve requests (N log-uniform 128..4096, tolerance log-uniform 1e-10..1e-6,
+    Gaussian-sum source, random edges) at a mean rate, served by continuous batching under a 150 GB budget;
+    compared with one-at-a-time plain FP64 solves of the same requests (queueing simulated from their
+    measured service times)."""
+    import numpy as np
+    count = args.count or 48
+    rate = args.rate
+    reqs = wl.request_stream(count, rate, args.seed)
+    inputs = []
+    for r in reqs:
+        u0, f = wl.request_inputs(r)
+        inputs.append((np.ascontiguousarray(u0), np.ascontiguousarray(f), np.empty_like(u0)))
+    t_start = time.perf_counter()
+    tickets = []
+    for r, (u0, f, o) in zip(reqs, inputs):
+        now = time.perf_counter() - t_start
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        t, _ = ctx.submit(u0, f, out=o, precision=capi.SOR_FP32_REFINE, omega=capi.sor_omega_opt(r.n), tol=r.tol,
+                          max_iters=2000000, inner_sweeps=20)
+        tickets.append((t, time.perf_counter() - t_start))
+    lat, done_at = [], []
+    for t, t_sub in tickets:
+        st, res = ctx.wait(t, 1200.0)
+        if st != capi.SOR_OK:
+            raise capi.SorError(st, ctx.last_error())
+        lat.append(res["latency_s"])
+        done_at.append(t_sub + res["latency_s"])
+    makespan = max(done_at) - reqs[0].arrival_s
+    served = {"p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99), "solves_per_s": count / makespan,
+              "makespan_s": makespan}
+    # one at a time, plain FP64 with the residual test every 20 iterations
+    sub = min(count, args.fp64_sample)
+    service = []
+    for r, (u0, f, o) in list(zip(reqs, inputs))[:sub]:
+        t0 = time.perf_counter()
+        ctx.solve(u0, f, out=o, precision=capi.SOR_FP64, omega=capi.sor_omega_opt(r.n), tol=r.tol,
+                  max_iters=2000000, check_every=20, stop=capi.SOR_STOP_RESID_REL)
+        service.append(time.perf_counter() - t0)
+    finish, lat64 = 0.0, []
+    for r, sv in zip(reqs[:sub], service):
+        finish = max(finish, r.arrival_s) + sv
+        lat64.append(finish - r.arrival_s)
+    fp64 = {"p50_s": _pct(lat64, 50), "p99_s": _pct(lat64, 99), "solves_per_s": sub / (finish - reqs[0].arrival_s),
+            "requests": sub, "mean_service_s": float(np.mean(service))}
+    return {"metric": "p99 latency of served solves (Poisson arrivals) to their tolerance",
+            "value": served["p99_s"], "unit": "s", "higher_is_better": False,
+            "detail": {"continuous_batching_fp32_refine": served, "one_at_a_time_fp64": fp64,
+                       "offered_rate_per_s": rate, "requests": count},
+            "config": {"workload": f"{count} requests, rate {rate}/s, seed {args.seed}, budget 150 GB"}}
+
+
+WORKLOADS = {"plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
+             "serve": workload_serve}
+
+
+def run_workload(args):
+    import torch
+
+    from paper_1401_0763_gb300 import capi
+    from paper_1401_0763_gb300 import workloads as wl
+    capi.load()
+    budget = 150 << 30 if args.workload == "serve" else 0
+    with capi.Context(0, budget) as ctx:
+        ctx.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, args.tdepth)
+        line = WORKLOADS[args.workload](args, ctx, capi, wl)
+        torch.cuda.synchronize()
+    line.update({"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+                 "workload_key": args.workload})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,12 +480,21 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tdepth", type=int, default=0, help="FP32 iterations fused per tile pass (0 = library default)")
+    ap.add_argument("--workload", default="plate4096", choices=["plate4096"] + sorted(WORKLOADS),
+                    help="plate4096 is the default benchmark line; the others print their own line")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--count", type=int, default=0, help="batch512 / serve: number of grids or requests")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate per second")
+    ap.add_argument("--fp64-sample", type=int, default=16, help="serve: requests timed one at a time in FP64")
+    ap.add_argument("--check", action="store_true", help="poisson4096: error against the exact DST solution")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     from paper_1401_0763_gb300 import _build
     _build.build()
+    if args.workload != "plate4096":
+        return run_workload(args) if rank == 0 else 0
     return run_ours(args, ws, rank, local)
 
 

@@ -53,6 +53,10 @@ __device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
+// The same for a float: FP32 kernels keep their max|change| as float bits
+// (integer max, no FP64 instruction) and widen once per thread.
+__device__ __forceinline__ unsigned abs_bits32(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned long long abs_bits_of(float x) { return abs_bits((double)x); }
 __device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
   return a > b ? a : b;
 }
@@ -178,6 +182,91 @@ __device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st
   if (k >= sd.max_iters) st->done = 1;
 }
 
+// Rows [i0, i1) of one warp's share of a tile for k_sweep (one colour phase,
+// exact operation order).  MEASURE: also return max |change| (as the bits of
+// a non-negative double); a compile-time flag so that no |change| work is
+// issued on the iterations that do not test it.
+template <typename T, int MODE, bool MEASURE>
+__device__ __forceinline__ unsigned long long sweep_rows(T* __restrict__ X, const T* __restrict__ O,
+                                                         const T* __restrict__ G, T a, T b, int pitch, int n,
+                                                         int colour, int q0, int i0, int i1, int lane, bool zero_all,
+                                                         bool zero_own) {
+  unsigned long long dm = 0;
+  unsigned dm32 = 0;
+  if (i0 < i1) {
+    T om[4], oc[4], op[4];
+    if (zero_all) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { om[v] = T(0); oc[v] = T(0); }
+    } else {
+      load4(O + eidx(i0 - 1, q0, pitch), om);
+      load4(O + eidx(i0, q0, pitch), oc);
+    }
+    for (int i = i0; i < i1; ++i) {
+      T own[4], gv[4];
+      if (zero_all) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) op[v] = T(0);
+      } else {
+        load4(O + eidx(i + 1, q0, pitch), op);
+      }
+      if (zero_own) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) own[v] = T(0);
+      } else {
+        load4(X + eidx(i, q0, pitch), own);
+      }
+      if (G) load4(G + eidx(i, q0, pitch), gv);
+      T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
+      T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
+      if (!zero_all) {
+        if (lane == 0) left = O[eidx(i, q0 - 1, pitch)];
+        if (lane == 31) right = O[eidx(i, q0 + kVec, pitch)];
+      } else {
+        left = T(0); right = T(0);
+      }
+      const int s = (i + colour) & 1;
+      const int qlim = (n + s) >> 1;
+      T W[4], E[4];
+      if (s == 0) {
+        W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+        E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
+      } else {
+        W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+        E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+      }
+      T nv[4];
+      bool all_in = true;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        T sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
+        if (G) sum = radd(sum, gv[v]);
+        const T nu = radd(rmul(a, own[v]), rmul(b, sum));
+        const bool in = (q0 + v) <= qlim;
+        all_in = all_in && in;
+        nv[v] = in ? nu : own[v];
+        if (MEASURE && in) {
+          if (sizeof(T) == 4)
+            dm32 = max(dm32, abs_bits32((float)radd(nu, -own[v])));
+          else
+            dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
+        }
+      }
+      if (all_in) {
+        store4(X + eidx(i, q0, pitch), nv);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { om[v] = oc[v]; oc[v] = op[v]; }
+    }
+  }
+  if (sizeof(T) == 4 && MEASURE) dm = abs_bits_of(__uint_as_float(dm32));
+  return dm;
+}
+
 // MODE 0: plain iteration on x (type T) with optional rhs g (type T).
 // MODE 1: inner sweep of defect correction on d (FP32) with rhs r~ (FP32);
 //         `sweep` is the index of this iteration within the correction; at
@@ -221,71 +310,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__
     const int i0 = tl.row0 + wy * rows_per_warp;
     const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
     unsigned long long dm = 0;
-    if (i0 < i1) {
-      T om[4], oc[4], op[4];
-      if (zero_all) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { om[v] = T(0); oc[v] = T(0); }
-      } else {
-        load4(O + eidx(i0 - 1, q0, pitch), om);
-        load4(O + eidx(i0, q0, pitch), oc);
-      }
-      for (int i = i0; i < i1; ++i) {
-        T own[4], gv[4];
-        if (zero_all) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) op[v] = T(0);
-        } else {
-          load4(O + eidx(i + 1, q0, pitch), op);
-        }
-        if (zero_own) {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) own[v] = T(0);
-        } else {
-          load4(X + eidx(i, q0, pitch), own);
-        }
-        if (G) load4(G + eidx(i, q0, pitch), gv);
-        T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
-        T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
-        if (!zero_all) {
-          if (lane == 0) left = O[eidx(i, q0 - 1, pitch)];
-          if (lane == 31) right = O[eidx(i, q0 + kVec, pitch)];
-        } else {
-          left = T(0); right = T(0);
-        }
-        const int s = (i + colour) & 1;
-        const int qlim = (n + s) >> 1;
-        T W[4], E[4];
-        if (s == 0) {
-          W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
-          E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
-        } else {
-          W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
-          E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
-        }
-        T nv[4];
-        bool all_in = true;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          T sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
-          if (G) sum = radd(sum, gv[v]);
-          const T nu = radd(rmul(a, own[v]), rmul(b, sum));
-          const bool in = (q0 + v) <= qlim;
-          all_in = all_in && in;
-          nv[v] = in ? nu : own[v];
-          if (MODE == 0 && c.measure && in) dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
-        }
-        if (all_in) {
-          store4(X + eidx(i, q0, pitch), nv);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) { om[v] = oc[v]; oc[v] = op[v]; }
-      }
-    }
+    if (MODE == 0 && c.measure)
+      dm = sweep_rows<T, MODE, true>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own);
+    else
+      (void)sweep_rows<T, MODE, false>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own);
     if (MODE == 0) {
       if (c.measure) block_max_to(dm, &st->dmax_bits, red);
       if (colour == 1) {
@@ -688,7 +716,7 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
     __syncthreads();
 
     const float a = sd.a32, b = sd.b32;
-    unsigned long long dm = 0;
+    unsigned dm32 = 0;
     for (int it = 0; it < nt; ++it) {
       const bool last = it == nt - 1;
 #pragma unroll
@@ -738,7 +766,7 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
             const bool in = q >= 1 && q <= qlim && col >= 1 && col <= Gm::C - 2;
             nv[v] = in ? nu : own[v];
             if (MODE == 0 && measure && last && in && out_row && col >= Gm::HQ && col < Gm::HQ + kTbCols)
-              dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
+              dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
           }
           store4(Sc + r * Gm::C + 4 * g, nv);
         }
@@ -771,7 +799,7 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
     }
     if (MODE == 0) {
       if (measure) {
-        dm = warp_max64(dm);
+        unsigned long long dm = warp_max64(abs_bits_of(__uint_as_float(dm32)));
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
         __syncthreads();
         if (threadIdx.x == 0) {
