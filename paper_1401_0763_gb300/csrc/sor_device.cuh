@@ -25,7 +25,6 @@ constexpr int kWarpsY = 4;             // warps per block, stacked in rows
 constexpr int kThreads = 32 * kWarpsY; // 128 threads per block
 constexpr int kTileRows = 32;          // rows per sweep tile (8 per warp)
 constexpr int kTbRows = 64;            // output rows of a temporally blocked FP32 tile
-constexpr int kTbCols = 128;           // output packed columns of a temporally blocked FP32 tile
 constexpr int kTbThreads = 256;        // threads of a temporally blocked tile
 
 struct Layout {

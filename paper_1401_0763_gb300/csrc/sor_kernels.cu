@@ -617,24 +617,29 @@ int fast_blocks_per_sm() {
 // FP32 colour phases fused over several iterations per tile (temporal blocking)
 // ------------------------------------------------------------------------------------------------
 //
-// A tile of kTbRows x kTbCols packed cells of both colours is staged in
-// shared memory together with a halo of 2T rows and HQ >= T+1 packed columns
-// (a cell's value after t red-black iterations depends on cells at most 2t
-// rows and t packed columns away), then T iterations -- red phase, black
-// phase, each the exact update of k_sweep -- run on the staged copy.  After
-// each phase the cells within 1 of the staged border are stale, the stale
-// band growing inward; the centre tile stays exact and is written to the
-// other buffer of the ping-pong pair, so neighbouring tiles keep reading the
-// previous iterate.  HBM traffic per cell: one read and one write per T
-// iterations (plus the halo re-reads, mostly served by L2).
+// A tile of kTbRows output rows and OQ = 128 - 2*HQ output packed columns of
+// both colours is staged in shared memory together with a halo of HR = 2T
+// rows and HQ >= T+1 packed columns (a cell's value after t red-black
+// iterations depends on cells at most 2t rows and t packed columns away), so
+// every staged row is exactly 128 packed columns: one float4 per lane of a
+// warp.  T iterations -- red phase, black phase, each the exact update of
+// k_sweep -- then run on the staged copy: each warp walks a segment of rows
+// keeping the neighbour colour's rows i-1, i in registers, W/E neighbours come
+// by shuffles, and a cell update costs two shared-memory loads and one store.
+// After each phase the cells next to the staged border are stale, the stale
+// band growing inward by at most one row and one packed column per phase; the
+// centre tile stays exact and is written to the other buffer of the
+// ping-pong pair, so neighbouring tiles keep reading the previous iterate.
+// HBM traffic per cell: one read and one write per T iterations plus the
+// halo re-reads, most of which L2 serves.
 
 template <int T>
 struct TbGeom {
-  static constexpr int HR = 2 * T;                  // halo rows
-  static constexpr int HQ = ((T + 1 + 3) / 4) * 4;  // halo packed columns, a multiple of 4 (16-byte rows)
-  static constexpr int R = kTbRows + 2 * HR;
-  static constexpr int C = kTbCols + 2 * HQ;
-  static constexpr int G = C / 4;                   // float4 groups per staged row
+  static constexpr int HR = 2 * T;                              // halo rows
+  static constexpr int HQ = T <= 3 ? 4 : (T <= 7 ? 8 : 12);     // halo packed columns (multiple of 4, >= T+1)
+  static constexpr int C = 128;                                 // staged packed columns
+  static constexpr int OQ = C - 2 * HQ;                         // output packed columns
+  static constexpr int R = kTbRows + 2 * HR;                    // staged rows
   static constexpr size_t smem = 2ull * R * C * sizeof(float);
 };
 
@@ -648,21 +653,86 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-// MODE 0: plain FP32 iterations on x (rhs g optional), src buffer from the
+// One colour phase on the staged tile: rows [r0, r1) of the staged arrays
+// for this warp.  LASTM: this phase belongs to a measured iteration, track
+// max |change| over the tile's output cells.
+template <int T, bool LASTM>
+__device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
+                                         const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
+                                         int r1, int n, int pitch, int out_rows, int lane, float a, float b,
+                                         unsigned& dm32) {
+  using Gm = TbGeom<T>;
+  if (r0 >= r1) return;
+  const int col = 4 * lane;
+  const int qf = base_q + col;
+  float om[4], oc[4];
+  load4(So + (r0 - 1) * Gm::C + col, om);
+  load4(So + r0 * Gm::C + col, oc);
+  for (int r = r0; r < r1; ++r) {
+    float op[4];
+    load4(So + (r + 1) * Gm::C + col, op);
+    const float left = __shfl_up_sync(0xffffffffu, oc[3], 1);
+    const float right = __shfl_down_sync(0xffffffffu, oc[0], 1);
+    const int i = base_r + r;
+    if (i >= 1 && i <= n) {  // warp-uniform
+      const int s = (i + colour) & 1;
+      const int qlim = (n + s) >> 1;
+      const bool any = qf >= 1 && qf <= qlim;  // qf is 1 mod 4: the group has an interior cell iff qf in [1, qlim]
+      float own[4], gv[4];
+      load4(Sc + r * Gm::C + col, own);
+      if (Gc && any) {
+        load4(Gc + (size_t)i * pitch + qf + kOff, gv);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
+      }
+      float W[4], E[4];
+      if (s == 0) {
+        W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+        E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
+      } else {
+        W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+        E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+      }
+      float nv[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
+        if (Gc) sum = radd(sum, gv[v]);
+        const float nu = radd(rmul(a, own[v]), rmul(b, sum));
+        const int q = qf + v;
+        const bool in = q >= 1 && q <= qlim && col + v >= 1 && col + v <= Gm::C - 2;
+        nv[v] = in ? nu : own[v];
+        if (LASTM && in && r >= Gm::HR && r < Gm::HR + out_rows && col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ)
+          dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
+      }
+      store4(Sc + r * Gm::C + col, nv);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      om[v] = oc[v];
+      oc[v] = op[v];
+    }
+  }
+}
+
+// MODE 0: plain FP32 iterations on x (rhs g optional), source buffer from the
 //         slot state; the last iteration of the launch may be a measured one.
 // MODE 1: inner sweeps of defect correction on d with rhs r~; `src` is the
 //         buffer holding d (the first launch of a correction, sweep0 == 0,
 //         starts from d = 0 and reads nothing).
 template <int T, int MODE>
-__global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restrict__ slots, SlotState* states,
-                                                         const Tile* __restrict__ tiles, int ntiles, int nt_req,
-                                                         int src_param, int sweep0) {
+__global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                            const Tile* __restrict__ tiles, int ntiles, int nt_req,
+                                                            int src_param, int sweep0) {
   using Gm = TbGeom<T>;
+  constexpr int kWarps = kTbThreads / 32;
   extern __shared__ __align__(16) float tb_smem[];
   float* const S0 = tb_smem;
   float* const S1 = tb_smem + Gm::R * Gm::C;
-  __shared__ unsigned long long red[kTbThreads / 32];
+  __shared__ unsigned long long red[kWarps];
   __shared__ int ctl[5];  // skip, nt, k_end, measure, src
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
     const SlotDesc& sd = slots[tl.slot];
@@ -700,94 +770,58 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
     const int base_q = tl.col0 - Gm::HQ;
     const int base_e = base_q + kOff;  // element index of staged column 0 (a multiple of 4)
     const bool zero_start = (MODE == 1) && sweep0 == 0;
-    // stage both colours (rows outside the array and columns outside the row read as 0)
-    for (int idx = threadIdx.x; idx < 2 * Gm::R * Gm::G; idx += blockDim.x) {
-      const int c = idx / (Gm::R * Gm::G);
-      const int rem = idx - c * (Gm::R * Gm::G);
-      const int r = rem / Gm::G;
-      const int g = rem - r * Gm::G;
+    // stage both colours: warp per row, lane per float4; rows outside the
+    // array and columns outside the row read as 0
+    for (int row = warp; row < 2 * Gm::R; row += kWarps) {
+      const int c = row >= Gm::R;
+      const int r = row - c * Gm::R;
       const int i = base_r + r;
-      const int e = base_e + 4 * g;
+      const int e = base_e + 4 * lane;
       const bool valid = !zero_start && i >= 0 && i <= n + 1 && e >= 0 && e + 4 <= pitch;
       const float* gp = valid ? (const float*)sd.x[src][c] + (size_t)i * pitch + e : nullptr;
-      cp_async16((c ? S1 : S0) + r * Gm::C + 4 * g, gp, valid);
+      cp_async16((c ? S1 : S0) + r * Gm::C + 4 * lane, gp, valid);
     }
     cp_async_wait_all();
     __syncthreads();
 
     const float a = sd.a32, b = sd.b32;
     unsigned dm32 = 0;
+    constexpr int U = Gm::R - 2;                 // updatable staged rows 1 .. R-2
+    constexpr int SEG = (U + kWarps - 1) / kWarps;
+    const int r0 = 1 + warp * SEG;
+    const int r1 = min(r0 + SEG, Gm::R - 1);
     for (int it = 0; it < nt; ++it) {
-      const bool last = it == nt - 1;
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float* Sc = c ? S1 : S0;
-        const float* So = c ? S0 : S1;
-        const float* Gc = (const float*)sd.g[c];
-        for (int idx = threadIdx.x; idx < (Gm::R - 2) * Gm::G; idx += blockDim.x) {
-          const int r = 1 + idx / Gm::G;
-          const int g = idx - (r - 1) * Gm::G;
-          const int i = base_r + r;
-          if (i < 1 || i > n) continue;
-          const int s = (i + c) & 1;
-          const int qlim = (n + s) >> 1;
-          const int qf = base_q + 4 * g;
-          if (qf + 3 < 1 || qf > qlim) continue;  // no interior cell in this group
-          float own[4], nm[4], np[4], oc[4], gv[4];
-          load4(Sc + r * Gm::C + 4 * g, own);
-          load4(So + (r - 1) * Gm::C + 4 * g, nm);
-          load4(So + (r + 1) * Gm::C + 4 * g, np);
-          load4(So + r * Gm::C + 4 * g, oc);
-          const float left = g > 0 ? So[r * Gm::C + 4 * g - 1] : 0.0f;
-          const float right = g + 1 < Gm::G ? So[r * Gm::C + 4 * g + 4] : 0.0f;
-          if (Gc) {
-            load4(Gc + (size_t)i * pitch + qf + kOff, gv);
-          } else {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
-          }
-          float W[4], E[4];
-          if (s == 0) {
-            W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
-            E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
-          } else {
-            W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
-            E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
-          }
-          const bool out_row = r >= Gm::HR && r < Gm::HR + tl.nrows;
-          float nv[4];
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int q = qf + v;
-            const int col = 4 * g + v;
-            float sum = radd(radd(nm[v], np[v]), radd(W[v], E[v]));
-            if (Gc) sum = radd(sum, gv[v]);
-            const float nu = radd(rmul(a, own[v]), rmul(b, sum));
-            const bool in = q >= 1 && q <= qlim && col >= 1 && col <= Gm::C - 2;
-            nv[v] = in ? nu : own[v];
-            if (MODE == 0 && measure && last && in && out_row && col >= Gm::HQ && col < Gm::HQ + kTbCols)
-              dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
-          }
-          store4(Sc + r * Gm::C + 4 * g, nv);
-        }
+      const bool lastm = (MODE == 0) && measure && it == nt - 1;
+      if (lastm) {
+        tb_phase<T, true>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
+                          dm32);
         __syncthreads();
+        tb_phase<T, true>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
+                          dm32);
+      } else {
+        tb_phase<T, false>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
+                           b, dm32);
+        __syncthreads();
+        tb_phase<T, false>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
+                           b, dm32);
       }
+      __syncthreads();
     }
-    // write the centre tile to the other buffer
+    // write the centre tile to the other buffer: warp per row, lane per float4
     const int dst = src ^ 1;
-    for (int idx = threadIdx.x; idx < 2 * kTbRows * (kTbCols / 4); idx += blockDim.x) {
-      const int c = idx / (kTbRows * (kTbCols / 4));
-      const int rem = idx - c * (kTbRows * (kTbCols / 4));
-      const int r = rem / (kTbCols / 4);
-      const int g = rem - r * (kTbCols / 4);
+    for (int row = warp; row < 2 * kTbRows; row += kWarps) {
+      const int c = row >= kTbRows;
+      const int r = row - c * kTbRows;
       if (r >= tl.nrows) continue;
+      const int col = 4 * lane;
+      if (col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
       const int i = tl.row0 + r;
       const int s = (i + c) & 1;
       const int qlim = (n + s) >> 1;
-      const int qf = tl.col0 + 4 * g;
+      const int qf = base_q + col;
       if (qf > qlim) continue;
       float v4[4];
-      load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + Gm::HQ + 4 * g, v4);
+      load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4);
       float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
       if (qf + 3 <= qlim) {
         store4(Xd, v4);
@@ -800,11 +834,11 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
     if (MODE == 0) {
       if (measure) {
         unsigned long long dm = warp_max64(abs_bits_of(__uint_as_float(dm32)));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dm;
+        if (lane == 0) red[warp] = dm;
         __syncthreads();
         if (threadIdx.x == 0) {
           unsigned long long m = 0;
-          for (int k = 0; k < kTbThreads / 32; ++k) m = umax64(m, red[k]);
+          for (int k = 0; k < kWarps; ++k) m = umax64(m, red[k]);
           if (m) atomicMax(&st->dmax_bits, m);
         }
       }
@@ -820,6 +854,17 @@ __global__ void __launch_bounds__(kTbThreads) k_sweep_tb(const SlotDesc* __restr
       }
     }
     __syncthreads();  // the next tile reuses the staged arrays
+  }
+}
+
+int tb_out_cols(int T) {
+  switch (T) {
+    case 2: return TbGeom<2>::OQ;
+    case 3: return TbGeom<3>::OQ;
+    case 4: return TbGeom<4>::OQ;
+    case 6: return TbGeom<6>::OQ;
+    case 8: return TbGeom<8>::OQ;
+    default: return kWarpCols;
   }
 }
 

@@ -40,11 +40,14 @@ int fast_blocks_per_sm();
 cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
                                 int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s);
 // FP32 phases fused over nt <= T iterations per tile (temporal blocking);
-// tiles are kTbRows x kTbCols.  inner: correction sweeps of defect
+// tiles are kTbRows x tb_out_cols(T).  inner: correction sweeps of defect
 // correction (src = buffer holding d, sweep0 = index of the first sweep of
 // this launch within the correction); otherwise plain FP32 iterations
 // (buffer and iteration count from the slot state).  Writes buffer src ^ 1.
 bool tb_depth_supported(int T);
+// Output packed columns of a fused-iteration tile of depth T (tiles are
+// kTbRows rows by tb_out_cols(T) packed columns, starting at column 1).
+int tb_out_cols(int T);
 cudaError_t launch_sweep_tb(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
                             int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,

@@ -213,13 +213,15 @@ void fill_desc(const Plan& p, SlotBuffers* b) {
   d.resid_tiles = d.sweep_tiles;
 }
 
-void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid, int tile_rows) {
+void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid, int tile_rows,
+                 int tile_cols) {
   const int row_tiles = (L.n + tile_rows - 1) / tile_rows;
+  const int col_tiles = (L.qmax + tile_cols - 1) / tile_cols;
   for (int r = 0; r < row_tiles; ++r) {
     const int row0 = 1 + r * tile_rows;
     const int nrows = std::min(tile_rows, L.n - r * tile_rows);
-    for (int t = 0; t < L.col_tiles(); ++t) {
-      Tile tl{slot, row0, 1 + t * kWarpCols, nrows};
+    for (int t = 0; t < col_tiles; ++t) {
+      Tile tl{slot, row0, 1 + t * tile_cols, nrows};
       if (sweep) sweep->push_back(tl);
       if (resid) resid->push_back(tl);
     }
@@ -318,7 +320,7 @@ int resolve_tdepth(Ctx* c, const Plan& p) {
 
 static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   const bool pingpong = p.tdepth > 1;
-  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f && c->ws->pingpong == pingpong) {
+  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f && c->ws->tdepth == p.tdepth) {
     *out = c->ws.get();
     return SOR_OK;
   }
@@ -328,11 +330,12 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->kind = p.kind;
   w->has_f = p.has_f;
   w->pingpong = pingpong;
+  w->tdepth = p.tdepth;
   const Layout L = Layout::make(p.n);
   std::vector<Tile> st, rt, ft, tt;
   build_tiles(L, 0, &st, &rt, kTileRows);
   build_strips(L, 0, c->sm_count * fast_blocks_per_sm() * kWarpsY, &ft);
-  build_tiles(L, 0, &tt, nullptr, kTbRows);
+  if (p.tdepth > 1) build_tiles(L, 0, &tt, nullptr, kTbRows, tb_out_cols(p.tdepth));
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
   const size_t small =
@@ -356,7 +359,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_sweep_tiles = (Tile*)ctx_dev_alloc(c, st.size() * sizeof(Tile));
   w->d_resid_tiles = (Tile*)ctx_dev_alloc(c, rt.size() * sizeof(Tile));
   w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
-  w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, tt.size() * sizeof(Tile));
+  w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, std::max<size_t>(1, tt.size()) * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
@@ -382,7 +385,8 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->n_resid_tiles = (int)rt.size();
   w->n_fast_tiles = (int)ft.size();
   w->n_tb_tiles = (int)tt.size();
-  SOR_CK(c, cudaMemcpyAsync(w->d_tb_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  if (!tt.empty())
+    SOR_CK(c, cudaMemcpyAsync(w->d_tb_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_sweep_tiles, st.data(), st.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_resid_tiles, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_fast_tiles, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));

@@ -64,6 +64,7 @@ struct SolveWorkspace {
   int n = -1, kind = -1;
   bool has_f = false;
   bool pingpong = false;
+  int tdepth = 1;
   SlotBuffers slot;
   SlotDesc* d_desc = nullptr;
   SlotState* d_state = nullptr;
@@ -159,7 +160,7 @@ sor_status alloc_slot(Ctx* c, const Plan& p, bool pingpong, SlotBuffers* out);
 void free_slot(Ctx* c, SlotBuffers* b);
 void fill_desc(const Plan& p, SlotBuffers* b);
 void build_tiles(const Layout& L, int slot, std::vector<Tile>* sweep, std::vector<Tile>* resid,
-                 int tile_rows = kTileRows);
+                 int tile_rows = kTileRows, int tile_cols = kWarpCols);
 
 void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out);
 sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
