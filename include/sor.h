@@ -87,7 +87,10 @@ typedef struct {
                            (Section 3.3).  SOR_FP32_REFINE tests after every correction. */
   int32_t inner_sweeps; /* SOR_FP32_REFINE: sweeps per correction (>= 1); 0 = 20 */
   int32_t flags;        /* SOR_FLAG_* */
-  int32_t reserved;     /* must be 0 */
+  int32_t stall_window; /* > 0: residual tests only (SOR_FP32_REFINE, or SOR_STOP_RESID_REL): also
+                           stop, with converged = 0, once this many residual tests in a row have
+                           not produced a new smallest residual -- the tolerance is below what
+                           FP64 can reach for this problem.  0 = off.  Must be >= 0. */
 } sor_params;
 
 typedef struct {

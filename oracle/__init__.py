@@ -63,12 +63,12 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             lib.oracle_sor_f64.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
-                                           ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _dp]
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _dp]
             lib.oracle_sor_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
             lib.oracle_refine.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
+                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
             for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine):
                 fn.restype = ctypes.c_int
             _lib = lib
@@ -102,10 +102,13 @@ def omega_opt(n: int) -> float:
     return 2.0 / (1.0 + np.sin(np.pi / (n + 1)))
 
 
-def sor_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):
+def sor_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, stall_window=0,
+            trace=False):
     """Plain FP64 red-black SOR (Algorithm 1).  Returns a dict with ``u``,
     ``iterations``, ``converged``, ``final_maxdelta``, ``final_resid_rel`` and,
-    when ``trace`` is set, ``trace`` = m_k for k = 1..iterations."""
+    when ``trace`` is set, ``trace`` = m_k for k = 1..iterations.  With
+    stop_mode 1 and stall_window > 0 the loop also stops (not converged) once
+    that many residual tests in a row gave no new smallest residual."""
     n = int(np.asarray(u0).shape[0]) - 2
     u0 = _grid(u0, n)
     f = _src(f, n)
@@ -114,8 +117,8 @@ def sor_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_
     md, rr = ctypes.c_double(0), ctypes.c_double(0)
     tr = np.zeros(max(max_iters, 1)) if trace else None
     rc = _load().oracle_sor_f64(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
-                                int(stop_mode), _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md),
-                                ctypes.byref(rr), _ptr(tr))
+                                int(stop_mode), int(stall_window), _ptr(u), ctypes.byref(it), ctypes.byref(cv),
+                                ctypes.byref(md), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_sor_f64: bad arguments")
     out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
@@ -164,8 +167,11 @@ def resid_rel(u, *, f=None):
     return rm / bm if bm > 0 else rm
 
 
-def refine(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, trace=False):
-    """FP64 defect correction around reduced-precision red-black SOR sweeps."""
+def refine(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, stall_window=0,
+           trace=False):
+    """FP64 defect correction around reduced-precision red-black SOR sweeps
+    (stall_window > 0: stop, not converged, after that many residual tests in
+    a row without a new smallest residual)."""
     n = int(np.asarray(u0).shape[0]) - 2
     u0 = _grid(u0, n)
     f = _src(f, n)
@@ -174,7 +180,8 @@ def refine(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max
     rr = ctypes.c_double(0)
     tr = np.zeros(max_outer + 1) if trace else None
     rc = _load().oracle_refine(n, float(omega), _ptr(u0), _ptr(f), int(inner_sweeps), int(bool(inner_f32)),
-                               float(tol), int(max_outer), _ptr(u), ctypes.byref(ou), ctypes.byref(sw),
+                               float(tol), int(max_outer), int(stall_window), _ptr(u), ctypes.byref(ou),
+                               ctypes.byref(sw),
                                ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_refine: bad arguments")

@@ -132,8 +132,8 @@ static double rel(double rmax, double bmax) { return bmax > 0.0 ? rmax / bmax : 
  *   receives m_k for every iteration.  Returns 0, or -1 on bad arguments /
  *   allocation failure. */
 int oracle_sor_f64(int n, double omega, const double *u0, const double *f, int max_iters, int check_every,
-                   double tol, int stop_mode, double *u, int *iterations, int *converged, double *final_maxdelta,
-                   double *final_resid_rel, double *trace) {
+                   double tol, int stop_mode, int stall_window, double *u, int *iterations, int *converged,
+                   double *final_maxdelta, double *final_resid_rel, double *trace) {
   if (n < 1 || max_iters < 0 || check_every < 1 || !u0 || !u) return -1;
   const int m = n + 2;
   if (u != u0) memcpy(u, u0, sizeof(double) * (size_t)m * m);
@@ -141,6 +141,10 @@ int oracle_sor_f64(int n, double omega, const double *u0, const double *f, int m
   if (f && !g) return -1;
   int it = 0, conv = 0;
   double mk = 0.0, rho = -1.0;
+  /* stall rule (residual tests only): stop without convergence once
+   * stall_window consecutive tests have not produced a new smallest rho */
+  double best = HUGE_VAL;
+  int tests = 0, best_test = 0;
   for (int k = 1; k <= max_iters; ++k) {
     const double dr = phase_f64(n, u, g, omega, 0); /* red   */
     const double db = phase_f64(n, u, g, omega, 1); /* black */
@@ -155,6 +159,9 @@ int oracle_sor_f64(int n, double omega, const double *u0, const double *f, int m
         residual_f64(n, u, g, NULL, &rm, &bm);
         rho = rel(rm, bm);
         if (rho < tol) { conv = 1; break; }
+        ++tests;
+        if (rho < best) { best = rho; best_test = tests; }
+        else if (stall_window > 0 && tests - best_test >= stall_window) break;
       }
     }
   }
@@ -236,8 +243,8 @@ int oracle_residual(int n, const double *u, const double *f, double *r, double *
  * done, total inner sweeps, final rho.  trace (optional, length max_outer+1)
  * receives rho per residual evaluation. */
 int oracle_refine(int n, double omega, const double *u0, const double *f, int inner_sweeps, int inner_f32,
-                  double tol, int max_outer, double *u, int *outer_steps, int *sweeps, int *converged,
-                  double *final_resid_rel, double *trace) {
+                  double tol, int max_outer, int stall_window, double *u, int *outer_steps, int *sweeps,
+                  int *converged, double *final_resid_rel, double *trace) {
   if (n < 1 || inner_sweeps < 1 || max_outer < 0 || !u0 || !u) return -1;
   const int m = n + 2;
   const size_t cells = (size_t)m * m;
@@ -253,7 +260,8 @@ int oracle_refine(int n, double omega, const double *u0, const double *f, int in
   }
   const float a32 = (float)(1.0 - omega), b32 = (float)(omega / 4.0);
   int outer = 0, conv = 0;
-  double rho = 0.0;
+  double rho = 0.0, best = HUGE_VAL;
+  int best_test = 0;
   for (;;) {
     double rm, bm;
     residual_f64(n, u, g, r, &rm, &bm);
@@ -261,6 +269,9 @@ int oracle_refine(int n, double omega, const double *u0, const double *f, int in
     if (trace) trace[outer] = rho;
     if (rho < tol) { conv = 1; break; }
     if (outer == max_outer) break;
+    /* stall rule: no new smallest rho in stall_window consecutive tests */
+    if (rho < best) { best = rho; best_test = outer; }
+    else if (stall_window > 0 && outer - best_test >= stall_window) break;
     if (inner_f32) {
       for (size_t c = 0; c < cells; ++c) { d32[c] = 0.0f; r32[c] = (float)r[c]; }
       for (int s = 0; s < inner_sweeps; ++s) {

@@ -54,7 +54,7 @@ class sor_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("precision", ctypes.c_int32), ("omega", ctypes.c_double),
                 ("tol", ctypes.c_double), ("stop", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("inner_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("stall_window", ctypes.c_int32)]
 
 
 class sor_result(ctypes.Structure):
@@ -145,9 +145,9 @@ def sor_omega_opt(n: int) -> float:
 
 
 def make_params(n, *, precision=SOR_FP64, omega=0.0, tol=1e-8, stop=SOR_STOP_MAXDELTA, max_iters=5000,
-                check_every=1, inner_sweeps=0, flags=0) -> sor_params:
+                check_every=1, inner_sweeps=0, flags=0, stall_window=0) -> sor_params:
     return sor_params(int(n), int(precision), float(omega), float(tol), int(stop), int(max_iters),
-                      int(check_every), int(inner_sweeps), int(flags), 0)
+                      int(check_every), int(inner_sweeps), int(flags), int(stall_window))
 
 
 def _ptr(a):

@@ -59,12 +59,16 @@ struct Batcher {
   SlotState* h_state = nullptr;  // pinned
   Tile* d_tiles = nullptr;       // [refine sweep | refine resid | plain64 | plain32 | retire]
   size_t tiles_cap = 0;
-  int nt_refine = 0, nt_p64 = 0, nt_p32 = 0;
-  size_t off_p64 = 0, off_p32 = 0, off_retire = 0;
+  int nt_refine = 0, nt_p64 = 0, nt_p32 = 0, nt_reftb = 0;
+  size_t off_p64 = 0, off_p32 = 0, off_reftb = 0;
   int max_inner = 1;
+  bool uniform_inner = true;  // every refine slot runs the same number of inner sweeps
+  int tdepth = 1;             // fused iterations of the refine sweeps this step (1 = unfused)
+  int dbuf_in = 0;            // buffer holding the corrections the next residual pass applies
   bool any_resid_stop = false;
   uint64_t version = 0;       // bumps when the active set changes
   uint64_t graph_version = ~0ull;
+  int graph_dbuf = -1;
   cudaGraphExec_t graph = nullptr;
   size_t reserved_tables = 0;
 };
@@ -115,15 +119,28 @@ static sor_status ensure_tables(Batcher* b, int cap, size_t ntiles) {
 
 // Rebuild the tile table after the active set changed.
 static sor_status rebuild_tiles(Batcher* b) {
-  std::vector<Tile> ref, p64, p32;
+  std::vector<Tile> ref, p64, p32, reftb;
   b->max_inner = 1;
   b->any_resid_stop = false;
+  int inner0 = -1;
+  b->uniform_inner = true;
+  for (size_t s = 0; s < b->slots.size(); ++s) {
+    Request* r = b->slots[s].get();
+    if (r && r->plan.kind == kRefine) {
+      if (inner0 < 0) inner0 = r->plan.inner;
+      if (r->plan.inner != inner0) b->uniform_inner = false;
+    }
+  }
+  Plan probe;
+  probe.kind = kRefine;
+  const int T = b->uniform_inner ? resolve_tdepth(b->c, probe) : 1;
   for (size_t s = 0; s < b->slots.size(); ++s) {
     Request* r = b->slots[s].get();
     if (!r) continue;
     const Layout& L = r->buf.L;
     if (r->plan.kind == kRefine) {
       build_tiles(L, (int)s, &ref, nullptr);
+      if (T > 1) build_tiles(L, (int)s, &reftb, nullptr, kTbRows, tb_out_cols(T));
       b->max_inner = std::max(b->max_inner, r->plan.inner);
     } else if (r->plan.kind == kPlain64) {
       build_tiles(L, (int)s, &p64, nullptr);
@@ -133,7 +150,7 @@ static sor_status rebuild_tiles(Batcher* b) {
       if (r->plan.stop == kStopResid) b->any_resid_stop = true;
     }
   }
-  const size_t total = ref.size() + p64.size() + p32.size();
+  const size_t total = ref.size() + p64.size() + p32.size() + reftb.size();
   sor_status rs = ensure_tables(b, (int)b->slots.size(), total + 1);
   if (rs != SOR_OK) return rs;
   std::vector<Tile> all;
@@ -141,11 +158,15 @@ static sor_status rebuild_tiles(Batcher* b) {
   all.insert(all.end(), ref.begin(), ref.end());
   all.insert(all.end(), p64.begin(), p64.end());
   all.insert(all.end(), p32.begin(), p32.end());
+  all.insert(all.end(), reftb.begin(), reftb.end());
   b->nt_refine = (int)ref.size();
   b->nt_p64 = (int)p64.size();
   b->nt_p32 = (int)p32.size();
+  b->nt_reftb = (int)reftb.size();
   b->off_p64 = ref.size();
   b->off_p32 = ref.size() + p64.size();
+  b->off_reftb = ref.size() + p64.size() + p32.size();
+  b->tdepth = T;
   Ctx* c = b->c;
   if (!all.empty())
     SOR_BCK(cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, b->stream));
@@ -158,10 +179,20 @@ static sor_status enqueue_step(Batcher* b) {
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
   if (b->nt_refine) {
-    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 0, s));
-    for (int sw = 0; sw < b->max_inner; ++sw) {
-      SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 0, sw, s));
-      SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 1, sw, s));
+    // residual pass: applies the corrections of the previous step, tests, writes r~
+    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, b->dbuf_in, s));
+    if (b->tdepth > 1) {
+      const Tile* t = b->d_tiles + b->off_reftb;
+      for (int j = 0, sw = 0; sw < b->max_inner; ++j, sw += b->tdepth) {
+        const int nt = std::min(b->tdepth, b->max_inner - sw);
+        SOR_BCK(launch_sweep_tb(true, b->tdepth, b->d_desc, b->d_state, t, b->nt_reftb, 0, nt, (j % 2 == 0) ? 1 : 0,
+                                sw, s));
+      }
+    } else {
+      for (int sw = 0; sw < b->max_inner; ++sw) {
+        SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 0, sw, s));
+        SOR_BCK(launch_sweep(kSweepInner32, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, 1, sw, s));
+      }
     }
   }
   for (int kind = 0; kind < 2; ++kind) {
@@ -182,7 +213,7 @@ static sor_status enqueue_step(Batcher* b) {
 static sor_status run_step(Batcher* b) {
   Ctx* c = b->c;
   if (!c->opt_graphs.load()) return enqueue_step(b);
-  if (b->graph_version != b->version || !b->graph) {
+  if (b->graph_version != b->version || !b->graph || b->graph_dbuf != b->dbuf_in) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -200,21 +231,32 @@ static sor_status run_step(Batcher* b) {
     cudaGraphDestroy(g);
     SOR_BCK(e);
     b->graph_version = b->version;
+    b->graph_dbuf = b->dbuf_in;
   }
   SOR_BCK(cudaGraphLaunch(b->graph, b->stream));
   return SOR_OK;
 }
 
+// Buffer the next residual pass reads the corrections from, after a step
+// whose sweeps ran with depth b->tdepth.
+static int step_dbuf_out(const Batcher* b) {
+  Plan q;
+  q.kind = kRefine;
+  q.inner = b->max_inner;
+  q.tdepth = b->tdepth;
+  return refine_dbuf(q);
+}
+
 static size_t request_bytes(const Plan& p) {
   const size_t stage = (size_t)(p.n + 2) * (p.n + 2) * 8 + (p.has_f ? (size_t)p.n * p.n * 8 : 0);
-  return slot_bytes(p, false) + stage;
+  return slot_bytes(p, p.kind == kRefine) + stage;
 }
 
 // Allocate, copy and pack one request into slot `s` (scheduler thread).
 static sor_status activate(Batcher* b, Request* r, int s) {
   Ctx* c = b->c;
   const Plan& p = r->plan;
-  sor_status rs = alloc_slot(c, p, false, &r->buf);
+  sor_status rs = alloc_slot(c, p, p.kind == kRefine, &r->buf);
   if (rs != SOR_OK) return rs;
   r->stage_bytes = (size_t)(p.n + 2) * (p.n + 2) * 8 + (p.has_f ? (size_t)p.n * p.n * 8 : 0);
   r->d_stage = (double*)ctx_dev_alloc(c, r->stage_bytes);
@@ -429,7 +471,10 @@ static void scheduler_main(Batcher* b) {
       b->slots[sidx] = std::move(r);
     }
     if (rs == SOR_OK && !admitted.empty()) rs = rebuild_tiles(b);
-    if (rs == SOR_OK && active_count(b) > 0) rs = run_step(b);
+    if (rs == SOR_OK && active_count(b) > 0) {
+      rs = run_step(b);
+      b->dbuf_in = step_dbuf_out(b);
+    }
     if (rs == SOR_OK) {
       for (size_t k = 0; k < b->slots.size(); ++k)
         if (b->slots[k]) {

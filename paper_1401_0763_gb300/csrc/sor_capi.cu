@@ -102,6 +102,7 @@ sor_status sor_create(sor_ctx** out, int device, size_t hbm_budget_bytes, void* 
     }
     c->own_stream = true;
   }
+  load_tune_cache(c);
   *out = h;
   return SOR_OK;
 }

@@ -66,6 +66,7 @@ struct SlotDesc {
   int sweep_tiles;      // tiles of this slot in one sweep launch
   int resid_tiles;      // tiles of this slot in one residual launch
   int K, max_iters, stop, inner;
+  int stall;            // residual tests without a new minimum that end the solve (0 = never)
   float a32, b32;       // (float)(1 - w), (float)(w / 4)
   double a64, b64;      // 1 - w, w / 4
   double tol;
@@ -86,6 +87,9 @@ struct SlotState {
   int ubuf;                      // buffer of u holding the current solution (refine)
   int checked_iter;              // iteration of the last residual test
   int error;                     // nonzero: device-side consistency failure
+  int tests;                     // residual tests done (plain residual stop)
+  int best_test;                 // test (plain) or correction count (refine) of the smallest rho so far
+  double best_rho;               // smallest rho so far (+inf before the first test)
   double last_dmax;              // m_k of the last iteration that measured it (-1 if none)
   double last_rho;               // relative residual of the last residual pass (-1 if none)
 };

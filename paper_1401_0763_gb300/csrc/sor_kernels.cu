@@ -388,6 +388,66 @@ struct FastWalk {
   double om[4], oc[4], dlp[4];
 };
 
+// Rows are staged through shared memory by asynchronous copies issued
+// kFastStages - 1 rows ahead (a per-warp pipeline), so the loads' latency
+// leaves the critical path without holding registers.  A stage holds, for
+// row i: the neighbour-colour row i+1, the own row i, the source row i and the
+// two strip-edge neighbours O[i][q0-1] (lane 0) and O[i][q0+4] (lane 31).
+// Each lane reads back only what it copied itself, so the pipeline needs no
+// synchronisation beyond each thread's own wait_group.
+constexpr int kFastStages = 4;
+
+template <bool HAS_G>
+struct FastStage {
+  double op[32 * kVec];
+  double own[32 * kVec];
+  double g[HAS_G ? 32 * kVec : 2];
+  double edge[2];
+};
+
+template <bool HAS_G>
+constexpr size_t fast_smem_bytes() {
+  return (size_t)kWarpsY * kFastStages * sizeof(FastStage<HAS_G>);
+}
+
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Issue the copies of row i into a stage (nothing when !valid) and close the
+// group either way, so every row accounts for exactly one group.
+template <bool HAS_G>
+__device__ __forceinline__ void fast_issue(FastStage<HAS_G>* st, int i, bool valid, const double* __restrict__ O,
+                                           const double* __restrict__ X, const double* __restrict__ G, int pitch,
+                                           int q0, int lane) {
+  if (valid) {
+    const double* o = O + eidx(i + 1, q0, pitch);
+    const double* x = X + eidx(i, q0, pitch);
+    cp_async_16(st->op + lane * kVec, o);
+    cp_async_16(st->op + lane * kVec + 2, o + 2);
+    cp_async_16(st->own + lane * kVec, x);
+    cp_async_16(st->own + lane * kVec + 2, x + 2);
+    if (HAS_G) {
+      const double* gp = G + eidx(i, q0, pitch);
+      cp_async_16(st->g + lane * kVec, gp);
+      cp_async_16(st->g + lane * kVec + 2, gp + 2);
+    }
+    if (lane == 0) cp_async_8(&st->edge[0], O + eidx(i, q0 - 1, pitch));
+    if (lane == 31) cp_async_8(&st->edge[1], O + eidx(i, q0 + kVec, pitch));
+  }
+  cp_async_commit();
+}
+
 // One row of a strip.  S = (i + colour) & 1 is known at compile time, which
 // fixes where W / E come from and how the upper-left pair sum of this row is
 // obtained from the previous row's lower-right ones: S == 0 -> the same
@@ -396,27 +456,33 @@ struct FastWalk {
 // EDGE: this strip touches the first or last packed column, so Dirichlet ring
 // values may be among the loaded neighbours and are rescaled by ph.bscale.
 template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST>
-__device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, const double* __restrict__ O,
-                                         double* __restrict__ X, const double* __restrict__ G, int pitch, int n,
-                                         int ocol, int q0, int lane, const FastPhase& ph, unsigned long long& dm) {
+__device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, FastStage<HAS_G>* stages, int i0,
+                                         int i1, const double* __restrict__ O, double* __restrict__ X,
+                                         const double* __restrict__ G, int pitch, int n, int ocol, int q0, int lane,
+                                         const FastPhase& ph, unsigned long long& dm) {
+  // keep the pipeline kFastStages - 1 rows ahead, then wait for this row
+  const int ahead = i + kFastStages - 1;
+  fast_issue<HAS_G>(stages + ((ahead - i0) & (kFastStages - 1)), ahead, ahead < i1, O, X, G, pitch, q0, lane);
+  cp_async_wait<kFastStages - 1>();
+  const FastStage<HAS_G>* st = stages + ((i - i0) & (kFastStages - 1));
   double op[4], own[4], gv[4];
-  load4(O + eidx(i + 1, q0, pitch), op);
+  load4(st->op + lane * kVec, op);
   if (ring_below) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) op[v] = __dmul_rn(op[v], ph.bscale);
   } else if (EDGE) {
     scale_ring4(op, i + 1, q0, n, ocol, ph.bscale, true);
   }
-  load4(X + eidx(i, q0, pitch), own);
-  if (HAS_G) load4(G + eidx(i, q0, pitch), gv);
+  load4(st->own + lane * kVec, own);
+  if (HAS_G) load4(st->g + lane * kVec, gv);
   double left = __shfl_up_sync(0xffffffffu, w.oc[3], 1);
   double right = __shfl_down_sync(0xffffffffu, w.oc[0], 1);
   if (lane == 0) {
-    left = O[eidx(i, q0 - 1, pitch)];
+    left = st->edge[0];
     if (EDGE) left = scale_ring1(left, i, q0 - 1, n, ocol, ph.bscale);
   }
   if (lane == 31) {
-    right = O[eidx(i, q0 + kVec, pitch)];
+    right = st->edge[1];
     if (EDGE) right = scale_ring1(right, i, q0 + kVec, n, ocol, ph.bscale);
   }
   double W[4], E[4];
@@ -476,11 +542,13 @@ __device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, co
 // Rows [i0, i1) of one strip; rows alternate parity, so the body is unrolled
 // by two with the parity of each half fixed at compile time.
 template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE>
-__device__ __forceinline__ unsigned long long fast_walk(const double* __restrict__ O, double* __restrict__ X,
-                                                        const double* __restrict__ G, int pitch, int n, int colour,
-                                                        int q0, int i0, int i1, int lane, const FastPhase& ph,
-                                                        bool rescale) {
+__device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages, const double* __restrict__ O,
+                                                        double* __restrict__ X, const double* __restrict__ G,
+                                                        int pitch, int n, int colour, int q0, int i0, int i1,
+                                                        int lane, const FastPhase& ph, bool rescale) {
   const int ocol = colour ^ 1;
+  for (int k = 0; k < kFastStages - 1; ++k)  // prologue: rows i0 .. i0 + kFastStages - 2
+    fast_issue<HAS_G>(stages + k, i0 + k, i0 + k < i1, O, X, G, pitch, q0, lane);
   FastWalk w;
   load4(O + eidx(i0 - 1, q0, pitch), w.om);
   load4(O + eidx(i0, q0, pitch), w.oc);
@@ -493,30 +561,31 @@ __device__ __forceinline__ unsigned long long fast_walk(const double* __restrict
   const int iend = (rescale && i1 == n + 1) ? n : i1;
   int i = i0;
   const int s0 = (i0 + colour) & 1;
+#define FAST_ROW(SS, FF, II, RB)                                                                                 \
+  fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, SS, FF>(w, II, RB, stages, i0, i1, O, X, G, pitch, n, ocol, q0, lane, \
+                                                    ph, dm)
   if (i < iend) {
     if (s0 == 0)
-      fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, true>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+      FAST_ROW(0, true, i, false);
     else
-      fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, true>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+      FAST_ROW(1, true, i, false);
     ++i;
     if (s0 == 0) {
       for (; i + 1 < iend; i += 2) {
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i + 1, false, O, X, G, pitch, n, ocol, q0, lane, ph,
-                                                            dm);
+        FAST_ROW(1, false, i, false);
+        FAST_ROW(0, false, i + 1, false);
       }
       if (i < iend) {
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(1, false, i, false);
         ++i;
       }
     } else {
       for (; i + 1 < iend; i += 2) {
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i + 1, false, O, X, G, pitch, n, ocol, q0, lane, ph,
-                                                            dm);
+        FAST_ROW(0, false, i, false);
+        FAST_ROW(1, false, i + 1, false);
       }
       if (i < iend) {
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, false, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(0, false, i, false);
         ++i;
       }
     }
@@ -526,16 +595,18 @@ __device__ __forceinline__ unsigned long long fast_walk(const double* __restrict
     const int s = (i + colour) & 1;
     if (first) {
       if (s == 0)
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, true>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(0, true, i, true);
       else
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, true>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(1, true, i, true);
     } else {
       if (s == 0)
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 0, false>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(0, false, i, true);
       else
-        fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, 1, false>(w, i, true, O, X, G, pitch, n, ocol, q0, lane, ph, dm);
+        FAST_ROW(1, false, i, true);
     }
   }
+#undef FAST_ROW
+  cp_async_wait<0>();  // no copy may still target the stages when the warp moves on
   return dm;
 }
 
@@ -543,10 +614,12 @@ __device__ __forceinline__ unsigned long long fast_walk(const double* __restrict
 // packed column, rows) of 128 packed columns; a persistent grid strides over
 // a strip table cut so that every warp gets the same number of rows.
 template <bool UNIT_BETA, bool HAS_G>
-__global__ void __launch_bounds__(kThreads) k_sweep_fast(const SlotDesc* __restrict__ slots, SlotState* states,
-                                                         const Tile* __restrict__ strips, int nstrips, int colour,
-                                                         FastPhase ph) {
+__global__ void __launch_bounds__(kThreads, 3) k_sweep_fast(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                            const Tile* __restrict__ strips, int nstrips, int colour,
+                                                            FastPhase ph) {
+  extern __shared__ __align__(16) unsigned char fast_smem[];
   const int lane = threadIdx.x & 31;
+  FastStage<HAS_G>* stages = reinterpret_cast<FastStage<HAS_G>*>(fast_smem) + (threadIdx.x >> 5) * kFastStages;
   const int warp = blockIdx.x * kWarpsY + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * kWarpsY;
   for (int t = warp; t < nstrips; t += nwarps) {
@@ -581,13 +654,17 @@ __global__ void __launch_bounds__(kThreads) k_sweep_fast(const SlotDesc* __restr
     const bool edge = rescale && (tl.col0 == 1 || tl.col0 + kWarpCols > (n >> 1));
     unsigned long long dm;
     if (measure) {
-      dm = edge ? fast_walk<UNIT_BETA, HAS_G, true, true>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale)
-                : fast_walk<UNIT_BETA, HAS_G, true, false>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale);
+      dm = edge ? fast_walk<UNIT_BETA, HAS_G, true, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
+                                                          rescale)
+                : fast_walk<UNIT_BETA, HAS_G, true, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
+                                                           rescale);
       dm = warp_max64(dm);
       if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
     } else {
-      dm = edge ? fast_walk<UNIT_BETA, HAS_G, false, true>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale)
-                : fast_walk<UNIT_BETA, HAS_G, false, false>(O, X, G, pitch, n, colour, q0, i0, i1, lane, ph, rescale);
+      dm = edge ? fast_walk<UNIT_BETA, HAS_G, false, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
+                                                           rescale)
+                : fast_walk<UNIT_BETA, HAS_G, false, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
+                                                            rescale);
     }
     if (colour == 1) {
       __threadfence();
@@ -606,7 +683,10 @@ __global__ void __launch_bounds__(kThreads) k_sweep_fast(const SlotDesc* __restr
 
 int fast_blocks_per_sm() {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_fast<true, false>, kThreads, 0) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_sweep_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fast_smem_bytes<true>()) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_fast<true, true>, kThreads,
+                                                    fast_smem_bytes<true>()) != cudaSuccess) {
     cudaGetLastError();
     return 4;
   }
@@ -1038,7 +1118,18 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
         st->last_rho = rho;
         if (ROLE == kResidCheck) {
           st->checked_iter = c.k;
-          if (rho < sd.tol) { st->converged = 1; st->done = 1; }
+          if (rho < sd.tol) {
+            st->converged = 1;
+            st->done = 1;
+          } else {
+            st->tests += 1;
+            if (rho < st->best_rho) {
+              st->best_rho = rho;
+              st->best_test = st->tests;
+            } else if (sd.stall > 0 && st->tests - st->best_test >= sd.stall) {
+              st->done = 1;  // no new smallest residual in sd.stall tests: below the reachable floor
+            }
+          }
         } else if (ROLE == kResidRefine) {
           if (c.measure) {
             st->ubuf = c.xbuf ^ 1;
@@ -1050,6 +1141,11 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
             st->converged = 1;
             st->done = 1;
           } else if (st->iters + sd.inner > sd.max_iters) {
+            st->done = 1;
+          } else if (rho < st->best_rho) {
+            st->best_rho = rho;
+            st->best_test = st->outer;
+          } else if (sd.stall > 0 && st->outer - st->best_test >= sd.stall) {
             st->done = 1;
           }
         }
@@ -1121,14 +1217,31 @@ cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const 
   if (grid <= 0 || grid > need) grid = need;
   FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.bscale, a.last};
   const bool unit = a.beta == 1.0;
+  static bool attr_set = false;  // benign race: setting the attributes twice is harmless
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fast_smem_bytes<false>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fast_smem_bytes<false>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fast_smem_bytes<true>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)fast_smem_bytes<true>());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const size_t sm0 = fast_smem_bytes<false>(), sm1 = fast_smem_bytes<true>();
   if (unit && !has_g)
-    k_sweep_fast<true, false><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+    k_sweep_fast<true, false><<<grid, kThreads, sm0, s>>>(slots, states, tiles, ntiles, colour, ph);
   else if (unit && has_g)
-    k_sweep_fast<true, true><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+    k_sweep_fast<true, true><<<grid, kThreads, sm1, s>>>(slots, states, tiles, ntiles, colour, ph);
   else if (!has_g)
-    k_sweep_fast<false, false><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+    k_sweep_fast<false, false><<<grid, kThreads, sm0, s>>>(slots, states, tiles, ntiles, colour, ph);
   else
-    k_sweep_fast<false, true><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, ph);
+    k_sweep_fast<false, true><<<grid, kThreads, sm1, s>>>(slots, states, tiles, ntiles, colour, ph);
   return cudaGetLastError();
 }
 

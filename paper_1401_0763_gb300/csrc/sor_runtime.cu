@@ -7,6 +7,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <sstream>
 
 namespace sorgb {
@@ -50,7 +52,7 @@ sor_status make_plan(const sor_params* p, bool has_f, Plan* out, std::string* wh
   if (p->check_every < 1) { *why = "check_every < 1"; return SOR_ERR_INVALID_ARG; }
   if (p->inner_sweeps < 0) { *why = "inner_sweeps < 0"; return SOR_ERR_INVALID_ARG; }
   if (p->flags & ~SOR_FLAG_EXACT_ORDER) { *why = "unknown flag bits"; return SOR_ERR_INVALID_ARG; }
-  if (p->reserved != 0) { *why = "reserved must be 0"; return SOR_ERR_INVALID_ARG; }
+  if (p->stall_window < 0) { *why = "stall_window < 0"; return SOR_ERR_INVALID_ARG; }
   if (std::isnan(p->tol)) { *why = "tol is NaN"; return SOR_ERR_INVALID_ARG; }
   double w = p->omega;
   if (std::isnan(w)) { *why = "omega is NaN"; return SOR_ERR_INVALID_ARG; }
@@ -63,6 +65,7 @@ sor_status make_plan(const sor_params* p, bool has_f, Plan* out, std::string* wh
   P.max_iters = p->max_iters;
   P.has_f = has_f;
   P.exact = (p->flags & SOR_FLAG_EXACT_ORDER) != 0;
+  P.stall = p->stall_window;
   if (p->precision == SOR_FP32_REFINE) {
     P.kind = kRefine;
     P.stop = kStopResid;
@@ -204,6 +207,7 @@ void fill_desc(const Plan& p, SlotBuffers* b) {
   d.max_iters = p.max_iters;
   d.stop = p.stop;
   d.inner = p.inner;
+  d.stall = p.stall;
   d.a64 = 1.0 - p.omega;
   d.b64 = p.omega / 4.0;
   d.a32 = (float)(1.0 - p.omega);
@@ -249,6 +253,7 @@ SlotState initial_state(const Plan& p) {
   s.checked_iter = -1;
   s.last_dmax = -1.0;
   s.last_rho = -1.0;
+  s.best_rho = HUGE_VAL;
   if (p.kind != kRefine && p.max_iters == 0) s.done = 1;
   return s;
 }
@@ -613,12 +618,131 @@ static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, 
   return SOR_OK;
 }
 
+static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+                               sor_result* res, double t0);
+
+// ------------------------------------------------------------------------------------------------
+// autotuner: iterations fused per tile pass of the FP32 sweeps
+// ------------------------------------------------------------------------------------------------
+//
+// On the first FP32 or defect-correction solve of a size bucket (and source
+// presence), each candidate depth runs a short plain FP32 solve on the call's
+// own inputs with the sweep chunks timed by CUDA events; the fastest depth is
+// kept for the bucket.  Every depth gives bit-identical results, so the choice
+// affects time only.  SOR_AUTOTUNE_CACHE names an optional file holding the
+// choices across processes ("<n_bucket> <has_f> <depth>" per line).
+
+static const int kTuneDepths[] = {1, 2, 3, 4, 6, 8};
+static constexpr int kTuneIters = 48;  // a multiple of every candidate depth
+
+static int n_bucket(int n) {
+  int b = 16;
+  while (b < n) b <<= 1;
+  return b;
+}
+
+static std::string tune_key(int n, bool has_f) {
+  std::ostringstream os;
+  os << n_bucket(n) << " " << (has_f ? 1 : 0);
+  return os.str();
+}
+
+void load_tune_cache(Ctx* c) {
+  const char* path = std::getenv("SOR_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "r");
+  if (!fp) return;
+  int nb = 0, hf = 0, d = 0;
+  std::lock_guard<std::mutex> g(c->tune_mu);
+  while (std::fscanf(fp, "%d %d %d", &nb, &hf, &d) == 3)
+    if (tb_depth_supported(d) || d == 1) c->tuned[tune_key(nb, hf != 0)] = d;
+  std::fclose(fp);
+}
+
+static void save_tune_cache(Ctx* c) {
+  const char* path = std::getenv("SOR_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* fp = std::fopen(path, "w");
+  if (!fp) return;
+  for (const auto& kv : c->tuned) std::fprintf(fp, "%s %d\n", kv.first.c_str(), kv.second);
+  std::fclose(fp);
+}
+
+static sor_status autotune_depth(Ctx* c, const Plan& p, const double* u0, const double* f, int* best_out) {
+  Plan q = p;
+  q.kind = kPlain32;
+  q.stop = kStopDelta;
+  q.K = kTuneIters;
+  q.max_iters = kTuneIters;
+  q.tol = -1.0;
+  q.exact = false;
+  const int saved_timing = c->opt_timing.exchange(1);
+  sor_stats keep;
+  {
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    keep = c->stats;
+  }
+  double best_ms = 1e300;
+  int best = 4;
+  sor_status rs = SOR_OK;
+  for (int d : kTuneDepths) {
+    q.tdepth = d;
+    double ms = 0.0;
+    for (int rep = 0; rep < 2 && rs == SOR_OK; ++rep) {  // the first run builds buffers and graphs
+      {
+        std::lock_guard<std::mutex> g(c->stats_mu);
+        c->stats.sweep_ms = 0.0;
+      }
+      SolveWorkspace* w = nullptr;
+      rs = get_workspace(c, q, &w);
+      if (rs != SOR_OK) break;
+      rs = solve_locked(c, q, u0, f, w->d_nat_u, nullptr, now_s());  // result into the workspace staging
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      ms = c->stats.sweep_ms;
+    }
+    if (rs != SOR_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = d;
+    }
+  }
+  c->opt_timing = saved_timing;
+  {
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    c->stats = keep;
+  }
+  *best_out = best;
+  return rs;
+}
+
 sor_status solve_blocking(Ctx* c, const Plan& plan_in, const double* u0, const double* f, double* u_out,
                           sor_result* res) {
   const double t0 = now_s();
   std::lock_guard<std::mutex> lock(c->solve_mu);
   Plan p = plan_in;
   p.tdepth = resolve_tdepth(c, p);
+  if (p.kind != kPlain64 && c->opt_tdepth.load() == 0 && c->opt_autotune.load()) {
+    const std::string key = tune_key(p.n, p.has_f || p.kind == kRefine);
+    int d = -1;
+    {
+      std::lock_guard<std::mutex> g(c->tune_mu);
+      auto it = c->tuned.find(key);
+      if (it != c->tuned.end()) d = it->second;
+    }
+    if (d < 0) {
+      sor_status rs = autotune_depth(c, p, u0, f, &d);
+      if (rs != SOR_OK) return rs;
+      std::lock_guard<std::mutex> g(c->tune_mu);
+      c->tuned[key] = d;
+      save_tune_cache(c);
+    }
+    p.tdepth = d;
+  }
+  return solve_locked(c, p, u0, f, u_out, res, t0);
+}
+
+static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+                               sor_result* res, double t0) {
   cudaStream_t s = c->stream;
   SolveWorkspace* w = nullptr;
   sor_status rs = get_workspace(c, p, &w);

@@ -46,6 +46,7 @@ struct Plan {
   bool exact = false;
   bool has_f = false;
   int tdepth = 1;  // FP32 sweeps: iterations fused per tile pass (1 = one launch per colour phase)
+  int stall = 0;   // residual tests without a new minimum that end the solve (0 = never)
   double omega = 0.0;
   double tol = 0.0;
 };
@@ -141,6 +142,9 @@ struct Ctx {
   std::atomic<int> opt_autotune{0};
   std::atomic<int> opt_max_slots{0};
 
+  std::mutex tune_mu;
+  std::map<std::string, int> tuned;  // autotuned FP32 depth per "<n bucket> <has source>"
+
   std::unique_ptr<Batcher, BatcherDeleter> batcher;
   std::mutex batcher_mu;
 
@@ -167,6 +171,7 @@ sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
 SlotState initial_state(const Plan& p);
 void release_solve_workspace(Ctx* c);
 int resolve_tdepth(Ctx* c, const Plan& p);
+void load_tune_cache(Ctx* c);
 int refine_dbuf(const Plan& p);
 sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
                           sor_result* res);

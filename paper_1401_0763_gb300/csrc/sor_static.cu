@@ -73,7 +73,7 @@ sor_status static_plan(const sor_params* p, bool has_f, Plan* out) {
   if (p->precision != SOR_FP64) return SOR_ERR_INVALID_ARG;
   if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) return SOR_ERR_INVALID_ARG;
   if (p->max_iters < 0 || p->check_every < 1 || p->inner_sweeps < 0) return SOR_ERR_INVALID_ARG;
-  if ((p->flags & ~SOR_FLAG_EXACT_ORDER) || p->reserved != 0) return SOR_ERR_INVALID_ARG;
+  if ((p->flags & ~SOR_FLAG_EXACT_ORDER) || p->stall_window < 0) return SOR_ERR_INVALID_ARG;
   if (std::isnan(p->tol) || std::isnan(p->omega)) return SOR_ERR_INVALID_ARG;
   double w = p->omega <= 0.0 ? sor_omega_opt(p->n) : p->omega;
   if (!(w > 0.0 && w < 2.0)) return SOR_ERR_INVALID_ARG;
@@ -88,6 +88,7 @@ sor_status static_plan(const sor_params* p, bool has_f, Plan* out) {
   P.has_f = has_f;
   P.omega = w;
   P.tol = p->tol;
+  P.stall = p->stall_window;
   *out = P;
   return SOR_OK;
 }
@@ -148,6 +149,7 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   d.max_iters = plan.max_iters;
   d.stop = plan.stop;
   d.inner = 0;
+  d.stall = plan.stall;
   d.a64 = 1.0 - plan.omega;
   d.b64 = plan.omega / 4.0;
   d.a32 = (float)d.a64;
@@ -165,6 +167,7 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   st.checked_iter = -1;
   st.last_dmax = -1.0;
   st.last_rho = -1.0;
+  st.best_rho = HUGE_VAL;
   st.done = plan.max_iters == 0;
 
   // The scratch keeps whatever the previous call left: clear the arrays this

@@ -178,7 +178,7 @@ def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.heat_plate(8, 1.0)
     for kw in ({"omega": 2.0}, {"omega": 2.5}, {"max_iters": -1}, {"check_every": 0}, {"precision": 7},
-               {"stop": 3}, {"flags": 8}, {"tol": float("nan")}):
+               {"stop": 3}, {"flags": 8}, {"tol": float("nan")}, {"stall_window": -1}):
         with pytest.raises(capi.SorError) as e:
             ctx.solve(u0, **kw)
         assert e.value.status == capi.SOR_ERR_INVALID_ARG
@@ -304,3 +304,51 @@ def test_fp32_fused_full_size(ctx_depth):
     ref = oracle.sor_f32(u0, w, max_iters=100, check_every=50, tol=-1.0)
     got, res = run(ctx, u0, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=100, check_every=50)
     assert np.array_equal(got, ref["u"]) and res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+def test_autotuner_picks_a_depth_and_keeps_results(tmp_path, monkeypatch):
+    """With SOR_OPT_AUTOTUNE the first FP32 / refine solve of a size bucket
+    times every fused depth; results stay bit-identical to the oracle and the
+    choice is written to SOR_AUTOTUNE_CACHE."""
+    from paper_1401_0763_gb300 import _build, capi
+    _build.build()
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SOR_AUTOTUNE_CACHE", str(cache))
+    n = 300
+    u0 = wl.random_edges(n, 3)
+    w = oracle.omega_opt(n)
+    with capi.Context(0) as ctx:
+        ctx.set_option(capi.SOR_OPT_AUTOTUNE, 1)
+        got, res = run(ctx, u0, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=77, check_every=11)
+        ref = oracle.sor_f32(u0, w, max_iters=77, check_every=11, tol=-1.0)
+        assert np.array_equal(got, ref["u"])
+        u0p, f = wl.poisson_problem(n, 4)
+        got, res = run(ctx, u0p, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-10, max_iters=20000)
+        refr = oracle.refine(u0p, w, f=f, inner_sweeps=20, tol=1e-10, max_outer=1000)
+        assert np.array_equal(got, refr["u"]) and res["outer_steps"] == refr["outer_steps"]
+        assert ctx.stats()["solves"] == 2  # tuning runs are not counted
+    lines = [l.split() for l in cache.read_text().splitlines()]
+    assert {(int(a), int(b)) for a, b, _ in lines} == {(512, 0), (512, 1)}
+    assert all(int(d) in (1, 2, 3, 4, 6, 8) for _, _, d in lines)
+
+
+def test_stall_window_stops_at_the_fp64_floor(ctx):
+    """A tolerance below what FP64 reaches: with stall_window the solve stops,
+    not converged, once that many residual tests gave no new minimum -- at the
+    same step as the oracle, with the same result bit for bit."""
+    capi = capi_mod()
+    n = 96
+    u0, f = wl.poisson_problem(n, 7)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine(u0, w, f=f, inner_sweeps=10, tol=1e-17, max_outer=5000, stall_window=15)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-17, max_iters=50000,
+                   inner_sweeps=10, stall_window=15)
+    assert not ref["converged"] and ref["outer_steps"] < 5000
+    assert res["outer_steps"] == ref["outer_steps"] and not res["converged"]
+    assert np.array_equal(got, ref["u"])
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=50000, check_every=10, tol=1e-17, stop_mode=1, stall_window=12)
+    got, res = run(ctx, u0, f, omega=w, tol=1e-17, max_iters=50000, check_every=10, stop=capi.SOR_STOP_RESID_REL,
+                   stall_window=12, flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert not ref["converged"] and ref["iterations"] < 50000
+    assert res["iterations"] == ref["iterations"] and not res["converged"]
+    assert np.array_equal(got, ref["u"])
