@@ -159,7 +159,10 @@ typedef enum {
   SOR_OPT_CHUNK = 3,           /* iterations per launched chunk between convergence polls (0 = auto) */
   SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per tile pass (0 = autotuned) */
   SOR_OPT_AUTOTUNE = 5,        /* 1: time candidate kernel configurations on first use of a size */
-  SOR_OPT_BATCH_MAX_SLOTS = 6  /* cap on concurrently admitted batch requests (0 = no cap) */
+  SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
+  SOR_OPT_CLUSTER = 7          /* 1 (default): plain solves of grids small enough for one thread-block
+                                  cluster (N <= 384 in FP64, N <= 768 in FP32) run all their iterations
+                                  in a single launch, exact operation order; 0: never */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);

@@ -44,6 +44,7 @@ SOR_OPT_CHUNK = 3
 SOR_OPT_TEMPORAL_DEPTH = 4
 SOR_OPT_AUTOTUNE = 5
 SOR_OPT_BATCH_MAX_SLOTS = 6
+SOR_OPT_CLUSTER = 7
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",

@@ -1,0 +1,70 @@
+// Device helpers shared by the kernel translation units: operations rounded
+// one at a time (no contraction), vector loads / stores of 4 consecutive
+// packed cells, and order-preserving bit patterns for max reductions.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sor_device.cuh"
+
+namespace sorgb {
+
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  double2 a = reinterpret_cast<const double2*>(p)[0];
+  double2 b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// |x| as the bit pattern of a non-negative double: unsigned order == numeric
+// order, and any NaN compares above +inf, so a NaN is never lost by max.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+// The same for a float: FP32 kernels keep their max|change| as float bits
+// (integer max, no FP64 instruction) and widen once per thread.
+__device__ __forceinline__ unsigned abs_bits32(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned long long abs_bits_of(float x) { return abs_bits((double)x); }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double bits_to_double(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Block-wide max of v into *dst (atomic).  All threads of the block call it.
+__device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long long* dst,
+                                             unsigned long long* smem /* [kWarpsY] */) {
+  v = warp_max64(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long m = smem[0];
+#pragma unroll
+    for (int k = 1; k < kWarpsY; ++k) m = umax64(m, smem[k]);
+    if (m) atomicMax(dst, m);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ size_t eidx(int i, int q, int pitch) { return (size_t)i * pitch + q + kOff; }
+
+}  // namespace sorgb

@@ -50,6 +50,11 @@ bool tb_depth_supported(int T);
 int tb_out_cols(int T);
 cudaError_t launch_sweep_tb(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
                             int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+// Whole plain solve of a small grid inside one thread-block cluster (one
+// launch runs every iteration and the stopping test); exact-order update.
+bool cluster_solve_fits(bool fp32, int n, int pitch);
+cudaError_t launch_cluster_solve(bool fp32, int n, int pitch, const SlotDesc* slots, SlotState* states, int slot,
+                                 cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int dbuf, cudaStream_t s);
 

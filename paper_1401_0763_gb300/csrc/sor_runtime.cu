@@ -239,8 +239,11 @@ void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out) 
   const int ct = L.col_tiles();
   int m = std::max(1, warps / std::max(1, ct));
   m = std::min(m, std::max(1, L.n / 8));  // at least 8 rows per strip
-  for (int t = 0; t < ct; ++t)
-    for (int r = 0; r < m; ++r) {
+  // column tiles vary fastest: consecutive warps (hence every block and SM)
+  // get strips of different column tiles, spreading the first and last
+  // column tiles -- whose strips also read Dirichlet ring values -- evenly
+  for (int r = 0; r < m; ++r)
+    for (int t = 0; t < ct; ++t) {
       const int a = 1 + (int)((long long)r * L.n / m);
       const int b = 1 + (int)((long long)(r + 1) * L.n / m);
       if (b > a) out->push_back(Tile{slot, a, 1 + t * kWarpCols, b - a});
@@ -823,6 +826,20 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
     last_iters = hs.iters;
     return SOR_OK;
   };
+  // small plain grids: the whole solve in one cluster launch
+  const bool small = p.kind == kPlain64 ? p.n <= 384 : p.n <= 768;
+  if (!finished && p.kind != kRefine && small && c->opt_cluster.load() &&
+      cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch)) {
+    const int k = slot_i;
+    if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
+    SOR_CK(c, launch_cluster_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, w->d_desc, w->d_state, 0, s));
+    if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].second, s));
+    SOR_CK(c, cudaMemcpyAsync(&w->h_state[k], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR_CK(c, cudaEventRecord(w->poll_events[k], s));
+    rs = harvest(k);
+    if (rs != SOR_OK) return rs;
+    finished = true;
+  }
   while (!finished && planned < total_units) {
     if ((int)inflight.size() == kInflight - 1) {
       rs = harvest(inflight.front());

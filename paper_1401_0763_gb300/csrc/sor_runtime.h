@@ -141,6 +141,7 @@ struct Ctx {
   std::atomic<int> opt_tdepth{0};
   std::atomic<int> opt_autotune{0};
   std::atomic<int> opt_max_slots{0};
+  std::atomic<int> opt_cluster{1};
 
   std::mutex tune_mu;
   std::map<std::string, int> tuned;  // autotuned FP32 depth per "<n bucket> <has source>"

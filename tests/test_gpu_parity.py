@@ -23,12 +23,30 @@ TOL64 = 1e-12
 
 
 @pytest.fixture(scope="module")
-def ctx():
+def ctxs():
+    """Two contexts: the default one (small plain grids solved inside one
+    thread-block cluster) and one with that path switched off, so the
+    multi-CTA kernels are exercised at every size."""
     from paper_1401_0763_gb300 import _build, capi
     _build.build()
-    c = capi.Context(0)
-    yield c
-    c.close()
+    made = {"cluster": capi.Context(0), "multi": capi.Context(0)}
+    made["multi"].set_option(capi.SOR_OPT_CLUSTER, 0)
+    yield made
+    for c in made.values():
+        c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx(ctxs):
+    return ctxs["cluster"]
+
+
+@pytest.fixture(scope="module")
+def ctx_mc(ctxs):
+    return ctxs["multi"]
+
+
+PATHS = ["cluster", "multi"]
 
 
 def capi_mod():
@@ -50,7 +68,9 @@ SIZES = [1, 2, 3, 5, 31, 64, 127, 128, 129, 255, 256, 257, 300]
 
 
 @pytest.mark.parametrize("n", SIZES)
-def test_fp64_exact_bitwise(ctx, n):
+@pytest.mark.parametrize("path", PATHS)
+def test_fp64_exact_bitwise(ctxs, path, n):
+    ctx = ctxs[path]
     capi = capi_mod()
     u0 = wl.random_edges(n, n)
     f = wl.gaussian_source(n, n + 1) * 50 if n % 2 else None
@@ -66,7 +86,9 @@ def test_fp64_exact_bitwise(ctx, n):
 
 
 @pytest.mark.parametrize("n", SIZES)
-def test_fp64_default_within_tolerance(ctx, n):
+@pytest.mark.parametrize("path", PATHS)
+def test_fp64_default_within_tolerance(ctxs, path, n):
+    ctx = ctxs[path]
     u0 = wl.random_edges(n, 2 * n)
     f = wl.gaussian_source(n, n) * 20 if n % 3 == 0 else None
     w = oracle.omega_opt(n)
@@ -77,7 +99,9 @@ def test_fp64_default_within_tolerance(ctx, n):
 
 
 @pytest.mark.parametrize("n", SIZES)
-def test_fp32_bitwise(ctx, n):
+@pytest.mark.parametrize("path", PATHS)
+def test_fp32_bitwise(ctxs, path, n):
+    ctx = ctxs[path]
     capi = capi_mod()
     u0 = wl.random_edges(n, 3 * n)
     f = wl.gaussian_source(n, n) * 30 if n % 2 == 0 else None
@@ -102,6 +126,12 @@ def test_config1_heat_plate_converges_like_oracle(ctx):
     assert np.array_equal(got, ref["u"])
     got2, res2 = run(ctx, u0, omega=w, tol=1e-8, max_iters=5000, check_every=1)
     assert res2["converged"] and abs(res2["iterations"] - ref["iterations"]) <= 1
+    from paper_1401_0763_gb300 import capi as _c
+    with _c.Context(0) as mc:  # the multi-CTA rescaled path on the same plate
+        mc.set_option(_c.SOR_OPT_CLUSTER, 0)
+        got3, res3 = run(mc, u0, omega=w, tol=1e-8, max_iters=5000, check_every=1)
+    assert res3["converged"] and abs(res3["iterations"] - ref["iterations"]) <= 1
+    assert pins.rel_err(got3, ref["u"]) <= TOL64 * 10
     assert pins.rel_err(got2, ref["u"]) <= TOL64 * 10
 
 
@@ -117,7 +147,9 @@ def test_config1_harmonic_case(ctx):
 
 
 @pytest.mark.parametrize("K", [1, 7, 50])
-def test_check_interval_and_resid_stop(ctx, K):
+@pytest.mark.parametrize("path", PATHS)
+def test_check_interval_and_resid_stop(ctxs, path, K):
+    ctx = ctxs[path]
     capi = capi_mod()
     n = 100
     u0 = wl.random_edges(n, 5)
@@ -206,7 +238,8 @@ def test_fp64_full_size_sampled(ctx):
     (129, 1.0, 3, 90, True),       # Gauss-Seidel: alpha = 0
     (5, 1.9, 2, 31, True),
 ])
-def test_fp64_rescaled_phases(ctx, n, omega, K, iters, with_f):
+def test_fp64_rescaled_phases(ctx_mc, n, omega, K, iters, with_f):
+    ctx = ctx_mc
     w = oracle.omega_opt(n) if omega is None else omega
     u0 = wl.random_edges(n, n + K)
     f = wl.gaussian_source(n, K) * 100 if with_f else None
@@ -217,7 +250,8 @@ def test_fp64_rescaled_phases(ctx, n, omega, K, iters, with_f):
     assert res["final_maxdelta"] == pytest.approx(ref["final_maxdelta"], rel=1e-8, abs=1e-13)
 
 
-def test_fp64_rescaled_converges_like_oracle(ctx):
+def test_fp64_rescaled_converges_like_oracle(ctx_mc):
+    ctx = ctx_mc
     n = 180
     u0 = wl.random_edges(n, 44)
     w = oracle.omega_opt(n)
@@ -243,6 +277,7 @@ def ctx_depth():
         if depth not in made:
             c = capi.Context(0)
             c.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, depth)
+            c.set_option(capi.SOR_OPT_CLUSTER, 0)  # keep small grids on the fused-iteration kernel
             made[depth] = c
         return made[depth]
     yield get
@@ -332,7 +367,9 @@ def test_autotuner_picks_a_depth_and_keeps_results(tmp_path, monkeypatch):
     assert all(int(d) in (1, 2, 3, 4, 6, 8) for _, _, d in lines)
 
 
-def test_stall_window_stops_at_the_fp64_floor(ctx):
+@pytest.mark.parametrize("path", PATHS)
+def test_stall_window_stops_at_the_fp64_floor(ctxs, path):
+    ctx = ctxs[path]
     """A tolerance below what FP64 reaches: with stall_window the solve stops,
     not converged, once that many residual tests gave no new minimum -- at the
     same step as the oracle, with the same result bit for bit."""
@@ -352,3 +389,23 @@ def test_stall_window_stops_at_the_fp64_floor(ctx):
     assert not ref["converged"] and ref["iterations"] < 50000
     assert res["iterations"] == ref["iterations"] and not res["converged"]
     assert np.array_equal(got, ref["u"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 100, 255, 384])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cluster_path_converges_like_oracle(ctx, n, precision):
+    """Whole solves inside one thread-block cluster: the stop decision is taken
+    on the device after each tested iteration; results equal the oracle."""
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 5 * n + 1)
+    w = oracle.omega_opt(n)
+    f = wl.gaussian_source(n, n) * 10 if n % 2 else None
+    if precision == "fp64":
+        ref = oracle.sor_f64(u0, w, f=f, max_iters=20000, check_every=3, tol=1e-9)
+        got, res = run(ctx, u0, f, omega=w, tol=1e-9, max_iters=20000, check_every=3)
+    else:
+        ref = oracle.sor_f32(u0, w, f=f, max_iters=20000, check_every=3, tol=2e-3)
+        got, res = run(ctx, u0, f, precision=capi.SOR_FP32, omega=w, tol=2e-3, max_iters=20000, check_every=3)
+    assert res["converged"] == ref["converged"] and res["iterations"] == ref["iterations"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
