@@ -89,6 +89,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def max_over_ranks(value: float, ws: int) -> float:
+    """Largest value over the ranks of the default process group (the timing
+    rule: the slowest rank's time counts); the value itself when ws == 1."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_glups(lups_per_rank: float, ms_max: float, ws: int) -> float:
+    """Whole-job throughput: every rank solved its own plate (replicas), so
+    the work is ws * lups_per_rank over the slowest rank's time."""
+    return ws * lups_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -192,14 +210,9 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
-    ms_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, ws)
     lups_rank = float(N) * N * ITERS * args.steps
-    value = ws * lups_rank / (ms_max * 1e-3) / 1e9
+    value = aggregate_glups(lups_rank, ms_max, ws)
     launches = int(st["sweep_launches"]) + 3 * args.steps  # + pack, final residual, unpack per solve
     sweep_ms_per_launch = st["sweep_ms"] / max(1, st["timed_launches"])
     lups_per_launch = float(N) * N / 2.0  # one colour phase updates half the cells
@@ -241,13 +254,8 @@ def run_ours(args, ws, rank, local):
         step(capi.SOR_FP64, h_u0, h_out)
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max(e2.elapsed_time(e3), 1e3 * (time.perf_counter() - t0))
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": ws * lups_rank / (e2e_ms * 1e-3) / 1e9, "unit": "GLUP/s",
+    e2e_ms = max_over_ranks(max(e2.elapsed_time(e3), 1e3 * (time.perf_counter() - t0)), ws)
+    e2e = {"value": aggregate_glups(lups_rank, e2e_ms, ws), "unit": "GLUP/s",
            "h2d_bytes_per_step": int(h_u0.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)}
     assert np.isfinite(h_out.numpy()).all()
 
@@ -320,45 +328,52 @@ def workload_plate256(args, ctx, capi, wl):
 
 
 def workload_poisson4096(args, ctx, capi, wl):
-    """4098^2 Poisson, 8-Gaussian source, zero edges: FP32 sweeps + FP64 defect correction to
-    ||f-Au||/||f|| < 1e-10 versus plain FP64 SOR with the residual test every 20 iterations."""
-    import numpy as np
+    """Poisson -Laplace(u) = f with the 8-Gaussian source, zero edges: FP32 sweeps + FP64 defect correction
+    (20 sweeps per correction) versus plain FP64 SOR with the residual test every 20 iterations, to the same
+    relative residual ||f - Au|| / ||f||.  The 1e-10 target is below what an FP64 solution can reach beyond
+    N ~ 1024 (the floor grows like (N+1)^2), so the 4098^2 plate is run to 1e-7 and 1e-8 and the 1e-10 target
+    on 1026^2; both solvers stop at their floor (stall window of 50 residual tests)."""
     import torch
-    n = 4096
-    u0_np, f_np = wl.poisson_problem(n, args.seed)
-    u0 = torch.from_numpy(u0_np).cuda()
-    f = torch.from_numpy(f_np).cuda()
-    out = torch.empty_like(u0)
-    w = capi.sor_omega_opt(n)
-    runs = {"fp32_refine": dict(precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-10, max_iters=400000, inner_sweeps=20),
-            "fp64_plain": dict(precision=capi.SOR_FP64, omega=w, tol=1e-10, max_iters=400000, check_every=20,
-                               stop=capi.SOR_STOP_RESID_REL)}
+    cases = [(4096, 1e-7), (4096, 1e-8), (1024, 1e-10)]
     detail = {}
-    sol = {}
-    for name, kw in runs.items():
-        ctx.solve(u0, f, out=out, **dict(kw, max_iters=200))  # warm-up: workspace, graphs
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(max(1, args.steps // 2)):
+    exact_cache = {}
+    for n, tol in cases:
+        u0_np, f_np = wl.poisson_problem(n, args.seed)
+        u0 = torch.from_numpy(u0_np).cuda()
+        f = torch.from_numpy(f_np).cuda()
+        out = torch.empty_like(u0)
+        w = capi.sor_omega_opt(n)
+        runs = {"fp32_refine": dict(precision=capi.SOR_FP32_REFINE, omega=w, tol=tol, max_iters=400000,
+                                    inner_sweeps=20, stall_window=50),
+                "fp64_plain": dict(precision=capi.SOR_FP64, omega=w, tol=tol, max_iters=400000, check_every=20,
+                                   stop=capi.SOR_STOP_RESID_REL, stall_window=50)}
+        key = f"n{n}_tol{tol:g}"
+        detail[key] = {}
+        for name, kw in runs.items():
+            ctx.solve(u0, f, out=out, **dict(kw, max_iters=200))  # warm-up: workspace, graphs
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             _, res = ctx.solve(u0, f, out=out, **kw)
             torch.cuda.synchronize()
-            ts.append(time.perf_counter() - t0)
-        dt = min(ts)
-        sol[name] = out.cpu().numpy()
-        detail[name] = {"time_to_solution_s": dt, "sweeps": res["iterations"], "outer_steps": res["outer_steps"],
-                        "final_resid_rel": res["final_resid_rel"], "converged": res["converged"],
-                        "glups": float(n) * n * res["iterations"] / dt / 1e9}
-    if args.check:
-        from tests import pins  # the DST-I exact discrete solution (test-side mathematics)
-        exact = pins.dst_solve(u0_np, f_np)
-        for name in sol:
-            detail[name]["rel_err_vs_exact"] = pins.rel_err(sol[name], exact)
-    speed = detail["fp64_plain"]["time_to_solution_s"] / detail["fp32_refine"]["time_to_solution_s"]
-    return {"metric": "time to 1e-10 relative residual, 4098^2 Poisson (8 Gaussians)",
-            "value": detail["fp32_refine"]["time_to_solution_s"], "unit": "s", "higher_is_better": False,
-            "speedup_vs_plain_fp64": speed, "detail": detail,
-            "config": {"workload": "4098^2, zero edges, f = 8-Gaussian sum (seeded), w_opt, inner 20 FP32 sweeps"}}
+            dt = time.perf_counter() - t0
+            rec = {"time_to_solution_s": dt, "sweeps": res["iterations"], "outer_steps": res["outer_steps"],
+                   "final_resid_rel": res["final_resid_rel"], "converged": res["converged"],
+                   "glups": float(n) * n * res["iterations"] / dt / 1e9}
+            if args.check:
+                from tests import pins  # the DST-I exact discrete solution (test-side mathematics)
+                if n not in exact_cache:
+                    exact_cache[n] = pins.dst_solve(u0_np, f_np)
+                rec["rel_err_vs_exact"] = pins.rel_err(out.cpu().numpy(), exact_cache[n])
+            detail[key][name] = rec
+        r, p = detail[key]["fp32_refine"], detail[key]["fp64_plain"]
+        detail[key]["speedup_refine_vs_plain"] = p["time_to_solution_s"] / r["time_to_solution_s"]
+    head = detail["n4096_tol1e-07"]
+    return {"metric": "time to solution, 4098^2 Poisson (8 Gaussians) to relative residual 1e-7 "
+                      "(and 1e-8; 1026^2 to 1e-10)",
+            "value": head["fp32_refine"]["time_to_solution_s"], "unit": "s", "higher_is_better": False,
+            "detail": detail,
+            "config": {"workload": "zero edges, f = 8-Gaussian sum (seeded), w_opt, inner 20 FP32 sweeps, "
+                                   "stall window 50"}}
 
 
 def workload_batch512(args, ctx, capi, wl):
@@ -416,7 +431,7 @@ def workload_serve(args, ctx, capi, wl):
         if r.arrival_s > now:
             time.sleep(r.arrival_s - now)
         t, _ = ctx.submit(u0, f, out=o, precision=capi.SOR_FP32_REFINE, omega=capi.sor_omega_opt(r.n), tol=r.tol,
-                          max_iters=2000000, inner_sweeps=20)
+                          max_iters=2000000, inner_sweeps=20, stall_window=50)
         tickets.append((t, time.perf_counter() - t_start))
     lat, done_at = [], []
     for t, t_sub in tickets:
@@ -434,7 +449,7 @@ def workload_serve(args, ctx, capi, wl):
     for r, (u0, f, o) in list(zip(reqs, inputs))[:sub]:
         t0 = time.perf_counter()
         ctx.solve(u0, f, out=o, precision=capi.SOR_FP64, omega=capi.sor_omega_opt(r.n), tol=r.tol,
-                  max_iters=2000000, check_every=20, stop=capi.SOR_STOP_RESID_REL)
+                  max_iters=2000000, check_every=20, stop=capi.SOR_STOP_RESID_REL, stall_window=50)
         service.append(time.perf_counter() - t0)
     finish, lat64 = 0.0, []
     for r, sv in zip(reqs[:sub], service):
@@ -449,7 +464,36 @@ def workload_serve(args, ctx, capi, wl):
             "config": {"workload": f"{count} requests, rate {rate}/s, seed {args.seed}, budget 150 GB"}}
 
 
-WORKLOADS = {"plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
+def workload_paper(args, ctx, capi, wl):
+    """The paper's own experiment (Section 3.4, Section 4): 4096x4096 plate, north edge 1.0, the others 0,
+    w = 0.376, stop when max|change| < 1e-5 checked every K = 4000 iterations, at most 50000 iterations,
+    FP64.  Table 1's times (unnamed multicore host) are context: the speedup is reported against them."""
+    import json as _json
+    import torch
+    n = 4096
+    with open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")) as fh:
+        pc = _json.load(fh)
+    u0 = torch.from_numpy(wl.heat_plate(n, pc["north_boundary"])).cuda()
+    out = torch.empty_like(u0)
+    kw = dict(omega=pc["omega"], tol=pc["epsilon"], max_iters=pc["max_iterations"], check_every=pc["K"])
+    ctx.solve(u0, out=out, **dict(kw, max_iters=pc["K"]))  # warm-up: workspace, graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, res = ctx.solve(u0, out=out, **kw)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    table = {row["threads"]: row["time_s"] for row in pc["table1"]}
+    best = min(table[8].values())
+    return {"metric": "time to solution of the paper's 4096^2 heat plate (w = 0.376, eps = 1e-5, K = 4000)",
+            "value": dt, "unit": "s", "higher_is_better": False,
+            "detail": {"iterations": res["iterations"], "converged": res["converged"],
+                       "final_maxdelta": res["final_maxdelta"], "glups": float(n) * n * res["iterations"] / dt / 1e9,
+                       "paper_table1_best_8_threads_s": best, "speedup_vs_paper_best": best / dt,
+                       "paper_table1_serial_chapel_s": table[1]["chapel"]},
+            "config": {"workload": "4096^2 interior, north 1.0, w 0.376, eps 1e-5, K 4000, cap 50000, FP64"}}
+
+
+WORKLOADS = {"paper": workload_paper, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
              "serve": workload_serve}
 
 

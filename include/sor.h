@@ -89,8 +89,9 @@ typedef struct {
   int32_t flags;        /* SOR_FLAG_* */
   int32_t stall_window; /* > 0: residual tests only (SOR_FP32_REFINE, or SOR_STOP_RESID_REL): also
                            stop, with converged = 0, once this many residual tests in a row have
-                           not produced a new smallest residual -- the tolerance is below what
-                           FP64 can reach for this problem.  0 = off.  Must be >= 0. */
+                           not produced a new smallest residual while staying within a factor 4
+                           of it (a plateau: the tolerance is below what FP64 can reach for this
+                           problem); a test further above ends the run.  0 = off.  Must be >= 0. */
 } sor_params;
 
 typedef struct {

@@ -142,9 +142,12 @@ int oracle_sor_f64(int n, double omega, const double *u0, const double *f, int m
   int it = 0, conv = 0;
   double mk = 0.0, rho = -1.0;
   /* stall rule (residual tests only): stop without convergence once
-   * stall_window consecutive tests have not produced a new smallest rho */
+   * stall_window consecutive tests gave no new smallest rho while staying
+   * within a factor 4 of it (a plateau at the attainable floor); a test
+   * further above the smallest rho (the growth SOR shows early on) ends the
+   * run of such tests */
   double best = HUGE_VAL;
-  int tests = 0, best_test = 0;
+  int run = 0;
   for (int k = 1; k <= max_iters; ++k) {
     const double dr = phase_f64(n, u, g, omega, 0); /* red   */
     const double db = phase_f64(n, u, g, omega, 1); /* black */
@@ -159,9 +162,9 @@ int oracle_sor_f64(int n, double omega, const double *u0, const double *f, int m
         residual_f64(n, u, g, NULL, &rm, &bm);
         rho = rel(rm, bm);
         if (rho < tol) { conv = 1; break; }
-        ++tests;
-        if (rho < best) { best = rho; best_test = tests; }
-        else if (stall_window > 0 && tests - best_test >= stall_window) break;
+        if (rho < best) { best = rho; run = 0; }
+        else if (rho < 4.0 * best) { ++run; if (stall_window > 0 && run >= stall_window) break; }
+        else run = 0;
       }
     }
   }
@@ -261,7 +264,7 @@ int oracle_refine(int n, double omega, const double *u0, const double *f, int in
   const float a32 = (float)(1.0 - omega), b32 = (float)(omega / 4.0);
   int outer = 0, conv = 0;
   double rho = 0.0, best = HUGE_VAL;
-  int best_test = 0;
+  int run = 0;
   for (;;) {
     double rm, bm;
     residual_f64(n, u, g, r, &rm, &bm);
@@ -269,9 +272,10 @@ int oracle_refine(int n, double omega, const double *u0, const double *f, int in
     if (trace) trace[outer] = rho;
     if (rho < tol) { conv = 1; break; }
     if (outer == max_outer) break;
-    /* stall rule: no new smallest rho in stall_window consecutive tests */
-    if (rho < best) { best = rho; best_test = outer; }
-    else if (stall_window > 0 && outer - best_test >= stall_window) break;
+    /* stall rule, as in oracle_sor_f64 */
+    if (rho < best) { best = rho; run = 0; }
+    else if (rho < 4.0 * best) { ++run; if (stall_window > 0 && run >= stall_window) break; }
+    else run = 0;
     if (inner_f32) {
       for (size_t c = 0; c < cells; ++c) { d32[c] = 0.0f; r32[c] = (float)r[c]; }
       for (int s = 0; s < inner_sweeps; ++s) {

@@ -64,11 +64,14 @@ struct Batcher {
   int max_inner = 1;
   bool uniform_inner = true;  // every refine slot runs the same number of inner sweeps
   int tdepth = 1;             // fused iterations of the refine sweeps this step (1 = unfused)
+  size_t live_tiles = 0;      // tiles in the table at the last rebuild
+  size_t dead_tiles = 0;      // of those, tiles of slots finished since
   int dbuf_in = 0;            // buffer holding the corrections the next residual pass applies
   bool any_resid_stop = false;
   uint64_t version = 0;       // bumps when the active set changes
   uint64_t graph_version = ~0ull;
   int graph_dbuf = -1;
+  int graph_steps = 0;
   cudaGraphExec_t graph = nullptr;
   size_t reserved_tables = 0;
 };
@@ -138,6 +141,7 @@ static sor_status rebuild_tiles(Batcher* b) {
     Request* r = b->slots[s].get();
     if (!r) continue;
     const Layout& L = r->buf.L;
+    const size_t before = ref.size() + p64.size() + p32.size() + reftb.size();
     if (r->plan.kind == kRefine) {
       build_tiles(L, (int)s, &ref, nullptr);
       if (T > 1) build_tiles(L, (int)s, &reftb, nullptr, kTbRows, tb_out_cols(T));
@@ -149,8 +153,11 @@ static sor_status rebuild_tiles(Batcher* b) {
       build_tiles(L, (int)s, &p32, nullptr);
       if (r->plan.stop == kStopResid) b->any_resid_stop = true;
     }
+    r->ntiles = ref.size() + p64.size() + p32.size() + reftb.size() - before;
   }
   const size_t total = ref.size() + p64.size() + p32.size() + reftb.size();
+  b->live_tiles = total;
+  b->dead_tiles = 0;
   sor_status rs = ensure_tables(b, (int)b->slots.size(), total + 1);
   if (rs != SOR_OK) return rs;
   std::vector<Tile> all;
@@ -175,12 +182,12 @@ static sor_status rebuild_tiles(Batcher* b) {
 }
 
 // The launches of one scheduler step over every active slot.
-static sor_status enqueue_step(Batcher* b) {
+static sor_status enqueue_step(Batcher* b, int dbuf_in) {
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
   if (b->nt_refine) {
     // residual pass: applies the corrections of the previous step, tests, writes r~
-    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, b->dbuf_in, s));
+    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, dbuf_in, s));
     if (b->tdepth > 1) {
       const Tile* t = b->d_tiles + b->off_reftb;
       for (int j = 0, sw = 0; sw < b->max_inner; ++j, sw += b->tdepth) {
@@ -210,17 +217,51 @@ static sor_status enqueue_step(Batcher* b) {
   return SOR_OK;
 }
 
-static sor_status run_step(Batcher* b) {
+// Buffer the next residual pass reads the corrections from, after a step
+// whose sweeps ran with depth b->tdepth.
+static int step_dbuf_out(const Batcher* b) {
+  Plan q;
+  q.kind = kRefine;
+  q.inner = b->max_inner;
+  q.tdepth = b->tdepth;
+  return refine_dbuf(q);
+}
+
+// Steps replayed per host round trip: with little work active a step is a few
+// short launches, so several of them go into one graph (slots that finish
+// mid-way skip the rest on the device) and the host polls less often.
+static int steps_per_round(const Batcher* b) {
+  double cells = 0.0, sweeps = 0.0;
+  for (const auto& r : b->slots)
+    if (r) {
+      cells += (double)r->plan.n * r->plan.n;
+      sweeps = std::max(sweeps, (double)(r->plan.kind == kRefine ? r->plan.inner : kPlainStepIters));
+    }
+  const double step_s = cells * sweeps / 4.0e11 + 40e-6;  // rough cost of one step
+  return (int)std::max(1.0, std::min(16.0, std::floor(400e-6 / step_s)));
+}
+
+static sor_status run_step(Batcher* b, int* steps_out) {
   Ctx* c = b->c;
-  if (!c->opt_graphs.load()) return enqueue_step(b);
-  if (b->graph_version != b->version || !b->graph || b->graph_dbuf != b->dbuf_in) {
+  const int m = steps_per_round(b);
+  *steps_out = m;
+  const int dbuf_next = step_dbuf_out(b);
+  if (!c->opt_graphs.load()) {
+    for (int k = 0; k < m; ++k) {
+      sor_status rs = enqueue_step(b, k == 0 ? b->dbuf_in : dbuf_next);
+      if (rs != SOR_OK) return rs;
+    }
+    return SOR_OK;
+  }
+  if (b->graph_version != b->version || !b->graph || b->graph_dbuf != b->dbuf_in || b->graph_steps != m) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
     }
     cudaGraph_t g = nullptr;
     SOR_BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    sor_status rs = enqueue_step(b);
+    sor_status rs = SOR_OK;
+    for (int k = 0; k < m && rs == SOR_OK; ++k) rs = enqueue_step(b, k == 0 ? b->dbuf_in : dbuf_next);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rs != SOR_OK) {
       if (g) cudaGraphDestroy(g);
@@ -232,20 +273,12 @@ static sor_status run_step(Batcher* b) {
     SOR_BCK(e);
     b->graph_version = b->version;
     b->graph_dbuf = b->dbuf_in;
+    b->graph_steps = m;
   }
   SOR_BCK(cudaGraphLaunch(b->graph, b->stream));
   return SOR_OK;
 }
 
-// Buffer the next residual pass reads the corrections from, after a step
-// whose sweeps ran with depth b->tdepth.
-static int step_dbuf_out(const Batcher* b) {
-  Plan q;
-  q.kind = kRefine;
-  q.inner = b->max_inner;
-  q.tdepth = b->tdepth;
-  return refine_dbuf(q);
-}
 
 static size_t request_bytes(const Plan& p) {
   const size_t stage = (size_t)(p.n + 2) * (p.n + 2) * 8 + (p.has_f ? (size_t)p.n * p.n * 8 : 0);
@@ -472,20 +505,17 @@ static void scheduler_main(Batcher* b) {
     }
     if (rs == SOR_OK && !admitted.empty()) rs = rebuild_tiles(b);
     if (rs == SOR_OK && active_count(b) > 0) {
-      rs = run_step(b);
+      int steps = 1;
+      rs = run_step(b, &steps);
       b->dbuf_in = step_dbuf_out(b);
     }
-    if (rs == SOR_OK) {
-      for (size_t k = 0; k < b->slots.size(); ++k)
-        if (b->slots[k]) {
-          cudaError_t e =
-              cudaMemcpyAsync(&b->h_state[k], b->d_state + k, sizeof(SlotState), cudaMemcpyDeviceToHost, b->stream);
-          if (e != cudaSuccess) {
-            c->set_error(cudaGetErrorString(e));
-            rs = SOR_ERR_CUDA;
-            break;
-          }
-        }
+    if (rs == SOR_OK) {  // one copy of the whole state table
+      cudaError_t e = cudaMemcpyAsync(b->h_state, b->d_state, sizeof(SlotState) * b->slots.size(),
+                                      cudaMemcpyDeviceToHost, b->stream);
+      if (e != cudaSuccess) {
+        c->set_error(cudaGetErrorString(e));
+        rs = SOR_ERR_CUDA;
+      }
     }
     if (rs == SOR_OK) {
       cudaError_t e = cudaStreamSynchronize(b->stream);
@@ -499,8 +529,12 @@ static void scheduler_main(Batcher* b) {
       for (size_t k = 0; k < b->slots.size(); ++k)
         if (b->slots[k] && b->h_state[k].done) fin.push_back((int)k);
       if (!fin.empty()) {
+        for (int k : fin) b->dead_tiles += b->slots[k]->ntiles;
         rs = retire(b, fin);
-        if (rs == SOR_OK) rs = rebuild_tiles(b);
+        // finished slots' tiles stay in the table (their state says done, so
+        // every kernel skips them) until admissions rebuild it anyway or they
+        // are a sizeable share of the launches
+        if (rs == SOR_OK && b->dead_tiles * 10 > b->live_tiles * 3) rs = rebuild_tiles(b);
       }
     }
     if (rs != SOR_OK) {

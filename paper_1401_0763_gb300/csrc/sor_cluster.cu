@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
   const int r_first = max(rlo, 1), r_last = min(rhi, n + 1);  // interior rows held here: [r_first, r_last)
   const int cells = max(0, r_last - r_first) * qc;
   const double bmax = bits_to_double(st->bmax_bits);
-  int k = st->iters, converged = 0, tests = st->tests, best_test = st->best_test;
+  int k = st->iters, converged = 0, run = st->stall_run;
   double best_rho = st->best_rho, last_dmax = st->last_dmax, last_rho = st->last_rho;
   int checked = st->checked_iter;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -152,12 +152,14 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
         converged = 1;
         break;
       }
-      tests += 1;
       if (rho < best_rho) {
         best_rho = rho;
-        best_test = tests;
-      } else if (sd.stall > 0 && tests - best_test >= sd.stall) {
-        break;
+        run = 0;
+      } else if (rho < 4.0 * best_rho) {
+        run += 1;
+        if (sd.stall > 0 && run >= sd.stall) break;
+      } else {
+        run = 0;
       }
     }
   }
@@ -175,8 +177,7 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
     st->last_dmax = last_dmax;
     st->last_rho = last_rho;
     st->checked_iter = checked;
-    st->tests = tests;
-    st->best_test = best_test;
+    st->stall_run = run;
     st->best_rho = best_rho;
   }
   cluster.sync();  // no CTA leaves while others may still read its shared memory

@@ -87,8 +87,8 @@ struct SlotState {
   int ubuf;                      // buffer of u holding the current solution (refine)
   int checked_iter;              // iteration of the last residual test
   int error;                     // nonzero: device-side consistency failure
-  int tests;                     // residual tests done (plain residual stop)
-  int best_test;                 // test (plain) or correction count (refine) of the smallest rho so far
+  int stall_run;                 // residual tests in a row without a new minimum, within 4x of it
+  int reserved_;
   double best_rho;               // smallest rho so far (+inf before the first test)
   double last_dmax;              // m_k of the last iteration that measured it (-1 if none)
   double last_rho;               // relative residual of the last residual pass (-1 if none)

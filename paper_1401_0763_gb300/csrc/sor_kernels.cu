@@ -674,11 +674,21 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // One colour phase on the staged tile: rows [r0, r1) of the staged arrays
 // for this warp.  LASTM: this phase belongs to a measured iteration, track
 // max |change| over the tile's output cells.
+// Right-hand-side values of staged row r (global row i) for this lane, copied
+// asynchronously into the warp's buffer (nothing for rows or lanes without
+// interior cells); one commit per row either way.
+__device__ __forceinline__ void tb_g_issue(float* gslot, const float* __restrict__ Gc, int i, int qf, int n, int pitch,
+                                           int colour, int lane) {
+  const int s = (i + colour) & 1;
+  if (i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1)) cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
+  asm volatile("cp.async.commit_group;\n" ::);
+}
+
 template <int T, bool LASTM>
 __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
                                          const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
                                          int r1, int n, int pitch, int out_rows, int lane, float a, float b,
-                                         unsigned& dm32) {
+                                         unsigned& dm32, float* gbuf /* [2][128] for this warp */) {
   using Gm = TbGeom<T>;
   if (r0 >= r1) return;
   const int col = 4 * lane;
@@ -686,7 +696,16 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
   float om[4], oc[4];
   load4(So + (r0 - 1) * Gm::C + col, om);
   load4(So + r0 * Gm::C + col, oc);
+  if (Gc) tb_g_issue(gbuf, Gc, base_r + r0, qf, n, pitch, colour, lane);  // one row ahead
   for (int r = r0; r < r1; ++r) {
+    if (Gc) {
+      if (r + 1 < r1) {
+        tb_g_issue(gbuf + ((r + 1 - r0) & 1) * Gm::C, Gc, base_r + r + 1, qf, n, pitch, colour, lane);
+        asm volatile("cp.async.wait_group 1;\n" ::);
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+      }
+    }
     float op[4];
     load4(So + (r + 1) * Gm::C + col, op);
     const float left = __shfl_up_sync(0xffffffffu, oc[3], 1);
@@ -699,7 +718,7 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
       float own[4], gv[4];
       load4(Sc + r * Gm::C + col, own);
       if (Gc && any) {
-        load4(Gc + (size_t)i * pitch + qf + kOff, gv);
+        load4(gbuf + ((r - r0) & 1) * Gm::C + col, gv);
       } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
@@ -750,6 +769,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
   float* const S1 = tb_smem + Gm::R * Gm::C;
   __shared__ unsigned long long red[kWarps];
   __shared__ int ctl[5];  // skip, nt, k_end, measure, src
+  __shared__ __align__(16) float gbufs[kWarps][2][Gm::C];  // right-hand-side rows, double-buffered per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
@@ -812,16 +832,16 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
       const bool lastm = (MODE == 0) && measure && it == nt - 1;
       if (lastm) {
         tb_phase<T, true>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
-                          dm32);
+                          dm32, &gbufs[warp][0][0]);
         __syncthreads();
         tb_phase<T, true>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
-                          dm32);
+                          dm32, &gbufs[warp][0][0]);
       } else {
         tb_phase<T, false>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
-                           b, dm32);
+                           b, dm32, &gbufs[warp][0][0]);
         __syncthreads();
         tb_phase<T, false>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
-                           b, dm32);
+                           b, dm32, &gbufs[warp][0][0]);
       }
       __syncthreads();
     }
@@ -917,9 +937,59 @@ __device__ __forceinline__ double load_u1(const T* X, const float* D, size_t e) 
   return D ? __dadd_rn((double)X[e], (double)D[e]) : (double)X[e];
 }
 
+// Defect correction, first half of a correction step: u += (double)d over the
+// interior of every pending refine slot (d from buffer dbuf of x), in place.
+// Elementwise, so the residual pass that follows reads corrected values
+// without recomputing them for each of a cell's four neighbours.
+__global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                      const Tile* __restrict__ tiles, int ntiles, int dbuf) {
+  __shared__ int ctl[2];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const SlotDesc& sd = slots[tl.slot];
+    SlotState* st = states + tl.slot;
+    if (threadIdx.x == 0) {
+      ctl[0] = *((volatile int*)&st->done) || *((volatile int*)&st->checked_iter) < 0;  // nothing pending
+      ctl[1] = *((volatile int*)&st->ubuf);
+    }
+    __syncthreads();
+    const int skip = ctl[0], ubuf = ctl[1];
+    __syncthreads();
+    if (skip) continue;
+    const int pitch = sd.pitch, n = sd.n;
+    const int q0 = tl.col0 + lane * kVec;
+    const int rows_per_warp = (tl.nrows + kWarpsY - 1) / kWarpsY;
+    const int i0 = tl.row0 + wy * rows_per_warp;
+    const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
+    for (int i = i0; i < i1; ++i) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int qlim = (n + ((i + c) & 1)) >> 1;
+        if (q0 > qlim) continue;
+        double* U = sd.u[ubuf][c] + eidx(i, q0, pitch);
+        const float* D = (const float*)sd.x[dbuf][c] + eidx(i, q0, pitch);
+        double u[4];
+        float d[4];
+        load4(U, u);
+        load4(D, d);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) u[v] = __dadd_rn(u[v], (double)d[v]);
+        if (q0 + 3 <= qlim) {
+          store4(U, u);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (q0 + v <= qlim) U[v] = u[v];
+        }
+      }
+    }
+  }
+}
+
 // ROLE kResidFinal / kResidCheck: plain slots, iterate x[xbuf] (type T).
-// ROLE kResidRefine: refine slots; u[ubuf] (+ d from x[0] unless this is the
-// first pass) -> u[ubuf^1], r~ rounded to FP32 into g[c].
+// ROLE kResidRefine: refine slots; residual of u[ubuf] (already corrected by
+// k_correct), r~ rounded to FP32 into g[c]; counts the correction.
 template <typename T, int ROLE>
 __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__ slots, SlotState* states,
                                                     const Tile* __restrict__ tiles, int ntiles, int dbuf) {
@@ -963,12 +1033,6 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
     if (ROLE == kResidRefine) {
       X0 = (const T*)sd.u[c.xbuf][0];
       X1 = (const T*)sd.u[c.xbuf][1];
-      if (c.measure) {  // apply the pending correction
-        D0 = (const float*)sd.x[dbuf][0];
-        D1 = (const float*)sd.x[dbuf][1];
-        W0 = sd.u[c.xbuf ^ 1][0];
-        W1 = sd.u[c.xbuf ^ 1][1];
-      }
     } else {
       X0 = (const T*)sd.x[c.xbuf][0];
       X1 = (const T*)sd.x[c.xbuf][1];
@@ -1059,18 +1123,17 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
           if (rho < sd.tol) {
             st->converged = 1;
             st->done = 1;
+          } else if (rho < st->best_rho) {
+            st->best_rho = rho;
+            st->stall_run = 0;
+          } else if (rho < 4.0 * st->best_rho) {  // a plateau near the smallest residual so far
+            st->stall_run += 1;
+            if (sd.stall > 0 && st->stall_run >= sd.stall) st->done = 1;  // the floor: tol is out of reach
           } else {
-            st->tests += 1;
-            if (rho < st->best_rho) {
-              st->best_rho = rho;
-              st->best_test = st->tests;
-            } else if (sd.stall > 0 && st->tests - st->best_test >= sd.stall) {
-              st->done = 1;  // no new smallest residual in sd.stall tests: below the reachable floor
-            }
+            st->stall_run = 0;  // far above it: still the early growth, not a plateau
           }
         } else if (ROLE == kResidRefine) {
-          if (c.measure) {
-            st->ubuf = c.xbuf ^ 1;
+          if (c.measure) {  // the correction k_correct applied counts now
             st->outer += 1;
             st->iters += sd.inner;
           }
@@ -1082,9 +1145,12 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
             st->done = 1;
           } else if (rho < st->best_rho) {
             st->best_rho = rho;
-            st->best_test = st->outer;
-          } else if (sd.stall > 0 && st->outer - st->best_test >= sd.stall) {
-            st->done = 1;
+            st->stall_run = 0;
+          } else if (rho < 4.0 * st->best_rho) {
+            st->stall_run += 1;
+            if (sd.stall > 0 && st->stall_run >= sd.stall) st->done = 1;
+          } else {
+            st->stall_run = 0;
           }
         }
       }
@@ -1223,6 +1289,11 @@ cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* state
                          int grid, int dbuf, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
+  if (kind == kResidRefine64) {  // u += d first (nothing when no correction is pending)
+    k_correct<<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   switch (kind) {
     case kResidFinal64:
       k_resid<double, kResidFinal><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);

@@ -95,6 +95,7 @@ struct Request {
   double t_submit = 0.0;
   // filled while active
   int slot = -1;
+  size_t ntiles = 0;  // tiles of this request in the batch tile table
   SlotBuffers buf;
   double* d_stage = nullptr;  // natural staging for inputs / output
   size_t stage_bytes = 0;
