@@ -409,19 +409,29 @@ __device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, Fa
 #pragma unroll
     for (int v = 0; v < 4; ++v) op[v] = __dmul_rn(op[v], ph.bscale);
   } else if (EDGE) {
-    scale_ring4(op, i + 1, q0, n, ocol, ph.bscale, true);
+    // the only ring value of row i+1 an interior cell reads is the east ring
+    // cell q = lim + 1 (q >= 1 holds in every strip); one multiply per lane
+    const int vr = ((n + (((i + 1) + ocol) & 1)) >> 1) + 1 - q0;
+    double x = vr <= 0 ? op[0] : vr == 1 ? op[1] : vr == 2 ? op[2] : op[3];
+    x = __dmul_rn(x, ph.bscale);
+    if (vr == 0) op[0] = x;
+    else if (vr == 1) op[1] = x;
+    else if (vr == 2) op[2] = x;
+    else if (vr == 3) op[3] = x;
   }
   load4(st->own + lane * kVec, own);
   if (HAS_G) load4(st->g + lane * kVec, gv);
   double left = __shfl_up_sync(0xffffffffu, w.oc[3], 1);
   double right = __shfl_down_sync(0xffffffffu, w.oc[0], 1);
-  if (lane == 0) {
-    left = st->edge[0];
-    if (EDGE) left = scale_ring1(left, i, q0 - 1, n, ocol, ph.bscale);
-  }
-  if (lane == 31) {
-    right = st->edge[1];
-    if (EDGE) right = scale_ring1(right, i, q0 + kVec, n, ocol, ph.bscale);
+  if (lane == 0) left = st->edge[0];
+  if (lane == 31) right = st->edge[1];
+  if (EDGE) {  // strip-edge scalars of row i (lane 0: west, lane 31: east), one multiply for both
+    const int lim = (n + ((i + ocol) & 1)) >> 1;
+    const bool ring_l = lane == 0 && (q0 - 1 < 1 || q0 - 1 > lim);
+    const bool ring_r = lane == 31 && (q0 + kVec < 1 || q0 + kVec > lim);
+    const double e = __dmul_rn(lane == 0 ? left : right, ph.bscale);
+    if (ring_l) left = e;
+    if (ring_r) right = e;
   }
   double W[4], E[4];
   if (S == 0) {
