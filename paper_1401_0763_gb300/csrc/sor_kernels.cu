@@ -327,13 +327,17 @@ struct FastWalk {
 };
 
 // Rows are staged through shared memory by asynchronous copies issued
-// kFastStages - 1 rows ahead (a per-warp pipeline), so the loads' latency
-// leaves the critical path without holding registers.  A stage holds, for
-// row i: the neighbour-colour row i+1, the own row i, the source row i and the
-// two strip-edge neighbours O[i][q0-1] (lane 0) and O[i][q0+4] (lane 31).
-// Each lane reads back only what it copied itself, so the pipeline needs no
-// synchronisation beyond each thread's own wait_group.
-constexpr int kFastStages = 4;
+// kFastAhead rows ahead (a per-warp pipeline), so the loads' latency leaves
+// the critical path without holding registers.  A stage holds, for row i: the
+// neighbour-colour row i+1, the own row i, the source row i and the two
+// strip-edge neighbours O[i][q0-1] (lane 0) and O[i][q0+4] (lane 31).  Each
+// lane reads back only what it copied itself, so the pipeline needs no
+// synchronisation beyond each thread's own wait_group.  A buffer is refilled
+// kFastStages - kFastAhead = 2 rows after it was read: by then every value
+// read from it has fed an instruction that already issued, so the refill
+// cannot overtake the read.
+constexpr int kFastStages = 6;
+constexpr int kFastAhead = 4;
 
 template <bool HAS_G>
 struct FastStage {
@@ -348,85 +352,98 @@ constexpr size_t fast_smem_bytes() {
   return (size_t)kWarpsY * kFastStages * sizeof(FastStage<HAS_G>);
 }
 
-__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gsrc) {
+// 16-byte asynchronous copy; nbytes 0 copies nothing and zero-fills.
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gsrc, int nbytes) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gsrc));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gsrc), "r"(nbytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_8(void* smem_dst, const void* gsrc) {
+// 8-byte asynchronous copy by the lanes with pred set (nbytes as above).
+__device__ __forceinline__ void cp_async_8_if(void* smem_dst, const void* gsrc, int nbytes, bool pred) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(saddr), "l"(gsrc));
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p cp.async.ca.shared.global [%0], [%1], 8, %2;\n}\n" ::"r"(saddr),
+      "l"(gsrc), "r"(nbytes), "r"((int)pred)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Issue the copies of row i into a stage (nothing when !valid) and close the
-// group either way, so every row accounts for exactly one group.
+// Issue the copies of row i into a stage (zero-fill, no global read, when
+// !valid) and close the group, so every row accounts for exactly one group.
 template <bool HAS_G>
 __device__ __forceinline__ void fast_issue(FastStage<HAS_G>* st, int i, bool valid, const double* __restrict__ O,
                                            const double* __restrict__ X, const double* __restrict__ G, int pitch,
                                            int q0, int lane) {
-  if (valid) {
-    const double* o = O + eidx(i + 1, q0, pitch);
-    const double* x = X + eidx(i, q0, pitch);
-    cp_async_16(st->op + lane * kVec, o);
-    cp_async_16(st->op + lane * kVec + 2, o + 2);
-    cp_async_16(st->own + lane * kVec, x);
-    cp_async_16(st->own + lane * kVec + 2, x + 2);
-    if (HAS_G) {
-      const double* gp = G + eidx(i, q0, pitch);
-      cp_async_16(st->g + lane * kVec, gp);
-      cp_async_16(st->g + lane * kVec + 2, gp + 2);
-    }
-    if (lane == 0) cp_async_8(&st->edge[0], O + eidx(i, q0 - 1, pitch));
-    if (lane == 31) cp_async_8(&st->edge[1], O + eidx(i, q0 + kVec, pitch));
+  const int nb = valid ? 16 : 0;
+  const double* o = valid ? O + eidx(i + 1, q0, pitch) : O;
+  const double* x = valid ? X + eidx(i, q0, pitch) : X;
+  cp_async_16(st->op + lane * kVec, o, nb);
+  cp_async_16(st->op + lane * kVec + 2, o + 2, nb);
+  cp_async_16(st->own + lane * kVec, x, nb);
+  cp_async_16(st->own + lane * kVec + 2, x + 2, nb);
+  if (HAS_G) {
+    const double* gp = valid ? G + eidx(i, q0, pitch) : G;
+    cp_async_16(st->g + lane * kVec, gp, nb);
+    cp_async_16(st->g + lane * kVec + 2, gp + 2, nb);
   }
+  const bool right = lane == 31;
+  const double* e = valid ? O + eidx(i, right ? q0 + kVec : q0 - 1, pitch) : O;
+  cp_async_8_if(&st->edge[right ? 1 : 0], e, valid ? 8 : 0, lane == 0 || right);
   cp_async_commit();
 }
 
-// One row of a strip.  S = (i + colour) & 1 is known at compile time, which
-// fixes where W / E come from and how the upper-left pair sum of this row is
-// obtained from the previous row's lower-right ones: S == 0 -> the same
-// columns; S == 1 -> one column to the left (a shuffle; lane 0 forms the
-// strip-edge pair itself).  FIRST: no previous row, form the pair directly.
-// EDGE: this strip touches the first or last packed column, so Dirichlet ring
-// values may be among the loaded neighbours and are rescaled by ph.bscale.
+// One staged row as this lane reads it back.
+struct FastIn {
+  double op[4], own[4], g[4], el, er;
+};
+
+template <bool HAS_G>
+__device__ __forceinline__ void fast_read(const FastStage<HAS_G>* st, int lane, FastIn& r) {
+  load4(st->op + lane * kVec, r.op);
+  load4(st->own + lane * kVec, r.own);
+  if (HAS_G) load4(st->g + lane * kVec, r.g);
+  r.el = st->edge[0];
+  r.er = st->edge[1];
+}
+
+// EDGE strips: the only ring value of row i+1 an interior cell of row i reads
+// is the east ring cell q = qlim_i + 1 (q >= 1 holds in every strip), where
+// qlim_i is this row's own interior limit; one multiply per lane.
+template <int S>
+__device__ __forceinline__ void fast_scale_east(double (&op)[4], int n, int q0, double bs) {
+  const int vr = ((n + S) >> 1) + 1 - q0;
+  double x = vr <= 0 ? op[0] : vr == 1 ? op[1] : vr == 2 ? op[2] : op[3];
+  x = __dmul_rn(x, bs);
+  if (vr == 0) op[0] = x;
+  else if (vr == 1) op[1] = x;
+  else if (vr == 2) op[2] = x;
+  else if (vr == 3) op[3] = x;
+}
+
+// The cells of one row (parity S = (i + colour) & 1, known at compile time,
+// which fixes where W / E come from and how the upper-left pair sums follow
+// from the previous row's lower-right ones: S == 0 -> the same columns;
+// S == 1 -> one column to the left, a shuffle, lane 0 forming the strip-edge
+// pair itself).  om / oc: neighbour-colour rows i-1 / i; dlp: lower-right pair
+// sums of row i-1; op: neighbour-colour row i+1 (ring values already scaled).
+// FIRST: no previous row, form the upper-left pairs directly.  EDGE: the
+// strip touches the first or last packed column, so the strip-edge scalars may
+// be Dirichlet ring values, rescaled by ph.bscale.  Pure register work: the
+// caller loads and stores, so two rows can be scheduled together.
 template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST>
-__device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, FastStage<HAS_G>* stages, int i0,
-                                         int i1, const double* __restrict__ O, double* __restrict__ X,
-                                         const double* __restrict__ G, int pitch, int n, int ocol, int q0, int lane,
-                                         const FastPhase& ph, unsigned long long& dm) {
-  // keep the pipeline kFastStages - 1 rows ahead, then wait for this row
-  const int ahead = i + kFastStages - 1;
-  fast_issue<HAS_G>(stages + ((ahead - i0) & (kFastStages - 1)), ahead, ahead < i1, O, X, G, pitch, q0, lane);
-  cp_async_wait<kFastStages - 1>();
-  const FastStage<HAS_G>* st = stages + ((i - i0) & (kFastStages - 1));
-  double op[4], own[4], gv[4];
-  load4(st->op + lane * kVec, op);
-  if (ring_below) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) op[v] = __dmul_rn(op[v], ph.bscale);
-  } else if (EDGE) {
-    // the only ring value of row i+1 an interior cell reads is the east ring
-    // cell q = lim + 1 (q >= 1 holds in every strip); one multiply per lane
-    const int vr = ((n + (((i + 1) + ocol) & 1)) >> 1) + 1 - q0;
-    double x = vr <= 0 ? op[0] : vr == 1 ? op[1] : vr == 2 ? op[2] : op[3];
-    x = __dmul_rn(x, ph.bscale);
-    if (vr == 0) op[0] = x;
-    else if (vr == 1) op[1] = x;
-    else if (vr == 2) op[2] = x;
-    else if (vr == 3) op[3] = x;
-  }
-  load4(st->own + lane * kVec, own);
-  if (HAS_G) load4(st->g + lane * kVec, gv);
-  double left = __shfl_up_sync(0xffffffffu, w.oc[3], 1);
-  double right = __shfl_down_sync(0xffffffffu, w.oc[0], 1);
-  if (lane == 0) left = st->edge[0];
-  if (lane == 31) right = st->edge[1];
-  if (EDGE) {  // strip-edge scalars of row i (lane 0: west, lane 31: east), one multiply for both
-    const int lim = (n + ((i + ocol) & 1)) >> 1;
+__device__ __forceinline__ void fast_cells(const double (&om)[4], const double (&oc)[4], const double (&dlp)[4],
+                                           const double (&op)[4], const FastIn& in, int n, int q0, int lane,
+                                           const FastPhase& ph, double (&nv)[4], double (&DL)[4],
+                                           unsigned long long& dm) {
+  double left = __shfl_up_sync(0xffffffffu, oc[3], 1);
+  double right = __shfl_down_sync(0xffffffffu, oc[0], 1);
+  if (lane == 0) left = in.el;
+  if (lane == 31) right = in.er;
+  if (EDGE) {  // strip-edge scalars (lane 0: west, lane 31: east), one multiply for both
+    const int lim = (n + (1 - S)) >> 1;  // neighbour-colour interior limit of row i
     const bool ring_l = lane == 0 && (q0 - 1 < 1 || q0 - 1 > lim);
     const bool ring_r = lane == 31 && (q0 + kVec < 1 || q0 + kVec > lim);
     const double e = __dmul_rn(lane == 0 ? left : right, ph.bscale);
@@ -435,67 +452,152 @@ __device__ __forceinline__ void fast_row(FastWalk& w, int i, bool ring_below, Fa
   }
   double W[4], E[4];
   if (S == 0) {
-    W[0] = w.oc[0]; W[1] = w.oc[1]; W[2] = w.oc[2]; W[3] = w.oc[3];
-    E[0] = w.oc[1]; E[1] = w.oc[2]; E[2] = w.oc[3]; E[3] = right;
+    W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+    E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
   } else {
-    W[0] = left; W[1] = w.oc[0]; W[2] = w.oc[1]; W[3] = w.oc[2];
-    E[0] = w.oc[0]; E[1] = w.oc[1]; E[2] = w.oc[2]; E[3] = w.oc[3];
+    W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+    E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
   }
-  double DL[4], DU[4];
+  double DU[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) DL[v] = __dadd_rn(E[v], op[v]);
   if (FIRST) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(w.om[v], W[v]);
+    for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(om[v], W[v]);
   } else if (S == 0) {  // previous row had s = 1: same columns
 #pragma unroll
-    for (int v = 0; v < 4; ++v) DU[v] = w.dlp[v];
+    for (int v = 0; v < 4; ++v) DU[v] = dlp[v];
   } else {  // previous row had s = 0: one column to the left
-    double d0 = __shfl_up_sync(0xffffffffu, w.dlp[3], 1);
-    if (lane == 0) d0 = __dadd_rn(w.om[0], left);
-    DU[0] = d0; DU[1] = w.dlp[0]; DU[2] = w.dlp[1]; DU[3] = w.dlp[2];
+    double d0 = __shfl_up_sync(0xffffffffu, dlp[3], 1);
+    if (lane == 0) d0 = __dadd_rn(om[0], left);
+    DU[0] = d0; DU[1] = dlp[0]; DU[2] = dlp[1]; DU[3] = dlp[2];
   }
   const int qlim = (n + S) >> 1;
-  double nv[4];
-  bool all_in = true;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const double sum = __dadd_rn(DU[v], DL[v]);
     double t2;
     if (UNIT_BETA)
-      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], sum) : sum;
+      t2 = HAS_G ? __fma_rn(ph.gamma, in.g[v], sum) : sum;
     else
-      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
-    const double nu = __fma_rn(ph.alpha, own[v], t2);
-    const bool in = (q0 + v) <= qlim;
-    all_in = all_in && in;
-    nv[v] = in ? nu : own[v];
-    if (MEASURE && in) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
+      t2 = HAS_G ? __fma_rn(ph.gamma, in.g[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
+    const double nu = __fma_rn(ph.alpha, in.own[v], t2);
+    const bool inside = (q0 + v) <= qlim;
+    // cells past the interior (the ring cell, padding) keep their value; the
+    // whole vector is written back, so no other lane's or warp's cell is touched
+    nv[v] = inside ? nu : in.own[v];
+    if (MEASURE && inside) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, in.own[v], nu)));
   }
-  if (all_in) {
-    store4(X + eidx(i, q0, pitch), nv);
-  } else {
+}
+
+__device__ __forceinline__ int wrap_stage(int b) { return b >= kFastStages ? b - kFastStages : b; }
+
+// One row i in buffer b; RB: row n, the south ring below it is rescaled.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST, bool RB>
+__device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
+                                           const double* __restrict__ O, double* __restrict__ X,
+                                           const double* __restrict__ G, int pitch, int n, int q0, int lane,
+                                           const FastPhase& ph, unsigned long long& dm) {
+  cp_async_wait<kFastAhead - 1>();  // rows up to i + 3 are in flight: row i has landed
+  FastIn a;
+  fast_read<HAS_G>(stages + b, lane, a);
+  if (RB) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      if ((q0 + v) <= qlim) X[eidx(i, q0 + v, pitch)] = nv[v];
+    for (int v = 0; v < 4; ++v) a.op[v] = __dmul_rn(a.op[v], ph.bscale);
+  } else if (EDGE) {
+    fast_scale_east<S>(a.op, n, q0, ph.bscale);
   }
+  double nv[4], DL[4];
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm);
+  fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
+                    lane);
+  store4(X + eidx(i, q0, pitch), nv);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     w.dlp[v] = DL[v];
     w.om[v] = w.oc[v];
-    w.oc[v] = op[v];
+    w.oc[v] = a.op[v];
+  }
+  b = wrap_stage(b + 1);
+}
+
+// Rows i (parity S) and i + 1 (parity 1 - S), neither of them row n with a
+// rescaled ring below; both rows' arithmetic is independent enough to be
+// interleaved, which doubles the FP64 work in flight per warp.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S>
+__device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
+                                           const double* __restrict__ O, double* __restrict__ X,
+                                           const double* __restrict__ G, int pitch, int n, int q0, int lane,
+                                           const FastPhase& ph, unsigned long long& dm) {
+  cp_async_wait<kFastAhead - 2>();  // rows i and i + 1 have landed
+  FastIn a, c;
+  fast_read<HAS_G>(stages + b, lane, a);
+  fast_read<HAS_G>(stages + wrap_stage(b + 1), lane, c);
+  if (EDGE) {
+    fast_scale_east<S>(a.op, n, q0, ph.bscale);
+    fast_scale_east<1 - S>(c.op, n, q0, ph.bscale);
+  }
+  double nva[4], DLa[4], nvc[4], DLc[4];
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm);
+  fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
+                    lane);
+  fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead + 1), i + kFastAhead + 1, i + kFastAhead + 1 < i1, O, X, G,
+                    pitch, q0, lane);
+  store4(X + eidx(i, q0, pitch), nva);
+  store4(X + eidx(i + 1, q0, pitch), nvc);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    w.dlp[v] = DLc[v];
+    w.om[v] = a.op[v];
+    w.oc[v] = c.op[v];
+  }
+  b = wrap_stage(b + 2);
+}
+
+// Rows [i0, i1) of one strip: the first row, then pairs (whose first row has
+// the parity of i0 + 1, fixed at compile time), an odd row left over, and the
+// last grid row on its own when the south ring below it needs rescaling.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S0>
+__device__ __forceinline__ void fast_rows(FastWalk& w, FastStage<HAS_G>* stages, const double* __restrict__ O,
+                                          double* __restrict__ X, const double* __restrict__ G, int pitch, int n,
+                                          int q0, int i0, int i1, int iend, int lane, const FastPhase& ph,
+                                          unsigned long long& dm) {
+  int i = i0, b = 0;
+  if (i < iend) {
+    fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, true, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
+                                                                 ph, dm);
+    ++i;
+    for (; i + 1 < iend; i += 2)
+      fast_step2<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
+    if (i < iend) {
+      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0, false, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0,
+                                                                        lane, ph, dm);
+      ++i;
+    }
+  }
+  if (i < i1) {  // row n with the south ring below (only when rescaling); its parity is that of i - i0
+    const bool first = i == i0;
+    const bool same = ((i - i0) & 1) == 0;
+    if (first)
+      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, true, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
+                                                                  ph, dm);
+    else if (same)
+      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, false, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
+                                                                   ph, dm);
+    else
+      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0, false, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0,
+                                                                       lane, ph, dm);
   }
 }
 
-// Rows [i0, i1) of one strip; rows alternate parity, so the body is unrolled
-// by two with the parity of each half fixed at compile time.
 template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE>
 __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages, const double* __restrict__ O,
                                                         double* __restrict__ X, const double* __restrict__ G,
                                                         int pitch, int n, int colour, int q0, int i0, int i1,
                                                         int lane, const FastPhase& ph, bool rescale) {
   const int ocol = colour ^ 1;
-  for (int k = 0; k < kFastStages - 1; ++k)  // prologue: rows i0 .. i0 + kFastStages - 2
+  for (int k = 0; k < kFastAhead; ++k)  // prologue: rows i0 .. i0 + kFastAhead - 1 into buffers 0 ..
     fast_issue<HAS_G>(stages + k, i0 + k, i0 + k < i1, O, X, G, pitch, q0, lane);
   FastWalk w;
   load4(O + eidx(i0 - 1, q0, pitch), w.om);
@@ -504,56 +606,15 @@ __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages
     scale_ring4(w.om, i0 - 1, q0, n, ocol, ph.bscale, EDGE);
     if (EDGE) scale_ring4(w.oc, i0, q0, n, ocol, ph.bscale, true);
   }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
   unsigned long long dm = 0;
-  // the last grid row reads the south ring; give it its own call
+  // the last grid row reads the south ring; give it its own step
   const int iend = (rescale && i1 == n + 1) ? n : i1;
-  int i = i0;
-  const int s0 = (i0 + colour) & 1;
-#define FAST_ROW(SS, FF, II, RB)                                                                                 \
-  fast_row<UNIT_BETA, HAS_G, MEASURE, EDGE, SS, FF>(w, II, RB, stages, i0, i1, O, X, G, pitch, n, ocol, q0, lane, \
-                                                    ph, dm)
-  if (i < iend) {
-    if (s0 == 0)
-      FAST_ROW(0, true, i, false);
-    else
-      FAST_ROW(1, true, i, false);
-    ++i;
-    if (s0 == 0) {
-      for (; i + 1 < iend; i += 2) {
-        FAST_ROW(1, false, i, false);
-        FAST_ROW(0, false, i + 1, false);
-      }
-      if (i < iend) {
-        FAST_ROW(1, false, i, false);
-        ++i;
-      }
-    } else {
-      for (; i + 1 < iend; i += 2) {
-        FAST_ROW(0, false, i, false);
-        FAST_ROW(1, false, i + 1, false);
-      }
-      if (i < iend) {
-        FAST_ROW(0, false, i, false);
-        ++i;
-      }
-    }
-  }
-  if (i < i1) {  // row n with the south ring below (only when rescaling)
-    const bool first = (i == i0);
-    const int s = (i + colour) & 1;
-    if (first) {
-      if (s == 0)
-        FAST_ROW(0, true, i, true);
-      else
-        FAST_ROW(1, true, i, true);
-    } else {
-      if (s == 0)
-        FAST_ROW(0, false, i, true);
-      else
-        FAST_ROW(1, false, i, true);
-    }
-  }
-#undef FAST_ROW
+  if (((i0 + colour) & 1) == 0)
+    fast_rows<UNIT_BETA, HAS_G, MEASURE, EDGE, 0>(w, stages, O, X, G, pitch, n, q0, i0, i1, iend, lane, ph, dm);
+  else
+    fast_rows<UNIT_BETA, HAS_G, MEASURE, EDGE, 1>(w, stages, O, X, G, pitch, n, q0, i0, i1, iend, lane, ph, dm);
   cp_async_wait<0>();  // no copy may still target the stages when the warp moves on
   return dm;
 }
@@ -920,31 +981,13 @@ int tb_out_cols(int T) {
 // residual pass (FP64), both colours per tile
 // ------------------------------------------------------------------------------------------------
 
-// r~ for the cell (i, q) of colour c given rows of the other colour.
-template <typename U>
-struct ResidRows {
-  double m[4], c[4], p[4];  // other colour rows i-1, i, i+1 (FP64 values)
-};
-
-// Loads 4 consecutive values of row i (colour arrays in FP64 or FP32, plus an
-// optional FP32 correction) as FP64.
+// Loads 4 consecutive values of a colour array (FP64 or FP32) as FP64.
 template <typename T>
-__device__ __forceinline__ void load_u4(const T* X, const float* D, size_t e, double (&v)[4]) {
+__device__ __forceinline__ void load_u4(const T* X, size_t e, double (&v)[4]) {
   T t[4];
   load4(X + e, t);
-  if (D) {
-    float d[4];
-    load4(D + e, d);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __dadd_rn((double)t[k], (double)d[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (double)t[k];
-  }
-}
-template <typename T>
-__device__ __forceinline__ double load_u1(const T* X, const float* D, size_t e) {
-  return D ? __dadd_rn((double)X[e], (double)D[e]) : (double)X[e];
+  for (int k = 0; k < 4; ++k) v[k] = (double)t[k];
 }
 
 // Defect correction, first half of a correction step: u += (double)d over the
@@ -1036,10 +1079,6 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
     const int pitch = sd.pitch, n = sd.n;
     const T* X0;
     const T* X1;
-    const float* D0 = nullptr;
-    const float* D1 = nullptr;
-    double* W0 = nullptr;
-    double* W1 = nullptr;
     if (ROLE == kResidRefine) {
       X0 = (const T*)sd.u[c.xbuf][0];
       X1 = (const T*)sd.u[c.xbuf][1];
@@ -1062,13 +1101,11 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
       for (int c0 = 0; c0 < 2; ++c0) {
         const T* Xs = c0 ? X1 : X0;  // own colour
         const T* Xo = c0 ? X0 : X1;  // other colour
-        const float* Ds = c0 ? D1 : D0;
-        const float* Do = c0 ? D0 : D1;
         double own[4], nm[4], nc[4], np[4], gv[4];
-        load_u4(Xs, Ds, eidx(i, q0, pitch), own);
-        load_u4(Xo, Do, eidx(i - 1, q0, pitch), nm);
-        load_u4(Xo, Do, eidx(i, q0, pitch), nc);
-        load_u4(Xo, Do, eidx(i + 1, q0, pitch), np);
+        load_u4(Xs, eidx(i, q0, pitch), own);
+        load_u4(Xo, eidx(i - 1, q0, pitch), nm);
+        load_u4(Xo, eidx(i, q0, pitch), nc);
+        load_u4(Xo, eidx(i + 1, q0, pitch), np);
         if (G0) {
           load4((c0 ? G1 : G0) + eidx(i, q0, pitch), gv);
         } else {
@@ -1077,8 +1114,8 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
         }
         double left = __shfl_up_sync(0xffffffffu, nc[3], 1);
         double right = __shfl_down_sync(0xffffffffu, nc[0], 1);
-        if (lane == 0) left = load_u1(Xo, Do, eidx(i, q0 - 1, pitch));
-        if (lane == 31) right = load_u1(Xo, Do, eidx(i, q0 + kVec, pitch));
+        if (lane == 0) left = (double)Xo[eidx(i, q0 - 1, pitch)];
+        if (lane == 31) right = (double)Xo[eidx(i, q0 + kVec, pitch)];
         const int s = (i + c0) & 1;
         const int qlim = (n + s) >> 1;
         double Wv[4], Ev[4];
@@ -1101,17 +1138,12 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
         const bool all_in = (q0 + 3) <= qlim;
         if (ROLE == kResidRefine) {
           float* R = c0 ? R1 : R0;
-          double* Wd = c0 ? W1 : W0;
           if (all_in) {
             store4(R + eidx(i, q0, pitch), rv);
-            if (Wd) store4(Wd + eidx(i, q0, pitch), own);
           } else {
 #pragma unroll
             for (int v = 0; v < 4; ++v)
-              if ((q0 + v) <= qlim) {
-                R[eidx(i, q0 + v, pitch)] = rv[v];
-                if (Wd) Wd[eidx(i, q0 + v, pitch)] = own[v];
-              }
+              if ((q0 + v) <= qlim) R[eidx(i, q0 + v, pitch)] = rv[v];
           }
         }
       }
