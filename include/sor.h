@@ -158,7 +158,8 @@ typedef enum {
   SOR_OPT_TIMING = 1,          /* 1: time the sweep kernels with CUDA events (sor_get_stats) */
   SOR_OPT_GRAPHS = 2,          /* 1 (default): replay launch sequences as CUDA graphs */
   SOR_OPT_CHUNK = 3,           /* iterations per launched chunk between convergence polls (0 = auto) */
-  SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per tile pass (0 = autotuned) */
+  SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per tile pass (0 = autotuned when
+                                  SOR_OPT_AUTOTUNE is 1, else 6; supported: 1, 2, 3, 4, 6, 8) */
   SOR_OPT_AUTOTUNE = 5,        /* 1: time candidate kernel configurations on first use of a size */
   SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
   SOR_OPT_CLUSTER = 7          /* 1 (default): plain solves of grids small enough for one thread-block

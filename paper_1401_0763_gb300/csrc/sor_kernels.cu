@@ -735,11 +735,12 @@ struct TbGeom {
 __device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc, bool valid) {
   const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
   const int n = valid ? 16 : 0;  // src-size 0 fills the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(valid ? gsrc : nullptr), "r"(n));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(valid ? gsrc : nullptr), "r"(n)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::);
-  asm volatile("cp.async.wait_group 0;\n" ::);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // One colour phase on the staged tile: rows [r0, r1) of the staged arrays
@@ -752,10 +753,12 @@ __device__ __forceinline__ void tb_g_issue(float* gslot, const float* __restrict
                                            int colour, int lane) {
   const int s = (i + colour) & 1;
   if (i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1)) cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
-  asm volatile("cp.async.commit_group;\n" ::);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-template <int T, bool LASTM>
+// FULL: every staged column of the tile is an interior packed column of both
+// colours (no ring or padding cell among them), so no cell needs masking.
+template <int T, bool LASTM, bool FULL>
 __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
                                          const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
                                          int r1, int n, int pitch, int out_rows, int lane, float a, float b,
@@ -764,6 +767,23 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
   if (r0 >= r1) return;
   const int col = 4 * lane;
   const int qf = base_q + col;
+  // this lane's interior cells for row parity 0 / 1 (bit v: packed column qf + v)
+  // and, for the measured phase, its cells inside the output columns
+  unsigned in0 = 0xF, in1 = 0xF, outc = 0;
+  if (!FULL) {
+    in0 = 0;
+    in1 = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int q = qf + v;
+      in0 |= (unsigned)(q >= 1 && q <= (n >> 1)) << v;
+      in1 |= (unsigned)(q >= 1 && q <= ((n + 1) >> 1)) << v;
+    }
+  }
+  if (LASTM) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) outc |= (unsigned)(col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ) << v;
+  }
   float om[4], oc[4];
   load4(So + (r0 - 1) * Gm::C + col, om);
   load4(So + r0 * Gm::C + col, oc);
@@ -772,9 +792,9 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
     if (Gc) {
       if (r + 1 < r1) {
         tb_g_issue(gbuf + ((r + 1 - r0) & 1) * Gm::C, Gc, base_r + r + 1, qf, n, pitch, colour, lane);
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
       } else {
-        asm volatile("cp.async.wait_group 0;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
       }
     }
     float op[4];
@@ -784,11 +804,10 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
     const int i = base_r + r;
     if (i >= 1 && i <= n) {  // warp-uniform
       const int s = (i + colour) & 1;
-      const int qlim = (n + s) >> 1;
-      const bool any = qf >= 1 && qf <= qlim;  // qf is 1 mod 4: the group has an interior cell iff qf in [1, qlim]
+      const unsigned m = s ? in1 : in0;
       float own[4], gv[4];
       load4(Sc + r * Gm::C + col, own);
-      if (Gc && any) {
+      if (Gc && m) {
         load4(gbuf + ((r - r0) & 1) * Gm::C + col, gv);
       } else {
 #pragma unroll
@@ -802,17 +821,19 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
         W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
         E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
       }
+      // Cells of staged columns 0 and C-1 see a wrong W or E (no staged
+      // neighbour); like every cell near the staged border they are stale,
+      // and the stale band never reaches the output tile.
       float nv[4];
+      const bool out_row = LASTM && r >= Gm::HR && r < Gm::HR + out_rows;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         float sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
         if (Gc) sum = radd(sum, gv[v]);
         const float nu = radd(rmul(a, own[v]), rmul(b, sum));
-        const int q = qf + v;
-        const bool in = q >= 1 && q <= qlim && col + v >= 1 && col + v <= Gm::C - 2;
+        const bool in = FULL || ((m >> v) & 1u);
         nv[v] = in ? nu : own[v];
-        if (LASTM && in && r >= Gm::HR && r < Gm::HR + out_rows && col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ)
-          dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
+        if (LASTM && out_row && in && ((outc >> v) & 1u)) dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
       }
       store4(Sc + r * Gm::C + col, nv);
     }
@@ -895,26 +916,37 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
 
     const float a = sd.a32, b = sd.b32;
     unsigned dm32 = 0;
-    constexpr int U = Gm::R - 2;                 // updatable staged rows 1 .. R-2
-    constexpr int SEG = (U + kWarps - 1) / kWarps;
-    const int r0 = 1 + warp * SEG;
-    const int r1 = min(r0 + SEG, Gm::R - 1);
+    const bool full = base_q >= 1 && base_q + Gm::C - 1 <= (n >> 1);
     for (int it = 0; it < nt; ++it) {
       const bool lastm = (MODE == 0) && measure && it == nt - 1;
-      if (lastm) {
-        tb_phase<T, true>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
-                          dm32, &gbufs[warp][0][0]);
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        // Phase p = 2it + c + 1 of 2nt: only rows within 2nt - p of the output
+        // rows can still reach them, so the updated band shrinks by one row
+        // at each end per phase (it starts at staged rows 1 .. R-2 when nt = T).
+        const int reach = 2 * nt - (2 * it + c + 1);
+        const int lo = Gm::HR - reach, hi = Gm::HR + tl.nrows + reach;
+        const int seg = (hi - lo + kWarps - 1) / kWarps;
+        const int r0 = lo + warp * seg;
+        const int r1 = min(r0 + seg, hi);
+        float* Sc = c ? S1 : S0;
+        const float* So = c ? S0 : S1;
+        const float* Gc = (const float*)sd.g[c];
+        float* gb = &gbufs[warp][0][0];
+        if (full) {
+          if (lastm)
+            tb_phase<T, true, true>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
+          else
+            tb_phase<T, false, true>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
+        } else {
+          if (lastm)
+            tb_phase<T, true, false>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
+          else
+            tb_phase<T, false, false>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32,
+                                      gb);
+        }
         __syncthreads();
-        tb_phase<T, true>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b,
-                          dm32, &gbufs[warp][0][0]);
-      } else {
-        tb_phase<T, false>(S0, S1, (const float*)sd.g[0], 0, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
-                           b, dm32, &gbufs[warp][0][0]);
-        __syncthreads();
-        tb_phase<T, false>(S1, S0, (const float*)sd.g[1], 1, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a,
-                           b, dm32, &gbufs[warp][0][0]);
       }
-      __syncthreads();
     }
     // write the centre tile to the other buffer: warp per row, lane per float4
     const int dst = src ^ 1;
