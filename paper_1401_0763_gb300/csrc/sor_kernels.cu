@@ -743,106 +743,188 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// One colour phase on the staged tile: rows [r0, r1) of the staged arrays
-// for this warp.  LASTM: this phase belongs to a measured iteration, track
-// max |change| over the tile's output cells.
+// Right-hand-side rows are fetched kTbGAhead rows ahead into a ring of
+// kTbGSlots row buffers per warp (one asynchronous-copy group per row).
+constexpr int kTbGAhead = 3;
+constexpr int kTbGSlots = 4;
+
 // Right-hand-side values of staged row r (global row i) for this lane, copied
 // asynchronously into the warp's buffer (nothing for rows or lanes without
 // interior cells); one commit per row either way.
 __device__ __forceinline__ void tb_g_issue(float* gslot, const float* __restrict__ Gc, int i, int qf, int n, int pitch,
-                                           int colour, int lane) {
+                                           int colour, int lane, bool valid) {
   const int s = (i + colour) & 1;
-  if (i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1)) cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
+  if (valid && i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1))
+    cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
+// One row r of a phase on the staged tile.  om / oc / op: the neighbour
+// colour's staged rows r-1, r, r+1 (this lane's 4 columns, in registers);
+// S = (i + colour) & 1 for the global row i, fixed at compile time, which
+// decides which single neighbour value comes from the next lane (S == 0: the
+// east one of the last cell; S == 1: the west one of the first cell).  m: this
+// lane's interior cells (unused when FULL); out_row / outc: the cells counted
+// by the max|change| of a measured phase.  Exact operation order of the oracle.
+template <bool LASTM, bool FULL, bool HAS_G, int S>
+__device__ __forceinline__ void tb_row(const float (&om)[4], const float (&oc)[4], const float (&op)[4],
+                                       float* __restrict__ own_p, const float* __restrict__ g_p, unsigned m,
+                                       bool out_row, unsigned outc, float a, float b, unsigned& dm32) {
+  float W[4], E[4];
+  if (S == 0) {
+    const float side = __shfl_down_sync(0xffffffffu, oc[0], 1);
+    W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+    E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = side;
+  } else {
+    const float side = __shfl_up_sync(0xffffffffu, oc[3], 1);
+    W[0] = side; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+    E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+  }
+  float own[4], gv[4];
+  load4(own_p, own);
+  if (HAS_G) {
+    if (FULL || m) {
+      load4(g_p, gv);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
+    }
+  }
+  // Cells of staged columns 0 and C-1 see a wrong W or E (no staged
+  // neighbour); like every cell near the staged border they are stale, and
+  // the stale band never reaches the output tile.
+  float nv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
+    if (HAS_G) sum = radd(sum, gv[v]);
+    const float nu = radd(rmul(a, own[v]), rmul(b, sum));
+    const bool in = FULL || ((m >> v) & 1u);
+    nv[v] = in ? nu : own[v];
+    if (LASTM && out_row && in && ((outc >> v) & 1u)) dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
+  }
+  store4(own_p, nv);
+}
+
+// Per-phase constants of one warp's rows.
+struct TbRows {
+  float* Sc;        // own colour, staged
+  const float* So;  // neighbour colour, staged
+  const float* Gc;  // right-hand side of the own colour (HAS_G)
+  float* gbuf;      // this warp's kTbGSlots right-hand-side row buffers
+  int base_r, qf, n, pitch, colour, lane, r0, out_lo, out_hi;
+  unsigned in0, in1, outc;
+  float a, b;
+};
+
+template <int C, bool LASTM, bool FULL, bool HAS_G, int S>
+__device__ __forceinline__ void tb_row_at(const TbRows& R, int r, int r1, const float (&om)[4], const float (&oc)[4],
+                                          const float (&op)[4], unsigned& dm32) {
+  const float* gp = nullptr;
+  if (HAS_G) {  // fetch row r + kTbGAhead's right-hand side, then wait for row r's
+    const int ra = r + kTbGAhead;
+    tb_g_issue(R.gbuf + ((ra - R.r0) & (kTbGSlots - 1)) * C, R.Gc, R.base_r + ra, R.qf, R.n, R.pitch, R.colour,
+               R.lane, ra < r1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTbGAhead) : "memory");
+    gp = R.gbuf + ((r - R.r0) & (kTbGSlots - 1)) * C + 4 * R.lane;
+  }
+  const bool out_row = LASTM && r >= R.out_lo && r < R.out_hi;
+  tb_row<LASTM, FULL, HAS_G, S>(om, oc, op, R.Sc + r * C + 4 * R.lane, gp, S ? R.in1 : R.in0, out_row, R.outc, R.a,
+                                R.b, dm32);
+}
+
+// Rows [R.r0, r1) of the staged tile, the first with parity S0.  Bodies of
+// four rows cycle four register rows in place (rows r-1 .. r+4 pass through
+// X, Y, P, Q and leave X, Y holding r+3, r+4), so no row values are moved.
+template <int C, bool LASTM, bool FULL, bool HAS_G, int S0>
+__device__ __forceinline__ void tb_rows(const TbRows& R, int r1, unsigned& dm32) {
+  const float* So = R.So + 4 * R.lane;
+  int r = R.r0;
+  float X[4], Y[4], P[4], Q[4];
+  load4(So + (r - 1) * C, X);
+  load4(So + r * C, Y);
+  if (HAS_G)
+    for (int k = 0; k < kTbGAhead; ++k)
+      tb_g_issue(R.gbuf + k * C, R.Gc, R.base_r + r + k, R.qf, R.n, R.pitch, R.colour, R.lane, r + k < r1);
+  for (; r + 4 <= r1; r += 4) {
+    load4(So + (r + 1) * C, P);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
+    load4(So + (r + 2) * C, Q);
+    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
+    load4(So + (r + 3) * C, X);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
+    load4(So + (r + 4) * C, Y);
+    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 3, r1, Q, X, Y, dm32);
+  }
+  if (r < r1) {
+    load4(So + (r + 1) * C, P);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
+    if (r + 1 < r1) {
+      load4(So + (r + 2) * C, Q);
+      tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
+      if (r + 2 < r1) {
+        load4(So + (r + 3) * C, X);
+        tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
+      }
+    }
+  }
+  if (HAS_G) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the groups past r1 are empty
+}
+
+// One colour phase on the staged tile: rows [r0, r1) of the staged arrays for
+// this warp, clipped to global interior rows.  LASTM: this phase belongs to a
+// measured iteration, track max |change| over the tile's output cells.
 // FULL: every staged column of the tile is an interior packed column of both
 // colours (no ring or padding cell among them), so no cell needs masking.
-template <int T, bool LASTM, bool FULL>
+template <int T, bool LASTM, bool FULL, bool HAS_G>
 __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
                                          const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
                                          int r1, int n, int pitch, int out_rows, int lane, float a, float b,
-                                         unsigned& dm32, float* gbuf /* [2][128] for this warp */) {
+                                         unsigned& dm32, float* gbuf /* [kTbGSlots][128] for this warp */) {
   using Gm = TbGeom<T>;
+  r0 = max(r0, 1 - base_r);  // global rows 1 .. n only
+  r1 = min(r1, n + 1 - base_r);
   if (r0 >= r1) return;
-  const int col = 4 * lane;
-  const int qf = base_q + col;
+  TbRows R;
+  R.Sc = Sc;
+  R.So = So;
+  R.Gc = Gc;
+  R.gbuf = gbuf;
+  R.base_r = base_r;
+  R.qf = base_q + 4 * lane;
+  R.n = n;
+  R.pitch = pitch;
+  R.colour = colour;
+  R.lane = lane;
+  R.r0 = r0;
+  R.out_lo = Gm::HR;
+  R.out_hi = Gm::HR + out_rows;
+  R.a = a;
+  R.b = b;
   // this lane's interior cells for row parity 0 / 1 (bit v: packed column qf + v)
   // and, for the measured phase, its cells inside the output columns
-  unsigned in0 = 0xF, in1 = 0xF, outc = 0;
+  R.in0 = 0xF;
+  R.in1 = 0xF;
+  R.outc = 0;
   if (!FULL) {
-    in0 = 0;
-    in1 = 0;
+    R.in0 = 0;
+    R.in1 = 0;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      const int q = qf + v;
-      in0 |= (unsigned)(q >= 1 && q <= (n >> 1)) << v;
-      in1 |= (unsigned)(q >= 1 && q <= ((n + 1) >> 1)) << v;
+      const int q = R.qf + v;
+      R.in0 |= (unsigned)(q >= 1 && q <= (n >> 1)) << v;
+      R.in1 |= (unsigned)(q >= 1 && q <= ((n + 1) >> 1)) << v;
     }
   }
   if (LASTM) {
+    const int col = 4 * lane;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) outc |= (unsigned)(col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ) << v;
+    for (int v = 0; v < 4; ++v) R.outc |= (unsigned)(col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ) << v;
   }
-  float om[4], oc[4];
-  load4(So + (r0 - 1) * Gm::C + col, om);
-  load4(So + r0 * Gm::C + col, oc);
-  if (Gc) tb_g_issue(gbuf, Gc, base_r + r0, qf, n, pitch, colour, lane);  // one row ahead
-  for (int r = r0; r < r1; ++r) {
-    if (Gc) {
-      if (r + 1 < r1) {
-        tb_g_issue(gbuf + ((r + 1 - r0) & 1) * Gm::C, Gc, base_r + r + 1, qf, n, pitch, colour, lane);
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-      } else {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      }
-    }
-    float op[4];
-    load4(So + (r + 1) * Gm::C + col, op);
-    const float left = __shfl_up_sync(0xffffffffu, oc[3], 1);
-    const float right = __shfl_down_sync(0xffffffffu, oc[0], 1);
-    const int i = base_r + r;
-    if (i >= 1 && i <= n) {  // warp-uniform
-      const int s = (i + colour) & 1;
-      const unsigned m = s ? in1 : in0;
-      float own[4], gv[4];
-      load4(Sc + r * Gm::C + col, own);
-      if (Gc && m) {
-        load4(gbuf + ((r - r0) & 1) * Gm::C + col, gv);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
-      }
-      float W[4], E[4];
-      if (s == 0) {
-        W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
-        E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = right;
-      } else {
-        W[0] = left; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
-        E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
-      }
-      // Cells of staged columns 0 and C-1 see a wrong W or E (no staged
-      // neighbour); like every cell near the staged border they are stale,
-      // and the stale band never reaches the output tile.
-      float nv[4];
-      const bool out_row = LASTM && r >= Gm::HR && r < Gm::HR + out_rows;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        float sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
-        if (Gc) sum = radd(sum, gv[v]);
-        const float nu = radd(rmul(a, own[v]), rmul(b, sum));
-        const bool in = FULL || ((m >> v) & 1u);
-        nv[v] = in ? nu : own[v];
-        if (LASTM && out_row && in && ((outc >> v) & 1u)) dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
-      }
-      store4(Sc + r * Gm::C + col, nv);
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      om[v] = oc[v];
-      oc[v] = op[v];
-    }
-  }
+  if (((base_r + r0 + colour) & 1) == 0)
+    tb_rows<Gm::C, LASTM, FULL, HAS_G, 0>(R, r1, dm32);
+  else
+    tb_rows<Gm::C, LASTM, FULL, HAS_G, 1>(R, r1, dm32);
 }
 
 // MODE 0: plain FP32 iterations on x (rhs g optional), source buffer from the
@@ -861,7 +943,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
   float* const S1 = tb_smem + Gm::R * Gm::C;
   __shared__ unsigned long long red[kWarps];
   __shared__ int ctl[5];  // skip, nt, k_end, measure, src
-  __shared__ __align__(16) float gbufs[kWarps][2][Gm::C];  // right-hand-side rows, double-buffered per warp
+  __shared__ __align__(16) float gbufs[kWarps][kTbGSlots][Gm::C];  // right-hand-side rows, a ring per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
@@ -933,18 +1015,22 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
         const float* So = c ? S0 : S1;
         const float* Gc = (const float*)sd.g[c];
         float* gb = &gbufs[warp][0][0];
-        if (full) {
-          if (lastm)
-            tb_phase<T, true, true>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
-          else
-            tb_phase<T, false, true>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
+#define TB_PHASE(LM, FL, HG) \
+  tb_phase<T, LM, FL, HG>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb)
+        if (Gc) {
+          if (full) {
+            if (lastm) TB_PHASE(true, true, true); else TB_PHASE(false, true, true);
+          } else {
+            if (lastm) TB_PHASE(true, false, true); else TB_PHASE(false, false, true);
+          }
         } else {
-          if (lastm)
-            tb_phase<T, true, false>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb);
-          else
-            tb_phase<T, false, false>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32,
-                                      gb);
+          if (full) {
+            if (lastm) TB_PHASE(true, true, false); else TB_PHASE(false, true, false);
+          } else {
+            if (lastm) TB_PHASE(true, false, false); else TB_PHASE(false, false, false);
+          }
         }
+#undef TB_PHASE
         __syncthreads();
       }
     }
