@@ -7,7 +7,8 @@ imports the other; the seeded input generators in
 ``paper_1401_0763_gb300.workloads`` hold no arithmetic of the method and are
 the only thing both sides use.
 
-What each function computes is stated in ``sor_oracle.c``; in short:
+What each function computes is stated in ``sor_oracle.c`` (2D) and
+``sor3d_oracle.c`` (3D); in short:
 
 * :func:`sor_f64` -- Algorithm 1 of the paper (red phase, then black phase,
   convergence test every K iterations, Section 2.1 / Section 3.3) with the
@@ -17,11 +18,14 @@ What each function computes is stated in ``sor_oracle.c``; in short:
   norm relative to the right-hand side (boundary moved to the right).
 * :func:`refine` -- FP64 defect correction around FP32 (or FP64) inner
   red-black SOR sweeps.
+* :func:`sor3d_f64`, :func:`sor3d_f32`, :func:`residual3d` -- the same
+  iteration and residual on a cube with the 7-point stencil (the 3D grids the
+  paper names as its next step, Section 5).
 
-Parity status: every function is pinned by ``tests/test_oracle_pins.py``
-(dense direct solve, the explicit SOR iteration matrix, closed-form harmonic
-and quadratic solutions, a DST-I fast Poisson solve, SOR convergence theory
-and superposition/symmetry invariants).
+Parity status: every function is pinned by ``tests/test_oracle_pins.py`` and
+``tests/test_oracle3d_pins.py`` (dense direct solves, the explicit SOR
+iteration matrix, closed-form harmonic and quadratic solutions, a DST-I fast
+Poisson solve, SOR convergence theory and superposition/symmetry invariants).
 """
 from __future__ import annotations
 
@@ -33,7 +37,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "sor_oracle.c")
+_SRCS = [os.path.join(_HERE, "sor_oracle.c"), os.path.join(_HERE, "sor3d_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -44,14 +48,14 @@ _ip = ctypes.POINTER(ctypes.c_int)
 
 
 def build(force: bool = False) -> str:
-    """Compile ``sor_oracle.c`` with gcc (contraction off) into ``_build/``."""
+    """Compile the oracle's C sources with gcc (contraction off) into ``_build/``."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
+           "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -69,7 +73,13 @@ def _load():
             lib.oracle_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
             lib.oracle_refine.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
-            for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine):
+            lib.oracle_sor3d_f64.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _dp]
+            lib.oracle_sor3d_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
+            lib.oracle_residual3d.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine,
+                       lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -189,3 +199,82 @@ def refine(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max
     if trace:
         out["trace"] = tr[: ou.value + 1].copy()
     return out
+
+
+def _cube(u0, n):
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    if u0.shape != (n + 2, n + 2, n + 2):
+        raise ValueError(f"u0 must be ({n + 2},{n + 2},{n + 2}), got {u0.shape}")
+    return u0
+
+
+def _src3(f, n):
+    if f is None:
+        return None
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.shape != (n, n, n):
+        raise ValueError(f"f must be ({n},{n},{n}), got {f.shape}")
+    return f
+
+
+def sor3d_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):
+    """Plain FP64 red-black SOR on an (n+2)^3 cube, 7-point stencil (index
+    order [k, i, j] = plane, row, column).  Returns a dict like
+    :func:`sor_f64`."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _cube(u0, n)
+    f = _src3(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md, rr = ctypes.c_double(0), ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor3d_f64(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
+                                  int(stop_mode), _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md),
+                                  ctypes.byref(rr), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor3d_f64: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
+               final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def sor3d_f32(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, trace=False):
+    """Red-black SOR on a cube in FP32 arithmetic and storage (stop on
+    max|change|)."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _cube(u0, n)
+    f = _src3(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md = ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor3d_f32(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
+                                  _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor3d_f32: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def residual3d(u, *, f=None):
+    """Scaled residual r~ = h^2 f + sum_nb(u) - 6u on the (n+2)^3 cube (shell
+    0) and (max|r~|, max|b~|)."""
+    n = int(np.asarray(u).shape[0]) - 2
+    u = _cube(u, n)
+    f = _src3(f, n)
+    r = np.zeros_like(u)
+    rm, bm = ctypes.c_double(0), ctypes.c_double(0)
+    rc = _load().oracle_residual3d(n, _ptr(u), _ptr(f), _ptr(r), ctypes.byref(rm), ctypes.byref(bm))
+    if rc != 0:
+        raise ValueError("oracle_residual3d: bad arguments")
+    return r, rm.value, bm.value
+
+
+def resid_rel3d(u, *, f=None):
+    """max|r~| / max|b~| on a cube (or max|r~| when the right side is zero)."""
+    _, rm, bm = residual3d(u, f=f)
+    return rm / bm if bm > 0 else rm

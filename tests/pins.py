@@ -112,3 +112,109 @@ def rel_err(a, b):
     a, b = np.asarray(a)[1:-1, 1:-1], np.asarray(b)[1:-1, 1:-1]
     s = np.max(np.abs(b))
     return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
+
+
+# ---------------------------------------------------------------------------
+# 3D: the 7-point Dirichlet problem on an n^3 interior, scaled by h^2:
+#     6 u - (sum of the six neighbours) = h^2 f,  arrays indexed [k, i, j].
+# ---------------------------------------------------------------------------
+
+_NB3 = ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))
+
+
+def dense_system3(u0, f=None):
+    """Dense A (n^3 x n^3, natural ordering k, i, j) and b for the cube u0."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    N = n ** 3
+    A = np.zeros((N, N))
+    b = np.zeros(N)
+    idx = np.arange(N).reshape(n, n, n)
+    for k in range(1, n + 1):
+        for i in range(1, n + 1):
+            for j in range(1, n + 1):
+                r = idx[k - 1, i - 1, j - 1]
+                A[r, r] = 6.0
+                b[r] = h2 * f[k - 1, i - 1, j - 1] if f is not None else 0.0
+                for dk, di, dj in _NB3:
+                    kk, ii, jj = k + dk, i + di, j + dj
+                    if 1 <= kk <= n and 1 <= ii <= n and 1 <= jj <= n:
+                        A[r, idx[kk - 1, ii - 1, jj - 1]] = -1.0
+                    else:
+                        b[r] += u0[kk, ii, jj]
+    return A, b
+
+
+def dense_solve3(u0, f=None):
+    """Exact discrete solution on the full (n+2)^3 cube (LAPACK)."""
+    n = u0.shape[0] - 2
+    A, b = dense_system3(u0, f)
+    u = u0.copy()
+    u[1:-1, 1:-1, 1:-1] = np.linalg.solve(A, b).reshape(n, n, n)
+    return u
+
+
+def dst_solve3(u0, f=None):
+    """Exact discrete solution by the 3D type-I discrete sine transform
+    (eigenvalues: the sum of three 1D terms 2 - 2cos(p pi/(n+1)))."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    b = np.zeros((n, n, n)) if f is None else h2 * np.asarray(f, dtype=np.float64).copy()
+    b[0] += u0[0, 1:-1, 1:-1]
+    b[-1] += u0[-1, 1:-1, 1:-1]
+    b[:, 0] += u0[1:-1, 0, 1:-1]
+    b[:, -1] += u0[1:-1, -1, 1:-1]
+    b[:, :, 0] += u0[1:-1, 1:-1, 0]
+    b[:, :, -1] += u0[1:-1, 1:-1, -1]
+    p = np.arange(1, n + 1)
+    lam = 2.0 - 2.0 * np.cos(p * np.pi / (n + 1))
+    uh = scipy.fft.dstn(b, type=1) / (lam[:, None, None] + lam[None, :, None] + lam[None, None, :])
+    u = u0.copy()
+    u[1:-1, 1:-1, 1:-1] = scipy.fft.idstn(uh, type=1)
+    return u
+
+
+def red_black_iteration3(u0, omega, iters, f=None):
+    """3D red-black SOR as a matrix splitting, unknowns ordered red first
+    ((i+j+k) even): x_{k+1} = (D - wL)^{-1}[((1-w)D + wU) x_k + w b]."""
+    n = u0.shape[0] - 2
+    A, b = dense_system3(u0, f)
+    kk, ii, jj = np.meshgrid(*(np.arange(1, n + 1),) * 3, indexing="ij")
+    red = ((kk + ii + jj) % 2 == 0).ravel()
+    order = np.concatenate([np.nonzero(red)[0], np.nonzero(~red)[0]])
+    P = A[np.ix_(order, order)]
+    bp = b[order]
+    D = np.diag(np.diag(P))
+    L = -np.tril(P, -1)
+    U = -np.triu(P, 1)
+    lhs = D - omega * L
+    M = np.linalg.solve(lhs, (1.0 - omega) * D + omega * U)
+    c = np.linalg.solve(lhs, omega * bp)
+    x = u0[1:-1, 1:-1, 1:-1].ravel()[order].copy()
+    out = []
+    for _ in range(iters):
+        x = M @ x + c
+        full = np.empty(n ** 3)
+        full[order] = x
+        u = u0.copy()
+        u[1:-1, 1:-1, 1:-1] = full.reshape(n, n, n)
+        out.append(u)
+    return out
+
+
+def rel_err3(a, b):
+    """Normwise relative difference over the interior of two cubes."""
+    a, b = np.asarray(a)[1:-1, 1:-1, 1:-1], np.asarray(b)[1:-1, 1:-1, 1:-1]
+    s = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (s if s > 0 else 1.0))
+
+
+def cube_from(fn, n):
+    """(n+2)^3 cube with the values fn(x, y, z) on the shell and 0 inside
+    (x = j h, y = i h, z = k h)."""
+    h = 1.0 / (n + 1)
+    t = np.arange(n + 2) * h
+    z, y, x = np.meshgrid(t, t, t, indexing="ij")
+    u = fn(x, y, z)
+    u[1:-1, 1:-1, 1:-1] = 0.0
+    return u, fn(x, y, z)
