@@ -131,6 +131,29 @@ sor_status sor_create(sor_ctx **out, int device, size_t hbm_budget_bytes, void *
 sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
                      sor_result *res);
 
+/* Blocking solve of one problem on a cube: the 3D grids the paper names as
+ * the next step of its study (Section 5, Conclusion and Future Work), solved
+ * by the same method -- Algorithm 1 with the update of Eq. 1, the
+ * Gauss-Seidel value taken from the 7-point stencil:
+ *   U <- (1-w) U + (w/6) ((((N + S) + (W + E)) + (D + U)) + h^2 f),
+ * red = (i + j + k) even, red phase first.  Every product and sum is rounded
+ * on its own in that order, in FP64 (precision SOR_FP64) or FP32
+ * (SOR_FP32); the residual r~ = (h^2 f + sum of the six neighbours) - 6 u is
+ * formed in FP64.
+ *   params: n = interior side N (1 <= N <= 1200); omega <= 0 selects
+ *           2 / (1 + sin(pi / (N+1))); stop, tol, max_iters, check_every as
+ *           for sor_solve; precision SOR_FP64 or SOR_FP32; flags 0 or
+ *           SOR_FLAG_EXACT_ORDER (the only order on cubes); stall_window 0.
+ *           Anything else returns SOR_ERR_INVALID_ARG.
+ *   u0:    (N+2)^3 array indexed [k][i][j] (plane, row, column), its outer
+ *          shell the Dirichlet data.  Host or device memory.
+ *   f:     N^3 interior source of -Laplace(u) = f ([k][i][j]), or NULL.
+ *   u_out: (N+2)^3 final values (may equal u0).  res: optional.
+ * Device memory comes from the context's allocator and counts against its
+ * budget (SOR_ERR_BUDGET when the solve does not fit). */
+sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
+                       sor_result *res);
+
 /* Non-blocking submission to the context's continuous-batching scheduler.
  * u0 and f are copied before the call returns.  u_out must stay valid until
  * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.

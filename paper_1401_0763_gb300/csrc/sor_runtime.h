@@ -178,6 +178,10 @@ int refine_dbuf(const Plan& p);
 sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
                           sor_result* res);
 
+// 3D cube solve (sor_solve3d); the caller holds solve_mu.
+sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                            sor_result* res);
+
 sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out, uint64_t* ticket);
 sor_status batch_poll(Ctx* c, uint64_t ticket, double timeout_s, sor_result* res);
 void batch_shutdown(Ctx* c);

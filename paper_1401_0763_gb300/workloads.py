@@ -138,3 +138,43 @@ def request_stream(count: int, rate: float, seed: int, n_lo: int = 128, n_hi: in
 def request_inputs(req: Request):
     """Boundary uniform[0, 100] and a Gaussian-sum source for one request."""
     return random_edges(req.n, req.seed), gaussian_source(req.n, req.seed + 1)
+
+
+# ---------------------------------------------------------------------------
+# Cubes (3D grids), arrays indexed [k, i, j] = plane (z), row (y), column (x).
+# ---------------------------------------------------------------------------
+
+def random_shell(n: int, seed: int, lo: float = 0.0, hi: float = 100.0) -> np.ndarray:
+    """(n+2)^3 cube whose outer shell holds i.i.d. uniform[lo, hi] values
+    (drawn for the whole cube in C order, interior then zeroed); interior 0."""
+    g = rng(seed)
+    u = g.uniform(lo, hi, size=(n + 2,) * 3)
+    u[1:-1, 1:-1, 1:-1] = 0.0
+    return u
+
+
+def heat_cube(n: int, top: float = 100.0) -> np.ndarray:
+    """Cube with the plane k = 0 held at `top`, the rest of the shell and the
+    interior at 0 (the 3D counterpart of the heated plate)."""
+    u = np.zeros((n + 2,) * 3)
+    u[0] = top
+    return u
+
+
+def gaussian_source3(n: int, seed: int, count: int = 8) -> np.ndarray:
+    """f(x, y, z) = sum_k a_k exp(-|p - p_k|^2 / (2 s_k^2)) on the interior
+    nodes, a_k ~ U[-1, 1], s_k ~ U[0.02, 0.2], centres p_k ~ U[0, 1]^3, drawn
+    in that order from one PCG64 stream."""
+    g = rng(seed)
+    a = g.uniform(-1.0, 1.0, size=count)
+    s = g.uniform(0.02, 0.2, size=count)
+    c = g.uniform(0.0, 1.0, size=(count, 3))
+    h = 1.0 / (n + 1)
+    t = np.arange(1, n + 1, dtype=np.float64) * h
+    f = np.zeros((n, n, n))
+    for k in range(count):
+        ex = np.exp(-((t - c[k, 0]) ** 2) / (2.0 * s[k] ** 2))
+        ey = np.exp(-((t - c[k, 1]) ** 2) / (2.0 * s[k] ** 2))
+        ez = np.exp(-((t - c[k, 2]) ** 2) / (2.0 * s[k] ** 2))
+        f += a[k] * ez[:, None, None] * ey[None, :, None] * ex[None, None, :]
+    return f

@@ -1,0 +1,147 @@
+"""Parity of the 3D (cube, 7-point) CUDA path with the CPU oracle, through
+the C ABI (sor_solve3d).  Bar: bit identical to the oracle in FP64 and FP32
+(same operation order, every operation rounded on its own), same iteration
+counts.  Sizes span several 32 x 128 tiles per plane, ragged tails, two
+column tiles (n > 256) and the degenerate cubes n = 1, 2."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_0763_gb300 import workloads as wl
+from tests import pins
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1401_0763_gb300 import _build, capi
+    _build.build()
+    c = capi.Context(0)
+    yield c
+    c.close()
+
+
+def capi_mod():
+    from paper_1401_0763_gb300 import capi
+    return capi
+
+
+def run3(ctx, u0, f=None, device=True, **kw):
+    if device:
+        u0t = torch.from_numpy(np.ascontiguousarray(u0)).cuda()
+        ft = torch.from_numpy(np.ascontiguousarray(f)).cuda() if f is not None else None
+        out, res = ctx.solve3d(u0t, ft, **kw)
+        return out.cpu().numpy(), res
+    return ctx.solve3d(np.ascontiguousarray(u0), f, **kw)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 40, 65])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_fp64_bitwise(ctx, n, with_f):
+    capi = capi_mod()
+    u0 = wl.random_shell(n, 100 + n)
+    f = wl.gaussian_source3(n, 200 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, f=f, max_iters=60, check_every=5, tol=1e-9)
+    got, res = run3(ctx, u0, f, omega=w, max_iters=60, check_every=5, tol=1e-9, precision=capi.SOR_FP64)
+    assert res["iterations"] == ref["iterations"]
+    assert res["converged"] == ref["converged"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+@pytest.mark.parametrize("n", [3, 33, 64])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_fp32_bitwise(ctx, n, with_f):
+    capi = capi_mod()
+    u0 = wl.random_shell(n, 300 + n)
+    f = wl.gaussian_source3(n, 400 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f32(u0, w, f=f, max_iters=50, check_every=10, tol=1e-4)
+    got, res = run3(ctx, u0, f, omega=w, max_iters=50, check_every=10, tol=1e-4, precision=capi.SOR_FP32)
+    assert res["iterations"] == ref["iterations"]
+    assert res["converged"] == ref["converged"]
+    assert np.array_equal(got, ref["u"])
+
+
+def test_two_column_tiles_ragged(ctx):
+    """n = 259: 130 packed columns (two column tiles, the second ragged) and
+    a ragged last row tile in every plane."""
+    capi = capi_mod()
+    n = 259
+    u0 = wl.random_shell(n, 7)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, max_iters=3, check_every=1, tol=0.0)
+    got, res = run3(ctx, u0, omega=w, max_iters=3, check_every=1, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 3
+    assert np.array_equal(got, ref["u"])
+
+
+def test_residual_stop_matches(ctx):
+    capi = capi_mod()
+    n = 24
+    u0 = wl.random_shell(n, 11)
+    f = wl.gaussian_source3(n, 12)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, f=f, max_iters=2000, check_every=4, tol=1e-10, stop_mode=1)
+    got, res = run3(ctx, u0, f, omega=w, max_iters=2000, check_every=4, tol=1e-10, precision=capi.SOR_FP64,
+                    stop=capi.SOR_STOP_RESID_REL)
+    assert ref["converged"] and res["converged"]
+    assert res["iterations"] == ref["iterations"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_resid_rel"] == ref["final_resid_rel"] < 1e-10
+
+
+def test_harmonic_quadratic_and_dst(ctx):
+    """Converged cube against closed forms the oracle is pinned to."""
+    capi = capi_mod()
+    n = 48
+    u0, exact = pins.cube_from(lambda x, y, z: x * x + y * y - 2.0 * z * z, n)
+    got, res = run3(ctx, u0, max_iters=5000, check_every=10, tol=1e-14, precision=capi.SOR_FP64)
+    assert res["converged"]
+    assert np.max(np.abs(got - exact)) < 1e-11
+    u0 = wl.random_shell(n, 5)
+    f = wl.gaussian_source3(n, 6)
+    got, res = run3(ctx, u0, f, max_iters=5000, check_every=10, tol=1e-11, precision=capi.SOR_FP64)
+    assert res["converged"]
+    assert pins.rel_err3(got, pins.dst_solve3(u0, f)) < 1e-11
+
+
+def test_host_and_device_pointers_agree(ctx):
+    capi = capi_mod()
+    n = 20
+    u0 = wl.random_shell(n, 3)
+    a, ra = run3(ctx, u0, device=True, max_iters=30, tol=0.0, precision=capi.SOR_FP64)
+    b, rb = run3(ctx, u0, device=False, max_iters=30, tol=0.0, precision=capi.SOR_FP64)
+    assert np.array_equal(a, b) and ra["iterations"] == rb["iterations"] == 30
+
+
+def test_full_size_cube_bitwise(ctx):
+    """256^3 interior (258^3 array, the benchmark cube), 20 iterations with
+    the change measured every 10: the whole cube against the oracle."""
+    capi = capi_mod()
+    n = 256
+    u0 = wl.random_shell(n, 0)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, max_iters=20, check_every=10, tol=0.0)
+    got, res = run3(ctx, u0, omega=w, max_iters=20, check_every=10, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 20
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+def test_invalid_arguments(ctx):
+    capi = capi_mod()
+    u0 = wl.random_shell(4, 1)
+    for kw in (dict(precision=capi.SOR_FP32_REFINE), dict(stall_window=3), dict(omega=2.5),
+               dict(check_every=0), dict(flags=8)):
+        p = capi.make_params(4, **kw)
+        out = np.empty_like(u0)
+        st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, out.ctypes.data)
+        assert st == capi.SOR_ERR_INVALID_ARG, kw
+    p = capi.make_params(0)
+    st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, u0.ctypes.data)
+    assert st == capi.SOR_ERR_INVALID_ARG
