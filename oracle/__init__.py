@@ -7,8 +7,9 @@ imports the other; the seeded input generators in
 ``paper_1401_0763_gb300.workloads`` hold no arithmetic of the method and are
 the only thing both sides use.
 
-What each function computes is stated in ``sor_oracle.c`` (2D) and
-``sor3d_oracle.c`` (3D); in short:
+What each function computes is stated in ``sor_oracle.c`` (2D),
+``sor3d_oracle.c`` (3D) and ``sor9_oracle.c`` (four-colour, 9-point); in
+short:
 
 * :func:`sor_f64` -- Algorithm 1 of the paper (red phase, then black phase,
   convergence test every K iterations, Section 2.1 / Section 3.3) with the
@@ -21,9 +22,13 @@ What each function computes is stated in ``sor_oracle.c`` (2D) and
 * :func:`sor3d_f64`, :func:`sor3d_f32`, :func:`residual3d` -- the same
   iteration and residual on a cube with the 7-point stencil (the 3D grids the
   paper names as its next step, Section 5).
+* :func:`sor9_f64`, :func:`sor9_f32`, :func:`residual9` -- multi-colour SOR
+  (Section 3.1 names it beside red-black SOR): four colours for the compact
+  9-point stencil.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` and
-``tests/test_oracle3d_pins.py`` (dense direct solves, the explicit SOR
+``tests/test_oracle3d_pins.py`` and ``tests/test_oracle9_pins.py`` (dense
+direct solves, the explicit SOR
 iteration matrix, closed-form harmonic and quadratic solutions, a DST-I fast
 Poisson solve, SOR convergence theory and superposition/symmetry invariants).
 """
@@ -37,7 +42,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "sor_oracle.c"), os.path.join(_HERE, "sor3d_oracle.c")]
+_SRCS = [os.path.join(_HERE, "sor_oracle.c"), os.path.join(_HERE, "sor3d_oracle.c"),
+         os.path.join(_HERE, "sor9_oracle.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -78,8 +84,12 @@ def _load():
             lib.oracle_sor3d_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual3d.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.oracle_sor9_f64.argtypes = lib.oracle_sor3d_f64.argtypes
+            lib.oracle_sor9_f32.argtypes = lib.oracle_sor3d_f32.argtypes
+            lib.oracle_residual9.argtypes = lib.oracle_residual3d.argtypes
             for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine,
-                       lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d):
+                       lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d,
+                       lib.oracle_sor9_f64, lib.oracle_sor9_f32, lib.oracle_residual9):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -277,4 +287,64 @@ def residual3d(u, *, f=None):
 def resid_rel3d(u, *, f=None):
     """max|r~| / max|b~| on a cube (or max|r~| when the right side is zero)."""
     _, rm, bm = residual3d(u, f=f)
+    return rm / bm if bm > 0 else rm
+
+
+def sor9_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):
+    """Four-colour SOR on the 9-point stencil, FP64 (colour 2(i&1) + (j&1),
+    colours updated 0, 1, 2, 3).  Returns a dict like :func:`sor_f64`."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _grid(u0, n)
+    f = _src(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md, rr = ctypes.c_double(0), ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor9_f64(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
+                                 int(stop_mode), _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md),
+                                 ctypes.byref(rr), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor9_f64: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
+               final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def sor9_f32(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, trace=False):
+    """Four-colour 9-point SOR in FP32 arithmetic and storage."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _grid(u0, n)
+    f = _src(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md = ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor9_f32(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
+                                 _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor9_f32: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def residual9(u, *, f=None):
+    """Scaled 9-point residual r~ = 6h^2 f + 4 s4 + sd - 20u (ring 0) and
+    (max|r~|, max|b~|)."""
+    n = int(np.asarray(u).shape[0]) - 2
+    u = _grid(u, n)
+    f = _src(f, n)
+    r = np.zeros_like(u)
+    rm, bm = ctypes.c_double(0), ctypes.c_double(0)
+    rc = _load().oracle_residual9(n, _ptr(u), _ptr(f), _ptr(r), ctypes.byref(rm), ctypes.byref(bm))
+    if rc != 0:
+        raise ValueError("oracle_residual9: bad arguments")
+    return r, rm.value, bm.value
+
+
+def resid_rel9(u, *, f=None):
+    _, rm, bm = residual9(u, f=f)
     return rm / bm if bm > 0 else rm

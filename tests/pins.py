@@ -218,3 +218,105 @@ def cube_from(fn, n):
     u = fn(x, y, z)
     u[1:-1, 1:-1, 1:-1] = 0.0
     return u, fn(x, y, z)
+
+
+# ---------------------------------------------------------------------------
+# 9-point (compact) Laplacian, scaled by 6 h^2:
+#     20 u - 4 (N + S + W + E) - (NW + NE + SW + SE) = 6 h^2 f.
+# ---------------------------------------------------------------------------
+
+_NB9 = (((-1, 0), 4.0), ((1, 0), 4.0), ((0, -1), 4.0), ((0, 1), 4.0),
+        ((-1, -1), 1.0), ((-1, 1), 1.0), ((1, -1), 1.0), ((1, 1), 1.0))
+
+
+def dense_system9(u0, f=None):
+    """Dense A (n^2 x n^2) and b of the 9-point system for the grid u0."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    A = np.zeros((n * n, n * n))
+    b = np.zeros(n * n)
+    idx = interior_index(n)
+    for i in range(1, n + 1):
+        for j in range(1, n + 1):
+            r = idx[i - 1, j - 1]
+            A[r, r] = 20.0
+            b[r] = 6.0 * h2 * f[i - 1, j - 1] if f is not None else 0.0
+            for (di, dj), wgt in _NB9:
+                ii, jj = i + di, j + dj
+                if 1 <= ii <= n and 1 <= jj <= n:
+                    A[r, idx[ii - 1, jj - 1]] = -wgt
+                else:
+                    b[r] += wgt * u0[ii, jj]
+    return A, b
+
+
+def dense_solve9(u0, f=None):
+    n = u0.shape[0] - 2
+    A, b = dense_system9(u0, f)
+    u = u0.copy()
+    u[1:-1, 1:-1] = np.linalg.solve(A, b).reshape(n, n)
+    return u
+
+
+def dst_solve9(u0, f=None):
+    """Exact 9-point solution by the 2D DST-I: with cp = cos(p pi/(n+1)) the
+    operator's eigenvalues are 20 - 8 cp - 8 cq - 4 cp cq."""
+    n = u0.shape[0] - 2
+    h2 = (1.0 / (n + 1)) ** 2
+    b = np.zeros((n, n)) if f is None else 6.0 * h2 * np.asarray(f, dtype=np.float64).copy()
+    # ring contributions: 4 x edge neighbours, 1 x diagonal neighbours
+    b[0, :] += 4.0 * u0[0, 1:-1] + u0[0, :-2] + u0[0, 2:]
+    b[-1, :] += 4.0 * u0[-1, 1:-1] + u0[-1, :-2] + u0[-1, 2:]
+    b[:, 0] += 4.0 * u0[1:-1, 0] + u0[:-2, 0] + u0[2:, 0]
+    b[:, -1] += 4.0 * u0[1:-1, -1] + u0[:-2, -1] + u0[2:, -1]
+    # the four corner cells received their shared diagonal ring neighbour twice
+    b[0, 0] -= u0[0, 0]
+    b[0, -1] -= u0[0, -1]
+    b[-1, 0] -= u0[-1, 0]
+    b[-1, -1] -= u0[-1, -1]
+    p = np.arange(1, n + 1)
+    c = np.cos(p * np.pi / (n + 1))
+    lam = 20.0 - 8.0 * c[:, None] - 8.0 * c[None, :] - 4.0 * c[:, None] * c[None, :]
+    u = u0.copy()
+    u[1:-1, 1:-1] = scipy.fft.idstn(scipy.fft.dstn(b, type=1) / lam, type=1)
+    return u
+
+
+def multicolour_iteration9(u0, omega, iters, f=None):
+    """Four-colour SOR as a matrix splitting: unknowns ordered by colour
+    2(i&1) + (j&1) = 0, 1, 2, 3, x_{k+1} = (D - wL)^{-1}[((1-w)D + wU) x_k + w b]."""
+    n = u0.shape[0] - 2
+    A, b = dense_system9(u0, f)
+    ii, jj = np.meshgrid(np.arange(1, n + 1), np.arange(1, n + 1), indexing="ij")
+    colour = (2 * (ii & 1) + (jj & 1)).ravel()
+    order = np.concatenate([np.nonzero(colour == c)[0] for c in range(4)])
+    P = A[np.ix_(order, order)]
+    bp = b[order]
+    D = np.diag(np.diag(P))
+    L = -np.tril(P, -1)
+    U = -np.triu(P, 1)
+    lhs = D - omega * L
+    M = np.linalg.solve(lhs, (1.0 - omega) * D + omega * U)
+    cvec = np.linalg.solve(lhs, omega * bp)
+    x = u0[1:-1, 1:-1].ravel()[order].copy()
+    out = []
+    for _ in range(iters):
+        x = M @ x + cvec
+        full = np.empty(n * n)
+        full[order] = x
+        u = u0.copy()
+        u[1:-1, 1:-1] = full.reshape(n, n)
+        out.append(u)
+    return out
+
+
+def grid_from(fn, n):
+    """(n+2)^2 grid with fn(x, y) on the ring (corners included) and 0 inside,
+    plus fn on the whole grid (x = j h, y = i h)."""
+    h = 1.0 / (n + 1)
+    t = np.arange(n + 2) * h
+    y, x = np.meshgrid(t, t, indexing="ij")
+    full = fn(x, y)
+    u = full.copy()
+    u[1:-1, 1:-1] = 0.0
+    return u, full
