@@ -33,6 +33,8 @@ WORKLOAD = "paper-sized plain sweep: 4098x4098 array (4096^2 interior), random u
 FP64_FLOPS_PER_LUP = 6.0    # (1-w)u + (w/4)(N+S+W+E): 3 adds, 2 multiplies, 1 add
 HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once per iteration
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_fast<1,0> launch (ncu, this workload)
+FAST64_DRAM_BYTES_PER_LAUNCH = 157.64e6
 
 
 def dist_env():
@@ -277,9 +279,13 @@ def run_ours(args, ws, rank, local):
                        "l2": "inputs larger than L2 (134 MB natural in + 136 MB colour-split state + 134 MB out; "
                              "no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": None,
-                         "kernel": "k_sweep<double> (one colour phase)",
-                         "peak_source": "nominal GB300 FP64 rate (recipe); probe measured 1.20",
+                         "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": FAST64_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_unit": "bytes per launch (dram read + write)",
+                         "traffic_source": "ncu capture of k_sweep_fast<1,0> on this workload "
+                                           "(profiles/k_sweep_fast64_plate4096.md)",
+                         "kernel": "k_sweep_fast<1,0> (one FP64 colour phase)",
+                         "peak_source": "nominal GB300 FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz x 2 flops; "
+                                        "a probe of independent FP64 chains reached 5.29e11 operations/s",
                          "hbm_gbs": hbm_gbs_fp64, "hbm_frac": hbm_gbs_fp64 / peaks["hbm_gbs"],
                          "hbm_peak_source": peaks_src},
             "fp32": fp32,
@@ -547,8 +553,61 @@ def workload_cube256(args, ctx, capi, wl):
                        "l2": "inputs 2 x 68 MB FP64 per colour pair, above the 129 MB L2 in FP64"}}
 
 
+def workload_ninepoint4096(args, ctx, capi, wl):
+    """Four-colour SOR on the compact 9-point stencil (multi-colour SOR, Section 3.1): the 4098^2 plate of
+    the default workload (random edges U[0, 100], f = 0, w_opt), 1000 iterations with max|change| every 50,
+    FP64 and FP32, device-resident inputs, exact operation order (bitwise equal to the oracle).  The oracle is
+    timed on 10 iterations of the same plate on one host core."""
+    import numpy as np
+    import torch
+
+    import oracle
+    n, iters = 4096, 1000
+    u0_np = wl.random_edges(n, args.seed)
+    u0 = torch.from_numpy(u0_np).cuda()
+    out = torch.empty_like(u0)
+    w = capi.sor_omega_opt(n)
+    lines = {}
+    for name, prec in (("fp64", capi.SOR_FP64), ("fp32", capi.SOR_FP32)):
+        kw = dict(precision=prec, omega=w, tol=0.0, max_iters=iters, check_every=50)
+        for _ in range(args.warmup):
+            ctx.solve9(u0, out=out, **dict(kw, max_iters=100))
+        torch.cuda.synchronize()
+        dev = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, res = ctx.solve9(u0, out=out, **kw)
+            dev.append(res["device_s"])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        lup = float(n) * n * iters
+        lines[name] = {"glups": lup / float(np.median(dev)) / 1e9, "glups_call": lup / dt / 1e9,
+                       "solve_s": dt, "iterations": res["iterations"]}
+    # FP64: 11 flops per update (6 adds for the eight neighbours, 1 multiply by 4, 1 add, 2 multiplies, 1 add)
+    ach = 11.0 * lines["fp64"]["glups"] / 1e3
+    lines["fp64"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
+                                 "frac": ach / 1.25, "kernel": "k_sweep9<double,C>"}
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    lines["fp32"]["roofline"] = {"bound": "hbm", "achieved": 8.0 * lines["fp32"]["glups"], "peak": hbm,
+                                 "unit": "GB/s", "frac": 8.0 * lines["fp32"]["glups"] / hbm,
+                                 "kernel": "k_sweep9<float,C>", "peak_source": src}
+    cpu = None
+    if not args.no_cpu_baseline:
+        k = 10
+        t0 = time.perf_counter()
+        oracle.sor9_f64(u0_np, w, max_iters=k, check_every=50, tol=0.0)
+        ct = time.perf_counter() - t0
+        cpu = {"value": float(n) * n * k / ct / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} FP64 iterations of the same 4098^2 plate"}
+    return {"metric": "four-colour 9-point SOR GLUP/s (4098^2 plate)", "value": lines["fp64"]["glups"],
+            "unit": "GLUP/s", "higher_is_better": True, "dtype": "f64", "detail": lines, "cpu_baseline": cpu,
+            "config": {"workload": "4098^2 plate, random edges U[0,100], w_opt, 1000 iterations, max|change| every 50",
+                       "l2": "4 quarter arrays of 34 MB FP64 (134 MB in all), above the 129 MB L2"}}
+
+
 WORKLOADS = {"paper": workload_paper, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
-             "serve": workload_serve, "cube256": workload_cube256}
+             "serve": workload_serve, "cube256": workload_cube256, "ninepoint4096": workload_ninepoint4096}
 
 
 def run_workload(args):
