@@ -154,6 +154,24 @@ sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, c
 sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
                        sor_result *res);
 
+/* Blocking solve of one problem with the compact 9-point stencil by
+ * four-colour SOR (Section 3.1 names multi-colour SOR beside red-black SOR;
+ * the diagonal couplings of the 9-point stencil need four colours,
+ * c = 2 (i & 1) + (j & 1), updated in the order 0, 1, 2, 3).  Cell equation
+ * 20 u = 4 (N + S + W + E) + (NW + NE + SW + SE) + 6 h^2 f, update
+ *   U <- (1-w) U + (w/20) ((4 ((N + S) + (W + E)) + ((NW + NE) + (SW + SE))) + 6 h^2 f),
+ * every product and sum rounded on its own in that order (FP64 or FP32); the
+ * residual r~ = (6 h^2 f + (4 s4 + sd)) - 20 u is formed in FP64 and b~
+ * weighs the ring's edge neighbours by 4 and its diagonal ones by 1.
+ *   params: as for sor_solve with precision SOR_FP64 or SOR_FP32, flags 0 or
+ *           SOR_FLAG_EXACT_ORDER, stall_window 0 (else SOR_ERR_INVALID_ARG);
+ *           omega <= 0 selects 2 / (1 + sin(pi / (N+1))).
+ *   u0, f, u_out: as for sor_solve ((N+2)^2, N^2, (N+2)^2; host or device);
+ *          the 9-point stencil also reads the ring's corners.
+ * Device memory counts against the context's budget. */
+sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
+                      sor_result *res);
+
 /* Non-blocking submission to the context's continuous-batching scheduler.
  * u0 and f are copied before the call returns.  u_out must stay valid until
  * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.

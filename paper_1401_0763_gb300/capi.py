@@ -48,7 +48,8 @@ SOR_OPT_CLUSTER = 7
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
-            "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d")
+            "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d",
+            "sor_solve9")
 
 
 class sor_params(ctypes.Structure):
@@ -109,6 +110,7 @@ def load(build_if_missing: bool = False):
                                   P(sor_result)]
         lib.sor_solve3d.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     P(sor_result)]
+        lib.sor_solve9.argtypes = lib.sor_solve.argtypes
         lib.sor_batch_submit.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, P(ctypes.c_uint64)]
         lib.sor_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(sor_result)]
@@ -280,6 +282,29 @@ class Context:
         p = make_params(n, **kw)
         st, res = self.solve3d_raw(p, _ptr(u0), _ptr(f), _ptr(out))
         self._check(st, "sor_solve3d")
+        return out, res.as_dict()
+
+    def solve9_raw(self, params: sor_params, u0_ptr, f_ptr, out_ptr):
+        """sor_solve9 on raw addresses; returns (status, result)."""
+        res = sor_result()
+        st = self._lib.sor_solve9(self._h, ctypes.byref(params), ctypes.c_void_p(u0_ptr),
+                                  ctypes.c_void_p(f_ptr) if f_ptr else None, ctypes.c_void_p(out_ptr),
+                                  ctypes.byref(res))
+        return st, res
+
+    def solve9(self, u0, f=None, out=None, **kw) -> tuple:
+        """Blocking four-colour SOR solve with the 9-point stencil.  ``u0`` is
+        (n+2, n+2), ``f`` is (n, n) or None.  Returns (u_out, result dict)."""
+        n = int(u0.shape[0]) - 2
+        if tuple(u0.shape) != (n + 2, n + 2):
+            raise ValueError("u0 must be square (n+2, n+2)")
+        if f is not None and tuple(f.shape) != (n, n):
+            raise ValueError("f must be (n, n)")
+        if out is None:
+            out = np.empty_like(u0) if isinstance(u0, np.ndarray) else u0.new_empty(u0.shape)
+        p = make_params(n, **kw)
+        st, res = self.solve9_raw(p, _ptr(u0), _ptr(f), _ptr(out))
+        self._check(st, "sor_solve9")
         return out, res.as_dict()
 
     def submit(self, u0, f=None, out=None, **kw):

@@ -178,6 +178,10 @@ int refine_dbuf(const Plan& p);
 sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
                           sor_result* res);
 
+// Four-colour 9-point solve (sor_solve9); the caller holds solve_mu.
+sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                           sor_result* res);
+
 // 3D cube solve (sor_solve3d); the caller holds solve_mu.
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res);
