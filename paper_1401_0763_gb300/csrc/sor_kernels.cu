@@ -17,6 +17,7 @@
 // FP64 forms), so their results do not depend on compiler contraction.
 #include <cuda_runtime.h>
 
+#include "sor_bits.cuh"
 #include "sor_device.cuh"
 #include "sor_devfn.cuh"
 #include "sor_kernels.h"
@@ -1099,13 +1100,17 @@ int tb_out_cols(int T) {
 // residual pass (FP64), both colours per tile
 // ------------------------------------------------------------------------------------------------
 
+// FP32 or FP64 value as FP64 (the widening is exact; done on the integer units).
+__device__ __forceinline__ double as_f64(float x) { return widen_f32(x); }
+__device__ __forceinline__ double as_f64(double x) { return x; }
+
 // Loads 4 consecutive values of a colour array (FP64 or FP32) as FP64.
 template <typename T>
 __device__ __forceinline__ void load_u4(const T* X, size_t e, double (&v)[4]) {
   T t[4];
   load4(X + e, t);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) v[k] = (double)t[k];
+  for (int k = 0; k < 4; ++k) v[k] = as_f64(t[k]);
 }
 
 // Defect correction, first half of a correction step: u += (double)d over the
@@ -1145,7 +1150,7 @@ __global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict
         load4(U, u);
         load4(D, d);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) u[v] = __dadd_rn(u[v], (double)d[v]);
+        for (int v = 0; v < 4; ++v) u[v] = __dadd_rn(u[v], widen_f32(d[v]));
         if (q0 + 3 <= qlim) {
           store4(U, u);
         } else {
@@ -1156,6 +1161,48 @@ __global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict
       }
     }
   }
+}
+
+// Residual of this lane's 4 cells of one row with row parity S (fixed at
+// compile time, so W / E are plain register choices):
+//   r~ = (g + ((N + S) + (W + E))) - 4u,
+// 4u and the rounding of r~ to FP32 being exact bit operations on the integer
+// units (the FP64 rate bounds this pass).  Refine role: r~ (FP32) is written
+// to R (this lane's first cell).  Returns max |r~| over the interior cells.
+template <int ROLE, int S>
+__device__ __forceinline__ unsigned long long resid_cells(const double (&own)[4], const double (&nm)[4],
+                                                          const double (&nc)[4], const double (&np)[4],
+                                                          const double (&gv)[4], double left, double right, int q0,
+                                                          int n, float* R) {
+  double Wv[4], Ev[4];
+  if (S == 0) {
+    Wv[0] = nc[0]; Wv[1] = nc[1]; Wv[2] = nc[2]; Wv[3] = nc[3];
+    Ev[0] = nc[1]; Ev[1] = nc[2]; Ev[2] = nc[3]; Ev[3] = right;
+  } else {
+    Wv[0] = left; Wv[1] = nc[0]; Wv[2] = nc[1]; Wv[3] = nc[2];
+    Ev[0] = nc[0]; Ev[1] = nc[1]; Ev[2] = nc[2]; Ev[3] = nc[3];
+  }
+  const int qlim = (n + S) >> 1;
+  unsigned long long rm = 0;
+  float rv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const double nb = __dadd_rn(__dadd_rn(nm[v], np[v]), __dadd_rn(Wv[v], Ev[v]));
+    const double r = __dsub_rn(__dadd_rn(gv[v], nb), times4(own[v]));
+    const bool in = (q0 + v) <= qlim;
+    if (in) rm = umax64(rm, abs_bits(r));
+    if (ROLE == kResidRefine) rv[v] = in ? narrow_f64(r) : 0.0f;
+  }
+  if (ROLE == kResidRefine) {
+    if ((q0 + 3) <= qlim) {
+      store4(R, rv);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if ((q0 + v) <= qlim) R[v] = rv[v];
+    }
+  }
+  return rm;
 }
 
 // ROLE kResidFinal / kResidCheck: plain slots, iterate x[xbuf] (type T).
@@ -1232,38 +1279,13 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
         }
         double left = __shfl_up_sync(0xffffffffu, nc[3], 1);
         double right = __shfl_down_sync(0xffffffffu, nc[0], 1);
-        if (lane == 0) left = (double)Xo[eidx(i, q0 - 1, pitch)];
-        if (lane == 31) right = (double)Xo[eidx(i, q0 + kVec, pitch)];
-        const int s = (i + c0) & 1;
-        const int qlim = (n + s) >> 1;
-        double Wv[4], Ev[4];
-        if (s == 0) {
-          Wv[0] = nc[0]; Wv[1] = nc[1]; Wv[2] = nc[2]; Wv[3] = nc[3];
-          Ev[0] = nc[1]; Ev[1] = nc[2]; Ev[2] = nc[3]; Ev[3] = right;
-        } else {
-          Wv[0] = left; Wv[1] = nc[0]; Wv[2] = nc[1]; Wv[3] = nc[2];
-          Ev[0] = nc[0]; Ev[1] = nc[1]; Ev[2] = nc[2]; Ev[3] = nc[3];
-        }
-        float rv[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const double nb = __dadd_rn(__dadd_rn(nm[v], np[v]), __dadd_rn(Wv[v], Ev[v]));
-          const double r = __dadd_rn(__dadd_rn(gv[v], nb), -__dmul_rn(4.0, own[v]));
-          const bool in = (q0 + v) <= qlim;
-          if (in) rm = umax64(rm, abs_bits(r));
-          rv[v] = in ? (float)r : 0.0f;
-        }
-        const bool all_in = (q0 + 3) <= qlim;
-        if (ROLE == kResidRefine) {
-          float* R = c0 ? R1 : R0;
-          if (all_in) {
-            store4(R + eidx(i, q0, pitch), rv);
-          } else {
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-              if ((q0 + v) <= qlim) R[eidx(i, q0 + v, pitch)] = rv[v];
-          }
-        }
+        if (lane == 0) left = as_f64(Xo[eidx(i, q0 - 1, pitch)]);
+        if (lane == 31) right = as_f64(Xo[eidx(i, q0 + kVec, pitch)]);
+        float* R = (ROLE == kResidRefine) ? (c0 ? R1 : R0) + eidx(i, q0, pitch) : nullptr;
+        if (((i + c0) & 1) == 0)
+          rm = umax64(rm, resid_cells<ROLE, 0>(own, nm, nc, np, gv, left, right, q0, n, R));
+        else
+          rm = umax64(rm, resid_cells<ROLE, 1>(own, nm, nc, np, gv, left, right, q0, n, R));
       }
     }
     block_max_to(rm, &st->rmax_bits, red);
