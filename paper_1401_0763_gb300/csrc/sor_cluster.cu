@@ -5,14 +5,16 @@
 // arrays per CTA).  The kernel then runs Algorithm 1 to the end by itself:
 // each iteration is the red phase over every CTA's rows, a cluster barrier,
 // the black phase, a cluster barrier (the phase barrier of Section 3.2 as a
-// hardware barrier); the rows just above / below a band are read from the
-// neighbouring CTA's shared memory.  On tested iterations every CTA publishes
-// its max |change| (or its largest scaled residual), all of them read the
-// cluster-wide maximum after the barrier and take the same stop decision.
-// One launch replaces 2 launches per iteration, which dominate the time of a
-// small grid.  The update is the exact-order form of k_sweep (every product
-// and sum rounded on its own), so results match the unfused exact path and
-// the CPU oracle bit for bit.
+// hardware barrier).  Every CTA also keeps ghost copies of the row just above
+// and just below its band; after a phase it pushes the two edge rows it
+// updated into its neighbours' ghost rows (distributed shared memory stores),
+// so the update loop itself reads only local shared memory.  On tested
+// iterations every CTA publishes its max |change| (or its largest scaled
+// residual), all of them read the cluster-wide maximum after the barrier and
+// take the same stop decision.  One launch replaces 2 launches per iteration,
+// which dominate the time of a small grid.  The update is the exact-order
+// form of k_sweep (every product and sum rounded on its own), so results match
+// the unfused exact path and the CPU oracle bit for bit.
 #include <cooperative_groups.h>
 
 #include "sor_devfn.cuh"
@@ -23,6 +25,11 @@ namespace cg = cooperative_groups;
 namespace sorgb {
 
 constexpr int kClusterThreads = 512;
+constexpr int kClusterWarps = kClusterThreads / 32;
+
+// Shared-memory rows per colour of one CTA: its band of R rows plus a ghost
+// row on each side.
+__host__ __device__ __forceinline__ int cluster_band_rows(int m, int C) { return (m + C - 1) / C; }
 
 template <typename T>
 __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDesc* __restrict__ slots,
@@ -31,38 +38,32 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
   const int C = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ unsigned long long wmax[kClusterThreads / 32];
+  __shared__ unsigned long long wmax[kClusterWarps];
   __shared__ unsigned long long pub[2];  // this CTA's max |change| and max |r~| of the current test
   const SlotDesc& sd = slots[slot];
   SlotState* st = states + slot;
   const int n = sd.n, pitch = sd.pitch, m = n + 2;
-  const int R = (m + C - 1) / C;  // rows per CTA
-  const int rlo = rank * R, rhi = min(m, rlo + R);
-  T* S[2] = {(T*)csm, (T*)csm + (size_t)R * pitch};
+  const int R = cluster_band_rows(m, C);
+  const int rlo = min(m, rank * R), rhi = min(m, rlo + R);
+  const int nr = rhi - rlo;  // rows of the band (0 for CTAs past the grid)
+  // local row lr holds grid row rlo - 1 + lr: lr = 0 and lr = nr + 1 are the ghosts
+  T* const S0 = (T*)csm;
+  T* const S1 = (T*)csm + (size_t)(R + 2) * pitch;
   const int xbuf = st->xbuf;
-  const T* Xg[2] = {(const T*)sd.x[xbuf][0], (const T*)sd.x[xbuf][1]};
-  const T* Gg[2] = {(const T*)sd.g[0], (const T*)sd.g[1]};
 
-  // stage this CTA's rows of both colours
-  for (int idx = threadIdx.x; idx < 2 * (rhi - rlo) * pitch; idx += blockDim.x) {
-    const int c = idx / ((rhi - rlo) * pitch);
-    const int e = idx - c * (rhi - rlo) * pitch;
-    S[c][e] = Xg[c][(size_t)rlo * pitch + e];
+  // stage the band and both ghost rows of both colours
+  for (int idx = threadIdx.x; idx < 2 * (nr + 2) * pitch; idx += blockDim.x) {
+    const int c = idx / ((nr + 2) * pitch);
+    const int e = idx - c * (nr + 2) * pitch;
+    const int lr = e / pitch;
+    const int r = rlo - 1 + lr;
+    if (r >= 0 && r < m) (c ? S1 : S0)[e] = ((const T*)sd.x[xbuf][c])[(size_t)(rlo - 1) * pitch + e];
   }
   cluster.sync();
 
-  // neighbour-colour value of row `row` (any CTA's), packed column q
-  auto other = [&](int c, int row, int q) -> T {
-    const int owner = row / R;
-    const T* base = owner == rank ? S[c] : cluster.map_shared_rank(S[c], owner);
-    return base[(size_t)(row - owner * R) * pitch + q + kOff];
-  };
-
   const T a = sizeof(T) == 4 ? (T)sd.a32 : (T)sd.a64;
   const T b = sizeof(T) == 4 ? (T)sd.b32 : (T)sd.b64;
-  const int qc = (n + 1) / 2;                         // widest interior packed row
-  const int r_first = max(rlo, 1), r_last = min(rhi, n + 1);  // interior rows held here: [r_first, r_last)
-  const int cells = max(0, r_last - r_first) * qc;
+  const int r_first = max(rlo, 1), r_last = min(rhi, n + 1);  // interior rows of the band: [r_first, r_last)
   const double bmax = bits_to_double(st->bmax_bits);
   int k = st->iters, converged = 0, run = st->stall_run;
   double best_rho = st->best_rho, last_dmax = st->last_dmax, last_rho = st->last_rho;
@@ -75,13 +76,33 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned long long mm = 0;
-      for (int w = 0; w < kClusterThreads / 32; ++w) mm = umax64(mm, wmax[w]);
+      for (int w = 0; w < kClusterWarps; ++w) mm = umax64(mm, wmax[w]);
       pub[which] = mm;
     }
     cluster.sync();
     unsigned long long all = 0;
     for (int r = 0; r < C; ++r) all = umax64(all, *cluster.map_shared_rank(&pub[which], r));
     return all;
+  };
+
+  // after phase c: copy the band's first / last row of colour c into the
+  // ghost rows of the CTAs above / below (interior rows only: the ring never
+  // changes and was staged into the ghosts at the start)
+  auto push_edges = [&](T* Sc) {
+    __syncthreads();
+    if (nr > 0) {
+      if (rank > 0 && rlo >= 1 && rlo <= n) {
+        // the band above ends at row rlo - 1: its ghost row below is local row R + 1
+        T* dst = cluster.map_shared_rank(Sc, rank - 1) + (size_t)(R + 1) * pitch;
+        const T* src = Sc + (size_t)1 * pitch;
+        for (int e = threadIdx.x; e < pitch; e += blockDim.x) dst[e] = src[e];
+      }
+      if (rank + 1 < C && rhi < m && rhi - 1 >= 1 && rhi - 1 <= n) {
+        T* dst = cluster.map_shared_rank(Sc, rank + 1);  // its ghost row above is local row 0
+        const T* src = Sc + (size_t)nr * pitch;
+        for (int e = threadIdx.x; e < pitch; e += blockDim.x) dst[e] = src[e];
+      }
+    }
   };
 
   while (k < sd.max_iters) {
@@ -91,30 +112,29 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
     unsigned dm32 = 0;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
-      T* Sc = S[c];
-      for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
-        const int row = r_first + idx / qc;
-        const int q = 1 + idx % qc;
+      T* Sc = c ? S1 : S0;
+      const T* So = c ? S0 : S1;
+      const T* Gc = (const T*)sd.g[c];
+      for (int row = r_first + warp; row < r_last; row += kClusterWarps) {
         const int s = (row + c) & 1;
-        if (q > ((n + s) >> 1)) continue;
-        const int oc = c ^ 1;
-        const size_t le = (size_t)(row - rlo) * pitch + q + kOff;
-        const T own = Sc[le];
-        const T N = other(oc, row - 1, q);
-        const T Sv = other(oc, row + 1, q);
-        const T W = S[oc][le - s];
-        const T E = S[oc][le - s + 1];
-        T sum = radd(radd(N, Sv), radd(W, E));
-        if (Gg[c]) sum = radd(sum, Gg[c][(size_t)row * pitch + q + kOff]);
-        const T nu = radd(rmul(a, own), rmul(b, sum));
-        Sc[le] = nu;
-        if (measure) {
-          if (sizeof(T) == 4)
-            dm32 = max(dm32, abs_bits32((float)radd(nu, -own)));
-          else
-            dm = umax64(dm, abs_bits((double)radd(nu, -own)));
+        const int qlim = (n + s) >> 1;
+        const size_t lb = (size_t)(row - rlo + 1) * pitch + kOff;
+        for (int q = 1 + lane; q <= qlim; q += 32) {
+          const size_t le = lb + q;
+          const T own = Sc[le];
+          T sum = radd(radd(So[le - pitch], So[le + pitch]), radd(So[le - s], So[le - s + 1]));
+          if (Gc) sum = radd(sum, Gc[(size_t)row * pitch + q + kOff]);
+          const T nu = radd(rmul(a, own), rmul(b, sum));
+          Sc[le] = nu;
+          if (measure) {
+            if (sizeof(T) == 4)
+              dm32 = max(dm32, abs_bits32((float)radd(nu, -own)));
+            else
+              dm = umax64(dm, abs_bits((double)radd(nu, -own)));
+          }
         }
       }
+      push_edges(Sc);
       cluster.sync();
     }
     if (measure) {
@@ -130,18 +150,20 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
       unsigned long long rm = 0;
       for (int c = 0; c < 2; ++c) {
         const double* G64 = sd.g64[c];
-        for (int idx = threadIdx.x; idx < cells; idx += blockDim.x) {
-          const int row = r_first + idx / qc;
-          const int q = 1 + idx % qc;
+        const T* Sc = c ? S1 : S0;
+        const T* So = c ? S0 : S1;
+        for (int row = r_first + warp; row < r_last; row += kClusterWarps) {
           const int s = (row + c) & 1;
-          if (q > ((n + s) >> 1)) continue;
-          const int oc = c ^ 1;
-          const size_t le = (size_t)(row - rlo) * pitch + q + kOff;
-          const double nb = __dadd_rn(__dadd_rn((double)other(oc, row - 1, q), (double)other(oc, row + 1, q)),
-                                      __dadd_rn((double)S[oc][le - s], (double)S[oc][le - s + 1]));
-          const double g = G64 ? G64[(size_t)row * pitch + q + kOff] : 0.0;
-          const double r = __dadd_rn(__dadd_rn(g, nb), -__dmul_rn(4.0, (double)S[c][le]));
-          rm = umax64(rm, abs_bits(r));
+          const int qlim = (n + s) >> 1;
+          const size_t lb = (size_t)(row - rlo + 1) * pitch + kOff;
+          for (int q = 1 + lane; q <= qlim; q += 32) {
+            const size_t le = lb + q;
+            const double nb = __dadd_rn(__dadd_rn((double)So[le - pitch], (double)So[le + pitch]),
+                                        __dadd_rn((double)So[le - s], (double)So[le - s + 1]));
+            const double g = G64 ? G64[(size_t)row * pitch + q + kOff] : 0.0;
+            const double r = __dadd_rn(__dadd_rn(g, nb), -__dmul_rn(4.0, (double)Sc[le]));
+            rm = umax64(rm, abs_bits(r));
+          }
         }
       }
       const double rmax = bits_to_double(cluster_max(rm, 1));
@@ -163,12 +185,11 @@ __global__ void __launch_bounds__(kClusterThreads) k_cluster_solve(const SlotDes
       }
     }
   }
-  // write the rows back and record the outcome (every CTA took the same decisions)
-  T* Xo[2] = {(T*)sd.x[xbuf][0], (T*)sd.x[xbuf][1]};
-  for (int idx = threadIdx.x; idx < 2 * (rhi - rlo) * pitch; idx += blockDim.x) {
-    const int c = idx / ((rhi - rlo) * pitch);
-    const int e = idx - c * (rhi - rlo) * pitch;
-    Xo[c][(size_t)rlo * pitch + e] = S[c][e];
+  // write the band back and record the outcome (every CTA took the same decisions)
+  for (int idx = threadIdx.x; idx < 2 * nr * pitch; idx += blockDim.x) {
+    const int c = idx / (nr * pitch);
+    const int e = idx - c * nr * pitch;
+    ((T*)sd.x[xbuf][c])[(size_t)rlo * pitch + e] = (c ? S1 : S0)[(size_t)pitch + e];
   }
   if (rank == 0 && threadIdx.x == 0) {
     st->iters = k;
@@ -211,8 +232,8 @@ static cudaError_t cluster_config(int n, int pitch, int* csize, size_t* smem) {
     cached = cs >= 16 ? 16 : 8;
   }
   *csize = cached;
-  const int R = (n + 2 + cached - 1) / cached;
-  *smem = 2ull * R * pitch * sizeof(T);
+  const int R = cluster_band_rows(n + 2, cached);
+  *smem = 2ull * (R + 2) * pitch * sizeof(T);
   return cudaSuccess;
 }
 

@@ -125,7 +125,7 @@ __device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st
 // exact operation order).  MEASURE: also return max |change| (as the bits of
 // a non-negative double); a compile-time flag so that no |change| work is
 // issued on the iterations that do not test it.
-template <typename T, int MODE, bool MEASURE>
+template <typename T, int MODE, bool MEASURE, bool HAS_G>
 __device__ __forceinline__ unsigned long long sweep_rows(T* __restrict__ X, const T* __restrict__ O,
                                                          const T* __restrict__ G, T a, T b, int pitch, int n,
                                                          int colour, int q0, int i0, int i1, int lane, bool zero_all,
@@ -155,7 +155,7 @@ __device__ __forceinline__ unsigned long long sweep_rows(T* __restrict__ X, cons
       } else {
         load4(X + eidx(i, q0, pitch), own);
       }
-      if (G) load4(G + eidx(i, q0, pitch), gv);
+      if (HAS_G) load4(G + eidx(i, q0, pitch), gv);
       T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
       T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
       if (!zero_all) {
@@ -179,7 +179,7 @@ __device__ __forceinline__ unsigned long long sweep_rows(T* __restrict__ X, cons
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         T sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
-        if (G) sum = radd(sum, gv[v]);
+        if (HAS_G) sum = radd(sum, gv[v]);
         const T nu = radd(rmul(a, own[v]), rmul(b, sum));
         const bool in = (q0 + v) <= qlim;
         all_in = all_in && in;
@@ -249,10 +249,18 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__
     const int i0 = tl.row0 + wy * rows_per_warp;
     const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
     unsigned long long dm = 0;
-    if (MODE == 0 && c.measure)
-      dm = sweep_rows<T, MODE, true>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own);
-    else
-      (void)sweep_rows<T, MODE, false>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own);
+    // the source term is a compile-time choice: as a runtime test the compiler
+    // issues its addition speculatively, one more FP64 operation per cell
+    if (MODE == 0 && c.measure) {
+      dm = G ? sweep_rows<T, MODE, true, true>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own)
+             : sweep_rows<T, MODE, true, false>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all,
+                                                zero_own);
+    } else if (G) {
+      (void)sweep_rows<T, MODE, false, true>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all, zero_own);
+    } else {
+      (void)sweep_rows<T, MODE, false, false>(X, O, G, a, b, pitch, n, colour, q0, i0, i1, lane, zero_all,
+                                              zero_own);
+    }
     if (MODE == 0) {
       if (c.measure) block_max_to(dm, &st->dmax_bits, red);
       if (colour == 1) {
@@ -1189,9 +1197,10 @@ __device__ __forceinline__ unsigned long long resid_cells(const double (&own)[4]
   for (int v = 0; v < 4; ++v) {
     const double nb = __dadd_rn(__dadd_rn(nm[v], np[v]), __dadd_rn(Wv[v], Ev[v]));
     const double r = __dsub_rn(__dadd_rn(gv[v], nb), times4(own[v]));
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
     const bool in = (q0 + v) <= qlim;
-    if (in) rm = umax64(rm, abs_bits(r));
-    if (ROLE == kResidRefine) rv[v] = in ? narrow_f64(r) : 0.0f;
+    if (in) rm = umax64(rm, rb & 0x7fffffffffffffffull);
+    if (ROLE == kResidRefine) rv[v] = in ? narrow_f64(__longlong_as_double((long long)rb)) : 0.0f;
   }
   if (ROLE == kResidRefine) {
     if ((q0 + 3) <= qlim) {
