@@ -107,7 +107,7 @@ __global__ void k_unpack3d(const T* __restrict__ x0, const T* __restrict__ x1, i
 }
 
 // Rows [i0, i1) of plane k for one warp, one colour phase, exact order.
-template <typename T, bool MEASURE>
+template <typename T, bool MEASURE, bool HAS_G>
 __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, const T* __restrict__ O,
                                                           const T* __restrict__ G, T a, T b, int pitch, int m, int n,
                                                           int colour, int k, int q0, int i0, int i1, int lane) {
@@ -123,7 +123,7 @@ __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, con
     load4(X + e3(k, i, q0, m, pitch), own);
     load4(O + e3(k - 1, i, q0, m, pitch), dn);
     load4(O + e3(k + 1, i, q0, m, pitch), up);
-    if (G) load4(G + e3(k, i, q0, m, pitch), gv);
+    if (HAS_G) load4(G + e3(k, i, q0, m, pitch), gv);
     T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
     T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
     if (lane == 0) left = O[e3(k, i, q0 - 1, m, pitch)];
@@ -142,7 +142,7 @@ __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, con
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       T sum = radd(radd(radd(om[v], op[v]), radd(W[v], E[v])), radd(dn[v], up[v]));
-      if (G) sum = radd(sum, gv[v]);
+      if (HAS_G) sum = radd(sum, gv[v]);
       const T nu = radd(rmul(a, own[v]), rmul(b, sum));
       const bool in = (q0 + v) <= qlim;
       // cells past the interior keep their value (the whole vector is written back)
@@ -214,10 +214,15 @@ __global__ void __launch_bounds__(kThreads) k_sweep3d(const Desc3* __restrict__ 
     const int i0 = ib + wy * rpw;
     const int i1 = min(i0 + rpw, ib + tl.nrows);
     unsigned long long dm = 0;
+    // the source term is a compile-time choice: as a runtime test the compiler
+    // issues its addition speculatively, one more FP64 operation per cell
     if (measure)
-      dm = sweep3_rows<T, true>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
+      dm = G ? sweep3_rows<T, true, true>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane)
+             : sweep3_rows<T, true, false>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
+    else if (G)
+      (void)sweep3_rows<T, false, true>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
     else
-      (void)sweep3_rows<T, false>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
+      (void)sweep3_rows<T, false, false>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
     if (measure) block_max_to(dm, &st->dmax_bits, red);
     if (colour == 1) {
       __threadfence();

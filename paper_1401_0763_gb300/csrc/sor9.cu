@@ -118,7 +118,7 @@ __device__ __forceinline__ void we_of(const T (&v)[4], const T* __restrict__ row
 }
 
 // Rows [a0, a1) of quarter C for one warp, exact order.
-template <typename T, int C, bool MEASURE>
+template <typename T, int C, bool MEASURE, bool HAS_G>
 __device__ __forceinline__ unsigned long long sweep9_rows(const Desc9& d, int q0, int a0, int a1, int lane) {
   constexpr int PI = C >> 1, PJ = C & 1;
   unsigned long long dm = 0;
@@ -143,7 +143,7 @@ __device__ __forceinline__ unsigned long long sweep9_rows(const Desc9& d, int q0
     load4(Q3 + e9(r + 1 - PI, q0, pitch), s3);
     load4(Q1 + e9(r, q0, pitch), w1);
     load4(X + e9(r, q0, pitch), own);
-    if (G) load4(G + e9(r, q0, pitch), gv);
+    if (HAS_G) load4(G + e9(r, q0, pitch), gv);
     T W[4], E[4], NW[4], NE[4], SW[4], SE[4];
     we_of<T, PJ>(w1, Q1 + (size_t)r * pitch, q0, lane, W, E);
     we_of<T, PJ>(n3, Q3 + (size_t)(r - PI) * pitch, q0, lane, NW, NE);
@@ -154,7 +154,7 @@ __device__ __forceinline__ unsigned long long sweep9_rows(const Desc9& d, int q0
       const T s4 = radd(radd(n2[v], s2[v]), radd(W[v], E[v]));
       const T sd = radd(radd(NW[v], NE[v]), radd(SW[v], SE[v]));
       T s = radd(rmul(four, s4), sd);
-      if (G) s = radd(s, gv[v]);
+      if (HAS_G) s = radd(s, gv[v]);
       const T nu = radd(rmul(a, own[v]), rmul(b, s));
       const bool in = (q0 + v) <= blim;
       nv[v] = in ? nu : own[v];  // cells past the interior keep their value
@@ -217,10 +217,15 @@ __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ d
     const int a0 = tl.row0 + wy * rpw;
     const int a1 = min(min(a0 + rpw, tl.row0 + tl.nrows), alim + 1);
     unsigned long long dm = 0;
+    // the source term is a compile-time choice (as a runtime test its
+    // addition is issued speculatively)
+    const bool has_g = d.g[C] != nullptr;
     if (measure)
-      dm = sweep9_rows<T, C, true>(d, q0, a0, a1, lane);
+      dm = has_g ? sweep9_rows<T, C, true, true>(d, q0, a0, a1, lane) : sweep9_rows<T, C, true, false>(d, q0, a0, a1, lane);
+    else if (has_g)
+      (void)sweep9_rows<T, C, false, true>(d, q0, a0, a1, lane);
     else
-      (void)sweep9_rows<T, C, false>(d, q0, a0, a1, lane);
+      (void)sweep9_rows<T, C, false, false>(d, q0, a0, a1, lane);
     if (measure) block_max_to(dm, &st->dmax_bits, red);
     if (C == 3) {
       __threadfence();
