@@ -62,6 +62,9 @@ struct SlotDesc {
                         //          refine -> scaled residual r~ rounded to FP32
   double* u[2][2];      // refine: FP64 solution [buffer][colour]
   const double* g64[2]; // h^2 f in FP64 [colour] or null (residual passes)
+  const double* ring[2]; // FP64 default path: unscaled Dirichlet ring cells of each colour array, saved
+                         // after packing: [row 0: pitch][row N+1: pitch][column q = 0: N+2 rows]
+                         // [east ring column: N+2 rows]; null elsewhere
   int n, pitch, qmax, kind;
   int sweep_tiles;      // tiles of this slot in one sweep launch
   int resid_tiles;      // tiles of this slot in one residual launch

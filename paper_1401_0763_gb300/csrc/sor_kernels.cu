@@ -301,33 +301,22 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__
 //     of the chunk returns to unscaled values (X' = alpha X + beta Sigma),
 //     so between chunks -- where convergence is tested, max|change| measured
 //     and the result read -- the arrays hold u itself.
+//     The Dirichlet ring cells must be read at the scale of their colour in
+//     each phase.  The phase that updates colour c (and never reads colour
+//     c's ring) rewrites colour c's ring cells as (unscaled value) x (the scale
+//     the next phase reads colour c at), from a copy saved after packing; the
+//     last phases of a chunk write scale 1, so between chunks the ring is
+//     unscaled again.  Readers never rescale, and every strip does the same
+//     work per row.
 // Every cell's expression depends only on its own neighbours and the launch
 // constants, never on the tiling, so results are reproducible bit for bit
 // across tile shapes and batch compositions.
 struct FastPhase {
   double alpha, beta, gamma, dscale;
-  double bscale;  // scale the neighbour colour is carried at in this phase; Dirichlet ring values
-                  // (never updated, so always unscaled) are multiplied by it when read
+  double nscale;  // scale at which the next phase reads this phase's colour: this phase writes its
+                  // colour's Dirichlet ring cells as (unscaled value) x nscale
   int last;       // this phase belongs to the last iteration of its chunk (values unscaled after it)
 };
-
-// Multiplies the entries of a loaded neighbour vector (row r, packed columns
-// q..q+3 of the neighbour colour) that are not interior cells by bs.
-__device__ __forceinline__ void scale_ring4(double (&v)[4], int r, int q, int n, int ocol, double bs, bool edge) {
-  if (r == 0 || r == n + 1) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __dmul_rn(v[k], bs);
-  } else if (edge) {
-    const int lim = (n + ((r + ocol) & 1)) >> 1;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (q + k < 1 || q + k > lim) v[k] = __dmul_rn(v[k], bs);
-  }
-}
-__device__ __forceinline__ double scale_ring1(double v, int r, int q, int n, int ocol, double bs) {
-  const int lim = (n + ((r + ocol) & 1)) >> 1;
-  return (r == 0 || r == n + 1 || q < 1 || q > lim) ? __dmul_rn(v, bs) : v;
-}
 
 // Register state of one warp walking down a strip of rows: the neighbour-colour
 // rows i-1 and i, and the lower-right pair sums of the previous row.
@@ -418,31 +407,16 @@ __device__ __forceinline__ void fast_read(const FastStage<HAS_G>* st, int lane, 
   r.er = st->edge[1];
 }
 
-// EDGE strips: the only ring value of row i+1 an interior cell of row i reads
-// is the east ring cell q = qlim_i + 1 (q >= 1 holds in every strip), where
-// qlim_i is this row's own interior limit; one multiply per lane.
-template <int S>
-__device__ __forceinline__ void fast_scale_east(double (&op)[4], int n, int q0, double bs) {
-  const int vr = ((n + S) >> 1) + 1 - q0;
-  double x = vr <= 0 ? op[0] : vr == 1 ? op[1] : vr == 2 ? op[2] : op[3];
-  x = __dmul_rn(x, bs);
-  if (vr == 0) op[0] = x;
-  else if (vr == 1) op[1] = x;
-  else if (vr == 2) op[2] = x;
-  else if (vr == 3) op[3] = x;
-}
-
 // The cells of one row (parity S = (i + colour) & 1, known at compile time,
 // which fixes where W / E come from and how the upper-left pair sums follow
 // from the previous row's lower-right ones: S == 0 -> the same columns;
 // S == 1 -> one column to the left, a shuffle, lane 0 forming the strip-edge
 // pair itself).  om / oc: neighbour-colour rows i-1 / i; dlp: lower-right pair
 // sums of row i-1; op: neighbour-colour row i+1 (ring values already scaled).
-// FIRST: no previous row, form the upper-left pairs directly.  EDGE: the
-// strip touches the first or last packed column, so the strip-edge scalars may
-// be Dirichlet ring values, rescaled by ph.bscale.  Pure register work: the
-// caller loads and stores, so two rows can be scheduled together.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST>
+// FIRST: no previous row, form the upper-left pairs directly.  Ring values
+// arrive already at the phase's scale.  Pure register work: the caller loads
+// and stores, so two rows can be scheduled together.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
 __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (&oc)[4], const double (&dlp)[4],
                                            const double (&op)[4], const FastIn& in, int n, int q0, int lane,
                                            const FastPhase& ph, double (&nv)[4], double (&DL)[4],
@@ -451,14 +425,6 @@ __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (
   double right = __shfl_down_sync(0xffffffffu, oc[0], 1);
   if (lane == 0) left = in.el;
   if (lane == 31) right = in.er;
-  if (EDGE) {  // strip-edge scalars (lane 0: west, lane 31: east), one multiply for both
-    const int lim = (n + (1 - S)) >> 1;  // neighbour-colour interior limit of row i
-    const bool ring_l = lane == 0 && (q0 - 1 < 1 || q0 - 1 > lim);
-    const bool ring_r = lane == 31 && (q0 + kVec < 1 || q0 + kVec > lim);
-    const double e = __dmul_rn(lane == 0 ? left : right, ph.bscale);
-    if (ring_l) left = e;
-    if (ring_r) right = e;
-  }
   double W[4], E[4];
   if (S == 0) {
     W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
@@ -501,8 +467,8 @@ __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (
 
 __device__ __forceinline__ int wrap_stage(int b) { return b >= kFastStages ? b - kFastStages : b; }
 
-// One row i in buffer b; RB: row n, the south ring below it is rescaled.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S, bool FIRST, bool RB>
+// One row i in buffer b.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
 __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
                                            const double* __restrict__ O, double* __restrict__ X,
                                            const double* __restrict__ G, int pitch, int n, int q0, int lane,
@@ -510,14 +476,8 @@ __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage
   cp_async_wait<kFastAhead - 1>();  // rows up to i + 3 are in flight: row i has landed
   FastIn a;
   fast_read<HAS_G>(stages + b, lane, a);
-  if (RB) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) a.op[v] = __dmul_rn(a.op[v], ph.bscale);
-  } else if (EDGE) {
-    fast_scale_east<S>(a.op, n, q0, ph.bscale);
-  }
   double nv[4], DL[4];
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   store4(X + eidx(i, q0, pitch), nv);
@@ -530,10 +490,10 @@ __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage
   b = wrap_stage(b + 1);
 }
 
-// Rows i (parity S) and i + 1 (parity 1 - S), neither of them row n with a
-// rescaled ring below; both rows' arithmetic is independent enough to be
-// interleaved, which doubles the FP64 work in flight per warp.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S>
+// Rows i (parity S) and i + 1 (parity 1 - S); both rows' arithmetic is
+// independent enough to be interleaved, which doubles the FP64 work in flight
+// per warp.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S>
 __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
                                            const double* __restrict__ O, double* __restrict__ X,
                                            const double* __restrict__ G, int pitch, int n, int q0, int lane,
@@ -542,13 +502,9 @@ __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage
   FastIn a, c;
   fast_read<HAS_G>(stages + b, lane, a);
   fast_read<HAS_G>(stages + wrap_stage(b + 1), lane, c);
-  if (EDGE) {
-    fast_scale_east<S>(a.op, n, q0, ph.bscale);
-    fast_scale_east<1 - S>(c.op, n, q0, ph.bscale);
-  }
   double nva[4], DLa[4], nvc[4], DLc[4];
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm);
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead + 1), i + kFastAhead + 1, i + kFastAhead + 1 < i1, O, X, G,
@@ -565,67 +521,77 @@ __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage
 }
 
 // Rows [i0, i1) of one strip: the first row, then pairs (whose first row has
-// the parity of i0 + 1, fixed at compile time), an odd row left over, and the
-// last grid row on its own when the south ring below it needs rescaling.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE, int S0>
+// the parity of i0 + 1, fixed at compile time) and an odd row left over.
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S0>
 __device__ __forceinline__ void fast_rows(FastWalk& w, FastStage<HAS_G>* stages, const double* __restrict__ O,
                                           double* __restrict__ X, const double* __restrict__ G, int pitch, int n,
-                                          int q0, int i0, int i1, int iend, int lane, const FastPhase& ph,
+                                          int q0, int i0, int i1, int lane, const FastPhase& ph,
                                           unsigned long long& dm) {
   int i = i0, b = 0;
-  if (i < iend) {
-    fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, true, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
-                                                                 ph, dm);
-    ++i;
-    for (; i + 1 < iend; i += 2)
-      fast_step2<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
-    if (i < iend) {
-      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0, false, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0,
-                                                                        lane, ph, dm);
-      ++i;
-    }
-  }
-  if (i < i1) {  // row n with the south ring below (only when rescaling); its parity is that of i - i0
-    const bool first = i == i0;
-    const bool same = ((i - i0) & 1) == 0;
-    if (first)
-      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, true, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
+  fast_step1<UNIT_BETA, HAS_G, MEASURE, S0, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
+  ++i;
+  for (; i + 1 < i1; i += 2)
+    fast_step2<UNIT_BETA, HAS_G, MEASURE, 1 - S0>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
+  if (i < i1) fast_step1<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
                                                                   ph, dm);
-    else if (same)
-      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, S0, false, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
-                                                                   ph, dm);
-    else
-      fast_step1<UNIT_BETA, HAS_G, MEASURE, EDGE, 1 - S0, false, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0,
-                                                                       lane, ph, dm);
-  }
 }
 
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool EDGE>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE>
 __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages, const double* __restrict__ O,
                                                         double* __restrict__ X, const double* __restrict__ G,
                                                         int pitch, int n, int colour, int q0, int i0, int i1,
-                                                        int lane, const FastPhase& ph, bool rescale) {
-  const int ocol = colour ^ 1;
+                                                        int lane, const FastPhase& ph) {
   for (int k = 0; k < kFastAhead; ++k)  // prologue: rows i0 .. i0 + kFastAhead - 1 into buffers 0 ..
     fast_issue<HAS_G>(stages + k, i0 + k, i0 + k < i1, O, X, G, pitch, q0, lane);
   FastWalk w;
   load4(O + eidx(i0 - 1, q0, pitch), w.om);
   load4(O + eidx(i0, q0, pitch), w.oc);
-  if (rescale) {
-    scale_ring4(w.om, i0 - 1, q0, n, ocol, ph.bscale, EDGE);
-    if (EDGE) scale_ring4(w.oc, i0, q0, n, ocol, ph.bscale, true);
-  }
 #pragma unroll
   for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
   unsigned long long dm = 0;
-  // the last grid row reads the south ring; give it its own step
-  const int iend = (rescale && i1 == n + 1) ? n : i1;
-  if (((i0 + colour) & 1) == 0)
-    fast_rows<UNIT_BETA, HAS_G, MEASURE, EDGE, 0>(w, stages, O, X, G, pitch, n, q0, i0, i1, iend, lane, ph, dm);
-  else
-    fast_rows<UNIT_BETA, HAS_G, MEASURE, EDGE, 1>(w, stages, O, X, G, pitch, n, q0, i0, i1, iend, lane, ph, dm);
+  if (i0 < i1) {
+    if (((i0 + colour) & 1) == 0)
+      fast_rows<UNIT_BETA, HAS_G, MEASURE, 0>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
+    else
+      fast_rows<UNIT_BETA, HAS_G, MEASURE, 1>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
+  }
   cp_async_wait<0>();  // no copy may still target the stages when the warp moves on
   return dm;
+}
+
+// This phase's colour X: rewrite the Dirichlet ring cells next to the strip
+// (ring rows 0 / N+1 above / below its columns, the column q = 0 and the east
+// ring column beside its rows) as (unscaled value) x ph.nscale, the scale at
+// which the next phase reads this colour.  Row stores of the strip may have
+// written the same cells back unchanged just before; the warp barrier orders
+// them.  Cells that hold no ring value in a given row (the other parity's
+// padding) receive the saved padding value times the scale and are never read.
+__device__ __forceinline__ void fast_ring(const SlotDesc& sd, double* __restrict__ X, int colour, const Tile& tl,
+                                          int q0, int lane, double ns) {
+  const int n = sd.n, pitch = sd.pitch, m = n + 2;
+  const double* __restrict__ R = sd.ring[colour];
+  __syncwarp();
+  if (tl.row0 == 1) {  // ring row 0 above the strip's columns
+    double v[4];
+    load4(R + q0 + kOff, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __dmul_rn(v[k], ns);
+    store4(X + eidx(0, q0, pitch), v);
+  }
+  if (tl.row0 + tl.nrows == n + 1) {  // ring row N+1 below them
+    double v[4];
+    load4(R + pitch + q0 + kOff, v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __dmul_rn(v[k], ns);
+    store4(X + eidx(n + 1, q0, pitch), v);
+  }
+  const bool west = tl.col0 == 1, east = tl.col0 + kWarpCols > ((n + 1) >> 1);
+  if (west || east) {
+    for (int r = tl.row0 + lane; r < tl.row0 + tl.nrows; r += 32) {
+      if (west) X[eidx(r, 0, pitch)] = __dmul_rn(R[2 * pitch + r], ns);
+      if (east) X[eidx(r, ((n + ((r + colour) & 1)) >> 1) + 1, pitch)] = __dmul_rn(R[2 * pitch + m + r], ns);
+    }
+  }
 }
 
 // Warp-per-strip kernel: each warp walks one strip (slot, first row, first
@@ -668,22 +634,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fast(const SlotDesc* __re
     const double* G = (const double*)sd.g[colour];
     const int q0 = tl.col0 + lane * kVec;
     const int i0 = tl.row0, i1 = tl.row0 + tl.nrows;
-    const bool rescale = ph.bscale != 1.0;
-    const bool edge = rescale && (tl.col0 == 1 || tl.col0 + kWarpCols > (n >> 1));
     unsigned long long dm;
     if (measure) {
-      dm = edge ? fast_walk<UNIT_BETA, HAS_G, true, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
-                                                          rescale)
-                : fast_walk<UNIT_BETA, HAS_G, true, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
-                                                           rescale);
+      dm = fast_walk<UNIT_BETA, HAS_G, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
       dm = warp_max64(dm);
       if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
     } else {
-      dm = edge ? fast_walk<UNIT_BETA, HAS_G, false, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
-                                                           rescale)
-                : fast_walk<UNIT_BETA, HAS_G, false, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph,
-                                                            rescale);
+      dm = fast_walk<UNIT_BETA, HAS_G, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
     }
+    fast_ring(sd, X, colour, tl, q0, lane, ph.nscale);
     if (colour == 1) {
       __threadfence();
       __syncwarp();
@@ -697,6 +656,37 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fast(const SlotDesc* __re
       __syncwarp();
     }
   }
+}
+
+// Saves the unscaled Dirichlet ring cells of both colour arrays of slot 0 into
+// d.ring[c] (layout in SlotDesc): rows 0 and N+1 whole, then the column q = 0
+// and the east ring column q = ((N + ((r + c) & 1)) >> 1) + 1 of every row r.
+__global__ void k_ring_save(const SlotDesc* __restrict__ slots) {
+  const SlotDesc& d = slots[0];
+  const int n = d.n, pitch = d.pitch, m = n + 2;
+  const int c = blockIdx.y;
+  const double* X = (const double*)d.x[0][c];
+  double* R = (double*)d.ring[c];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * pitch + 2 * m; e += gridDim.x * blockDim.x) {
+    double v;
+    if (e < pitch) {
+      v = X[e];
+    } else if (e < 2 * pitch) {
+      v = X[(size_t)(n + 1) * pitch + (e - pitch)];
+    } else if (e < 2 * pitch + m) {
+      const int r = e - 2 * pitch;
+      v = X[eidx(r, 0, pitch)];
+    } else {
+      const int r = e - 2 * pitch - m;
+      v = X[eidx(r, ((n + ((r + c) & 1)) >> 1) + 1, pitch)];
+    }
+    R[e] = v;
+  }
+}
+
+cudaError_t launch_ring_save(const SlotDesc* slots, cudaStream_t s) {
+  k_ring_save<<<dim3(8, 2), 256, 0, s>>>(slots);
+  return cudaGetLastError();
 }
 
 int fast_blocks_per_sm() {
@@ -1410,7 +1400,7 @@ cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const 
   if (ntiles <= 0) return cudaSuccess;
   const int need = (ntiles + kWarpsY - 1) / kWarpsY;  // one warp per strip
   if (grid <= 0 || grid > need) grid = need;
-  FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.bscale, a.last};
+  FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.nscale, a.last};
   const bool unit = a.beta == 1.0;
   static bool attr_set = false;  // benign race: setting the attributes twice is harmless
   if (!attr_set) {

@@ -28,12 +28,17 @@ cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* state
                          int grid, int colour, int sweep, cudaStream_t s);
 // Constants of one FP64 colour phase of the rescaled formulation:
 //   X' = alpha * X + beta * (pair-sum of neighbours) + gamma * g,
-// with |change| measured as |X' - dscale * X| (last iteration of a chunk only)
-// and Dirichlet ring values read as bscale * value.
+// with |change| measured as |X' - dscale * X| (last iteration of a chunk only);
+// the phase rewrites its colour's Dirichlet ring cells at nscale x value.
 struct FastPhaseArgs {
-  double alpha, beta, gamma, dscale, bscale;
+  double alpha, beta, gamma, dscale;
+  double nscale;  // scale at which the next phase reads this phase's colour (its ring cells are written so)
   int last;
 };
+// Saves the unscaled Dirichlet ring cells of slot 0's colour arrays into
+// slots[0].ring (needed by the FP64 default phases, which rewrite the ring at
+// the scale of the next phase).
+cudaError_t launch_ring_save(const SlotDesc* slots, cudaStream_t s);
 // Resident blocks per SM of the FP64 phase kernel (sizes its persistent grid).
 int fast_blocks_per_sm();
 // ntiles counts warp strips (one warp each); grid <= 0: one warp per strip.

@@ -279,6 +279,7 @@ static void free_workspace(Ctx* c, SolveWorkspace* w) {
   ctx_dev_free(c, w->d_tb_tiles);
   ctx_dev_free(c, w->d_nat_u);
   ctx_dev_free(c, w->d_nat_f);
+  ctx_dev_free(c, w->d_ring);
   if (w->h_state) cudaFreeHost(w->h_state);
   for (auto e : w->poll_events) cudaEventDestroy(e);
   for (auto& pr : w->chunk_events) {
@@ -346,8 +347,9 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   if (p.tdepth > 1) build_tiles(L, 0, &tt, nullptr, kTbRows, tb_out_cols(p.tdepth));
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
-  const size_t small =
-      sizeof(SlotDesc) + sizeof(SlotState) + (st.size() + rt.size() + ft.size() + tt.size()) * sizeof(Tile);
+  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) +
+                       (st.size() + rt.size() + ft.size() + tt.size()) * sizeof(Tile) +
+                       2 * (2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2)) * sizeof(double);  // saved ring
   const size_t total = slot_bytes(p, pingpong) + nat_u + nat_f + small + 4096;
   sor_status rs = ctx_reserve(c, total, false, 0.0);
   if (rs != SOR_OK) {
@@ -370,9 +372,11 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, std::max<size_t>(1, tt.size()) * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
+  const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
+  if (p.kind == kPlain64) w->d_ring = (double*)ctx_dev_alloc(c, 2 * ring_elems * sizeof(double));
   ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
        w->d_nat_u &&
-       (!p.has_f || w->d_nat_f);
+       (!p.has_f || w->d_nat_f) && (p.kind != kPlain64 || w->d_ring);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
     cudaGetLastError();
     free_workspace(c, w.get());
@@ -534,12 +538,13 @@ static int next_chunk(Ctx* c, const Plan& p, long long k0, int L) {
 static FastPhaseArgs fast_phase(const Plan& p, int t, int L, int colour) {
   const double w4 = p.omega / 4.0, omc = 1.0 - p.omega;
   FastPhaseArgs a;
-  // scale of the neighbour colour during this phase: red reads black at
-  // b_{t-1} (1 at t = 1), black reads red at a_t (1 at t = L)
+  // scale at which the next phase reads this phase's colour (its ring cells
+  // are rewritten so): black at t reads red at a_t (1 at t = L); red at t + 1
+  // reads black at b_t (1 at t = L: the next chunk starts unscaled)
   if (colour == 0)
-    a.bscale = t == 1 ? 1.0 : std::pow(w4, -(2 * t - 2));
+    a.nscale = t == L ? 1.0 : std::pow(w4, -(2 * t - 1));
   else
-    a.bscale = t == L ? 1.0 : std::pow(w4, -(2 * t - 1));
+    a.nscale = t == L ? 1.0 : std::pow(w4, -(2 * t));
   if (colour == 0) {
     if (t == L) {  // back to unscaled values
       const double inv_a = t == 1 ? 1.0 : std::pow(w4, 2 * t - 3);  // 1 / a_{t-1}
@@ -769,6 +774,11 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
   }
   fill_desc(p, &w->slot);
   if (p.kind == kPlain64 && !p.exact) w->slot.desc.sweep_tiles = w->n_fast_tiles;  // warp strips
+  if (p.kind == kPlain64) {
+    const size_t ring_elems = 2 * (size_t)w->slot.L.pitch + 2 * (size_t)(p.n + 2);
+    w->slot.desc.ring[0] = w->d_ring;
+    w->slot.desc.ring[1] = w->d_ring + ring_elems;
+  }
   if (p.kind == kPlain32 && p.tdepth > 1) w->slot.desc.sweep_tiles = w->n_tb_tiles;  // fused-iteration tiles
   SlotState st0 = initial_state(p);
   SOR_CK(c, cudaMemcpyAsync(w->d_desc, &w->slot.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
@@ -798,6 +808,7 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
   }
   pa.state = w->d_state;
   SOR_CK(c, launch_pack(pa, s));
+  if (p.kind == kPlain64 && !p.exact) SOR_CK(c, launch_ring_save(w->d_desc, s));  // ring kept for the rescaled phases
 
   // chunks, polled with a lag of kInflight - 1 so the device never idles
   const int L = chunk_length(c, p);

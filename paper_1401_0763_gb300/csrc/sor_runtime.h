@@ -76,6 +76,7 @@ struct SolveWorkspace {
   int n_sweep_tiles = 0, n_resid_tiles = 0, n_fast_tiles = 0, n_tb_tiles = 0;
   double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
   double* d_nat_f = nullptr;  // n^2 staging
+  double* d_ring = nullptr;   // FP64: unscaled Dirichlet ring cells of both colours (SlotDesc::ring)
   SlotState* h_state = nullptr;  // pinned mirror, one per in-flight poll
   int h_state_count = 0;
   std::vector<cudaEvent_t> poll_events;
