@@ -33,9 +33,9 @@ WORKLOAD = "paper-sized plain sweep: 4098x4098 array (4096^2 interior), random u
 FP64_FLOPS_PER_LUP = 6.0    # (1-w)u + (w/4)(N+S+W+E): 3 adds, 2 multiplies, 1 add
 HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once per iteration
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_fast<1,0> launch (ncu, this workload);
-# None until the current kernel has been captured
-FAST64_DRAM_BYTES_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_fast<1,0> launch (ncu, this workload)
+# (capture of the current kernel, profiles/k_sweep_fast64_plate4096.md)
+FAST64_DRAM_BYTES_PER_LAUNCH = 157.77e6
 
 
 def dist_env():
