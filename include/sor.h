@@ -203,9 +203,12 @@ typedef enum {
                                   SOR_OPT_AUTOTUNE is 1, else 6; supported: 1, 2, 3, 4, 6, 8) */
   SOR_OPT_AUTOTUNE = 5,        /* 1: time candidate kernel configurations on first use of a size */
   SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
-  SOR_OPT_CLUSTER = 7          /* 1 (default): plain solves of grids small enough for one thread-block
+  SOR_OPT_CLUSTER = 7,         /* 1 (default): plain solves of grids small enough for one thread-block
                                   cluster (N <= 384 in FP64, N <= 768 in FP32) run all their iterations
                                   in a single launch, exact operation order; 0: never */
+  SOR_OPT_FAST_CHAIN = 8       /* 1 (default): the FP64 default path runs each chunk of iterations in one
+                                  cooperative launch with neighbour-to-neighbour progress counters; 0: one
+                                  launch per colour phase.  Results are identical either way */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);
@@ -222,6 +225,7 @@ typedef struct {
   uint64_t timed_updates;     /* lattice updates inside those timed chunks */
   uint64_t bytes_reserved;    /* device bytes currently held for solves */
   uint64_t bytes_peak;        /* high-water mark of bytes_reserved */
+  uint64_t kernel_launches;   /* kernel launches of sor_solve calls, every kind (graph replays included) */
 } sor_stats;
 
 sor_status sor_get_stats(sor_ctx *ctx, sor_stats *out);

@@ -45,6 +45,7 @@ SOR_OPT_TEMPORAL_DEPTH = 4
 SOR_OPT_AUTOTUNE = 5
 SOR_OPT_BATCH_MAX_SLOTS = 6
 SOR_OPT_CLUSTER = 7
+SOR_OPT_FAST_CHAIN = 8
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
@@ -74,7 +75,7 @@ class sor_stats(ctypes.Structure):
                 ("sweep_launches", ctypes.c_uint64), ("lattice_updates", ctypes.c_uint64),
                 ("sweep_ms", ctypes.c_double), ("timed_launches", ctypes.c_uint64),
                 ("timed_updates", ctypes.c_uint64), ("bytes_reserved", ctypes.c_uint64),
-                ("bytes_peak", ctypes.c_uint64)]
+                ("bytes_peak", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

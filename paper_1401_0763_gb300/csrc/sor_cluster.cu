@@ -267,6 +267,7 @@ cudaError_t launch_cluster_solve(bool fp32, int n, int pitch, const SlotDesc* sl
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
+  count_kernel_launches(1);
   return fp32 ? cudaLaunchKernelEx(&cfg, k_cluster_solve<float>, slots, states, slot)
               : cudaLaunchKernelEx(&cfg, k_cluster_solve<double>, slots, states, slot);
 }

@@ -17,12 +17,20 @@
 // FP64 forms), so their results do not depend on compiler contraction.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "sor_bits.cuh"
 #include "sor_device.cuh"
 #include "sor_devfn.cuh"
 #include "sor_kernels.h"
 
 namespace sorgb {
+
+// Kernel launches issued by this host thread (statistics; captured launches
+// are counted once at capture, their replays by the runtime).
+static thread_local unsigned long long t_launches = 0;
+unsigned long long kernel_launch_count() { return t_launches; }
+void count_kernel_launches(int k) { t_launches += (unsigned long long)k; }
 
 // ------------------------------------------------------------------------------------------------
 // pack / unpack
@@ -658,6 +666,178 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fast(const SlotDesc* __re
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// a whole chunk of FP64 phases in one launch
+// ------------------------------------------------------------------------------------------------
+//
+// The per-phase launches above pay a grid start and a drain per colour phase
+// (about 8 % of a 4096^2 phase).  k_fast_chain runs the 2L phases of a chunk
+// in one cooperative launch (all warps resident): each warp walks its strip
+// phase after phase, and before phase p it waits until the strips above,
+// below, left and right of it -- the only ones whose cells its stencil reads
+// or whose readers it could overwrite -- have finished phase p-1.  A strip
+// publishes its progress with a release store after fencing its writes; every
+// lane of a waiting warp reads the counters with acquire loads.  Every wait
+// is bounded: past kChainSpins polls the warp records an error in the slot
+// state, marks it done and returns (the host reports SOR_ERR_INTERNAL).
+
+constexpr int kChainSpins = 1 << 21;  // polls of about 0.1 us each: far above any phase
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Waits until every listed neighbour has completed `target` phases; false on
+// timeout.  Lanes 0..3 poll one neighbour each; afterwards every lane takes
+// its own acquire of all of them, so its later loads see their writes.
+__device__ __forceinline__ bool chain_wait(const unsigned* progress, const int (&nb)[4], unsigned target, int lane) {
+  bool ok = true;
+  const int mine = lane == 0 ? nb[0] : lane == 1 ? nb[1] : lane == 2 ? nb[2] : lane == 3 ? nb[3] : -1;
+  if (mine >= 0) {
+    int spins = 0;
+    while (ld_acquire_u32(progress + mine) < target) {
+      if (++spins > kChainSpins) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (nb[k] >= 0) (void)ld_acquire_u32(progress + nb[k]);
+  }
+  return ok;
+}
+
+template <bool HAS_G>
+__global__ void __launch_bounds__(kThreads, 3) k_fast_chain(const SlotDesc* __restrict__ slots, SlotState* states,
+                                                            const Tile* __restrict__ strips, int nstrips, int ct,
+                                                            const FastPhase* __restrict__ phases, int nphases,
+                                                            unsigned* progress) {
+  extern __shared__ __align__(16) unsigned char fast_smem[];
+  const int lane = threadIdx.x & 31;
+  FastStage<HAS_G>* stages = reinterpret_cast<FastStage<HAS_G>*>(fast_smem) + (threadIdx.x >> 5) * kFastStages;
+  const int t = blockIdx.x * kWarpsY + (threadIdx.x >> 5);
+  if (t >= nstrips) return;  // no strip: nobody waits for this warp
+  const Tile tl = strips[t];
+  const SlotDesc& sd = slots[tl.slot];
+  SlotState* st = states + tl.slot;
+  int skip = 0, k0 = 0, xbuf = 0;
+  if (lane == 0) {
+    skip = *((volatile int*)&st->done);
+    k0 = *((volatile int*)&st->iters);
+    xbuf = *((volatile int*)&st->xbuf);
+  }
+  skip = __shfl_sync(0xffffffffu, skip, 0);
+  if (skip) return;  // set only between launches: every warp sees the same value
+  k0 = __shfl_sync(0xffffffffu, k0, 0);
+  xbuf = __shfl_sync(0xffffffffu, xbuf, 0);
+  const int rows = nstrips / ct, r = t / ct, cc = t - r * ct;
+  const int nb[4] = {r > 0 ? t - ct : -1, r + 1 < rows ? t + ct : -1, cc > 0 ? t - 1 : -1,
+                     cc + 1 < ct ? t + 1 : -1};
+  const int pitch = sd.pitch, n = sd.n;
+  const int q0 = tl.col0 + lane * kVec;
+  const int i0 = tl.row0, i1 = tl.row0 + tl.nrows;
+  int measure_last = 0;
+  for (int p = 0; p < nphases; ++p) {
+    const int colour = p & 1;
+    const int k = k0 + (p >> 1) + 1;
+    const FastPhase ph = phases[p];
+    const int measure = ((k % sd.K) == 0) || (k >= sd.max_iters);
+    if (measure && !ph.last) {  // the host plan must end chunks at measured iterations
+      if (lane == 0) {
+        st->error = 1;
+        st->done = 1;
+      }
+      return;
+    }
+    if (p > 0 && !chain_wait(progress, nb, (unsigned)p, lane)) {
+      if (lane == 0) {
+        st->error = 1;
+        st->done = 1;
+      }
+      return;
+    }
+    double* X = (double*)sd.x[xbuf][colour];
+    const double* O = (const double*)sd.x[xbuf][colour ^ 1];
+    const double* G = (const double*)sd.g[colour];
+    const bool unit = ph.beta == 1.0;
+    unsigned long long dm = 0;
+    if (measure) {
+      dm = unit ? fast_walk<true, HAS_G, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph)
+                : fast_walk<false, HAS_G, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
+      dm = warp_max64(dm);
+      if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+      measure_last = 1;
+    } else if (unit) {
+      (void)fast_walk<true, HAS_G, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
+    } else {
+      (void)fast_walk<false, HAS_G, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
+    }
+    fast_ring(sd, X, colour, tl, q0, lane, ph.nscale);
+    __threadfence();  // this lane's cells are visible before the strip's progress is
+    __syncwarp();
+    if (lane == 0) st_release_u32(progress + t, (unsigned)(p + 1));
+  }
+  if (lane == 0) {
+    const unsigned prev = atomicAdd(&st->arrive, 1u);
+    if (prev == (unsigned)nstrips - 1u) {
+      __threadfence();
+      finalize_plain(sd, st, k0 + (nphases >> 1), measure_last);
+    }
+  }
+}
+
+int fast_chain_blocks_per_sm() {
+  int nb = 0;
+  if (cudaFuncSetAttribute(k_fast_chain<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fast_smem_bytes<true>()) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fast_chain<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fast_smem_bytes<false>()) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fast_chain<true>, kThreads, fast_smem_bytes<true>()) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+cudaError_t launch_fast_chain(const SlotDesc* slots, SlotState* states, const Tile* strips, int nstrips, int ct,
+                              const void* phases, int nphases, unsigned* progress, bool has_g, int grid,
+                              cudaStream_t s) {
+  if (nstrips <= 0 || nphases <= 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = has_g ? fast_smem_bytes<true>() : fast_smem_bytes<false>();
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeCooperative;  // every warp resident: the neighbour waits need it
+  at.val.cooperative = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  const FastPhase* ph = (const FastPhase*)phases;
+  t_launches += 1;
+  return has_g ? cudaLaunchKernelEx(&cfg, k_fast_chain<true>, slots, states, strips, nstrips, ct, ph, nphases, progress)
+               : cudaLaunchKernelEx(&cfg, k_fast_chain<false>, slots, states, strips, nstrips, ct, ph, nphases,
+                                    progress);
+}
+
+size_t fast_phase_bytes() { return sizeof(FastPhase); }
+
+void fast_phase_pack(const FastPhaseArgs& a, void* out) {
+  FastPhase ph{a.alpha, a.beta, a.gamma, a.dscale, a.nscale, a.last};
+  std::memcpy(out, &ph, sizeof(ph));
+}
+
 // Saves the unscaled Dirichlet ring cells of both colour arrays of slot 0 into
 // d.ring[c] (layout in SlotDesc): rows 0 and N+1 whole, then the column q = 0
 // and the east ring column q = ((N + ((r + c) & 1)) >> 1) + 1 of every row r.
@@ -685,6 +865,7 @@ __global__ void k_ring_save(const SlotDesc* __restrict__ slots) {
 }
 
 cudaError_t launch_ring_save(const SlotDesc* slots, cudaStream_t s) {
+  t_launches += 1;
   k_ring_save<<<dim3(8, 2), 256, 0, s>>>(slots);
   return cudaGetLastError();
 }
@@ -1351,6 +1532,7 @@ static dim3 pack_grid(int n) {
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t s) {
   const dim3 grid = pack_grid(a.n);
+  t_launches += 1;
   if (a.fp32) {
     k_pack<float><<<grid, kThreads, 0, s>>>(a.u0, a.f, a.n, a.pitch, a.h2, (float*)a.x[0][0], (float*)a.x[0][1],
                                             (float*)a.x[1][0], (float*)a.x[1][1], (float*)a.g[0], (float*)a.g[1],
@@ -1368,6 +1550,7 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t s) {
 cudaError_t launch_unpack(const void* c0, const void* c1, bool fp32, int n, int pitch, double* out,
                           cudaStream_t s) {
   const dim3 grid = pack_grid(n);
+  t_launches += 1;
   if (fp32)
     k_unpack<float><<<grid, kThreads, 0, s>>>((const float*)c0, (const float*)c1, n, pitch, out);
   else
@@ -1379,6 +1562,7 @@ cudaError_t launch_sweep(SweepKind kind, const SlotDesc* slots, SlotState* state
                          int grid, int colour, int sweep, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
+  t_launches += 1;
   switch (kind) {
     case kSweepPlain64:
       k_sweep<double, 0><<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, colour, sweep);
@@ -1419,6 +1603,7 @@ cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const 
     attr_set = true;
   }
   const size_t sm0 = fast_smem_bytes<false>(), sm1 = fast_smem_bytes<true>();
+  t_launches += 1;
   if (unit && !has_g)
     k_sweep_fast<true, false><<<grid, kThreads, sm0, s>>>(slots, states, tiles, ntiles, colour, ph);
   else if (unit && has_g)
@@ -1441,6 +1626,7 @@ static cudaError_t launch_tb_t(const SlotDesc* slots, SlotState* states, const T
     attr_set = true;
   }
   if (grid <= 0 || grid > ntiles) grid = ntiles;
+  t_launches += 1;
   k_sweep_tb<T, MODE><<<grid, kTbThreads, TbGeom<T>::smem, s>>>(slots, states, tiles, ntiles, nt, src, sweep0);
   return cudaGetLastError();
 }
@@ -1470,6 +1656,7 @@ cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* state
                          int grid, int dbuf, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
+  t_launches += kind == kResidRefine64 ? 2 : 1;
   if (kind == kResidRefine64) {  // u += d first (nothing when no correction is pending)
     k_correct<<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
     cudaError_t e = cudaGetLastError();

@@ -39,8 +39,21 @@ struct FastPhaseArgs {
 // slots[0].ring (needed by the FP64 default phases, which rewrite the ring at
 // the scale of the next phase).
 cudaError_t launch_ring_save(const SlotDesc* slots, cudaStream_t s);
+// Kernel launches issued by the calling thread through these wrappers.
+unsigned long long kernel_launch_count();
+void count_kernel_launches(int k);
 // Resident blocks per SM of the FP64 phase kernel (sizes its persistent grid).
 int fast_blocks_per_sm();
+// The 2L FP64 phases of a chunk in one cooperative launch: one warp per strip
+// of a table of rows x ct strips (row-major), neighbour-to-neighbour progress
+// counters (nstrips unsigned, zeroed before the launch) instead of a grid
+// barrier; `phases` holds nphases packed phase records (fast_phase_pack).
+int fast_chain_blocks_per_sm();
+cudaError_t launch_fast_chain(const SlotDesc* slots, SlotState* states, const Tile* strips, int nstrips, int ct,
+                              const void* phases, int nphases, unsigned* progress, bool has_g, int grid,
+                              cudaStream_t s);
+size_t fast_phase_bytes();
+void fast_phase_pack(const FastPhaseArgs& a, void* out);
 // ntiles counts warp strips (one warp each); grid <= 0: one warp per strip.
 cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
                                 int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s);

@@ -280,6 +280,9 @@ static void free_workspace(Ctx* c, SolveWorkspace* w) {
   ctx_dev_free(c, w->d_nat_u);
   ctx_dev_free(c, w->d_nat_f);
   ctx_dev_free(c, w->d_ring);
+  ctx_dev_free(c, w->d_progress);
+  for (auto& kv : w->chain_phases) ctx_dev_free(c, kv.second);
+  w->chain_phases.clear();
   if (w->h_state) cudaFreeHost(w->h_state);
   for (auto e : w->poll_events) cudaEventDestroy(e);
   for (auto& pr : w->chunk_events) {
@@ -374,9 +377,22 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
   if (p.kind == kPlain64) w->d_ring = (double*)ctx_dev_alloc(c, 2 * ring_elems * sizeof(double));
+  if (p.kind == kPlain64 && !p.exact) {
+    // chunk launches: cooperative, so the strip table's warps must all be
+    // resident at once in the chain kernel's own occupancy
+    w->d_progress = (unsigned*)ctx_dev_alloc(c, std::max<size_t>(1, ft.size()) * sizeof(unsigned));
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    const int bps = fast_blocks_per_sm();
+    w->fast_ct = L.col_tiles();
+    if (coop && fast_chain_blocks_per_sm() >= bps && (int)ft.size() % w->fast_ct == 0 &&
+        (int)ft.size() <= c->sm_count * bps * kWarpsY)
+      w->chain_grid = c->sm_count * bps;
+  }
   ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
        w->d_nat_u &&
-       (!p.has_f || w->d_nat_f) && (p.kind != kPlain64 || w->d_ring);
+       (!p.has_f || w->d_nat_f) && (p.kind != kPlain64 || w->d_ring) &&
+       (p.kind != kPlain64 || p.exact || w->d_progress);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
     cudaGetLastError();
     free_workspace(c, w.get());
@@ -581,7 +597,54 @@ static FastPhaseArgs fast_phase(const Plan& p, int t, int L, int colour) {
 }
 
 // L iterations of the rescaled FP64 phases (one chunk).
+static bool use_chain(Ctx* c, const SolveWorkspace* w) { return w->chain_grid > 0 && c->opt_fast_chain.load(); }
+
+static std::string chain_key(const Plan& p, int L) {
+  std::ostringstream k;
+  k.precision(17);
+  k << L << ":" << p.omega;
+  return k.str();
+}
+
+// Packed phase records of a chunk of L iterations (uploaded once per length
+// and omega, before any capture).
+static sor_status ensure_chain_phases(Ctx* c, SolveWorkspace* w, const Plan& p, int L) {
+  const std::string key = chain_key(p, L);
+  if (w->chain_phases.count(key)) return SOR_OK;
+  const size_t rec = fast_phase_bytes();
+  std::vector<unsigned char> host(rec * 2 * (size_t)L);
+  for (int t = 1; t <= L; ++t)
+    for (int colour = 0; colour < 2; ++colour)
+      fast_phase_pack(fast_phase(p, t, L, colour), host.data() + rec * (size_t)(2 * (t - 1) + colour));
+  void* d = ctx_dev_alloc(c, host.size());
+  if (!d) {
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  if (cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    ctx_dev_free(c, d);
+    c->set_error("copy of the phase records failed");
+    return SOR_ERR_CUDA;
+  }
+  w->chain_phases[key] = d;
+  return SOR_OK;
+}
+
 static sor_status enqueue_fast_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  if (use_chain(c, w)) {
+    auto it = w->chain_phases.find(chain_key(p, L));
+    if (it == w->chain_phases.end()) {
+      c->set_error("phase records of the chunk were not prepared");
+      return SOR_ERR_INTERNAL;
+    }
+    SOR_CK(c, cudaMemsetAsync(w->d_progress, 0, (size_t)w->n_fast_tiles * sizeof(unsigned), s));
+    SOR_CK(c, launch_fast_chain(w->d_desc, w->d_state, w->d_fast_tiles, w->n_fast_tiles, w->fast_ct, it->second,
+                                2 * L, w->d_progress, p.has_f, w->chain_grid, s));
+    if (p.stop == kStopResid)
+      SOR_CK(c, launch_resid(kResidCheck64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, 0, s));
+    return SOR_OK;
+  }
   for (int t = 1; t <= L; ++t) {
     for (int colour = 0; colour < 2; ++colour) {
       const FastPhaseArgs a = fast_phase(p, t, L, colour);
@@ -601,15 +664,24 @@ static sor_status enqueue_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L,
 }
 
 static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, cudaStream_t s) {
+  const bool chain = p.kind == kPlain64 && !p.exact && use_chain(c, w);
+  if (chain) {
+    sor_status rs = ensure_chain_phases(c, w, p, L);
+    if (rs != SOR_OK) return rs;
+  }
   if (!c->opt_graphs.load()) return enqueue_chunk(c, w, p, L, s);
   std::ostringstream key;
+  key.precision(17);
   key << p.kind << ":" << p.exact << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L << ":" << p.has_f
-      << ":" << p.omega << ":" << p.tdepth;
+      << ":" << p.omega << ":" << p.tdepth << ":" << chain;
   auto it = w->graphs.find(key.str());
   if (it == w->graphs.end()) {
     cudaGraph_t g = nullptr;
     SOR_CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long l0 = kernel_launch_count();
     sor_status rs = enqueue_chunk(c, w, p, L, s);
+    const unsigned long long captured = kernel_launch_count() - l0;
+    w->captured += captured;
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (rs != SOR_OK) {
       if (g) cudaGraphDestroy(g);
@@ -617,12 +689,14 @@ static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, 
     }
     SOR_CK(c, e);
     GraphEntry ge;
+    ge.launches = captured;
     e = cudaGraphInstantiate(&ge.exec, g, 0);
     cudaGraphDestroy(g);
     SOR_CK(c, e);
     it = w->graphs.emplace(key.str(), ge).first;
   }
   SOR_CK(c, cudaGraphLaunch(it->second.exec, s));
+  w->replayed += it->second.launches;
   return SOR_OK;
 }
 
@@ -755,6 +829,9 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
   SolveWorkspace* w = nullptr;
   sor_status rs = get_workspace(c, p, &w);
   if (rs != SOR_OK) return rs;
+  const unsigned long long launches0 = kernel_launch_count();
+  w->captured = 0;
+  w->replayed = 0;
 
   const bool timing = c->opt_timing.load() != 0;
   SOR_CK(c, cudaEventRecord(w->ev0, s));
@@ -922,6 +999,7 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
     c->stats.sweep_ms += ms_timed;
     c->stats.timed_launches += (unsigned long long)launches_timed;
     c->stats.timed_updates += (unsigned long long)updates_timed;
+    c->stats.kernel_launches += (kernel_launch_count() - launches0 - w->captured) + w->replayed;
   }
   return SOR_OK;
 }

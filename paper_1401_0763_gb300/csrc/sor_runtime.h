@@ -57,6 +57,7 @@ size_t slot_bytes(const Plan& p, bool pingpong);
 // A cached CUDA graph keyed by the launch sequence it replays.
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
+  unsigned long long launches = 0;  // kernel launches one replay runs
 };
 
 // Workspace of sor_solve: slot buffers plus the small device tables, kept
@@ -77,6 +78,11 @@ struct SolveWorkspace {
   double* d_nat_u = nullptr;  // (n+2)^2 staging (host inputs / outputs)
   double* d_nat_f = nullptr;  // n^2 staging
   double* d_ring = nullptr;   // FP64: unscaled Dirichlet ring cells of both colours (SlotDesc::ring)
+  unsigned* d_progress = nullptr;  // FP64 chunk launches: phases completed per strip
+  int fast_ct = 0;                 // column tiles of the strip table (strips are rows x fast_ct)
+  int chain_grid = 0;              // blocks of a chunk launch (0: chunk launches unavailable)
+  std::map<std::string, void*> chain_phases;  // packed phase records per chunk length and omega
+  unsigned long long captured = 0, replayed = 0;  // launch counting of the current solve
   SlotState* h_state = nullptr;  // pinned mirror, one per in-flight poll
   int h_state_count = 0;
   std::vector<cudaEvent_t> poll_events;
@@ -144,6 +150,7 @@ struct Ctx {
   std::atomic<int> opt_autotune{0};
   std::atomic<int> opt_max_slots{0};
   std::atomic<int> opt_cluster{1};
+  std::atomic<int> opt_fast_chain{1};
 
   std::mutex tune_mu;
   std::map<std::string, int> tuned;  // autotuned FP32 depth per "<n bucket> <has source>"

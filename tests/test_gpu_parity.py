@@ -409,3 +409,46 @@ def test_cluster_path_converges_like_oracle(ctx, n, precision):
     assert res["converged"] == ref["converged"] and res["iterations"] == ref["iterations"]
     assert np.array_equal(got, ref["u"])
     assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+@pytest.fixture(scope="module")
+def ctx_nochain():
+    """A context whose FP64 default path launches one kernel per colour phase."""
+    capi = capi_mod()
+    c = capi.Context(0)
+    c.set_option(capi.SOR_OPT_CLUSTER, 0)
+    c.set_option(capi.SOR_OPT_FAST_CHAIN, 0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,iters,K,with_f,stop", [(200, 90, 10, False, 0), (513, 77, 7, True, 0),
+                                                  (1000, 60, 20, True, 1), (4096, 30, 10, False, 0)])
+def test_fast_chain_equals_phase_launches(ctx_mc, ctx_nochain, n, iters, K, with_f, stop):
+    """A chunk in one cooperative launch (neighbour progress counters) and one
+    launch per colour phase compute the same numbers bit for bit."""
+    capi = capi_mod()
+    if with_f:
+        u0, f = wl.poisson_problem(n, n)
+    else:
+        u0, f = wl.random_edges(n, n), None
+    kw = dict(omega=oracle.omega_opt(n), tol=-1.0 if stop == 0 else 1e-30, max_iters=iters, check_every=K,
+              stop=stop)
+    a, ra = run(ctx_mc, u0, f, **kw)
+    b, rb = run(ctx_nochain, u0, f, **kw)
+    assert ra["iterations"] == rb["iterations"] == iters
+    assert np.array_equal(a, b)
+    assert ra["final_maxdelta"] == rb["final_maxdelta"]
+    assert ra["final_resid_rel"] == rb["final_resid_rel"]
+
+
+def test_kernel_launch_count(ctx_mc):
+    """Chunks of 50 iterations in one launch each: pack, ring save, 20 chunk
+    launches, final residual and unpack for 1000 iterations."""
+    capi = capi_mod()
+    n = 1024
+    u0 = wl.random_edges(n, 1)
+    ctx_mc.solve(u0, omega=oracle.omega_opt(n), tol=-1.0, max_iters=1000, check_every=50)  # warm graphs
+    ctx_mc.reset_stats()
+    ctx_mc.solve(u0, omega=oracle.omega_opt(n), tol=-1.0, max_iters=1000, check_every=50)
+    assert ctx_mc.stats()["kernel_launches"] == 2 + 20 + 2
