@@ -33,9 +33,9 @@ WORKLOAD = "paper-sized plain sweep: 4098x4098 array (4096^2 interior), random u
 FP64_FLOPS_PER_LUP = 6.0    # (1-w)u + (w/4)(N+S+W+E): 3 adds, 2 multiplies, 1 add
 HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once per iteration
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_sweep_fast<1,0> launch (ncu, this workload)
-# None until the current kernel has been captured
-FAST64_DRAM_BYTES_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fast_chain launch (50 iterations) on this workload
+# (ncu capture of the current kernel, profiles/k_fast_chain_plate4096.md)
+FAST64_DRAM_BYTES_PER_LAUNCH = 18.805e9
 
 
 def dist_env():
@@ -281,9 +281,10 @@ def run_ours(args, ws, rank, local):
                              "no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                          "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": FAST64_DRAM_BYTES_PER_LAUNCH,
-                         "traffic_unit": "bytes per launch (dram read + write)",
-                         "traffic_source": "ncu capture of k_sweep_fast<1,0> on this workload "
-                                           "(profiles/k_sweep_fast64_plate4096.md)",
+                         "traffic_unit": "bytes per launch of 50 iterations (dram read + write)",
+                         "traffic_source": "ncu capture of k_fast_chain on this workload "
+                                           "(profiles/k_fast_chain_plate4096.md)",
+                         "traffic_algorithmic": 16.0 * N * N * CHECK,
                          "kernel": "k_fast_chain<false> (a chunk of 50 iterations per launch; "
                                    "achieved from the per-phase CUDA-event time)",
                          "peak_source": "nominal GB300 FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz x 2 flops; "
