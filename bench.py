@@ -532,7 +532,7 @@ def workload_plate16384(args, ctx, capi, wl):
     hbm = float(peaks.get("hbm_gbs") or 6800.0)
     ach64 = FP64_FLOPS_PER_LUP * lines["fp64"]["glups"] / 1e3
     lines["fp64"]["roofline"] = {"bound": "alu", "achieved": ach64, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                                 "frac": ach64 / NOMINAL_FP64_TFLOPS, "kernel": "k_sweep_fast<1,0>",
+                                 "frac": ach64 / NOMINAL_FP64_TFLOPS, "kernel": "k_fast_chain<false>",
                                  "hbm_frac": HBM_BYTES_PER_LUP["f64"] * lines["fp64"]["glups"] / hbm}
     lines["fp32"]["roofline"] = {"bound": "hbm", "achieved": HBM_BYTES_PER_LUP["f32"] * lines["fp32"]["glups"],
                                  "peak": hbm, "unit": "GB/s",
