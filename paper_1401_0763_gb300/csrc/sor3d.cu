@@ -18,6 +18,7 @@
 // D = o[r - (N+2)][q], U = o[r + (N+2)][q] (same packed column: moving one
 // plane flips the colour and keeps j).  Interior: 1 <= k, i <= N and
 // 1 <= q <= (N + s) / 2.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -335,6 +336,458 @@ __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ 
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// FP64 default phases on cubes: shared in-plane pair sums and rescaled unknowns
+// ------------------------------------------------------------------------------------------------
+//
+// The reformulation of the 2D default path carried to the cube, with w = w/6:
+// within plane k the four in-plane neighbours split into an upper-left and a
+// lower-right pair, each formed once and used by two cells (s = (i + k + c) & 1
+// plays the role of the 2D row parity); the neighbours below and above form a
+// third pair; red values after step t of a chunk are carried as
+// w^-(2t-1) u and black ones as w^-2t u, so the update is one FMA,
+// X' = alpha X + ((DU + DL) + (D + U)) [+ gamma g].  The phase that updates a
+// colour rewrites that colour's shell cells next to its strip at the scale the
+// next phase reads them (from a copy saved after packing); chunks end at
+// every tested iteration with unscaled values.  5 FP64 operations per update
+// instead of 8.
+
+struct Phase3 {
+  double alpha, beta, gamma, dscale, nscale;
+  int last;
+};
+
+constexpr int kF3Stages = 4;  // row buffers per warp
+constexpr int kF3Ahead = 3;   // rows fetched ahead of the row being updated
+
+template <bool HAS_G>
+struct Stage3 {
+  double op[32 * kVec];   // neighbour colour, row i + 1
+  double own[32 * kVec];  // own colour, row i
+  double dn[32 * kVec];   // neighbour colour, plane k - 1
+  double up[32 * kVec];   // neighbour colour, plane k + 1
+  double g[HAS_G ? 32 * kVec : 2];
+  double edge[2];
+};
+template <bool HAS_G>
+constexpr size_t f3_smem() {
+  return (size_t)kWarpsY * kF3Stages * sizeof(Stage3<HAS_G>);
+}
+
+__device__ __forceinline__ void c3_copy16(void* dst, const void* src, int nbytes) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void c3_copy8_if(void* dst, const void* src, int nbytes, bool pred) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %3, 0;\n @p cp.async.ca.shared.global [%0], [%1], 8, %2;\n}\n" ::"r"(saddr),
+      "l"(src), "r"(nbytes), "r"((int)pred)
+      : "memory");
+}
+template <int N>
+__device__ __forceinline__ void c3_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copies row i of plane k (and its neighbours) into a stage; zero-fill when
+// !valid; one group per row either way.
+template <bool HAS_G>
+__device__ __forceinline__ void f3_issue(Stage3<HAS_G>* st, int k, int i, bool valid, const double* O,
+                                         const double* X, const double* G, int m, int pitch, int q0, int lane) {
+  const int nb = valid ? 16 : 0;
+  const double* o = valid ? O + e3(k, i + 1, q0, m, pitch) : O;
+  const double* x = valid ? X + e3(k, i, q0, m, pitch) : X;
+  const double* d = valid ? O + e3(k - 1, i, q0, m, pitch) : O;
+  const double* u = valid ? O + e3(k + 1, i, q0, m, pitch) : O;
+  c3_copy16(st->op + lane * kVec, o, nb);
+  c3_copy16(st->op + lane * kVec + 2, o + 2, nb);
+  c3_copy16(st->own + lane * kVec, x, nb);
+  c3_copy16(st->own + lane * kVec + 2, x + 2, nb);
+  c3_copy16(st->dn + lane * kVec, d, nb);
+  c3_copy16(st->dn + lane * kVec + 2, d + 2, nb);
+  c3_copy16(st->up + lane * kVec, u, nb);
+  c3_copy16(st->up + lane * kVec + 2, u + 2, nb);
+  if (HAS_G) {
+    const double* gp = valid ? G + e3(k, i, q0, m, pitch) : G;
+    c3_copy16(st->g + lane * kVec, gp, nb);
+    c3_copy16(st->g + lane * kVec + 2, gp + 2, nb);
+  }
+  const bool right = lane == 31;
+  const double* e = valid ? O + e3(k, i, right ? q0 + kVec : q0 - 1, m, pitch) : O;
+  c3_copy8_if(&st->edge[right ? 1 : 0], e, valid ? 8 : 0, lane == 0 || right);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+struct Walk3 {
+  double om[4], oc[4], dlp[4];
+};
+
+// One row i of plane k (parity S = (i + k + colour) & 1 fixed at compile
+// time; FIRST: no previous row, form the upper-left pairs directly).
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
+__device__ __forceinline__ void f3_row(Walk3& w, int k, int i, int i0, int i1, Stage3<HAS_G>* stages,
+                                       const double* O, double* X, const double* G, int n, int m, int pitch, int q0,
+                                       int lane, const Phase3& ph, unsigned long long& dm) {
+  const int ahead = i + kF3Ahead;
+  f3_issue<HAS_G>(stages + ((ahead - i0) & (kF3Stages - 1)), k, ahead, ahead < i1, O, X, G, m, pitch, q0, lane);
+  c3_wait<kF3Ahead>();  // the buffer refilled above was read one row ago
+  const Stage3<HAS_G>* st = stages + ((i - i0) & (kF3Stages - 1));
+  double op[4], own[4], dn[4], up[4], gv[4];
+  load4(st->op + lane * kVec, op);
+  load4(st->own + lane * kVec, own);
+  load4(st->dn + lane * kVec, dn);
+  load4(st->up + lane * kVec, up);
+  if (HAS_G) load4(st->g + lane * kVec, gv);
+  double left = __shfl_up_sync(0xffffffffu, w.oc[3], 1);
+  double right = __shfl_down_sync(0xffffffffu, w.oc[0], 1);
+  if (lane == 0) left = st->edge[0];
+  if (lane == 31) right = st->edge[1];
+  double W[4], E[4];
+  if (S == 0) {
+    W[0] = w.oc[0]; W[1] = w.oc[1]; W[2] = w.oc[2]; W[3] = w.oc[3];
+    E[0] = w.oc[1]; E[1] = w.oc[2]; E[2] = w.oc[3]; E[3] = right;
+  } else {
+    W[0] = left; W[1] = w.oc[0]; W[2] = w.oc[1]; W[3] = w.oc[2];
+    E[0] = w.oc[0]; E[1] = w.oc[1]; E[2] = w.oc[2]; E[3] = w.oc[3];
+  }
+  double DL[4], DU[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) DL[v] = __dadd_rn(E[v], op[v]);
+  if (FIRST) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) DU[v] = __dadd_rn(w.om[v], W[v]);
+  } else if (S == 0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) DU[v] = w.dlp[v];
+  } else {
+    double d0 = __shfl_up_sync(0xffffffffu, w.dlp[3], 1);
+    if (lane == 0) d0 = __dadd_rn(w.om[0], left);
+    DU[0] = d0; DU[1] = w.dlp[0]; DU[2] = w.dlp[1]; DU[3] = w.dlp[2];
+  }
+  const int qlim = (n + S) >> 1;
+  double nv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const double sum = __dadd_rn(__dadd_rn(DU[v], DL[v]), __dadd_rn(dn[v], up[v]));
+    double t2;
+    if (UNIT_BETA)
+      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], sum) : sum;
+    else
+      t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
+    const double nu = __fma_rn(ph.alpha, own[v], t2);
+    const bool inside = (q0 + v) <= qlim;
+    nv[v] = inside ? nu : own[v];  // cells past the interior keep their value
+    if (MEASURE && inside) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
+  }
+  store4(X + e3(k, i, q0, m, pitch), nv);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    w.dlp[v] = DL[v];
+    w.om[v] = w.oc[v];
+    w.oc[v] = op[v];
+  }
+}
+
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S0>
+__device__ __forceinline__ void f3_rows(Walk3& w, int k, int i0, int i1, Stage3<HAS_G>* stages, const double* O,
+                                        double* X, const double* G, int n, int m, int pitch, int q0, int lane,
+                                        const Phase3& ph, unsigned long long& dm) {
+  int i = i0;
+  f3_row<UNIT_BETA, HAS_G, MEASURE, S0, true>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+  ++i;
+  for (; i + 1 < i1; i += 2) {
+    f3_row<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    f3_row<UNIT_BETA, HAS_G, MEASURE, S0, false>(w, k, i + 1, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+  }
+  if (i < i1)
+    f3_row<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+}
+
+// Saved unscaled shell of one colour array: planes 0 and N+1 (m rows of pitch
+// elements each), rows 0 and N+1 of every plane (m x pitch each), and the
+// column q = 0 and the east shell column of every row (m x m each).
+__host__ __device__ __forceinline__ size_t shell3_elems(int m, int pitch) {
+  return 4 * (size_t)m * pitch + 2 * (size_t)m * m;
+}
+__device__ __forceinline__ int east3(int n, int k, int i, int c) { return ((n + ((i + k + c) & 1)) >> 1) + 1; }
+
+__global__ void k_shell_save3(const Desc3* __restrict__ dp, double* shell0, double* shell1) {
+  const Desc3& d = *dp;
+  const int n = d.n, m = d.m, pitch = d.pitch;
+  const int c = blockIdx.y;
+  const double* X = (const double*)d.x[c];
+  double* R = c ? shell1 : shell0;
+  const size_t mp = (size_t)m * pitch, mm = (size_t)m * m;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < shell3_elems(m, pitch);
+       e += (size_t)gridDim.x * blockDim.x) {
+    double v;
+    if (e < mp) {
+      v = X[e];  // plane 0
+    } else if (e < 2 * mp) {
+      v = X[(size_t)(n + 1) * mp + (e - mp)];  // plane N+1
+    } else if (e < 3 * mp) {
+      const size_t r = e - 2 * mp;  // row 0 of plane r / pitch
+      v = X[((r / pitch) * m + 0) * pitch + r % pitch];
+    } else if (e < 4 * mp) {
+      const size_t r = e - 3 * mp;  // row N+1 of plane r / pitch
+      v = X[((r / pitch) * m + (n + 1)) * pitch + r % pitch];
+    } else if (e < 4 * mp + mm) {
+      const size_t r = e - 4 * mp;
+      v = X[e3((int)(r / m), (int)(r % m), 0, m, pitch)];
+    } else {
+      const size_t r = e - 4 * mp - mm;
+      const int k = (int)(r / m), i = (int)(r % m);
+      v = X[e3(k, i, east3(n, k, i, c), m, pitch)];
+    }
+    R[e] = v;
+  }
+}
+
+// Rewrites this phase's colour's shell cells next to the strip at scale ns.
+__device__ __forceinline__ void f3_shell(const Desc3& d, const double* __restrict__ R, double* __restrict__ X,
+                                         int colour, int k, int i0, int i1, int col0, int q0, int lane, double ns) {
+  const int n = d.n, m = d.m, pitch = d.pitch;
+  const size_t mp = (size_t)m * pitch, mm = (size_t)m * m;
+  __syncwarp();
+  // the shell plane below (k = 1) and / or above (k = N), this strip's rows
+  // and columns (both for N = 1)
+  for (int side = 0; side < 2; ++side) {
+    if (side == 0 ? k != 1 : k != n) continue;
+    const size_t base = side == 0 ? 0 : mp;
+    const int kk = side == 0 ? 0 : n + 1;
+    for (int i = i0; i < i1; ++i) {
+      double v[4];
+      load4(R + base + (size_t)i * pitch + q0 + kOff, v);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = __dmul_rn(v[t], ns);
+      store4(X + e3(kk, i, q0, m, pitch), v);
+    }
+  }
+  if (i0 == 1) {  // row 0 of plane k
+    double v[4];
+    load4(R + 2 * mp + (size_t)k * pitch + q0 + kOff, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = __dmul_rn(v[t], ns);
+    store4(X + e3(k, 0, q0, m, pitch), v);
+  }
+  if (i1 == n + 1) {  // row N+1 of plane k
+    double v[4];
+    load4(R + 3 * mp + (size_t)k * pitch + q0 + kOff, v);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = __dmul_rn(v[t], ns);
+    store4(X + e3(k, n + 1, q0, m, pitch), v);
+  }
+  const bool west = col0 == 1, east = col0 + kWarpCols > ((n + 1) >> 1);
+  if (west || east) {
+    for (int i = i0 + lane; i < i1; i += 32) {
+      if (west) X[e3(k, i, 0, m, pitch)] = __dmul_rn(R[4 * mp + (size_t)k * m + i], ns);
+      if (east) X[e3(k, i, east3(n, k, i, colour), m, pitch)] = __dmul_rn(R[4 * mp + mm + (size_t)k * m + i], ns);
+    }
+  }
+}
+
+// One colour phase over warp strips (plane k, rows [i0, i1), 128 packed
+// columns); the last strip to finish the black phase closes the iteration.
+template <bool UNIT_BETA, bool HAS_G>
+__global__ void __launch_bounds__(kThreads, 2) k_sweep3_fast(const Desc3* __restrict__ dp, SlotState* st,
+                                                             const Tile* __restrict__ strips, int nstrips,
+                                                             const double* __restrict__ shell0,
+                                                             const double* __restrict__ shell1, int colour,
+                                                             Phase3 ph) {
+  extern __shared__ __align__(16) unsigned char f3_mem[];
+  const int lane = threadIdx.x & 31;
+  Stage3<HAS_G>* stages = reinterpret_cast<Stage3<HAS_G>*>(f3_mem) + (threadIdx.x >> 5) * kF3Stages;
+  const Desc3& d = *dp;
+  const int warp = blockIdx.x * kWarpsY + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * kWarpsY;
+  for (int t = warp; t < nstrips; t += nwarps) {
+    const Tile tl = strips[t];
+    int skip = 0, kk = 0, measure = 0;
+    if (lane == 0) {
+      skip = *((volatile int*)&st->done);
+      kk = *((volatile int*)&st->iters) + 1;
+      measure = ((kk % d.K) == 0) || (kk >= d.max_iters);
+      if (!skip && measure && !ph.last) {  // the host plan must end chunks at measured iterations
+        st->error = 1;
+        st->done = 1;
+        skip = 1;
+      }
+    }
+    skip = __shfl_sync(0xffffffffu, skip, 0);
+    if (skip) continue;
+    kk = __shfl_sync(0xffffffffu, kk, 0);
+    measure = __shfl_sync(0xffffffffu, measure, 0);
+    const int n = d.n, m = d.m, pitch = d.pitch;
+    const int k = tl.row0 / m, i0 = tl.row0 - k * m, i1 = i0 + tl.nrows;
+    double* X = (double*)d.x[colour];
+    const double* O = (const double*)d.x[colour ^ 1];
+    const double* G = (const double*)d.g[colour];
+    const int q0 = tl.col0 + lane * kVec;
+    for (int a = 0; a < kF3Ahead; ++a)
+      f3_issue<HAS_G>(stages + a, k, i0 + a, i0 + a < i1, O, X, G, m, pitch, q0, lane);
+    Walk3 w;
+    load4(O + e3(k, i0 - 1, q0, m, pitch), w.om);
+    load4(O + e3(k, i0, q0, m, pitch), w.oc);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
+    unsigned long long dm = 0;
+    const int s0 = (i0 + k + colour) & 1;
+    if (measure) {
+      if (s0 == 0) f3_rows<UNIT_BETA, HAS_G, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<UNIT_BETA, HAS_G, true, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    } else {
+      if (s0 == 0) f3_rows<UNIT_BETA, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<UNIT_BETA, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    }
+    c3_wait<0>();
+    f3_shell(d, colour ? shell1 : shell0, X, colour, k, i0, i1, tl.col0, q0, lane, ph.nscale);
+    if (measure) {
+      dm = warp_max64(dm);
+      if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+    }
+    if (colour == 1) {
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        if (prev == (unsigned)nstrips - 1u) {
+          __threadfence();
+          finalize3(d, st, kk, measure);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Constants of phase (t, colour) of a chunk of L iterations for w = omega/6.
+Phase3 phase3_of(double omega, int t, int L, int colour) {
+  const double w6 = omega / 6.0, omc = 1.0 - omega;
+  Phase3 a;
+  if (colour == 0)
+    a.nscale = t == L ? 1.0 : std::pow(w6, -(2 * t - 1));
+  else
+    a.nscale = t == L ? 1.0 : std::pow(w6, -(2 * t));
+  if (colour == 0) {
+    if (t == L) {
+      const double inv_a = t == 1 ? 1.0 : std::pow(w6, 2 * t - 3);
+      const double inv_b = t == 1 ? 1.0 : std::pow(w6, 2 * t - 2);
+      a.alpha = omc * inv_a;
+      a.beta = w6 * inv_b;
+      a.gamma = w6;
+      a.dscale = inv_a;
+      a.last = 1;
+    } else {
+      a.alpha = t == 1 ? omc / w6 : omc / (w6 * w6);
+      a.beta = 1.0;
+      a.gamma = std::pow(w6, -(2 * t - 2));
+      a.dscale = 0.0;
+      a.last = 0;
+    }
+  } else {
+    if (t == L) {
+      const double inv_b = t == 1 ? 1.0 : std::pow(w6, 2 * t - 2);
+      a.alpha = omc * inv_b;
+      a.beta = w6;
+      a.gamma = w6;
+      a.dscale = inv_b;
+      a.last = 1;
+    } else {
+      a.alpha = omc / (w6 * w6);
+      a.beta = 1.0;
+      a.gamma = std::pow(w6, -(2 * t - 1));
+      a.dscale = 0.0;
+      a.last = 0;
+    }
+  }
+  return a;
+}
+
+// Longest chunk whose carried scale stays below 2^400.
+int fast3_lmax(double omega) {
+  const double bits = 2.0 * std::log2(6.0 / omega);
+  const int L = bits > 0.0 ? (int)std::floor(400.0 / bits) : 256;
+  return std::max(1, std::min(L, 256));
+}
+
+// Opts the four instantiations into their dynamic shared memory (before any
+// capture: attribute calls stay out of graph capture).
+cudaError_t fast3_prepare() {
+  static cudaError_t state = cudaErrorNotReady;
+  if (state == cudaErrorNotReady) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep3_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)f3_smem<false>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep3_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)f3_smem<false>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep3_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)f3_smem<true>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_sweep3_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)f3_smem<true>());
+    state = e;
+  }
+  return state;
+}
+
+// Resident blocks per SM of the phase kernel (0 on failure).
+int fast3_blocks_per_sm(bool has_g) {
+  int nb = 0;
+  cudaError_t e = has_g ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3_fast<true, true>, kThreads,
+                                                                       f3_smem<true>())
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3_fast<true, false>, kThreads,
+                                                                       f3_smem<false>());
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+cudaError_t launch_sweep3_fast(const Desc3* d, SlotState* st, const Tile* strips, int nstrips, int grid,
+                               const double* shell0, const double* shell1, int colour, const Phase3& ph, bool has_g,
+                               cudaStream_t s) {
+  const bool unit = ph.beta == 1.0;
+  const size_t sm = has_g ? f3_smem<true>() : f3_smem<false>();
+  if (unit && !has_g)
+    k_sweep3_fast<true, false><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+  else if (unit)
+    k_sweep3_fast<true, true><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+  else if (!has_g)
+    k_sweep3_fast<false, false><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+  else
+    k_sweep3_fast<false, true><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+  return cudaGetLastError();
+}
+
+// Warp strips of the FP64 default phases: every plane cut into B row bands
+// (at least 8 rows each) per 128-column tile, B chosen so that the strips
+// fill whole waves of `warps` warps with little per-strip overhead (about two
+// rows' worth: the first row's pairs, the pipeline fill and the shell).
+void build_strips3(const Layout& L, int warps, std::vector<Tile>* out) {
+  const int n = L.n, m = n + 2, ct = L.col_tiles();
+  int best_b = 1;
+  double best = -1.0;
+  for (int b = 1; b <= std::max(1, n / 8); ++b) {
+    const long long total = (long long)n * ct * b;
+    const long long waves = (total + warps - 1) / warps;
+    const double rows = (double)n / b;
+    const double score = (double)total / (double)(waves * warps) * rows / (rows + 2.0);
+    if (score > best + 1e-9) {
+      best = score;
+      best_b = b;
+    }
+  }
+  for (int k = 1; k <= n; ++k)
+    for (int b = 0; b < best_b; ++b) {
+      const int a0 = 1 + (int)((long long)b * n / best_b), a1 = 1 + (int)((long long)(b + 1) * n / best_b);
+      for (int t = 0; t < ct; ++t)
+        if (a1 > a0) out->push_back(Tile{0, k * m + a0, 1 + t * kWarpCols, a1 - a0});
+    }
+}
+
 #define SOR3_CK(ctx, expr)                                                                    \
   do {                                                                                        \
     cudaError_t e_ = (expr);                                                                  \
@@ -376,6 +829,23 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   const bool in_dev = is_device_ptr(u0), f_dev = has_f && is_device_ptr(f), out_dev = is_device_ptr(u_out);
   const double w = p->omega <= 0.0 ? sor_omega_opt(n) : p->omega;
   const int stop = p->stop == SOR_STOP_MAXDELTA ? kStopDelta : kStopResid;
+  // FP64 default: the rescaled phases with shared pair sums (within 1e-12 of
+  // the exact order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
+  const bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
+  std::vector<Tile> strips;
+  int fast_grid = 0;
+  if (fast) {
+    SOR3_CK(c, fast3_prepare());
+    const int bps = fast3_blocks_per_sm(has_f);
+    if (bps < 1) {
+      c->set_error("3D phase kernel does not fit on an SM");
+      return SOR_ERR_CUDA;
+    }
+    build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
+    fast_grid = std::min(c->sm_count * bps, (int)((strips.size() + kWarpsY - 1) / kWarpsY));
+  }
+  const int nst = (int)strips.size();
+  const size_t shell_elems = shell3_elems(m, pitch);
 
   // tiles: plane k, rows of 32, columns of 128 packed cells
   std::vector<Tile> tiles;
@@ -386,6 +856,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   const int nt = (int)tiles.size();
 
   size_t bytes = 2 * elems * sizeof(T) + sizeof(Desc3) + sizeof(SlotState) + sizeof(Tile) * nt + 1024;
+  if (fast) bytes += sizeof(Tile) * nst + 2 * shell_elems * sizeof(double);
   if (has_f) bytes += 2 * elems * sizeof(T) + (sizeof(T) == 4 ? 2 * elems * sizeof(double) : 0);
   const bool stage_u = !in_dev || !out_dev;
   if (stage_u) bytes += ncube * sizeof(double);
@@ -415,10 +886,13 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   Desc3* d_desc = (Desc3*)B.get(sizeof(Desc3));
   SlotState* d_state = (SlotState*)B.get(sizeof(SlotState));
   Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
+  Tile* d_strips = fast ? (Tile*)B.get(sizeof(Tile) * nst) : nullptr;
+  double* d_shell0 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
+  double* d_shell1 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
   double* d_u = stage_u ? (double*)B.get(ncube * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
   if (!x[0] || !x[1] || (has_f && (!g[0] || !g[1] || !g64[0] || !g64[1])) || !d_desc || !d_state || !d_tiles ||
-      (stage_u && !d_u) || (has_f && !f_dev && !d_f)) {
+      (stage_u && !d_u) || (has_f && !f_dev && !d_f) || (fast && (!d_strips || !d_shell0 || !d_shell1))) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
@@ -460,6 +934,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   SOR3_CK(c, cudaMemcpyAsync(d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+  if (fast) SOR3_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
   const double* u_src = u0;
   if (!in_dev) {
     SOR3_CK(c, cudaMemcpyAsync(d_u, u0, ncube * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -476,6 +951,11 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
                                           sizeof(T) == 4 ? g64[0] : nullptr, sizeof(T) == 4 ? g64[1] : nullptr,
                                           d_state);
   SOR3_CK(c, cudaGetLastError());
+  if (fast) {  // unscaled copy of both colours' shells, for the per-phase rewrite
+    const int sb = (int)std::min<size_t>((shell_elems + 255) / 256, (size_t)c->sm_count * 8);
+    k_shell_save3<<<dim3(sb, 2), 256, 0, s>>>(d_desc, d_shell0, d_shell1);
+    SOR3_CK(c, cudaGetLastError());
+  }
 
   const int grid = std::min(nt, c->sm_count * 8);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -503,7 +983,29 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
 
   // one chunk of L iterations starting after iteration `first`: two phases per
   // iteration and, for the residual stop, the test after multiples of K
+  const int lmax = fast3_lmax(w);
   auto enqueue = [&](int first, int Lc) -> sor_status {
+    if (fast) {
+      // sub-chunks end at every tested iteration (a multiple of K or the
+      // cap) with unscaled values; the residual test follows those at K
+      int done_it = 0;
+      while (done_it < Lc) {
+        const int at = first + done_it;
+        const long long next_k = ((long long)at / d.K + 1) * d.K;
+        const long long next_m = std::min<long long>(next_k, p->max_iters);
+        const int Ls = (int)std::min<long long>({(long long)lmax, next_m - at, (long long)(Lc - done_it)});
+        for (int t = 1; t <= Ls; ++t)
+          for (int colour = 0; colour < 2; ++colour)
+            SOR3_CK(c, launch_sweep3_fast(d_desc, d_state, d_strips, nst, fast_grid, d_shell0, d_shell1, colour,
+                                          phase3_of(w, t, Ls, colour), has_f, s));
+        done_it += Ls;
+        if (stop == kStopResid && (first + done_it) % d.K == 0) {
+          k_resid3d<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+        }
+      }
+      SOR3_CK(c, cudaGetLastError());
+      return SOR_OK;
+    }
     for (int it = 1; it <= Lc; ++it) {
       k_sweep3d<T><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt, 0);
       k_sweep3d<T><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt, 1);
@@ -513,7 +1015,10 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     SOR3_CK(c, cudaGetLastError());
     return SOR_OK;
   };
-  const int chunk = c->opt_chunk.load() > 0 ? c->opt_chunk.load() : 64;
+  // iterations per host check: a whole number of test intervals when K fits,
+  // so every batch starts at a tested iteration and one graph serves them all
+  const int chunk0 = c->opt_chunk.load() > 0 ? c->opt_chunk.load() : 64;
+  const int chunk = d.K <= chunk0 ? (chunk0 / d.K) * d.K : chunk0;
   const bool use_graphs = c->opt_graphs.load() != 0;
   SOR3_CK(c, cudaEventRecord(ev0, s));
   long long planned = 0;
@@ -521,7 +1026,9 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   while (!finished && planned < p->max_iters) {
     const int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
     if (use_graphs) {
-      const std::pair<int, int> key(Lc, stop == kStopResid ? (int)(planned % d.K) : 0);
+      // the residual launches and the fast path's chunk ends depend on where
+      // the tested iterations fall in the batch
+      const std::pair<int, int> key(Lc, (stop == kStopResid || fast) ? (int)(planned % d.K) : 0);
       auto itg = cl.graphs.find(key);
       if (itg == cl.graphs.end()) {
         cudaGraph_t gr = nullptr;

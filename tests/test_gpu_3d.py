@@ -1,8 +1,11 @@
 """Parity of the 3D (cube, 7-point) CUDA path with the CPU oracle, through
-the C ABI (sor_solve3d).  Bar: bit identical to the oracle in FP64 and FP32
-(same operation order, every operation rounded on its own), same iteration
-counts.  Sizes span several 32 x 128 tiles per plane, ragged tails, two
-column tiles (n > 256) and the degenerate cubes n = 1, 2."""
+the C ABI (sor_solve3d).  Bars: with SOR_FLAG_EXACT_ORDER in FP64, and in
+FP32, bit identical to the oracle (same operation order, every operation
+rounded on its own), same iteration counts; the FP64 default path (rescaled
+unknowns, shared pair sums) within a normwise relative difference of 1e-12
+after equal iteration counts.  Sizes span several 32 x 128 tiles per plane,
+ragged tails, two column tiles (n > 256), ragged warp strips, chunks cut by
+the scale cap, and the degenerate cubes n = 1, 2."""
 import numpy as np
 import pytest
 
@@ -12,6 +15,8 @@ from tests import pins
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -26,6 +31,13 @@ def ctx():
 def capi_mod():
     from paper_1401_0763_gb300 import capi
     return capi
+
+
+def shell_of(a):
+    """The 6 faces of a cube (the Dirichlet values), interior zeroed."""
+    b = np.array(a, copy=True)
+    b[1:-1, 1:-1, 1:-1] = 0.0
+    return b
 
 
 def run3(ctx, u0, f=None, device=True, **kw):
@@ -45,7 +57,8 @@ def test_fp64_bitwise(ctx, n, with_f):
     f = wl.gaussian_source3(n, 200 + n) if with_f else None
     w = oracle.omega_opt(n)
     ref = oracle.sor3d_f64(u0, w, f=f, max_iters=60, check_every=5, tol=1e-9)
-    got, res = run3(ctx, u0, f, omega=w, max_iters=60, check_every=5, tol=1e-9, precision=capi.SOR_FP64)
+    got, res = run3(ctx, u0, f, omega=w, max_iters=60, check_every=5, tol=1e-9, precision=capi.SOR_FP64,
+                    flags=capi.SOR_FLAG_EXACT_ORDER)
     assert res["iterations"] == ref["iterations"]
     assert res["converged"] == ref["converged"]
     assert np.array_equal(got, ref["u"])
@@ -75,9 +88,13 @@ def test_two_column_tiles_ragged(ctx):
     u0 = wl.random_shell(n, 7)
     w = oracle.omega_opt(n)
     ref = oracle.sor3d_f64(u0, w, max_iters=3, check_every=1, tol=0.0)
-    got, res = run3(ctx, u0, omega=w, max_iters=3, check_every=1, tol=0.0, precision=capi.SOR_FP64)
+    got, res = run3(ctx, u0, omega=w, max_iters=3, check_every=1, tol=0.0, precision=capi.SOR_FP64,
+                    flags=capi.SOR_FLAG_EXACT_ORDER)
     assert res["iterations"] == 3
     assert np.array_equal(got, ref["u"])
+    got, res = run3(ctx, u0, omega=w, max_iters=3, check_every=1, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 3
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
 
 
 def test_residual_stop_matches(ctx):
@@ -88,11 +105,16 @@ def test_residual_stop_matches(ctx):
     w = oracle.omega_opt(n)
     ref = oracle.sor3d_f64(u0, w, f=f, max_iters=2000, check_every=4, tol=1e-10, stop_mode=1)
     got, res = run3(ctx, u0, f, omega=w, max_iters=2000, check_every=4, tol=1e-10, precision=capi.SOR_FP64,
-                    stop=capi.SOR_STOP_RESID_REL)
+                    stop=capi.SOR_STOP_RESID_REL, flags=capi.SOR_FLAG_EXACT_ORDER)
     assert ref["converged"] and res["converged"]
     assert res["iterations"] == ref["iterations"]
     assert np.array_equal(got, ref["u"])
     assert res["final_resid_rel"] == ref["final_resid_rel"] < 1e-10
+    got, res = run3(ctx, u0, f, omega=w, max_iters=2000, check_every=4, tol=1e-10, precision=capi.SOR_FP64,
+                    stop=capi.SOR_STOP_RESID_REL)
+    assert res["converged"] and res["iterations"] == ref["iterations"]
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
+    assert res["final_resid_rel"] < 1e-10
 
 
 def test_harmonic_quadratic_and_dst(ctx):
@@ -127,10 +149,68 @@ def test_full_size_cube_bitwise(ctx):
     u0 = wl.random_shell(n, 0)
     w = oracle.omega_opt(n)
     ref = oracle.sor3d_f64(u0, w, max_iters=20, check_every=10, tol=0.0)
-    got, res = run3(ctx, u0, omega=w, max_iters=20, check_every=10, tol=0.0, precision=capi.SOR_FP64)
+    got, res = run3(ctx, u0, omega=w, max_iters=20, check_every=10, tol=0.0, precision=capi.SOR_FP64,
+                    flags=capi.SOR_FLAG_EXACT_ORDER)
     assert res["iterations"] == 20
     assert np.array_equal(got, ref["u"])
     assert res["final_maxdelta"] == ref["final_maxdelta"]
+    got, res = run3(ctx, u0, omega=w, max_iters=20, check_every=10, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 20
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
+    assert abs(res["final_maxdelta"] - ref["final_maxdelta"]) <= 1e-10 * ref["final_maxdelta"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 40, 65, 130])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_fp64_default_within_tolerance(ctx, n, with_f):
+    """The default FP64 path: chunks of 5 rescaled iterations ending at the
+    tested iterations, every strip of a plane ragged for n = 65, 130."""
+    capi = capi_mod()
+    u0 = wl.random_shell(n, 500 + n)
+    f = wl.gaussian_source3(n, 600 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, f=f, max_iters=60, check_every=5, tol=0.0)
+    got, res = run3(ctx, u0, f, omega=w, max_iters=60, check_every=5, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 60 and not res["converged"]
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
+    assert np.array_equal(shell_of(got), shell_of(u0))  # shell back at scale 1 after every chunk
+    scale = max(1.0, float(np.max(np.abs(ref["u"]))))
+    assert abs(res["final_maxdelta"] - ref["final_maxdelta"]) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.6, 1.95])
+def test_fp64_default_chunks_cut_by_scale_cap(ctx, omega):
+    """Tests every 500 iterations, so the chunk length is set by the cap on
+    the carried scale (w/6)^-2L (120 iterations at w = 1.95) and by the
+    iteration cap; w = 1 drops the (1 - w) term, w < 1 under-relaxes."""
+    capi = capi_mod()
+    n = 19
+    u0 = wl.random_shell(n, 31)
+    f = wl.gaussian_source3(n, 32)
+    ref = oracle.sor3d_f64(u0, omega, f=f, max_iters=300, check_every=500, tol=0.0)
+    got, res = run3(ctx, u0, f, omega=omega, max_iters=300, check_every=500, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 300
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
+    assert np.array_equal(shell_of(got), shell_of(u0))
+
+
+def test_fp64_default_stops_like_oracle(ctx):
+    """Max-change stop: the default path takes the oracle's iteration count
+    (the tested changes sit far from the tolerance) and converges to the
+    closed-form harmonic cube."""
+    capi = capi_mod()
+    n = 33
+    u0 = wl.random_shell(n, 77)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, max_iters=3000, check_every=7, tol=1e-9)
+    got, res = run3(ctx, u0, omega=w, max_iters=3000, check_every=7, tol=1e-9, precision=capi.SOR_FP64)
+    assert ref["converged"] and res["converged"]
+    assert res["iterations"] == ref["iterations"]
+    assert pins.rel_err3(got, ref["u"]) <= TOL64
+    u0, exact = pins.cube_from(lambda x, y, z: x * y + 2.0 * y * z - z * x + 3.0 * x, 40)
+    got, res = run3(ctx, u0, max_iters=5000, check_every=10, tol=1e-14, precision=capi.SOR_FP64)
+    assert res["converged"]
+    assert np.max(np.abs(got - exact)) < 1e-11
 
 
 def test_invalid_arguments(ctx):
