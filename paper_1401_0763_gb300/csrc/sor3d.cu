@@ -587,38 +587,120 @@ __device__ __forceinline__ void f3_shell(const Desc3& d, const double* __restric
   }
 }
 
-// One colour phase over warp strips (plane k, rows [i0, i1), 128 packed
-// columns); the last strip to finish the black phase closes the iteration.
-template <bool UNIT_BETA, bool HAS_G>
-__global__ void __launch_bounds__(kThreads, 2) k_sweep3_fast(const Desc3* __restrict__ dp, SlotState* st,
-                                                             const Tile* __restrict__ strips, int nstrips,
-                                                             const double* __restrict__ shell0,
-                                                             const double* __restrict__ shell1, int colour,
-                                                             Phase3 ph) {
+// A whole chunk of 2L phases in one launch, scheduled as a data flow.  The
+// work items are (phase p, strip t), numbered p * nstrips + t; warps claim
+// them in that order from a counter.  Item (p, t) may start once strip t and
+// its neighbours -- the strips of the planes below and above, the row bands
+// above and below and the column tiles left and right, the only ones whose
+// cells its stencil reads or whose readers it could overwrite -- have
+// finished phase p-1 (progress[t] counts the phases a strip has finished).
+// Every dependency has a smaller number than the item that waits for it, so
+// the smallest unfinished item can always run: the schedule cannot
+// deadlock, needs no co-residency, lets fast SMs take more items and lets
+// phase p+1 start on planes whose neighbours are done while phase p is
+// still draining.  A strip publishes its progress with a release store after
+// fencing its writes; every lane of a waiting warp reads the counters with
+// acquire loads.  Every wait is bounded: past kFlowSpins polls the warp
+// records an error in the slot state and returns (the host reports
+// SOR_ERR_INTERNAL).  The last strip to finish the last phase closes the
+// chunk's iterations.
+
+constexpr int kFlowSpins = 1 << 21;  // polls of about 0.1 us each: far above any phase
+
+__device__ __forceinline__ unsigned f3_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void f3_st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lanes 0..6 poll one counter each (strip t itself and up to six
+// neighbours, -1 = none) until it reaches `target`; false on timeout.
+__device__ __forceinline__ bool f3_wait(const unsigned* progress, const int (&nb)[7], unsigned target, int lane) {
+  bool ok = true;
+  int mine = -1;
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    if (lane == k) mine = nb[k];
+  if (mine >= 0) {
+    int spins = 0;
+    while (f3_ld_acquire(progress + mine) < target) {
+      if (++spins > kFlowSpins) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+      if (nb[k] >= 0) (void)f3_ld_acquire(progress + nb[k]);
+  }
+  return ok;
+}
+
+template <bool HAS_G>
+__global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict__ dp, SlotState* st,
+                                                         const Tile* __restrict__ strips, int nstrips, int bands,
+                                                         int ct, const double* __restrict__ shell0,
+                                                         const double* __restrict__ shell1,
+                                                         const Phase3* __restrict__ phases, int nphases,
+                                                         unsigned* progress) {
   extern __shared__ __align__(16) unsigned char f3_mem[];
   const int lane = threadIdx.x & 31;
   Stage3<HAS_G>* stages = reinterpret_cast<Stage3<HAS_G>*>(f3_mem) + (threadIdx.x >> 5) * kF3Stages;
   const Desc3& d = *dp;
-  const int warp = blockIdx.x * kWarpsY + (threadIdx.x >> 5);
-  const int nwarps = gridDim.x * kWarpsY;
-  for (int t = warp; t < nstrips; t += nwarps) {
-    const Tile tl = strips[t];
-    int skip = 0, kk = 0, measure = 0;
-    if (lane == 0) {
-      skip = *((volatile int*)&st->done);
-      kk = *((volatile int*)&st->iters) + 1;
-      measure = ((kk % d.K) == 0) || (kk >= d.max_iters);
-      if (!skip && measure && !ph.last) {  // the host plan must end chunks at measured iterations
+  int skip = 0, k0 = 0;
+  if (lane == 0) {
+    skip = *((volatile int*)&st->done);
+    k0 = *((volatile int*)&st->iters);
+  }
+  skip = __shfl_sync(0xffffffffu, skip, 0);
+  if (skip) return;  // done changes inside a launch only after its last item
+  k0 = __shfl_sync(0xffffffffu, k0, 0);
+  const int n = d.n, m = d.m, pitch = d.pitch;
+  const long long items = (long long)nphases * nstrips;
+  unsigned* claim = progress + nstrips;
+  const int per_plane = bands * ct;
+  for (;;) {
+    long long g = 0;
+    if (lane == 0) g = (long long)atomicAdd(claim, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= items) break;
+    const int p = (int)(g / nstrips), t = (int)(g - (long long)p * nstrips);
+    const int colour = p & 1;
+    const int kk = k0 + (p >> 1) + 1;
+    const Phase3 ph = phases[p];
+    const int measure = ((kk % d.K) == 0) || (kk >= d.max_iters);
+    if (measure && !ph.last) {  // the host plan must end chunks at measured iterations
+      if (lane == 0) {
         st->error = 1;
         st->done = 1;
-        skip = 1;
+      }
+      return;
+    }
+    if (p > 0) {
+      const int kp = t / per_plane, r = t - kp * per_plane, band = r / ct, tc = r - band * ct;
+      const int nb[7] = {t,
+                         kp > 0 ? t - per_plane : -1,
+                         kp + 1 < n ? t + per_plane : -1,
+                         band > 0 ? t - ct : -1,
+                         band + 1 < bands ? t + ct : -1,
+                         tc > 0 ? t - 1 : -1,
+                         tc + 1 < ct ? t + 1 : -1};
+      if (!f3_wait(progress, nb, (unsigned)p, lane)) {
+        if (lane == 0) {
+          st->error = 1;
+          st->done = 1;
+        }
+        return;
       }
     }
-    skip = __shfl_sync(0xffffffffu, skip, 0);
-    if (skip) continue;
-    kk = __shfl_sync(0xffffffffu, kk, 0);
-    measure = __shfl_sync(0xffffffffu, measure, 0);
-    const int n = d.n, m = d.m, pitch = d.pitch;
+    const Tile tl = strips[t];
     const int k = tl.row0 / m, i0 = tl.row0 - k * m, i1 = i0 + tl.nrows;
     double* X = (double*)d.x[colour];
     const double* O = (const double*)d.x[colour ^ 1];
@@ -633,12 +715,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep3_fast(const Desc3* __rest
     for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
     unsigned long long dm = 0;
     const int s0 = (i0 + k + colour) & 1;
-    if (measure) {
-      if (s0 == 0) f3_rows<UNIT_BETA, HAS_G, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-      else f3_rows<UNIT_BETA, HAS_G, true, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    const bool unit = ph.beta == 1.0;
+    if (measure) {  // the last iteration of the chunk: unscaled, change measured
+      if (s0 == 0) f3_rows<false, HAS_G, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<false, HAS_G, true, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    } else if (unit) {
+      if (s0 == 0) f3_rows<true, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<true, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
     } else {
-      if (s0 == 0) f3_rows<UNIT_BETA, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-      else f3_rows<UNIT_BETA, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      if (s0 == 0) f3_rows<false, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<false, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
     }
     c3_wait<0>();
     f3_shell(d, colour ? shell1 : shell0, X, colour, k, i0, i1, tl.col0, q0, lane, ph.nscale);
@@ -646,18 +732,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep3_fast(const Desc3* __rest
       dm = warp_max64(dm);
       if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
     }
-    if (colour == 1) {
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) {
+    __threadfence();  // this lane's cells are visible before the strip's progress is
+    __syncwarp();
+    if (lane == 0) {
+      f3_st_release(progress + t, (unsigned)(p + 1));
+      if (p == nphases - 1) {
         const unsigned prev = atomicAdd(&st->arrive, 1u);
         if (prev == (unsigned)nstrips - 1u) {
           __threadfence();
-          finalize3(d, st, kk, measure);
+          finalize3(d, st, k0 + (nphases >> 1), measure);
         }
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -711,33 +798,25 @@ int fast3_lmax(double omega) {
   return std::max(1, std::min(L, 256));
 }
 
-// Opts the four instantiations into their dynamic shared memory (before any
+// Opts both instantiations into their dynamic shared memory (before any
 // capture: attribute calls stay out of graph capture).
 cudaError_t fast3_prepare() {
   static cudaError_t state = cudaErrorNotReady;
   if (state == cudaErrorNotReady) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep3_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_f3_flow<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)f3_smem<false>());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_sweep3_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)f3_smem<false>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_sweep3_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)f3_smem<true>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_sweep3_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)f3_smem<true>());
+      e = cudaFuncSetAttribute(k_f3_flow<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f3_smem<true>());
     state = e;
   }
   return state;
 }
 
-// Resident blocks per SM of the phase kernel (0 on failure).
+// Resident blocks per SM of the flow kernel (0 on failure).
 int fast3_blocks_per_sm(bool has_g) {
   int nb = 0;
-  cudaError_t e = has_g ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3_fast<true, true>, kThreads,
-                                                                       f3_smem<true>())
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3_fast<true, false>, kThreads,
+  cudaError_t e = has_g ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_f3_flow<true>, kThreads, f3_smem<true>())
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_f3_flow<false>, kThreads,
                                                                        f3_smem<false>());
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -746,46 +825,34 @@ int fast3_blocks_per_sm(bool has_g) {
   return nb;
 }
 
-cudaError_t launch_sweep3_fast(const Desc3* d, SlotState* st, const Tile* strips, int nstrips, int grid,
-                               const double* shell0, const double* shell1, int colour, const Phase3& ph, bool has_g,
-                               cudaStream_t s) {
-  const bool unit = ph.beta == 1.0;
+cudaError_t launch_f3_flow(const Desc3* d, SlotState* st, const Tile* strips, int nstrips, int bands, int ct,
+                           int grid, const double* shell0, const double* shell1, const Phase3* phases, int nphases,
+                           unsigned* progress, bool has_g, cudaStream_t s) {
   const size_t sm = has_g ? f3_smem<true>() : f3_smem<false>();
-  if (unit && !has_g)
-    k_sweep3_fast<true, false><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
-  else if (unit)
-    k_sweep3_fast<true, true><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
-  else if (!has_g)
-    k_sweep3_fast<false, false><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+  if (has_g)
+    k_f3_flow<true><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, bands, ct, shell0, shell1, phases, nphases,
+                                               progress);
   else
-    k_sweep3_fast<false, true><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, shell0, shell1, colour, ph);
+    k_f3_flow<false><<<grid, kThreads, sm, s>>>(d, st, strips, nstrips, bands, ct, shell0, shell1, phases, nphases,
+                                                progress);
   return cudaGetLastError();
 }
 
-// Warp strips of the FP64 default phases: every plane cut into B row bands
-// (at least 8 rows each) per 128-column tile, B chosen so that the strips
-// fill whole waves of `warps` warps with little per-strip overhead (about two
-// rows' worth: the first row's pairs, the pipeline fill and the shell).
-void build_strips3(const Layout& L, int warps, std::vector<Tile>* out) {
+// Warp strips of the FP64 default phases: every plane cut into `bands` row
+// bands per 128-column tile, about 32 rows each (at least 8), and at least
+// one strip per resident warp.  Numbered plane-major, then band, then column
+// tile (the flow kernel derives a strip's neighbours from its number).
+int build_strips3(const Layout& L, int warps, std::vector<Tile>* out) {
   const int n = L.n, m = n + 2, ct = L.col_tiles();
-  int best_b = 1;
-  double best = -1.0;
-  for (int b = 1; b <= std::max(1, n / 8); ++b) {
-    const long long total = (long long)n * ct * b;
-    const long long waves = (total + warps - 1) / warps;
-    const double rows = (double)n / b;
-    const double score = (double)total / (double)(waves * warps) * rows / (rows + 2.0);
-    if (score > best + 1e-9) {
-      best = score;
-      best_b = b;
-    }
-  }
+  const long long per_band = (long long)n * ct;
+  int b = std::max(n / 32, (int)((warps + per_band - 1) / per_band));
+  b = std::max(1, std::min(b, std::max(1, n / 8)));
   for (int k = 1; k <= n; ++k)
-    for (int b = 0; b < best_b; ++b) {
-      const int a0 = 1 + (int)((long long)b * n / best_b), a1 = 1 + (int)((long long)(b + 1) * n / best_b);
-      for (int t = 0; t < ct; ++t)
-        if (a1 > a0) out->push_back(Tile{0, k * m + a0, 1 + t * kWarpCols, a1 - a0});
+    for (int r = 0; r < b; ++r) {
+      const int a0 = 1 + (int)((long long)r * n / b), a1 = 1 + (int)((long long)(r + 1) * n / b);
+      for (int t = 0; t < ct; ++t) out->push_back(Tile{0, k * m + a0, 1 + t * kWarpCols, a1 - a0});
     }
+  return b;
 }
 
 #define SOR3_CK(ctx, expr)                                                                    \
@@ -833,7 +900,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   // the exact order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
   const bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
   std::vector<Tile> strips;
-  int fast_grid = 0;
+  int fast_grid = 0, bands = 0;
   if (fast) {
     SOR3_CK(c, fast3_prepare());
     const int bps = fast3_blocks_per_sm(has_f);
@@ -841,11 +908,13 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
       c->set_error("3D phase kernel does not fit on an SM");
       return SOR_ERR_CUDA;
     }
-    build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
-    fast_grid = std::min(c->sm_count * bps, (int)((strips.size() + kWarpsY - 1) / kWarpsY));
+    bands = build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
+    fast_grid = c->sm_count * bps;
   }
   const int nst = (int)strips.size();
   const size_t shell_elems = shell3_elems(m, pitch);
+  const int lmax = fast3_lmax(w);
+  constexpr int kTables = 16;  // phase tables of distinct chunk lengths held at once
 
   // tiles: plane k, rows of 32, columns of 128 packed cells
   std::vector<Tile> tiles;
@@ -856,7 +925,9 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   const int nt = (int)tiles.size();
 
   size_t bytes = 2 * elems * sizeof(T) + sizeof(Desc3) + sizeof(SlotState) + sizeof(Tile) * nt + 1024;
-  if (fast) bytes += sizeof(Tile) * nst + 2 * shell_elems * sizeof(double);
+  if (fast)
+    bytes += sizeof(Tile) * nst + 2 * shell_elems * sizeof(double) + sizeof(unsigned) * (nst + 1) +
+             sizeof(Phase3) * 2 * (size_t)lmax * kTables;
   if (has_f) bytes += 2 * elems * sizeof(T) + (sizeof(T) == 4 ? 2 * elems * sizeof(double) : 0);
   const bool stage_u = !in_dev || !out_dev;
   if (stage_u) bytes += ncube * sizeof(double);
@@ -888,11 +959,13 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
   Tile* d_strips = fast ? (Tile*)B.get(sizeof(Tile) * nst) : nullptr;
   double* d_shell0 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
+  unsigned* d_progress = fast ? (unsigned*)B.get(sizeof(unsigned) * (nst + 1)) : nullptr;
+  Phase3* d_tables = fast ? (Phase3*)B.get(sizeof(Phase3) * 2 * (size_t)lmax * kTables) : nullptr;
   double* d_shell1 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
   double* d_u = stage_u ? (double*)B.get(ncube * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
   if (!x[0] || !x[1] || (has_f && (!g[0] || !g[1] || !g64[0] || !g64[1])) || !d_desc || !d_state || !d_tiles ||
-      (stage_u && !d_u) || (has_f && !f_dev && !d_f) || (fast && (!d_strips || !d_shell0 || !d_shell1))) {
+      (stage_u && !d_u) || (has_f && !f_dev && !d_f) || (fast && (!d_strips || !d_shell0 || !d_shell1 || !d_progress || !d_tables))) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
@@ -981,27 +1054,57 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     }
   } cl{ev0, ev1, h_state, {}};
 
-  // one chunk of L iterations starting after iteration `first`: two phases per
-  // iteration and, for the residual stop, the test after multiples of K
-  const int lmax = fast3_lmax(w);
+  // FP64 default: a batch of Lc iterations after iteration `first` runs as
+  // chunks that end at every tested iteration (a multiple of K or the cap)
+  // and stay within the scale cap; each chunk is one flow launch whose phase
+  // constants come from a device table per chunk length
+  auto plan_chunks = [&](long long first, int Lc) {
+    std::vector<int> out;
+    int done_it = 0;
+    while (done_it < Lc) {
+      const long long at = first + done_it;
+      const long long next_m = std::min<long long>((at / d.K + 1) * d.K, p->max_iters);
+      const int Ls = (int)std::min<long long>({(long long)lmax, next_m - at, (long long)(Lc - done_it)});
+      out.push_back(Ls);
+      done_it += Ls;
+    }
+    return out;
+  };
+  std::map<int, int> table_of;  // chunk length -> table slot
+  std::vector<std::vector<Phase3>> host_tables(kTables);
+  // uploads the tables the batch needs (outside any capture); when the slots
+  // run out, the captured graphs that name them are dropped first
+  auto ensure_tables = [&](const std::vector<int>& lens) -> sor_status {
+    for (int Ls : lens) {
+      if (table_of.count(Ls)) continue;
+      if ((int)table_of.size() == kTables) {
+        SOR3_CK(c, cudaStreamSynchronize(s));
+        for (auto& kv : cl.graphs) cudaGraphExecDestroy(kv.second);
+        cl.graphs.clear();
+        table_of.clear();
+      }
+      const int slot = (int)table_of.size();
+      std::vector<Phase3>& h = host_tables[slot];
+      h.resize(2 * (size_t)Ls);
+      for (int t = 1; t <= Ls; ++t)
+        for (int colour = 0; colour < 2; ++colour) h[2 * (t - 1) + colour] = phase3_of(w, t, Ls, colour);
+      SOR3_CK(c, cudaMemcpyAsync(d_tables + (size_t)slot * 2 * lmax, h.data(), sizeof(Phase3) * h.size(),
+                                 cudaMemcpyHostToDevice, s));
+      table_of[Ls] = slot;
+    }
+    return SOR_OK;
+  };
   auto enqueue = [&](int first, int Lc) -> sor_status {
     if (fast) {
-      // sub-chunks end at every tested iteration (a multiple of K or the
-      // cap) with unscaled values; the residual test follows those at K
       int done_it = 0;
-      while (done_it < Lc) {
-        const int at = first + done_it;
-        const long long next_k = ((long long)at / d.K + 1) * d.K;
-        const long long next_m = std::min<long long>(next_k, p->max_iters);
-        const int Ls = (int)std::min<long long>({(long long)lmax, next_m - at, (long long)(Lc - done_it)});
-        for (int t = 1; t <= Ls; ++t)
-          for (int colour = 0; colour < 2; ++colour)
-            SOR3_CK(c, launch_sweep3_fast(d_desc, d_state, d_strips, nst, fast_grid, d_shell0, d_shell1, colour,
-                                          phase3_of(w, t, Ls, colour), has_f, s));
+      for (int Ls : plan_chunks(first, Lc)) {
+        const Phase3* tab = d_tables + (size_t)table_of.at(Ls) * 2 * lmax;
+        SOR3_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
+        SOR3_CK(c, launch_f3_flow(d_desc, d_state, d_strips, nst, bands, L.col_tiles(), fast_grid, d_shell0,
+                                  d_shell1, tab, 2 * Ls, d_progress, has_f, s));
         done_it += Ls;
-        if (stop == kStopResid && (first + done_it) % d.K == 0) {
+        if (stop == kStopResid && (first + done_it) % d.K == 0)
           k_resid3d<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
-        }
       }
       SOR3_CK(c, cudaGetLastError());
       return SOR_OK;
@@ -1024,7 +1127,13 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   long long planned = 0;
   bool finished = st.done != 0;
   while (!finished && planned < p->max_iters) {
-    const int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
+    int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
+    if (fast && d.K > chunk0)  // batches end at tested iterations: few distinct chunk lengths
+      Lc = (int)std::min<long long>(Lc, std::min<long long>((planned / d.K + 1) * d.K, p->max_iters) - planned);
+    if (fast) {
+      const sor_status ts = ensure_tables(plan_chunks(planned, Lc));
+      if (ts != SOR_OK) return ts;
+    }
     if (use_graphs) {
       // the residual launches and the fast path's chunk ends depend on where
       // the tested iterations fall in the batch
