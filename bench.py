@@ -579,7 +579,7 @@ def workload_cube256(args, ctx, capi, wl):
                        "solve_s": dt, "iterations": res["iterations"]}
     # FP64: 8 algorithmic flops per update ((1-w)u + (w/6)(sum of six neighbours): 5 adds, 2 multiplies,
     # 1 add); the default kernel issues 5 FP64 operations per update for them, the exact one 8
-    for name, kern in (("fp64", "k_f3_flow"), ("fp64_exact", "k_sweep3d<double>")):
+    for name, kern in (("fp64", "k_f3_flow"), ("fp64_exact", "k_3_flow<double>")):
         ach = 8.0 * lines[name]["glups"] / 1e3
         lines[name]["roofline"] = {"bound": "alu", "achieved": ach, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                                    "frac": ach / NOMINAL_FP64_TFLOPS, "kernel": kern}
@@ -588,7 +588,7 @@ def workload_cube256(args, ctx, capi, wl):
     hbm = float(peaks.get("hbm_gbs") or 6800.0)
     lines["fp32"]["roofline"] = {"bound": "hbm", "achieved": 8.0 * lines["fp32"]["glups"], "peak": hbm,
                                  "unit": "GB/s", "frac": 8.0 * lines["fp32"]["glups"] / hbm,
-                                 "kernel": "k_sweep3d<float>", "peak_source": src}
+                                 "kernel": "k_3_flow<float>", "peak_source": src}
     cpu = None
     if not args.no_cpu_baseline:
         k = 10

@@ -182,64 +182,6 @@ __device__ __forceinline__ void finalize3(const Desc3& d, SlotState* st, int k, 
   if (k >= d.max_iters) st->done = 1;
 }
 
-// One colour phase over tiles (plane, rows, 128 packed columns); a tile's
-// rows are split among the block's warps.  The last tile to finish the black
-// phase closes the iteration.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_sweep3d(const Desc3* __restrict__ dp, SlotState* st,
-                                                      const Tile* __restrict__ tiles, int ntiles, int colour) {
-  __shared__ unsigned long long red[kWarpsY];
-  __shared__ int ctl[3];
-  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-  const Desc3& d = *dp;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    if (threadIdx.x == 0) {
-      const int kk = *((volatile int*)&st->iters) + 1;
-      ctl[0] = *((volatile int*)&st->done);
-      ctl[1] = kk;
-      ctl[2] = ((kk % d.K) == 0) || (kk >= d.max_iters);
-    }
-    __syncthreads();
-    const int skip = ctl[0], kk = ctl[1], measure = ctl[2];
-    __syncthreads();
-    if (skip) continue;
-    T* X = (T*)d.x[colour];
-    const T* O = (const T*)d.x[colour ^ 1];
-    const T* G = (const T*)d.g[colour];
-    const T a = sizeof(T) == 4 ? (T)d.a32 : (T)d.a64;
-    const T b = sizeof(T) == 4 ? (T)d.b32 : (T)d.b64;
-    const int k = tl.row0 / d.m, ib = tl.row0 - k * d.m;
-    const int q0 = tl.col0 + lane * kVec;
-    const int rpw = (tl.nrows + kWarpsY - 1) / kWarpsY;
-    const int i0 = ib + wy * rpw;
-    const int i1 = min(i0 + rpw, ib + tl.nrows);
-    unsigned long long dm = 0;
-    // the source term is a compile-time choice: as a runtime test the compiler
-    // issues its addition speculatively, one more FP64 operation per cell
-    if (measure)
-      dm = G ? sweep3_rows<T, true, true>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane)
-             : sweep3_rows<T, true, false>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
-    else if (G)
-      (void)sweep3_rows<T, false, true>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
-    else
-      (void)sweep3_rows<T, false, false>(X, O, G, a, b, d.pitch, d.m, d.n, colour, k, q0, i0, i1, lane);
-    if (measure) block_max_to(dm, &st->dmax_bits, red);
-    if (colour == 1) {
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&st->arrive, 1u);
-        if (prev == (unsigned)d.tiles - 1u) {
-          __threadfence();
-          finalize3(d, st, kk, measure);
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
 // Scaled residual over tiles, both colours, in FP64.  CHECK: the residual
 // stop of Algorithm 1's test on iterations that are multiples of K (decided
 // by the last tile); otherwise only rho of the current iterate is recorded.
@@ -748,6 +690,94 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
   }
 }
 
+// The exact-order phases (FP32, and FP64 with SOR_FLAG_EXACT_ORDER) under the
+// same data-flow schedule: items (phase, strip) claimed in order, each
+// waiting for its strip and the six neighbouring strips to finish the
+// previous phase; the rows of a strip are swept by sweep3_rows.  A launch
+// covers the iterations up to the next tested one, whose change it measures.
+template <typename T, bool HAS_G>
+__global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ dp, SlotState* st,
+                                                     const Tile* __restrict__ strips, int nstrips, int bands, int ct,
+                                                     int nphases, unsigned* progress) {
+  const int lane = threadIdx.x & 31;
+  const Desc3& d = *dp;
+  int skip = 0, k0 = 0;
+  if (lane == 0) {
+    skip = *((volatile int*)&st->done);
+    k0 = *((volatile int*)&st->iters);
+  }
+  skip = __shfl_sync(0xffffffffu, skip, 0);
+  if (skip) return;  // done changes inside a launch only after its last item
+  k0 = __shfl_sync(0xffffffffu, k0, 0);
+  const int n = d.n, m = d.m, pitch = d.pitch;
+  const T a = sizeof(T) == 4 ? (T)d.a32 : (T)d.a64;
+  const T b = sizeof(T) == 4 ? (T)d.b32 : (T)d.b64;
+  const long long items = (long long)nphases * nstrips;
+  unsigned* claim = progress + nstrips;
+  const int per_plane = bands * ct;
+  const int last_it = k0 + (nphases >> 1);
+  for (;;) {
+    long long g = 0;
+    if (lane == 0) g = (long long)atomicAdd(claim, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= items) break;
+    const int p = (int)(g / nstrips), t = (int)(g - (long long)p * nstrips);
+    const int colour = p & 1;
+    const int kk = k0 + (p >> 1) + 1;
+    const int measure = ((kk % d.K) == 0) || (kk >= d.max_iters);
+    if (measure && kk != last_it) {  // the host plan must end launches at tested iterations
+      if (lane == 0) {
+        st->error = 1;
+        st->done = 1;
+      }
+      return;
+    }
+    if (p > 0) {
+      const int kp = t / per_plane, r = t - kp * per_plane, band = r / ct, tc = r - band * ct;
+      const int nb[7] = {t,
+                         kp > 0 ? t - per_plane : -1,
+                         kp + 1 < n ? t + per_plane : -1,
+                         band > 0 ? t - ct : -1,
+                         band + 1 < bands ? t + ct : -1,
+                         tc > 0 ? t - 1 : -1,
+                         tc + 1 < ct ? t + 1 : -1};
+      if (!f3_wait(progress, nb, (unsigned)p, lane)) {
+        if (lane == 0) {
+          st->error = 1;
+          st->done = 1;
+        }
+        return;
+      }
+    }
+    const Tile tl = strips[t];
+    const int k = tl.row0 / m, i0 = tl.row0 - k * m, i1 = i0 + tl.nrows;
+    T* X = (T*)d.x[colour];
+    const T* O = (const T*)d.x[colour ^ 1];
+    const T* G = (const T*)d.g[colour];
+    const int q0 = tl.col0 + lane * kVec;
+    if (measure) {
+      unsigned long long dm = sweep3_rows<T, true, HAS_G>(X, O, G, a, b, pitch, m, n, colour, k, q0, i0, i1, lane);
+      dm = warp_max64(dm);
+      if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+    } else {
+      (void)sweep3_rows<T, false, HAS_G>(X, O, G, a, b, pitch, m, n, colour, k, q0, i0, i1, lane);
+    }
+    __threadfence();  // this lane's cells are visible before the strip's progress is
+    __syncwarp();
+    if (lane == 0) {
+      f3_st_release(progress + t, (unsigned)(p + 1));
+      if (p == nphases - 1) {
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        if (prev == (unsigned)nstrips - 1u) {
+          __threadfence();
+          finalize3(d, st, last_it, measure);
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Constants of phase (t, colour) of a chunk of L iterations for w = omega/6.
 Phase3 phase3_of(double omega, int t, int L, int colour) {
   const double w6 = omega / 6.0, omc = 1.0 - omega;
@@ -838,7 +868,29 @@ cudaError_t launch_f3_flow(const Desc3* d, SlotState* st, const Tile* strips, in
   return cudaGetLastError();
 }
 
-// Warp strips of the FP64 default phases: every plane cut into `bands` row
+template <typename T>
+int exact3_blocks_per_sm(bool has_g) {
+  int nb = 0;
+  cudaError_t e = has_g ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_3_flow<T, true>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_3_flow<T, false>, kThreads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+template <typename T>
+cudaError_t launch_3_flow(const Desc3* d, SlotState* st, const Tile* strips, int nstrips, int bands, int ct,
+                          int grid, int nphases, unsigned* progress, bool has_g, cudaStream_t s) {
+  if (has_g)
+    k_3_flow<T, true><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
+  else
+    k_3_flow<T, false><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
+  return cudaGetLastError();
+}
+
+// Warp strips of the flow kernels: every plane cut into `bands` row
 // bands per 128-column tile, about 32 rows each (at least 8), and at least
 // one strip per resident warp.  Numbered plane-major, then band, then column
 // tile (the flow kernel derives a strip's neighbours from its number).
@@ -899,18 +951,15 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   // FP64 default: the rescaled phases with shared pair sums (within 1e-12 of
   // the exact order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
   const bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
-  std::vector<Tile> strips;
-  int fast_grid = 0, bands = 0;
-  if (fast) {
-    SOR3_CK(c, fast3_prepare());
-    const int bps = fast3_blocks_per_sm(has_f);
-    if (bps < 1) {
-      c->set_error("3D phase kernel does not fit on an SM");
-      return SOR_ERR_CUDA;
-    }
-    bands = build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
-    fast_grid = c->sm_count * bps;
+  if (fast) SOR3_CK(c, fast3_prepare());
+  const int bps = fast ? fast3_blocks_per_sm(has_f) : exact3_blocks_per_sm<T>(has_f);
+  if (bps < 1) {
+    c->set_error("3D phase kernel does not fit on an SM");
+    return SOR_ERR_CUDA;
   }
+  std::vector<Tile> strips;
+  const int bands = build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
+  const int flow_grid = c->sm_count * bps;
   const int nst = (int)strips.size();
   const size_t shell_elems = shell3_elems(m, pitch);
   const int lmax = fast3_lmax(w);
@@ -925,9 +974,8 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   const int nt = (int)tiles.size();
 
   size_t bytes = 2 * elems * sizeof(T) + sizeof(Desc3) + sizeof(SlotState) + sizeof(Tile) * nt + 1024;
-  if (fast)
-    bytes += sizeof(Tile) * nst + 2 * shell_elems * sizeof(double) + sizeof(unsigned) * (nst + 1) +
-             sizeof(Phase3) * 2 * (size_t)lmax * kTables;
+  bytes += sizeof(Tile) * nst + sizeof(unsigned) * (nst + 1);
+  if (fast) bytes += 2 * shell_elems * sizeof(double) + sizeof(Phase3) * 2 * (size_t)lmax * kTables;
   if (has_f) bytes += 2 * elems * sizeof(T) + (sizeof(T) == 4 ? 2 * elems * sizeof(double) : 0);
   const bool stage_u = !in_dev || !out_dev;
   if (stage_u) bytes += ncube * sizeof(double);
@@ -957,15 +1005,15 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   Desc3* d_desc = (Desc3*)B.get(sizeof(Desc3));
   SlotState* d_state = (SlotState*)B.get(sizeof(SlotState));
   Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
-  Tile* d_strips = fast ? (Tile*)B.get(sizeof(Tile) * nst) : nullptr;
+  Tile* d_strips = (Tile*)B.get(sizeof(Tile) * nst);
   double* d_shell0 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
-  unsigned* d_progress = fast ? (unsigned*)B.get(sizeof(unsigned) * (nst + 1)) : nullptr;
+  unsigned* d_progress = (unsigned*)B.get(sizeof(unsigned) * (nst + 1));
   Phase3* d_tables = fast ? (Phase3*)B.get(sizeof(Phase3) * 2 * (size_t)lmax * kTables) : nullptr;
   double* d_shell1 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
   double* d_u = stage_u ? (double*)B.get(ncube * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
   if (!x[0] || !x[1] || (has_f && (!g[0] || !g[1] || !g64[0] || !g64[1])) || !d_desc || !d_state || !d_tiles ||
-      (stage_u && !d_u) || (has_f && !f_dev && !d_f) || (fast && (!d_strips || !d_shell0 || !d_shell1 || !d_progress || !d_tables))) {
+      (stage_u && !d_u) || (has_f && !f_dev && !d_f) || !d_strips || !d_progress || (fast && (!d_shell0 || !d_shell1 || !d_tables))) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
@@ -1007,7 +1055,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   SOR3_CK(c, cudaMemcpyAsync(d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
-  if (fast) SOR3_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
+  SOR3_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
   const double* u_src = u0;
   if (!in_dev) {
     SOR3_CK(c, cudaMemcpyAsync(d_u, u0, ncube * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1054,17 +1102,18 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     }
   } cl{ev0, ev1, h_state, {}};
 
-  // FP64 default: a batch of Lc iterations after iteration `first` runs as
-  // chunks that end at every tested iteration (a multiple of K or the cap)
-  // and stay within the scale cap; each chunk is one flow launch whose phase
-  // constants come from a device table per chunk length
+  // A batch of Lc iterations after iteration `first` runs as chunks that end
+  // at every tested iteration (a multiple of K or the cap), one flow launch
+  // each; on the FP64 default path chunks also stay within the scale cap and
+  // take their phase constants from a device table per chunk length
+  const long long lcap = fast ? lmax : (1LL << 30);
   auto plan_chunks = [&](long long first, int Lc) {
     std::vector<int> out;
     int done_it = 0;
     while (done_it < Lc) {
       const long long at = first + done_it;
       const long long next_m = std::min<long long>((at / d.K + 1) * d.K, p->max_iters);
-      const int Ls = (int)std::min<long long>({(long long)lmax, next_m - at, (long long)(Lc - done_it)});
+      const int Ls = (int)std::min<long long>({lcap, next_m - at, (long long)(Lc - done_it)});
       out.push_back(Ls);
       done_it += Ls;
     }
@@ -1095,24 +1144,18 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     return SOR_OK;
   };
   auto enqueue = [&](int first, int Lc) -> sor_status {
-    if (fast) {
-      int done_it = 0;
-      for (int Ls : plan_chunks(first, Lc)) {
-        const Phase3* tab = d_tables + (size_t)table_of.at(Ls) * 2 * lmax;
-        SOR3_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
-        SOR3_CK(c, launch_f3_flow(d_desc, d_state, d_strips, nst, bands, L.col_tiles(), fast_grid, d_shell0,
-                                  d_shell1, tab, 2 * Ls, d_progress, has_f, s));
-        done_it += Ls;
-        if (stop == kStopResid && (first + done_it) % d.K == 0)
-          k_resid3d<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
-      }
-      SOR3_CK(c, cudaGetLastError());
-      return SOR_OK;
-    }
-    for (int it = 1; it <= Lc; ++it) {
-      k_sweep3d<T><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt, 0);
-      k_sweep3d<T><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt, 1);
-      if (stop == kStopResid && (first + it) % d.K == 0)
+    int done_it = 0;
+    for (int Ls : plan_chunks(first, Lc)) {
+      SOR3_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
+      if (fast)
+        SOR3_CK(c, launch_f3_flow(d_desc, d_state, d_strips, nst, bands, L.col_tiles(), flow_grid, d_shell0,
+                                  d_shell1, d_tables + (size_t)table_of.at(Ls) * 2 * lmax, 2 * Ls, d_progress,
+                                  has_f, s));
+      else
+        SOR3_CK(c, launch_3_flow<T>(d_desc, d_state, d_strips, nst, bands, L.col_tiles(), flow_grid, 2 * Ls,
+                                    d_progress, has_f, s));
+      done_it += Ls;
+      if (stop == kStopResid && (first + done_it) % d.K == 0)
         k_resid3d<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
     }
     SOR3_CK(c, cudaGetLastError());
@@ -1128,16 +1171,16 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   bool finished = st.done != 0;
   while (!finished && planned < p->max_iters) {
     int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
-    if (fast && d.K > chunk0)  // batches end at tested iterations: few distinct chunk lengths
+    if (d.K > chunk0)  // batches end at tested iterations: few distinct chunk lengths
       Lc = (int)std::min<long long>(Lc, std::min<long long>((planned / d.K + 1) * d.K, p->max_iters) - planned);
     if (fast) {
       const sor_status ts = ensure_tables(plan_chunks(planned, Lc));
       if (ts != SOR_OK) return ts;
     }
     if (use_graphs) {
-      // the residual launches and the fast path's chunk ends depend on where
-      // the tested iterations fall in the batch
-      const std::pair<int, int> key(Lc, (stop == kStopResid || fast) ? (int)(planned % d.K) : 0);
+      // the chunk ends and the residual launches depend on where the tested
+      // iterations fall in the batch
+      const std::pair<int, int> key(Lc, (int)(planned % d.K));
       auto itg = cl.graphs.find(key);
       if (itg == cl.graphs.end()) {
         cudaGraph_t gr = nullptr;
