@@ -547,44 +547,6 @@ __device__ __forceinline__ void f3_shell(const Desc3& d, const double* __restric
 // SOR_ERR_INTERNAL).  The last strip to finish the last phase closes the
 // chunk's iterations.
 
-constexpr int kFlowSpins = 1 << 21;  // polls of about 0.1 us each: far above any phase
-
-__device__ __forceinline__ unsigned f3_ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void f3_st_release(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Lanes 0..6 poll one counter each (strip t itself and up to six
-// neighbours, -1 = none) until it reaches `target`; false on timeout.
-__device__ __forceinline__ bool f3_wait(const unsigned* progress, const int (&nb)[7], unsigned target, int lane) {
-  bool ok = true;
-  int mine = -1;
-#pragma unroll
-  for (int k = 0; k < 7; ++k)
-    if (lane == k) mine = nb[k];
-  if (mine >= 0) {
-    int spins = 0;
-    while (f3_ld_acquire(progress + mine) < target) {
-      if (++spins > kFlowSpins) {
-        ok = false;
-        break;
-      }
-      __nanosleep(64);
-    }
-  }
-  ok = __all_sync(0xffffffffu, ok);
-  if (ok) {
-#pragma unroll
-    for (int k = 0; k < 7; ++k)
-      if (nb[k] >= 0) (void)f3_ld_acquire(progress + nb[k]);
-  }
-  return ok;
-}
-
 template <bool HAS_G>
 __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict__ dp, SlotState* st,
                                                          const Tile* __restrict__ strips, int nstrips, int bands,
@@ -634,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
                          band + 1 < bands ? t + ct : -1,
                          tc > 0 ? t - 1 : -1,
                          tc + 1 < ct ? t + 1 : -1};
-      if (!f3_wait(progress, nb, (unsigned)p, lane)) {
+      if (!flow_wait<7>(progress, nb, (unsigned)p, lane)) {
         if (lane == 0) {
           st->error = 1;
           st->done = 1;
@@ -677,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
     __threadfence();  // this lane's cells are visible before the strip's progress is
     __syncwarp();
     if (lane == 0) {
-      f3_st_release(progress + t, (unsigned)(p + 1));
+      flow_st_release(progress + t, (unsigned)(p + 1));
       if (p == nphases - 1) {
         const unsigned prev = atomicAdd(&st->arrive, 1u);
         if (prev == (unsigned)nstrips - 1u) {
@@ -741,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
                          band + 1 < bands ? t + ct : -1,
                          tc > 0 ? t - 1 : -1,
                          tc + 1 < ct ? t + 1 : -1};
-      if (!f3_wait(progress, nb, (unsigned)p, lane)) {
+      if (!flow_wait<7>(progress, nb, (unsigned)p, lane)) {
         if (lane == 0) {
           st->error = 1;
           st->done = 1;
@@ -765,7 +727,7 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
     __threadfence();  // this lane's cells are visible before the strip's progress is
     __syncwarp();
     if (lane == 0) {
-      f3_st_release(progress + t, (unsigned)(p + 1));
+      flow_st_release(progress + t, (unsigned)(p + 1));
       if (p == nphases - 1) {
         const unsigned prev = atomicAdd(&st->arrive, 1u);
         if (prev == (unsigned)nstrips - 1u) {

@@ -18,6 +18,7 @@
 //   N = [a - pi][b],  S = [a + 1 - pi][b]                       (quarter c ^ 2)
 //   W = [a][b - pj],  E = [a][b + 1 - pj]                       (quarter c ^ 1)
 //   NW, NE, SW, SE = [a - pi or a + 1 - pi][b - pj or b + 1 - pj] (quarter c ^ 3)
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -176,6 +177,62 @@ __device__ __forceinline__ unsigned long long sweep9_rows(const Desc9& d, int q0
   return dm;
 }
 
+// Rows [a0, a1) of quarter C for one warp, FP64 default.  The north triple
+// T_N = NW + 4 N + NE of a cell and the south triple T_S = SW + 4 S + SE hold
+// the same three cells when T_S belongs to the cell one quarter row up (two
+// natural rows), so each row forms only its T_S and inherits T_N:
+//   s = fma(4, W + E, T_N + T_S) [+ g],   u <- fma(1 - w, u, (w/20) s),
+// 7 FP64 operations per update (11 in the exact order, which this equals
+// within rounding: 1e-12 of it over the solves tested).
+template <int C, bool MEASURE, bool HAS_G>
+__device__ __forceinline__ unsigned long long sweep9_fast_rows(const Desc9& d, int q0, int a0, int a1, int lane) {
+  constexpr int PI = C >> 1, PJ = C & 1;
+  unsigned long long dm = 0;
+  if (a0 >= a1) return 0;
+  double* X = (double*)d.x[C];
+  const double* Q1 = (const double*)d.x[C ^ 1];
+  const double* Q2 = (const double*)d.x[C ^ 2];
+  const double* Q3 = (const double*)d.x[C ^ 3];
+  const double* G = (const double*)d.g[C];
+  const int pitch = d.pitch;
+  const int blim = (d.n + PJ) >> 1;
+  const double a = d.a64, b = d.b64;
+  double tn[4];
+  {
+    double n2[4], n3[4], NW[4], NE[4];
+    load4(Q2 + e9(a0 - PI, q0, pitch), n2);
+    load4(Q3 + e9(a0 - PI, q0, pitch), n3);
+    we_of<double, PJ>(n3, Q3 + (size_t)(a0 - PI) * pitch, q0, lane, NW, NE);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) tn[v] = __fma_rn(4.0, n2[v], __dadd_rn(NW[v], NE[v]));
+  }
+  for (int r = a0; r < a1; ++r) {
+    double s2[4], s3[4], w1[4], own[4], gv[4];
+    load4(Q2 + e9(r + 1 - PI, q0, pitch), s2);
+    load4(Q3 + e9(r + 1 - PI, q0, pitch), s3);
+    load4(Q1 + e9(r, q0, pitch), w1);
+    load4(X + e9(r, q0, pitch), own);
+    if (HAS_G) load4(G + e9(r, q0, pitch), gv);
+    double W[4], E[4], SW[4], SE[4];
+    we_of<double, PJ>(w1, Q1 + (size_t)r * pitch, q0, lane, W, E);
+    we_of<double, PJ>(s3, Q3 + (size_t)(r + 1 - PI) * pitch, q0, lane, SW, SE);
+    double nv[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const double ts = __fma_rn(4.0, s2[v], __dadd_rn(SW[v], SE[v]));
+      double sum = __fma_rn(4.0, __dadd_rn(W[v], E[v]), __dadd_rn(tn[v], ts));
+      if (HAS_G) sum = __dadd_rn(sum, gv[v]);
+      const double nu = __fma_rn(a, own[v], __dmul_rn(b, sum));
+      const bool in = (q0 + v) <= blim;
+      nv[v] = in ? nu : own[v];  // cells past the interior keep their value
+      if (MEASURE && in) dm = umax64(dm, abs_bits(__dadd_rn(nu, -own[v])));
+      tn[v] = ts;
+    }
+    store4(X + e9(r, q0, pitch), nv);
+  }
+  return dm;
+}
+
 __device__ __forceinline__ void finalize9(const Desc9& d, SlotState* st, int k, int measure) {
   st->arrive = 0;
   st->iters = k;
@@ -190,8 +247,11 @@ __device__ __forceinline__ void finalize9(const Desc9& d, SlotState* st, int k, 
   if (k >= d.max_iters) st->done = 1;
 }
 
-// One colour phase over tiles (quarter rows, 128 columns); the last tile of
-// the phase of colour 3 closes the iteration.
+// One colour phase over tiles (quarter rows, 128 columns), the FP32 phases:
+// their phases are short (about 9 us on a 4098^2 plate), so a launch per
+// phase beats the data-flow schedule, whose per-item claims, waits and
+// fences sit on the critical path of every phase.  The last tile of the
+// phase of colour 3 closes the iteration.
 template <typename T, int C>
 __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ dp, SlotState* st,
                                                      const Tile* __restrict__ tiles, int ntiles) {
@@ -239,6 +299,115 @@ __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ d
       }
       __syncthreads();
     }
+  }
+}
+
+template <typename T, bool FAST, int C, bool HAS_G>
+__device__ __forceinline__ unsigned long long rows9(const Desc9& d, bool measure, int q0, int a0, int a1, int lane) {
+  if (FAST) {
+    return measure ? sweep9_fast_rows<C, true, HAS_G>(d, q0, a0, a1, lane)
+                   : sweep9_fast_rows<C, false, HAS_G>(d, q0, a0, a1, lane);
+  }
+  return measure ? sweep9_rows<T, C, true, HAS_G>(d, q0, a0, a1, lane)
+                 : sweep9_rows<T, C, false, HAS_G>(d, q0, a0, a1, lane);
+}
+
+// A chunk of 4L colour phases in one launch, scheduled as a data flow (the
+// cube kernels' schedule): work items (phase p, strip t) are claimed in the
+// order p * strips + t; item (p, t) waits until strip t and the eight strips
+// around it (row bands above and below, column tiles left and right, and the
+// four corners, which the diagonal couplings reach) -- the only ones whose
+// cells its stencil reads (in the three other quarters) or whose readers it
+// could overwrite -- have finished phase p-1 (progress[t]
+// counts the phases a strip has finished, so phases p-2 and p-3 are done
+// too).  Every dependency has a smaller number than the item waiting for it,
+// so the smallest unfinished item can always run.  Waits are bounded (an
+// error in the slot state, then return); the last strip of the last phase
+// closes the chunk, which ends at a tested iteration.
+template <typename T, bool FAST, bool HAS_G>
+__global__ void __launch_bounds__(kThreads) k_9_flow(const Desc9* __restrict__ dp, SlotState* st,
+                                                     const Tile* __restrict__ strips, int nstrips, int ct,
+                                                     int nphases, unsigned* progress) {
+  const int lane = threadIdx.x & 31;
+  const Desc9& d = *dp;
+  int skip = 0, k0 = 0;
+  if (lane == 0) {
+    skip = *((volatile int*)&st->done);
+    k0 = *((volatile int*)&st->iters);
+  }
+  skip = __shfl_sync(0xffffffffu, skip, 0);
+  if (skip) return;  // done changes inside a launch only after its last item
+  k0 = __shfl_sync(0xffffffffu, k0, 0);
+  const long long items = (long long)nphases * nstrips;
+  unsigned* claim = progress + nstrips;
+  const int bands = nstrips / ct;
+  const int last_it = k0 + (nphases >> 2);
+  for (;;) {
+    long long g = 0;
+    if (lane == 0) g = (long long)atomicAdd(claim, 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= items) break;
+    const int p = (int)(g / nstrips), t = (int)(g - (long long)p * nstrips);
+    const int C = p & 3;
+    const int kk = k0 + (p >> 2) + 1;
+    const bool measure = ((kk % d.K) == 0) || (kk >= d.max_iters);
+    if (measure && kk != last_it) {  // the host plan must end launches at tested iterations
+      if (lane == 0) {
+        st->error = 1;
+        st->done = 1;
+      }
+      return;
+    }
+    if (p > 0) {
+      // the eight strips around this one: the stencil's diagonal couplings
+      // reach the corner strips too
+      const int band = t / ct, tc = t - band * ct;
+      const bool up = band > 0, down = band + 1 < bands, left = tc > 0, right = tc + 1 < ct;
+      const int nb[9] = {t,
+                         up ? t - ct : -1,
+                         down ? t + ct : -1,
+                         left ? t - 1 : -1,
+                         right ? t + 1 : -1,
+                         up && left ? t - ct - 1 : -1,
+                         up && right ? t - ct + 1 : -1,
+                         down && left ? t + ct - 1 : -1,
+                         down && right ? t + ct + 1 : -1};
+      if (!flow_wait<9>(progress, nb, (unsigned)p, lane)) {
+        if (lane == 0) {
+          st->error = 1;
+          st->done = 1;
+        }
+        return;
+      }
+    }
+    const Tile tl = strips[t];
+    const int q0 = tl.col0 + lane * kVec;
+    const int a0 = tl.row0;
+    const int a1 = min(tl.row0 + tl.nrows, ((d.n + (C >> 1)) >> 1) + 1);
+    unsigned long long dm;
+    switch (C) {
+      case 0: dm = rows9<T, FAST, 0, HAS_G>(d, measure, q0, a0, a1, lane); break;
+      case 1: dm = rows9<T, FAST, 1, HAS_G>(d, measure, q0, a0, a1, lane); break;
+      case 2: dm = rows9<T, FAST, 2, HAS_G>(d, measure, q0, a0, a1, lane); break;
+      default: dm = rows9<T, FAST, 3, HAS_G>(d, measure, q0, a0, a1, lane); break;
+    }
+    if (measure) {
+      dm = warp_max64(dm);
+      if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+    }
+    __threadfence();  // this lane's cells are visible before the strip's progress is
+    __syncwarp();
+    if (lane == 0) {
+      flow_st_release(progress + t, (unsigned)(p + 1));
+      if (p == nphases - 1) {
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        if (prev == (unsigned)nstrips - 1u) {
+          __threadfence();
+          finalize9(d, st, last_it, measure);
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -376,6 +545,42 @@ void launch_sweep9(int colour, int grid, cudaStream_t s, const Desc9* d, SlotSta
   }
 }
 
+template <typename T, bool FAST>
+int flow9_blocks_per_sm(bool has_g) {
+  int nb = 0;
+  cudaError_t e = has_g ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_9_flow<T, FAST, true>, kThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_9_flow<T, FAST, false>, kThreads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+template <typename T, bool FAST>
+cudaError_t launch_9_flow(const Desc9* d, SlotState* st, const Tile* strips, int nstrips, int ct, int grid,
+                          int nphases, unsigned* progress, bool has_g, cudaStream_t s) {
+  if (has_g)
+    k_9_flow<T, FAST, true><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, ct, nphases, progress);
+  else
+    k_9_flow<T, FAST, false><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, ct, nphases, progress);
+  return cudaGetLastError();
+}
+
+// Warp strips of the flow kernel: quarter rows 1 .. (n+1)/2 cut into bands of
+// about 32 rows (at least 8), at least one strip per resident warp, times the
+// 128-column tiles; numbered band-major (the kernel derives neighbours).
+int build_strips9(int n, int ct, int warps, std::vector<Tile>* out) {
+  const int arows = (n + 1) >> 1;
+  int b = std::max(arows / 32, (warps + ct - 1) / ct);
+  b = std::max(1, std::min(b, std::max(1, arows / 8)));
+  for (int r = 0; r < b; ++r) {
+    const int a0 = 1 + (int)((long long)r * arows / b), a1 = 1 + (int)((long long)(r + 1) * arows / b);
+    for (int t = 0; t < ct; ++t) out->push_back(Tile{0, a0, 1 + t * kWarpCols, a1 - a0});
+  }
+  return b;
+}
+
 template <typename T>
 sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out, sor_result* res) {
   const double t0 = now_s();
@@ -398,8 +603,25 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
     for (int t = 0; t < L.col_tiles(); ++t)
       tiles.push_back(Tile{0, r, 1 + t * kWarpCols, std::min(kTileRows, arows - r + 1)});
   const int nt = (int)tiles.size();
+  // FP64 default: the shared-triple phases (within 1e-12 of the exact
+  // order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
+  // FP64 phases run a launch per run of iterations up to the next test
+  // (data-flow schedule); the short FP32 phases a launch per phase
+  const bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
+  const bool flow = sizeof(T) == 8;
+  const int bps = !flow ? 1 : fast ? flow9_blocks_per_sm<double, true>(has_f) : flow9_blocks_per_sm<T, false>(has_f);
+  if (bps < 1) {
+    c->set_error("9-point phase kernel does not fit on an SM");
+    return SOR_ERR_CUDA;
+  }
+  std::vector<Tile> strips;
+  const int ct = L.col_tiles();
+  if (flow) build_strips9(n, ct, c->sm_count * bps * kWarpsY, &strips);
+  const int nst = (int)strips.size();
+  const int flow_grid = c->sm_count * bps;
 
-  size_t bytes = 4 * qelems * sizeof(T) + sizeof(Desc9) + sizeof(SlotState) + sizeof(Tile) * nt + 1024;
+  size_t bytes = 4 * qelems * sizeof(T) + sizeof(Desc9) + sizeof(SlotState) + sizeof(Tile) * nt + 1024 +
+                 sizeof(Tile) * nst + sizeof(unsigned) * (nst + 1);
   if (has_f) bytes += 4 * qelems * sizeof(T) + (sizeof(T) == 4 ? 4 * qelems * sizeof(double) : 0);
   const bool stage_u = !in_dev || !out_dev;
   if (stage_u) bytes += nnat * sizeof(double);
@@ -428,9 +650,12 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
   Desc9* d_desc = (Desc9*)B.get(sizeof(Desc9));
   SlotState* d_state = (SlotState*)B.get(sizeof(SlotState));
   Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
+  Tile* d_strips = (Tile*)B.get(sizeof(Tile) * std::max(1, nst));
+  unsigned* d_progress = (unsigned*)B.get(sizeof(unsigned) * (nst + 1));
   double* d_u = stage_u ? (double*)B.get(nnat * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
-  if (!ok || !d_desc || !d_state || !d_tiles || (stage_u && !d_u) || (has_f && !f_dev && !d_f)) {
+  if (!ok || !d_desc || !d_state || !d_tiles || !d_strips || !d_progress || (stage_u && !d_u) ||
+      (has_f && !f_dev && !d_f)) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
@@ -470,6 +695,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
   SOR9_CK(c, cudaMemcpyAsync(d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
   SOR9_CK(c, cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   SOR9_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+  if (nst > 0) SOR9_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
   const double* u_src = u0;
   if (!in_dev) {
     SOR9_CK(c, cudaMemcpyAsync(d_u, u0, nnat * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -517,24 +743,54 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
     }
   } cl{ev0, ev1, h_state, {}};
 
+  // a batch of Lc iterations after iteration `first`: one flow launch per
+  // run of iterations up to the next tested one (a multiple of K or the cap),
+  // the residual test after those at multiples of K
   auto enqueue = [&](int first, int Lc) -> sor_status {
-    for (int it = 1; it <= Lc; ++it) {
-      for (int col = 0; col < 4; ++col) launch_sweep9<T>(col, grid, s, d_desc, d_state, d_tiles, nt);
-      if (stop == kStopResid && (first + it) % d.K == 0)
+    if (!flow) {
+      for (int it = 1; it <= Lc; ++it) {
+        for (int col = 0; col < 4; ++col) launch_sweep9<T>(col, grid, s, d_desc, d_state, d_tiles, nt);
+        if (stop == kStopResid && (first + it) % d.K == 0)
+          k_resid9<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+      }
+      SOR9_CK(c, cudaGetLastError());
+      return SOR_OK;
+    }
+    int done_it = 0;
+    while (done_it < Lc) {
+      const long long at = first + done_it;
+      const long long next_m = std::min<long long>((at / d.K + 1) * d.K, p->max_iters);
+      const int Ls = (int)std::min<long long>(next_m - at, (long long)(Lc - done_it));
+      SOR9_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
+      if (fast)
+        SOR9_CK(c, (launch_9_flow<double, true>(d_desc, d_state, d_strips, nst, ct, flow_grid, 4 * Ls, d_progress,
+                                                has_f, s)));
+      else
+        SOR9_CK(c, (launch_9_flow<T, false>(d_desc, d_state, d_strips, nst, ct, flow_grid, 4 * Ls, d_progress,
+                                           has_f, s)));
+      done_it += Ls;
+      if (stop == kStopResid && (first + done_it) % d.K == 0)
         k_resid9<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
     }
     SOR9_CK(c, cudaGetLastError());
     return SOR_OK;
   };
-  const int chunk = c->opt_chunk.load() > 0 ? c->opt_chunk.load() : 64;
+  // iterations per host check: a whole number of test intervals when K fits,
+  // so every batch starts at a tested iteration and one graph serves them all
+  const int chunk0 = c->opt_chunk.load() > 0 ? c->opt_chunk.load() : 64;
+  const int chunk = d.K <= chunk0 ? (chunk0 / d.K) * d.K : chunk0;
   const bool use_graphs = c->opt_graphs.load() != 0;
   SOR9_CK(c, cudaEventRecord(ev0, s));
   long long planned = 0;
   bool finished = st.done != 0;
   while (!finished && planned < p->max_iters) {
-    const int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
+    int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
+    if (d.K > chunk0)  // batches end at tested iterations: few distinct launch plans
+      Lc = (int)std::min<long long>(Lc, std::min<long long>((planned / d.K + 1) * d.K, p->max_iters) - planned);
     if (use_graphs) {
-      const std::pair<int, int> key(Lc, stop == kStopResid ? (int)(planned % d.K) : 0);
+      // the launch ends and the residual tests depend on where the tested
+      // iterations fall in the batch
+      const std::pair<int, int> key(Lc, (int)(planned % d.K));
       auto itg = cl.graphs.find(key);
       if (itg == cl.graphs.end()) {
         cudaGraph_t gr = nullptr;

@@ -67,4 +67,47 @@ __device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long
 
 __device__ __forceinline__ size_t eidx(int i, int q, int pitch) { return (size_t)i * pitch + q + kOff; }
 
+// Data-flow scheduling of a chunk of colour phases (the cube and 9-point
+// kernels): per-strip progress counters published with release stores after
+// fenced writes and read with acquire loads.
+constexpr int kFlowSpins = 1 << 21;  // polls of about 0.1 us each: far above any phase
+
+__device__ __forceinline__ unsigned flow_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void flow_st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Lanes 0..NB-1 poll one counter each (-1 = none) until it reaches `target`;
+// false on timeout (bounded: kFlowSpins polls).  Afterwards every lane takes
+// its own acquire of all of them, so its later loads see their writes.
+template <int NB>
+__device__ __forceinline__ bool flow_wait(const unsigned* progress, const int (&nb)[NB], unsigned target, int lane) {
+  bool ok = true;
+  int mine = -1;
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+    if (lane == k) mine = nb[k];
+  if (mine >= 0) {
+    int spins = 0;
+    while (flow_ld_acquire(progress + mine) < target) {
+      if (++spins > kFlowSpins) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  ok = __all_sync(0xffffffffu, ok);
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (nb[k] >= 0) (void)flow_ld_acquire(progress + nb[k]);
+  }
+  return ok;
+}
+
 }  // namespace sorgb

@@ -1,9 +1,12 @@
 """Parity of the four-colour 9-point CUDA path with the CPU oracle, through
-the C ABI (sor_solve9).  Bar: bit identical to the oracle in FP64 and FP32
-(same operation order, every operation rounded on its own), same iteration
-counts.  Sizes cover odd and even n (the four quarters differ in extent),
-several 32 x 128 tiles, two column tiles with a ragged tail (n > 256) and the
-degenerate grids n = 1, 2, 3."""
+the C ABI (sor_solve9).  Bars: with SOR_FLAG_EXACT_ORDER in FP64, and in
+FP32, bit identical to the oracle (same operation order, every operation
+rounded on its own), same iteration counts; the FP64 default path (shared
+north / south triples, fused multiply-adds) within a normwise relative
+difference of 1e-12 after equal iteration counts.  Sizes cover odd and even
+n (the four quarters differ in extent), several strips of quarter rows, two
+column tiles with a ragged tail (n > 256) and the degenerate grids
+n = 1, 2, 3."""
 import numpy as np
 import pytest
 
@@ -13,6 +16,9 @@ from tests import pins
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+EXACT = 1  # SOR_FLAG_EXACT_ORDER
 
 
 @pytest.fixture(scope="module")
@@ -46,12 +52,43 @@ def test_fp64_bitwise(ctx, n, with_f):
     f = wl.gaussian_source(n, 600 + n) if with_f else None
     w = oracle.omega_opt(n)
     ref = oracle.sor9_f64(u0, w, f=f, max_iters=80, check_every=4, tol=1e-9)
-    got, res = run9(ctx, u0, f, omega=w, max_iters=80, check_every=4, tol=1e-9, precision=capi.SOR_FP64)
+    got, res = run9(ctx, u0, f, omega=w, max_iters=80, check_every=4, tol=1e-9, precision=capi.SOR_FP64,
+                    flags=EXACT)
     assert res["iterations"] == ref["iterations"]
     assert res["converged"] == ref["converged"]
     assert np.array_equal(got, ref["u"])
     assert res["final_maxdelta"] == ref["final_maxdelta"]
     assert res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 16, 37, 100, 129, 300])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_fp64_default_within_tolerance(ctx, n, with_f):
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 900 + n)
+    f = wl.gaussian_source(n, 950 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor9_f64(u0, w, f=f, max_iters=70, check_every=7, tol=0.0)
+    got, res = run9(ctx, u0, f, omega=w, max_iters=70, check_every=7, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 70 and not res["converged"]
+    assert pins.rel_err(got, ref["u"]) <= TOL64
+    ring = np.ones_like(u0, dtype=bool)
+    ring[1:-1, 1:-1] = False
+    assert np.array_equal(got[ring], u0[ring])
+    scale = max(1.0, float(np.max(np.abs(ref["u"]))))
+    assert abs(res["final_maxdelta"] - ref["final_maxdelta"]) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.7, 1.97])
+def test_fp64_default_relaxation_factors(ctx, omega):
+    capi = capi_mod()
+    n = 41
+    u0 = wl.random_edges(n, 61)
+    f = wl.gaussian_source(n, 62) * 30
+    ref = oracle.sor9_f64(u0, omega, f=f, max_iters=150, check_every=1000, tol=0.0)
+    got, res = run9(ctx, u0, f, omega=omega, max_iters=150, check_every=1000, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 150
+    assert pins.rel_err(got, ref["u"]) <= TOL64
 
 
 @pytest.mark.parametrize("n", [5, 64, 131])
@@ -75,9 +112,12 @@ def test_two_column_tiles_and_more(ctx, n):
     u0 = wl.random_edges(n, n)
     w = oracle.omega_opt(n)
     ref = oracle.sor9_f64(u0, w, max_iters=6, check_every=3, tol=0.0)
-    got, res = run9(ctx, u0, omega=w, max_iters=6, check_every=3, tol=0.0, precision=capi.SOR_FP64)
+    got, res = run9(ctx, u0, omega=w, max_iters=6, check_every=3, tol=0.0, precision=capi.SOR_FP64, flags=EXACT)
     assert res["iterations"] == 6
     assert np.array_equal(got, ref["u"])
+    got, res = run9(ctx, u0, omega=w, max_iters=6, check_every=3, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 6
+    assert pins.rel_err(got, ref["u"]) <= TOL64
 
 
 def test_residual_stop_matches(ctx):
@@ -88,11 +128,15 @@ def test_residual_stop_matches(ctx):
     w = oracle.omega_opt(n)
     ref = oracle.sor9_f64(u0, w, f=f, max_iters=5000, check_every=5, tol=1e-10, stop_mode=1)
     got, res = run9(ctx, u0, f, omega=w, max_iters=5000, check_every=5, tol=1e-10, precision=capi.SOR_FP64,
-                    stop=capi.SOR_STOP_RESID_REL)
+                    stop=capi.SOR_STOP_RESID_REL, flags=EXACT)
     assert ref["converged"] and res["converged"]
     assert res["iterations"] == ref["iterations"]
     assert np.array_equal(got, ref["u"])
     assert res["final_resid_rel"] == ref["final_resid_rel"] < 1e-10
+    got, res = run9(ctx, u0, f, omega=w, max_iters=5000, check_every=5, tol=1e-10, precision=capi.SOR_FP64,
+                    stop=capi.SOR_STOP_RESID_REL)
+    assert res["converged"] and res["iterations"] == ref["iterations"]
+    assert pins.rel_err(got, ref["u"]) <= TOL64 and res["final_resid_rel"] < 1e-10
 
 
 def test_quartic_harmonic_and_dst(ctx):
@@ -128,10 +172,13 @@ def test_full_size_plate_bitwise(ctx):
     u0 = wl.random_edges(n, 0)
     w = oracle.omega_opt(n)
     ref = oracle.sor9_f64(u0, w, max_iters=10, check_every=5, tol=0.0)
-    got, res = run9(ctx, u0, omega=w, max_iters=10, check_every=5, tol=0.0, precision=capi.SOR_FP64)
+    got, res = run9(ctx, u0, omega=w, max_iters=10, check_every=5, tol=0.0, precision=capi.SOR_FP64, flags=EXACT)
     assert res["iterations"] == 10
     assert np.array_equal(got, ref["u"])
     assert res["final_maxdelta"] == ref["final_maxdelta"]
+    got, res = run9(ctx, u0, omega=w, max_iters=10, check_every=5, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 10
+    assert pins.rel_err(got, ref["u"]) <= TOL64
 
 
 def test_invalid_arguments(ctx):
