@@ -136,15 +136,18 @@ sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, c
  * by the same method -- Algorithm 1 with the update of Eq. 1, the
  * Gauss-Seidel value taken from the 7-point stencil:
  *   U <- (1-w) U + (w/6) ((((N + S) + (W + E)) + (D + U)) + h^2 f),
- * red = (i + j + k) even, red phase first.  Every product and sum is rounded
- * on its own in that order, in FP64 (precision SOR_FP64) or FP32
- * (SOR_FP32); the residual r~ = (h^2 f + sum of the six neighbours) - 6 u is
- * formed in FP64.
+ * red = (i + j + k) even, red phase first.  FP32 (precision SOR_FP32), and
+ * FP64 with SOR_FLAG_EXACT_ORDER, round every product and sum on its own in
+ * that order; FP64 by default computes the same iteration with the neighbour
+ * sums regrouped (in-plane pairs shared by two cells) and the unknowns
+ * rescaled within each run of iterations between tests, one FMA per update
+ * (within 1e-12 of the exact order in the tested solves).  The residual
+ * r~ = (h^2 f + sum of the six neighbours) - 6 u is formed in FP64.
  *   params: n = interior side N (1 <= N <= 1200); omega <= 0 selects
  *           2 / (1 + sin(pi / (N+1))); stop, tol, max_iters, check_every as
  *           for sor_solve; precision SOR_FP64 or SOR_FP32; flags 0 or
- *           SOR_FLAG_EXACT_ORDER (the only order on cubes); stall_window 0.
- *           Anything else returns SOR_ERR_INVALID_ARG.
+ *           SOR_FLAG_EXACT_ORDER; stall_window 0.  Anything else returns
+ *           SOR_ERR_INVALID_ARG.
  *   u0:    (N+2)^3 array indexed [k][i][j] (plane, row, column), its outer
  *          shell the Dirichlet data.  Host or device memory.
  *   f:     N^3 interior source of -Laplace(u) = f ([k][i][j]), or NULL.
@@ -160,7 +163,11 @@ sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0,
  * c = 2 (i & 1) + (j & 1), updated in the order 0, 1, 2, 3).  Cell equation
  * 20 u = 4 (N + S + W + E) + (NW + NE + SW + SE) + 6 h^2 f, update
  *   U <- (1-w) U + (w/20) ((4 ((N + S) + (W + E)) + ((NW + NE) + (SW + SE))) + 6 h^2 f),
- * every product and sum rounded on its own in that order (FP64 or FP32); the
+ * every product and sum rounded on its own in that order in FP32 and in FP64
+ * with SOR_FLAG_EXACT_ORDER; FP64 by default regroups the sum as
+ * (NW + 4 N + NE) + (SW + 4 S + SE) + 4 (W + E), the south triple of a cell
+ * serving as the north triple of the cell two rows down, with fused
+ * multiply-adds (within 1e-12 of the exact order in the tested solves).  The
  * residual r~ = (6 h^2 f + (4 s4 + sd)) - 20 u is formed in FP64 and b~
  * weighs the ring's edge neighbours by 4 and its diagonal ones by 1.
  *   params: as for sor_solve with precision SOR_FP64 or SOR_FP32, flags 0 or
