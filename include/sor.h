@@ -179,6 +179,18 @@ sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0,
 sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
                       sor_result *res);
 
+/* Diagnostic of the failure path of the data-flow kernels (sor_solve3d and
+ * sor_solve9 in FP64).  Their device-side waits are bounded: a warp whose
+ * neighbours do not report progress gives up after a fixed number of polls,
+ * records an error that the solve returns as SOR_ERR_INTERNAL, and the
+ * context stays usable.  This call runs that wait, in one warp, on a progress
+ * counter preset to 0 (nothing advances it, so the wait must give up) or to
+ * 1 (complete: it must not), polling at most `polls` times (1 .. 2^21, about
+ * 0.1 us each).  *timed_out = 1 when the wait gave up, 0 when it saw the
+ * counter complete.  No GPU fault or hang is involved.
+ * Returns SOR_ERR_INVALID_ARG for arguments out of range. */
+sor_status sor_diag_flow_wait(sor_ctx *ctx, int polls, int preset, int *timed_out);
+
 /* Non-blocking submission to the context's continuous-batching scheduler.
  * u0 and f are copied before the call returns.  u_out must stay valid until
  * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.

@@ -50,7 +50,7 @@ SOR_OPT_FAST_CHAIN = 8
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
             "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d",
-            "sor_solve9")
+            "sor_solve9", "sor_diag_flow_wait")
 
 
 class sor_params(ctypes.Structure):
@@ -284,6 +284,14 @@ class Context:
         st, res = self.solve3d_raw(p, _ptr(u0), _ptr(f), _ptr(out))
         self._check(st, "sor_solve3d")
         return out, res.as_dict()
+
+    def diag_flow_wait(self, polls: int, preset: int) -> int:
+        """sor_diag_flow_wait: 1 when the bounded device wait gave up."""
+        out = ctypes.c_int32(-1)
+        st = self._lib.sor_diag_flow_wait(self._h, ctypes.c_int32(polls), ctypes.c_int32(preset),
+                                          ctypes.byref(out))
+        self._check(st, "sor_diag_flow_wait")
+        return out.value
 
     def solve9_raw(self, params: sor_params, u0_ptr, f_ptr, out_ptr):
         """sor_solve9 on raw addresses; returns (status, result)."""

@@ -107,7 +107,27 @@ __global__ void k_unpack3d(const T* __restrict__ x0, const T* __restrict__ x1, i
   }
 }
 
-// Rows [i0, i1) of plane k for one warp, one colour phase, exact order.
+// Rows [i0, i1) of plane k for one warp, one colour phase, exact order.  The
+// loads of row i+1 are issued before row i is computed (register double
+// buffering), so a warp waits for memory once per strip instead of once per
+// row; the arithmetic and its order do not change.
+template <typename T>
+struct Row3 {
+  T op[4], own[4], dn[4], up[4], gv[4];
+  T left, right;  // the in-row neighbours beyond the warp's columns (lanes 0 / 31)
+};
+template <typename T, bool HAS_G>
+__device__ __forceinline__ void row3_load(Row3<T>& r, const T* __restrict__ X, const T* __restrict__ O,
+                                          const T* __restrict__ G, int k, int i, int m, int pitch, int q0, int lane) {
+  load4(O + e3(k, i + 1, q0, m, pitch), r.op);
+  load4(X + e3(k, i, q0, m, pitch), r.own);
+  load4(O + e3(k - 1, i, q0, m, pitch), r.dn);
+  load4(O + e3(k + 1, i, q0, m, pitch), r.up);
+  if (HAS_G) load4(G + e3(k, i, q0, m, pitch), r.gv);
+  r.left = lane == 0 ? O[e3(k, i, q0 - 1, m, pitch)] : T(0);
+  r.right = lane == 31 ? O[e3(k, i, q0 + kVec, m, pitch)] : T(0);
+}
+
 template <typename T, bool MEASURE, bool HAS_G>
 __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, const T* __restrict__ O,
                                                           const T* __restrict__ G, T a, T b, int pitch, int m, int n,
@@ -115,20 +135,18 @@ __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, con
   unsigned long long dm = 0;
   unsigned dm32 = 0;
   if (i0 >= i1) return 0;
-  T om[4], oc[4], op[4];
+  T om[4], oc[4];
   load4(O + e3(k, i0 - 1, q0, m, pitch), om);
   load4(O + e3(k, i0, q0, m, pitch), oc);
+  Row3<T> cur;
+  row3_load<T, HAS_G>(cur, X, O, G, k, i0, m, pitch, q0, lane);
   for (int i = i0; i < i1; ++i) {
-    T own[4], dn[4], up[4], gv[4];
-    load4(O + e3(k, i + 1, q0, m, pitch), op);
-    load4(X + e3(k, i, q0, m, pitch), own);
-    load4(O + e3(k - 1, i, q0, m, pitch), dn);
-    load4(O + e3(k + 1, i, q0, m, pitch), up);
-    if (HAS_G) load4(G + e3(k, i, q0, m, pitch), gv);
+    Row3<T> nxt;
+    row3_load<T, HAS_G>(nxt, X, O, G, k, min(i + 1, i1 - 1), m, pitch, q0, lane);  // the last row reloads itself
     T left = __shfl_up_sync(0xffffffffu, oc[3], 1);
     T right = __shfl_down_sync(0xffffffffu, oc[0], 1);
-    if (lane == 0) left = O[e3(k, i, q0 - 1, m, pitch)];
-    if (lane == 31) right = O[e3(k, i, q0 + kVec, m, pitch)];
+    if (lane == 0) left = cur.left;
+    if (lane == 31) right = cur.right;
     const int s = (i + k + colour) & 1;
     const int qlim = (n + s) >> 1;
     T W[4], E[4];
@@ -142,25 +160,26 @@ __device__ __forceinline__ unsigned long long sweep3_rows(T* __restrict__ X, con
     T nv[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      T sum = radd(radd(radd(om[v], op[v]), radd(W[v], E[v])), radd(dn[v], up[v]));
-      if (HAS_G) sum = radd(sum, gv[v]);
-      const T nu = radd(rmul(a, own[v]), rmul(b, sum));
+      T sum = radd(radd(radd(om[v], cur.op[v]), radd(W[v], E[v])), radd(cur.dn[v], cur.up[v]));
+      if (HAS_G) sum = radd(sum, cur.gv[v]);
+      const T nu = radd(rmul(a, cur.own[v]), rmul(b, sum));
       const bool in = (q0 + v) <= qlim;
       // cells past the interior keep their value (the whole vector is written back)
-      nv[v] = in ? nu : own[v];
+      nv[v] = in ? nu : cur.own[v];
       if (MEASURE && in) {
         if (sizeof(T) == 4)
-          dm32 = max(dm32, abs_bits32((float)radd(nu, -own[v])));
+          dm32 = max(dm32, abs_bits32((float)radd(nu, -cur.own[v])));
         else
-          dm = umax64(dm, abs_bits((double)radd(nu, -own[v])));
+          dm = umax64(dm, abs_bits((double)radd(nu, -cur.own[v])));
       }
     }
     store4(X + e3(k, i, q0, m, pitch), nv);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       om[v] = oc[v];
-      oc[v] = op[v];
+      oc[v] = cur.op[v];
     }
+    cur = nxt;
   }
   if (sizeof(T) == 4 && MEASURE) dm = abs_bits_of(__uint_as_float(dm32));
   return dm;
@@ -1197,7 +1216,44 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   return SOR_OK;
 }
 
+// The bounded wait of the flow kernels on one progress counter: one warp
+// waits for counter >= 1 and records whether it gave up.
+__global__ void k_flow_wait_probe(const unsigned* progress, int polls, int* timed_out) {
+  const int lane = threadIdx.x & 31;
+  const int nb[1] = {0};
+  const bool ok = flow_wait<1>(progress, nb, 1u, lane, polls);
+  if (lane == 0) *timed_out = ok ? 0 : 1;
+}
+
 }  // namespace
+
+sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out) {
+  if (!timed_out || polls < 1 || polls > kFlowSpins || (preset != 0 && preset != 1)) {
+    c->set_error("polls must be in [1, 2^21], preset 0 or 1, timed_out non-NULL");
+    return SOR_ERR_INVALID_ARG;
+  }
+  Buffers3 B;
+  B.c = c;
+  unsigned* buf = (unsigned*)B.get(2 * sizeof(unsigned));
+  if (!buf) {
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  cudaStream_t s = c->stream;
+  const unsigned host[2] = {(unsigned)preset, 2u};
+  int out = -1;
+  SOR3_CK(c, cudaMemcpyAsync(buf, host, sizeof(host), cudaMemcpyHostToDevice, s));
+  k_flow_wait_probe<<<1, 32, 0, s>>>(buf, polls, (int*)(buf + 1));
+  SOR3_CK(c, cudaGetLastError());
+  SOR3_CK(c, cudaMemcpyAsync(&out, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SOR3_CK(c, cudaStreamSynchronize(s));
+  if (out != 0 && out != 1) {
+    c->set_error("wait probe did not report");
+    return SOR_ERR_INTERNAL;
+  }
+  *timed_out = out;
+  return SOR_OK;
+}
 
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res) {

@@ -82,10 +82,11 @@ __device__ __forceinline__ void flow_st_release(unsigned* p, unsigned v) {
 }
 
 // Lanes 0..NB-1 poll one counter each (-1 = none) until it reaches `target`;
-// false on timeout (bounded: kFlowSpins polls).  Afterwards every lane takes
+// false on timeout (bounded: `limit` polls).  Afterwards every lane takes
 // its own acquire of all of them, so its later loads see their writes.
 template <int NB>
-__device__ __forceinline__ bool flow_wait(const unsigned* progress, const int (&nb)[NB], unsigned target, int lane) {
+__device__ __forceinline__ bool flow_wait(const unsigned* progress, const int (&nb)[NB], unsigned target, int lane,
+                                          int limit = kFlowSpins) {
   bool ok = true;
   int mine = -1;
 #pragma unroll
@@ -94,7 +95,7 @@ __device__ __forceinline__ bool flow_wait(const unsigned* progress, const int (&
   if (mine >= 0) {
     int spins = 0;
     while (flow_ld_acquire(progress + mine) < target) {
-      if (++spins > kFlowSpins) {
+      if (++spins > limit) {
         ok = false;
         break;
       }

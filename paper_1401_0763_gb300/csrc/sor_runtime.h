@@ -191,6 +191,9 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
                            sor_result* res);
 
 // 3D cube solve (sor_solve3d); the caller holds solve_mu.
+// Runs the flow kernels' bounded device-side wait on a counter preset to 0
+// (nothing advances it: the wait gives up after `polls` polls) or 1.
+sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out);
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res);
 

@@ -213,6 +213,28 @@ def test_fp64_default_stops_like_oracle(ctx):
     assert np.max(np.abs(got - exact)) < 1e-11
 
 
+def test_bounded_wait_gives_up_and_context_survives(ctx):
+    """The failure path of the data-flow kernels without a fault: their
+    bounded device-side wait, run on a progress counter nothing advances,
+    gives up and reports it; on a completed counter it does not; and the
+    context solves normally afterwards."""
+    capi = capi_mod()
+    import time
+    t0 = time.perf_counter()
+    assert ctx.diag_flow_wait(4000, 0) == 1
+    assert time.perf_counter() - t0 < 5.0
+    assert ctx.diag_flow_wait(4000, 1) == 0
+    for polls, preset in ((0, 0), (1 << 22, 0), (10, 2)):
+        with pytest.raises(capi.SorError):
+            ctx.diag_flow_wait(polls, preset)
+    n = 12
+    u0 = wl.random_shell(n, 4)
+    ref = oracle.sor3d_f64(u0, oracle.omega_opt(n), max_iters=30, check_every=10, tol=0.0)
+    got, res = run3(ctx, u0, omega=oracle.omega_opt(n), max_iters=30, check_every=10, tol=0.0,
+                    precision=capi.SOR_FP64)
+    assert res["iterations"] == 30 and pins.rel_err3(got, ref["u"]) <= TOL64
+
+
 def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_shell(4, 1)
