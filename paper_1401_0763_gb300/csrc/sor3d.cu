@@ -1257,6 +1257,7 @@ sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out) {
 
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res) {
+  NvtxRange nvtx("sor_solve3d");
   if (!p || !u0 || !u_out) {
     c->set_error("params, u0 and u_out must be non-NULL");
     return SOR_ERR_INVALID_ARG;

@@ -849,6 +849,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
 
 sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                            sor_result* res) {
+  NvtxRange nvtx("sor_solve9");
   if (!p || !u0 || !u_out) {
     c->set_error("params, u0 and u_out must be non-NULL");
     return SOR_ERR_INVALID_ARG;

@@ -360,6 +360,7 @@ static void release_request(Batcher* b, Request* r) {
 
 // Retire finished slots: final residual for plain slots, unpack, copy out.
 static sor_status retire(Batcher* b, const std::vector<int>& fin) {
+  NvtxRange nvtx("sor_retire");
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
   std::vector<Tile> p64, p32;
@@ -503,8 +504,12 @@ static void scheduler_main(Batcher* b) {
       }
       b->slots[sidx] = std::move(r);
     }
-    if (rs == SOR_OK && !admitted.empty()) rs = rebuild_tiles(b);
+    if (rs == SOR_OK && !admitted.empty()) {
+      NvtxRange nvtx("sor_admit");
+      rs = rebuild_tiles(b);
+    }
     if (rs == SOR_OK && active_count(b) > 0) {
+      NvtxRange nvtx("sor_step");
       int steps = 1;
       rs = run_step(b, &steps);
       b->dbuf_in = step_dbuf_out(b);
@@ -573,6 +578,7 @@ static sor_status start_batcher(Ctx* c) {
 }
 
 sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out, uint64_t* ticket) {
+  NvtxRange nvtx("sor_batch_submit");
   if (request_bytes(p) > c->budget) {
     c->set_error("request needs more device memory than the whole budget");
     return SOR_ERR_BUDGET;

@@ -799,6 +799,7 @@ static sor_status autotune_depth(Ctx* c, const Plan& p, const double* u0, const 
 
 sor_status solve_blocking(Ctx* c, const Plan& plan_in, const double* u0, const double* f, double* u_out,
                           sor_result* res) {
+  NvtxRange nvtx("sor_solve");
   const double t0 = now_s();
   std::lock_guard<std::mutex> lock(c->solve_mu);
   Plan p = plan_in;

@@ -12,6 +12,8 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+
+#include <nvtx3/nvToolsExt.h>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -21,6 +23,16 @@
 #include "sor_kernels.h"
 
 namespace sorgb {
+
+// A named NVTX range for the lifetime of the object: solves, batch steps,
+// admissions and retirements show up on Nsight timelines (no cost unless a
+// tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct Ctx;
 
