@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "sor_devfn.cuh"
+#include "sor_strips.cuh"
 #include "sor_runtime.h"
 
 namespace sorgb {
@@ -588,7 +589,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
   const int n = d.n, m = d.m, pitch = d.pitch;
   const long long items = (long long)nphases * nstrips;
   unsigned* claim = progress + nstrips;
-  const int per_plane = bands * ct;
   for (;;) {
     long long g = 0;
     if (lane == 0) g = (long long)atomicAdd(claim, 1u);
@@ -607,14 +607,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
       return;
     }
     if (p > 0) {
-      const int kp = t / per_plane, r = t - kp * per_plane, band = r / ct, tc = r - band * ct;
-      const int nb[7] = {t,
-                         kp > 0 ? t - per_plane : -1,
-                         kp + 1 < n ? t + per_plane : -1,
-                         band > 0 ? t - ct : -1,
-                         band + 1 < bands ? t + ct : -1,
-                         tc > 0 ? t - 1 : -1,
-                         tc + 1 < ct ? t + 1 : -1};
+      int nb[7];
+      flow3_neighbours(t, n, bands, ct, nb);
       if (!flow_wait<7>(progress, nb, (unsigned)p, lane)) {
         if (lane == 0) {
           st->error = 1;
@@ -695,7 +689,6 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
   const T b = sizeof(T) == 4 ? (T)d.b32 : (T)d.b64;
   const long long items = (long long)nphases * nstrips;
   unsigned* claim = progress + nstrips;
-  const int per_plane = bands * ct;
   const int last_it = k0 + (nphases >> 1);
   for (;;) {
     long long g = 0;
@@ -714,14 +707,8 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
       return;
     }
     if (p > 0) {
-      const int kp = t / per_plane, r = t - kp * per_plane, band = r / ct, tc = r - band * ct;
-      const int nb[7] = {t,
-                         kp > 0 ? t - per_plane : -1,
-                         kp + 1 < n ? t + per_plane : -1,
-                         band > 0 ? t - ct : -1,
-                         band + 1 < bands ? t + ct : -1,
-                         tc > 0 ? t - 1 : -1,
-                         tc + 1 < ct ? t + 1 : -1};
+      int nb[7];
+      flow3_neighbours(t, n, bands, ct, nb);
       if (!flow_wait<7>(progress, nb, (unsigned)p, lane)) {
         if (lane == 0) {
           st->error = 1;
@@ -869,23 +856,6 @@ cudaError_t launch_3_flow(const Desc3* d, SlotState* st, const Tile* strips, int
   else
     k_3_flow<T, false><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
   return cudaGetLastError();
-}
-
-// Warp strips of the flow kernels: every plane cut into `bands` row
-// bands per 128-column tile, about 32 rows each (at least 8), and at least
-// one strip per resident warp.  Numbered plane-major, then band, then column
-// tile (the flow kernel derives a strip's neighbours from its number).
-int build_strips3(const Layout& L, int warps, std::vector<Tile>* out) {
-  const int n = L.n, m = n + 2, ct = L.col_tiles();
-  const long long per_band = (long long)n * ct;
-  int b = std::max(n / 32, (int)((warps + per_band - 1) / per_band));
-  b = std::max(1, std::min(b, std::max(1, n / 8)));
-  for (int k = 1; k <= n; ++k)
-    for (int r = 0; r < b; ++r) {
-      const int a0 = 1 + (int)((long long)r * n / b), a1 = 1 + (int)((long long)(r + 1) * n / b);
-      for (int t = 0; t < ct; ++t) out->push_back(Tile{0, k * m + a0, 1 + t * kWarpCols, a1 - a0});
-    }
-  return b;
 }
 
 #define SOR3_CK(ctx, expr)                                                                    \

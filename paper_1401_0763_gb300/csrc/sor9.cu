@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "sor_devfn.cuh"
+#include "sor_strips.cuh"
 #include "sor_runtime.h"
 
 namespace sorgb {
@@ -359,19 +360,8 @@ __global__ void __launch_bounds__(kThreads) k_9_flow(const Desc9* __restrict__ d
       return;
     }
     if (p > 0) {
-      // the eight strips around this one: the stencil's diagonal couplings
-      // reach the corner strips too
-      const int band = t / ct, tc = t - band * ct;
-      const bool up = band > 0, down = band + 1 < bands, left = tc > 0, right = tc + 1 < ct;
-      const int nb[9] = {t,
-                         up ? t - ct : -1,
-                         down ? t + ct : -1,
-                         left ? t - 1 : -1,
-                         right ? t + 1 : -1,
-                         up && left ? t - ct - 1 : -1,
-                         up && right ? t - ct + 1 : -1,
-                         down && left ? t + ct - 1 : -1,
-                         down && right ? t + ct + 1 : -1};
+      int nb[9];
+      flow9_neighbours(t, bands, ct, nb);
       if (!flow_wait<9>(progress, nb, (unsigned)p, lane)) {
         if (lane == 0) {
           st->error = 1;
@@ -565,20 +555,6 @@ cudaError_t launch_9_flow(const Desc9* d, SlotState* st, const Tile* strips, int
   else
     k_9_flow<T, FAST, false><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, ct, nphases, progress);
   return cudaGetLastError();
-}
-
-// Warp strips of the flow kernel: quarter rows 1 .. (n+1)/2 cut into bands of
-// about 32 rows (at least 8), at least one strip per resident warp, times the
-// 128-column tiles; numbered band-major (the kernel derives neighbours).
-int build_strips9(int n, int ct, int warps, std::vector<Tile>* out) {
-  const int arows = (n + 1) >> 1;
-  int b = std::max(arows / 32, (warps + ct - 1) / ct);
-  b = std::max(1, std::min(b, std::max(1, arows / 8)));
-  for (int r = 0; r < b; ++r) {
-    const int a0 = 1 + (int)((long long)r * arows / b), a1 = 1 + (int)((long long)(r + 1) * arows / b);
-    for (int t = 0; t < ct; ++t) out->push_back(Tile{0, a0, 1 + t * kWarpCols, a1 - a0});
-  }
-  return b;
 }
 
 template <typename T>
