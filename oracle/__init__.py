@@ -21,7 +21,8 @@ short:
   red-black SOR sweeps.
 * :func:`sor3d_f64`, :func:`sor3d_f32`, :func:`residual3d` -- the same
   iteration and residual on a cube with the 7-point stencil (the 3D grids the
-  paper names as its next step, Section 5).
+  paper names as its next step, Section 5); :func:`refine3d` -- the defect
+  correction on a cube.
 * :func:`sor9_f64`, :func:`sor9_f32`, :func:`residual9` -- multi-colour SOR
   (Section 3.1 names it beside red-black SOR): four colours for the compact
   9-point stencil.
@@ -84,11 +85,13 @@ def _load():
             lib.oracle_sor3d_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual3d.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.oracle_refine3d.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
             lib.oracle_sor9_f64.argtypes = lib.oracle_sor3d_f64.argtypes
             lib.oracle_sor9_f32.argtypes = lib.oracle_sor3d_f32.argtypes
             lib.oracle_residual9.argtypes = lib.oracle_residual3d.argtypes
             for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine,
-                       lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d,
+                       lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d, lib.oracle_refine3d,
                        lib.oracle_sor9_f64, lib.oracle_sor9_f32, lib.oracle_residual9):
                 fn.restype = ctypes.c_int
             _lib = lib
@@ -288,6 +291,27 @@ def resid_rel3d(u, *, f=None):
     """max|r~| / max|b~| on a cube (or max|r~| when the right side is zero)."""
     _, rm, bm = residual3d(u, f=f)
     return rm / bm if bm > 0 else rm
+
+
+def refine3d(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, trace=False):
+    """FP64 defect correction on a cube around FP32 (or FP64) inner red-black
+    SOR sweeps (7-point stencil).  Returns a dict like :func:`refine`."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _cube(u0, n)
+    f = _src3(f, n)
+    u = np.empty_like(u0)
+    ou, sw, cv = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    tr = np.zeros(max_outer + 1) if trace else None
+    rc = _load().oracle_refine3d(n, float(omega), _ptr(u0), _ptr(f), int(inner_sweeps), int(bool(inner_f32)),
+                                 float(tol), int(max_outer), _ptr(u), ctypes.byref(ou), ctypes.byref(sw),
+                                 ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_refine3d: bad arguments")
+    out = dict(u=u, outer_steps=ou.value, sweeps=sw.value, converged=bool(cv.value), final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: ou.value + 1].copy()
+    return out
 
 
 def sor9_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):

@@ -240,3 +240,72 @@ int oracle_residual3d(int n, const double *u, const double *f, double *r, double
   free(g);
   return 0;
 }
+
+/* Defect correction on a cube (the 2D oracle_refine carried to the 7-point
+ * stencil):
+ *   u <- u0; loop over outer steps:
+ *     r~ = g + sum_nb(u) - 6u (FP64), rho = max|r~|/max|b~|; stop if
+ *       rho < tol or when outer == max_outer;
+ *     d  <- 0 on the whole (n+2)^3 array (its shell stays 0);
+ *     inner_sweeps red-black SOR iterations on A d = r~ with right side
+ *       (float)r~ (already scaled by h^2) in FP32 (inner_f32 != 0) or r~ in
+ *       FP64, a = (float)(1 - w), b = (float)(w / 6) in FP32;
+ *     u_interior += (double)d.
+ * In exact arithmetic one outer step equals inner_sweeps plain SOR
+ * iterations on u (same splitting, error map M^s).  Outputs: outer steps
+ * done, total inner sweeps, final rho; trace (optional, length max_outer+1)
+ * receives rho per residual evaluation. */
+int oracle_refine3d(int n, double omega, const double *u0, const double *f, int inner_sweeps, int inner_f32,
+                    double tol, int max_outer, double *u, int *outer_steps, int *sweeps, int *converged,
+                    double *final_resid_rel, double *trace) {
+  if (n < 1 || inner_sweeps < 1 || max_outer < 0 || !u0 || !u) return -1;
+  const int m = n + 2;
+  const size_t cells = (size_t)m * m * m;
+  if (u != u0) memcpy(u, u0, sizeof(double) * cells);
+  double *g = make_g3(n, f);
+  double *r = (double *)calloc(cells, sizeof(double));
+  double *d64 = (double *)calloc(cells, sizeof(double));
+  float *d32 = (float *)calloc(cells, sizeof(float));
+  float *r32 = (float *)calloc(cells, sizeof(float));
+  if ((f && !g) || !r || !d64 || !d32 || !r32) {
+    free(g); free(r); free(d64); free(d32); free(r32);
+    return -1;
+  }
+  const float a32 = (float)(1.0 - omega), b32 = (float)(omega / 6.0);
+  int outer = 0, conv = 0;
+  double rho = 0.0;
+  for (;;) {
+    double rm, bm;
+    residual3_f64(n, u, g, r, &rm, &bm);
+    rho = rel3(rm, bm);
+    if (trace) trace[outer] = rho;
+    if (rho < tol) { conv = 1; break; }
+    if (outer == max_outer) break;
+    if (inner_f32) {
+      for (size_t c = 0; c < cells; ++c) { d32[c] = 0.0f; r32[c] = (float)r[c]; }
+      for (int s = 0; s < inner_sweeps; ++s) {
+        (void)phase3_f32(n, d32, r32, a32, b32, 0);
+        (void)phase3_f32(n, d32, r32, a32, b32, 1);
+      }
+      for (int k = 1; k <= n; ++k)
+        for (int i = 1; i <= n; ++i)
+          for (int j = 1; j <= n; ++j) u[IDX3(k, i, j, m)] = u[IDX3(k, i, j, m)] + (double)d32[IDX3(k, i, j, m)];
+    } else {
+      memset(d64, 0, sizeof(double) * cells);
+      for (int s = 0; s < inner_sweeps; ++s) {
+        (void)phase3_f64(n, d64, r, omega, 0);
+        (void)phase3_f64(n, d64, r, omega, 1);
+      }
+      for (int k = 1; k <= n; ++k)
+        for (int i = 1; i <= n; ++i)
+          for (int j = 1; j <= n; ++j) u[IDX3(k, i, j, m)] = u[IDX3(k, i, j, m)] + d64[IDX3(k, i, j, m)];
+    }
+    ++outer;
+  }
+  free(g); free(r); free(d64); free(d32); free(r32);
+  if (outer_steps) *outer_steps = outer;
+  if (sweeps) *sweeps = outer * inner_sweeps;
+  if (converged) *converged = conv;
+  if (final_resid_rel) *final_resid_rel = rho;
+  return 0;
+}

@@ -178,3 +178,56 @@ def test_f32_within_its_rounding():
     assert np.max(np.abs(r["u"] - exact)) < 2e-5
     # FP32 iterates are not FP64 ones: the rounding is really FP32
     assert pins.rel_err3(b, a) > 1e-9
+
+
+# --- defect correction on a cube ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("inner", [1, 4, 20])
+def test_refinement3d_with_fp64_inner_equals_plain_sor(inner):
+    """u + delta_s = x* + M^s (u - x*): one outer step equals s plain sweeps,
+    which pins the residual's sign, the zero start of the correction and the
+    update of u against the plain iteration (itself pinned to the splitting)."""
+    n = 7
+    u0, f = _random_cube(n, 41)
+    w = oracle.omega_opt(n)
+    steps = 3
+    ref = oracle.refine3d(u0, w, f=f, inner_sweeps=inner, inner_f32=False, tol=-1.0, max_outer=steps)
+    plain = oracle.sor3d_f64(u0, w, f=f, max_iters=inner * steps, check_every=1000, tol=0.0)
+    assert ref["outer_steps"] == steps and ref["sweeps"] == inner * steps and not ref["converged"]
+    assert pins.rel_err3(ref["u"], plain["u"]) < 1e-12
+
+
+def test_refinement3d_fp32_inner_tracks_plain_sor():
+    """FP32 inner sweeps follow plain SOR up to single-precision rounding of
+    each correction (and differ from it: the FP32 path is really taken)."""
+    n = 8
+    u0, f = _random_cube(n, 43)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine3d(u0, w, f=f, inner_sweeps=6, inner_f32=True, tol=-1.0, max_outer=3)
+    plain = oracle.sor3d_f64(u0, w, f=f, max_iters=18, check_every=1000, tol=0.0)
+    assert 0 < pins.rel_err3(ref["u"], plain["u"]) < 1e-5
+
+
+def test_refinement3d_reaches_tolerance_and_the_dst_solution():
+    n = 14
+    u0, f = _random_cube(n, 47)
+    w = oracle.omega_opt(n)
+    out = oracle.refine3d(u0, w, f=f, inner_sweeps=20, inner_f32=True, tol=1e-12, max_outer=500, trace=True)
+    assert out["converged"] and out["final_resid_rel"] < 1e-12
+    # the reported residual is that of the returned solution
+    assert oracle.resid_rel3d(out["u"], f=f) == out["final_resid_rel"]
+    # error <= cond(A) rho, cond ~ 12 / (3 pi^2 h^2) ~ 30 here
+    assert pins.rel_err3(out["u"], pins.dst_solve3(u0, f)) < 1e-12 * 1e2
+    tr = out["trace"]
+    assert tr[-1] < 1e-12 and tr[-1] < 1e-8 * tr[0]
+
+
+def test_refinement3d_caps_and_zero_steps():
+    n = 5
+    u0, f = _random_cube(n, 49)
+    w = oracle.omega_opt(n)
+    out = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=4)
+    assert out["outer_steps"] == 4 and out["sweeps"] == 12 and not out["converged"]
+    out0 = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=0)
+    assert out0["outer_steps"] == 0 and np.array_equal(out0["u"], u0)
+    assert out0["final_resid_rel"] == oracle.resid_rel3d(u0, f=f)
