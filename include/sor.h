@@ -143,11 +143,16 @@ sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, c
  * rescaled within each run of iterations between tests, one FMA per update
  * (within 1e-12 of the exact order in the tested solves).  The residual
  * r~ = (h^2 f + sum of the six neighbours) - 6 u is formed in FP64.
+ * SOR_FP32_REFINE runs the defect correction on the cube: per outer step
+ * the FP64 residual test (rho < tol), then inner_sweeps FP32 red-black sweeps
+ * (exact order) on A d = (float)r~ from d = 0, then u += d in FP64; at most
+ * max_iters / inner_sweeps corrections (results equal the CPU oracle's bit
+ * for bit).
  *   params: n = interior side N (1 <= N <= 1200); omega <= 0 selects
  *           2 / (1 + sin(pi / (N+1))); stop, tol, max_iters, check_every as
- *           for sor_solve; precision SOR_FP64 or SOR_FP32; flags 0 or
- *           SOR_FLAG_EXACT_ORDER; stall_window 0.  Anything else returns
- *           SOR_ERR_INVALID_ARG.
+ *           for sor_solve; precision SOR_FP64, SOR_FP32 or SOR_FP32_REFINE
+ *           (inner_sweeps >= 0, 0 = 20); flags 0 or SOR_FLAG_EXACT_ORDER;
+ *           stall_window 0.  Anything else returns SOR_ERR_INVALID_ARG.
  *   u0:    (N+2)^3 array indexed [k][i][j] (plane, row, column), its outer
  *          shell the Dirichlet data.  Host or device memory.
  *   f:     N^3 interior source of -Laplace(u) = f ([k][i][j]), or NULL.

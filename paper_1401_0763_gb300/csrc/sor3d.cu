@@ -28,6 +28,7 @@
 
 #include "sor_devfn.cuh"
 #include "sor_strips.cuh"
+#include "sor_bits.cuh"
 #include "sor_runtime.h"
 
 namespace sorgb {
@@ -46,6 +47,10 @@ struct Desc3 {
   float a32, b32;        // (float)(1 - w), (float)(w / 6)
   double a64, b64;       // 1 - w, w / 6
   double tol;
+  float* rhs32[2];       // defect correction, residual pass: r~ rounded to FP32, per colour (else null)
+  SlotState* inner;      // defect correction, residual pass: the inner solve's state (skipped once converged)
+  double* ucorr[2];      // defect correction, inner sweeps: u, corrected by the final d (else null)
+  SlotState* outer;      // defect correction, inner sweeps: the outer state (counts corrections)
 };
 
 // Thread (k, i, q) moves the natural cells j = 2q-1 and j = 2q of row i of
@@ -202,10 +207,12 @@ __device__ __forceinline__ void finalize3(const Desc3& d, SlotState* st, int k, 
   if (k >= d.max_iters) st->done = 1;
 }
 
-// Scaled residual over tiles, both colours, in FP64.  CHECK: the residual
-// stop of Algorithm 1's test on iterations that are multiples of K (decided
-// by the last tile); otherwise only rho of the current iterate is recorded.
-template <typename T, bool CHECK>
+// Scaled residual over tiles, both colours, in FP64.  ROLE kResidCheck: the
+// residual stop of Algorithm 1's test on iterations that are multiples of K
+// (decided by the last tile); kResidRefine: the defect correction's test
+// after every correction, with r~ rounded to FP32 into rhs32 for the inner
+// sweeps; kResidFinal: only rho of the current iterate is recorded.
+template <typename T, int ROLE>
 __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ dp, SlotState* st,
                                                       const Tile* __restrict__ tiles, int ntiles) {
   __shared__ unsigned long long red[kWarpsY];
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ 
     if (threadIdx.x == 0) {
       const int it = *((volatile int*)&st->iters);
       int skip = 0;
-      if (CHECK)
+      if (ROLE == kResidCheck)
         skip = *((volatile int*)&st->converged) || it == 0 || (it % d.K) != 0 ||
                it == *((volatile int*)&st->checked_iter);
       ctl[0] = skip;
@@ -263,14 +270,18 @@ __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ 
           W[0] = left; W[1] = nc[0]; W[2] = nc[1]; W[3] = nc[2];
           E[0] = nc[0]; E[1] = nc[1]; E[2] = nc[2]; E[3] = nc[3];
         }
+        float r32[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const double nb =
               __dadd_rn(__dadd_rn(__dadd_rn((double)nm[v], (double)np[v]), __dadd_rn((double)W[v], (double)E[v])),
                         __dadd_rn((double)dn[v], (double)up[v]));
           const double r = __dadd_rn(__dadd_rn(gv[v], nb), -__dmul_rn(6.0, (double)own[v]));
-          if ((q0 + v) <= qlim) rm = umax64(rm, abs_bits(r));
+          const bool in = (q0 + v) <= qlim;
+          if (in) rm = umax64(rm, abs_bits(r));
+          r32[v] = in ? narrow_f64(r) : 0.0f;  // round to nearest even, on the integer units
         }
+        if (ROLE == kResidRefine) store4(d.rhs32[c] + e3(k, i, q0, m, pitch), r32);
       }
     }
     block_max_to(rm, &st->rmax_bits, red);
@@ -285,12 +296,17 @@ __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ 
         const double bmax = bits_to_double(*((volatile unsigned long long*)&st->bmax_bits));
         const double rho = bmax > 0.0 ? __ddiv_rn(rmax, bmax) : rmax;
         st->last_rho = rho;
-        if (CHECK) {
+        if (ROLE == kResidCheck) {
           st->checked_iter = it;
           if (rho < d.tol) {
             st->done = 1;
             st->converged = 1;
           }
+        }
+        if (ROLE == kResidRefine && rho < d.tol) {
+          st->done = 1;
+          st->converged = 1;
+          d.inner->done = 1;  // the inner sweeps and the correction of this step are skipped
         }
       }
     }
@@ -665,12 +681,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
   }
 }
 
+// u += (double)d over the interior cells of colour c in rows [i0, i1) of
+// plane k (this lane's packed columns), d just written by this lane.
+__device__ __forceinline__ void correct3_rows(double* __restrict__ U, const float* __restrict__ D, int pitch,
+                                              int m, int n, int colour, int k, int q0, int i0, int i1) {
+  for (int i = i0; i < i1; ++i) {
+    const int qlim = (n + ((i + k + colour) & 1)) >> 1;
+    double u[4];
+    float dv[4];
+    load4(U + e3(k, i, q0, m, pitch), u);
+    load4(D + e3(k, i, q0, m, pitch), dv);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if ((q0 + v) <= qlim) u[v] = __dadd_rn(u[v], widen_f32(dv[v]));  // the widening is exact
+    store4(U + e3(k, i, q0, m, pitch), u);
+  }
+}
+
 // The exact-order phases (FP32, and FP64 with SOR_FLAG_EXACT_ORDER) under the
 // same data-flow schedule: items (phase, strip) claimed in order, each
 // waiting for its strip and the six neighbouring strips to finish the
 // previous phase; the rows of a strip are swept by sweep3_rows.  A launch
 // covers the iterations up to the next tested one, whose change it measures.
-template <typename T, bool HAS_G>
+// CORRECT (the inner sweeps of the defect correction): each colour's last
+// phase also adds its final d to u (d of that colour changes no more), and
+// the last strip counts the correction.
+template <typename T, bool HAS_G, bool CORRECT = false>
 __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ dp, SlotState* st,
                                                      const Tile* __restrict__ strips, int nstrips, int bands, int ct,
                                                      int nphases, unsigned* progress) {
@@ -730,6 +766,8 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
     } else {
       (void)sweep3_rows<T, false, HAS_G>(X, O, G, a, b, pitch, m, n, colour, k, q0, i0, i1, lane);
     }
+    if (CORRECT && p >= nphases - 2)
+      correct3_rows(d.ucorr[colour], (const float*)X, pitch, m, n, colour, k, q0, i0, i1);
     __threadfence();  // this lane's cells are visible before the strip's progress is
     __syncwarp();
     if (lane == 0) {
@@ -739,6 +777,7 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
         if (prev == (unsigned)nstrips - 1u) {
           __threadfence();
           finalize3(d, st, last_it, measure);
+          if (CORRECT) d.outer->outer += 1;
         }
       }
     }
@@ -850,8 +889,11 @@ int exact3_blocks_per_sm(bool has_g) {
 
 template <typename T>
 cudaError_t launch_3_flow(const Desc3* d, SlotState* st, const Tile* strips, int nstrips, int bands, int ct,
-                          int grid, int nphases, unsigned* progress, bool has_g, cudaStream_t s) {
-  if (has_g)
+                          int grid, int nphases, unsigned* progress, bool has_g, cudaStream_t s,
+                          bool correct = false) {
+  if (correct)
+    k_3_flow<T, true, true><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
+  else if (has_g)
     k_3_flow<T, true><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
   else
     k_3_flow<T, false><<<grid, kThreads, 0, s>>>(d, st, strips, nstrips, bands, ct, nphases, progress);
@@ -1107,7 +1149,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
                                     d_progress, has_f, s));
       done_it += Ls;
       if (stop == kStopResid && (first + done_it) % d.K == 0)
-        k_resid3d<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+        k_resid3d<T, kResidCheck><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
     }
     SOR3_CK(c, cudaGetLastError());
     return SOR_OK;
@@ -1160,7 +1202,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     finished = h_state->done != 0;
   }
   SOR3_CK(c, cudaEventRecord(ev1, s));
-  k_resid3d<T, false><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+  k_resid3d<T, kResidFinal><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
   SOR3_CK(c, cudaGetLastError());
   double* out_dst = out_dev ? u_out : d_u;
   k_unpack3d<T><<<pgrid, kWarpCols, 0, s>>>(x[0], x[1], n, pitch, out_dst);
@@ -1193,6 +1235,269 @@ __global__ void k_flow_wait_probe(const unsigned* progress, int polls, int* time
   const int nb[1] = {0};
   const bool ok = flow_wait<1>(progress, nb, 1u, lane, polls);
   if (lane == 0) *timed_out = ok ? 0 : 1;
+}
+
+// Defect correction on a cube (SOR_FP32_REFINE): per outer step the FP64
+// residual test, which also rounds r~ to FP32 as the right side; inner
+// red-black FP32 sweeps on A d = r~ from d = 0 (the exact-order flow
+// kernel, whose last phase of each colour also adds d to u in FP64).  One step is a graph replayed up to max_iters /
+// inner times; once the test passes, the device skips the remaining sweeps
+// and corrections, and the host stops at its next poll.
+sor_status run3d_refine(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                        sor_result* res) {
+  const double t0 = now_s();
+  const int n = p->n, m = n + 2;
+  const Layout L = Layout::make(n);
+  const int pitch = L.pitch;
+  const size_t elems = (size_t)m * m * pitch;
+  const size_t ncube = (size_t)m * m * m, nf = (size_t)n * n * n;
+  const bool has_f = f != nullptr;
+  const bool in_dev = is_device_ptr(u0), f_dev = has_f && is_device_ptr(f), out_dev = is_device_ptr(u_out);
+  const double w = p->omega <= 0.0 ? sor_omega_opt(n) : p->omega;
+  const int inner = p->inner_sweeps > 0 ? p->inner_sweeps : 20;
+  const int max_outer = p->max_iters / inner;
+
+  const int bps = exact3_blocks_per_sm<float>(true);
+  if (bps < 1) {
+    c->set_error("3D phase kernel does not fit on an SM");
+    return SOR_ERR_CUDA;
+  }
+  std::vector<Tile> strips;
+  const int bands = build_strips3(L, c->sm_count * bps * kWarpsY, &strips);
+  const int flow_grid = c->sm_count * bps, nst = (int)strips.size();
+  std::vector<Tile> tiles;
+  for (int k = 1; k <= n; ++k)
+    for (int r = 0; r < L.row_tiles(); ++r)
+      for (int t = 0; t < L.col_tiles(); ++t)
+        tiles.push_back(Tile{0, k * m + 1 + r * kTileRows, 1 + t * kWarpCols, std::min(kTileRows, n - r * kTileRows)});
+  const int nt = (int)tiles.size();
+
+  const bool stage_u = !in_dev || !out_dev;
+  size_t bytes = 2 * elems * (sizeof(double) + 2 * sizeof(float)) + 2 * sizeof(Desc3) + 3 * sizeof(SlotState) +
+                 sizeof(Tile) * (nt + nst) + sizeof(unsigned) * (nst + 1) + 1024;
+  if (has_f) bytes += 2 * elems * sizeof(double);
+  if (stage_u) bytes += ncube * sizeof(double);
+  if (has_f && !f_dev) bytes += nf * sizeof(double);
+  Buffers3 B;
+  B.c = c;
+  sor_status rs = ctx_reserve(c, bytes, false, 0.0);
+  if (rs != SOR_OK) {
+    c->set_error("3D solve does not fit the device-memory budget");
+    return rs;
+  }
+  B.reserved = bytes;
+  double* u64[2] = {(double*)B.get(elems * sizeof(double)), (double*)B.get(elems * sizeof(double))};
+  float* dbuf = (float*)B.get(2 * elems * sizeof(float));  // the correction, both colours
+  float* rbuf = (float*)B.get(2 * elems * sizeof(float));  // the rounded residual, both colours
+  double* g64[2] = {nullptr, nullptr};
+  if (has_f) {
+    g64[0] = (double*)B.get(elems * sizeof(double));
+    g64[1] = (double*)B.get(elems * sizeof(double));
+  }
+  Desc3* d_desc = (Desc3*)B.get(2 * sizeof(Desc3));  // [0] u (residual, correction), [1] d (inner sweeps)
+  SlotState* d_state = (SlotState*)B.get(3 * sizeof(SlotState));  // [0] outer, [1] inner, [2] inner at rest
+  Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
+  Tile* d_strips = (Tile*)B.get(sizeof(Tile) * nst);
+  unsigned* d_progress = (unsigned*)B.get(sizeof(unsigned) * (nst + 1));
+  double* d_u = stage_u ? (double*)B.get(ncube * sizeof(double)) : nullptr;
+  double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
+  if (!u64[0] || !u64[1] || !dbuf || !rbuf || (has_f && (!g64[0] || !g64[1])) || !d_desc || !d_state ||
+      !d_tiles || !d_strips || !d_progress || (stage_u && !d_u) || (has_f && !f_dev && !d_f)) {
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  cudaStream_t s = c->stream;
+  float* dcol[2] = {dbuf, dbuf + elems};
+  float* rcol[2] = {rbuf, rbuf + elems};
+
+  Desc3 du, dd;
+  std::memset(&du, 0, sizeof(du));
+  std::memset(&dd, 0, sizeof(dd));
+  du.x[0] = u64[0];
+  du.x[1] = u64[1];
+  du.g[0] = g64[0];
+  du.g[1] = g64[1];
+  du.g64[0] = g64[0];
+  du.g64[1] = g64[1];
+  du.n = dd.n = n;
+  du.m = dd.m = m;
+  du.pitch = dd.pitch = pitch;
+  du.tiles = dd.tiles = nt;
+  du.K = 1;
+  du.max_iters = 1 << 30;
+  du.stop = kStopResid;
+  du.tol = p->tol;
+  du.rhs32[0] = rcol[0];
+  du.rhs32[1] = rcol[1];
+  du.inner = d_state + 1;
+  dd.x[0] = dcol[0];
+  dd.x[1] = dcol[1];
+  dd.g[0] = rcol[0];
+  dd.g[1] = rcol[1];
+  dd.K = inner;
+  dd.max_iters = inner;  // one launch of `inner` iterations; its change test never stops it
+  dd.stop = kStopDelta;
+  dd.tol = -1.0;
+  dd.a32 = (float)(1.0 - w);
+  dd.b32 = (float)(w / 6.0);
+  dd.a64 = 1.0 - w;
+  dd.b64 = w / 6.0;
+  dd.ucorr[0] = u64[0];
+  dd.ucorr[1] = u64[1];
+  dd.outer = d_state;
+  SlotState st[3];
+  std::memset(st, 0, sizeof(st));
+  for (auto& x : st) {
+    x.checked_iter = -1;
+    x.last_dmax = -1.0;
+    x.last_rho = -1.0;
+    x.best_rho = HUGE_VAL;
+  }
+  for (int k = 0; k < 2; ++k) {
+    SOR3_CK(c, cudaMemsetAsync(u64[k], 0, elems * sizeof(double), s));
+    if (has_f) SOR3_CK(c, cudaMemsetAsync(g64[k], 0, elems * sizeof(double), s));
+  }
+  SOR3_CK(c, cudaMemsetAsync(dbuf, 0, 2 * elems * sizeof(float), s));
+  SOR3_CK(c, cudaMemsetAsync(rbuf, 0, 2 * elems * sizeof(float), s));
+  const Desc3 descs[2] = {du, dd};
+  SOR3_CK(c, cudaMemcpyAsync(d_desc, descs, sizeof(descs), cudaMemcpyHostToDevice, s));
+  SOR3_CK(c, cudaMemcpyAsync(d_state, st, sizeof(st), cudaMemcpyHostToDevice, s));
+  SOR3_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+  SOR3_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
+  const double* u_src = u0;
+  if (!in_dev) {
+    SOR3_CK(c, cudaMemcpyAsync(d_u, u0, ncube * sizeof(double), cudaMemcpyHostToDevice, s));
+    u_src = d_u;
+  }
+  const double* f_src = f;
+  if (has_f && !f_dev) {
+    SOR3_CK(c, cudaMemcpyAsync(d_f, f, nf * sizeof(double), cudaMemcpyHostToDevice, s));
+    f_src = d_f;
+  }
+  const double h = 1.0 / (double)(n + 1);
+  const dim3 pgrid((L.qw + kWarpCols - 1) / kWarpCols, m, m);
+  k_pack3d<double><<<pgrid, kWarpCols, 0, s>>>(u_src, f_src, n, pitch, h * h, u64[0], u64[1], g64[0], g64[1],
+                                               nullptr, nullptr, d_state);
+  SOR3_CK(c, cudaGetLastError());
+
+  const int grid = std::min(nt, c->sm_count * 8);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SOR3_CK(c, cudaEventCreate(&ev0));
+  if (cudaEventCreate(&ev1) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ev0);
+    c->set_error("event creation failed");
+    return SOR_ERR_CUDA;
+  }
+  SlotState* h_state = nullptr;  // [0], [1]: the outer state after alternate batches
+  if (cudaMallocHost(&h_state, 2 * sizeof(SlotState)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    c->set_error("pinned allocation failed");
+    return SOR_ERR_OOM;
+  }
+  cudaEvent_t pev[2] = {nullptr, nullptr};
+  struct Cleanup {
+    cudaEvent_t a, b;
+    SlotState* hs;
+    cudaGraphExec_t g;
+    cudaEvent_t* pe;
+    ~Cleanup() {
+      if (g) cudaGraphExecDestroy(g);
+      for (int k = 0; k < 2; ++k)
+        if (pe[k]) cudaEventDestroy(pe[k]);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaFreeHost(hs);
+    }
+  } cl{ev0, ev1, h_state, nullptr, pev};
+  for (int k = 0; k < 2; ++k) SOR3_CK(c, cudaEventCreateWithFlags(&pev[k], cudaEventDisableTiming));
+
+  // one outer step: inner state back to rest, d = 0, the residual test (and
+  // right side), the inner sweeps, the correction
+  auto enqueue_step = [&]() -> sor_status {
+    SOR3_CK(c, cudaMemcpyAsync(d_state + 1, d_state + 2, sizeof(SlotState), cudaMemcpyDeviceToDevice, s));
+    SOR3_CK(c, cudaMemsetAsync(dbuf, 0, 2 * elems * sizeof(float), s));
+    k_resid3d<double, kResidRefine><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+    SOR3_CK(c, cudaGetLastError());
+    SOR3_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
+    SOR3_CK(c, launch_3_flow<float>(d_desc + 1, d_state + 1, d_strips, nst, bands, L.col_tiles(), flow_grid,
+                                    2 * inner, d_progress, true, s, true));
+    return SOR_OK;
+  };
+  const bool use_graphs = c->opt_graphs.load() != 0;
+  if (use_graphs && max_outer > 0) {
+    cudaGraph_t gr = nullptr;
+    SOR3_CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const sor_status es = enqueue_step();
+    const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+    if (es != SOR_OK) {
+      if (gr) cudaGraphDestroy(gr);
+      return es;
+    }
+    SOR3_CK(c, ce);
+    const cudaError_t ie = cudaGraphInstantiate(&cl.g, gr, 0);
+    cudaGraphDestroy(gr);
+    SOR3_CK(c, ie);
+  }
+  SOR3_CK(c, cudaEventRecord(ev0, s));
+  // batches of about a millisecond of steps; the host reads the state after
+  // batch b while batch b+1 runs, so the device never waits for the poll
+  // (steps queued past convergence only repeat the residual test)
+  const double step_s = (double)n * n * n * inner / 4.0e11 + 20e-6;
+  const int per_poll = (int)std::max(1.0, std::min(32.0, std::floor(1e-3 / step_s)));
+  int planned = 0, batch = 0;
+  while (planned < max_outer) {
+    const int kk = std::min(per_poll, max_outer - planned);
+    for (int j = 0; j < kk; ++j) {
+      if (use_graphs) {
+        SOR3_CK(c, cudaGraphLaunch(cl.g, s));
+      } else {
+        const sor_status es = enqueue_step();
+        if (es != SOR_OK) return es;
+      }
+    }
+    planned += kk;
+    SOR3_CK(c, cudaMemcpyAsync(h_state + (batch & 1), d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR3_CK(c, cudaEventRecord(pev[batch & 1], s));
+    if (batch > 0) {  // the previous batch's state
+      SOR3_CK(c, cudaEventSynchronize(pev[(batch - 1) & 1]));
+      const SlotState& prev = h_state[(batch - 1) & 1];
+      if (prev.converged || prev.error) break;
+    }
+    ++batch;
+  }
+  // the test after the last correction (a no-op repeat once converged)
+  k_resid3d<double, kResidRefine><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+  SOR3_CK(c, cudaGetLastError());
+  SOR3_CK(c, cudaEventRecord(ev1, s));
+  double* out_dst = out_dev ? u_out : d_u;
+  k_unpack3d<double><<<pgrid, kWarpCols, 0, s>>>(u64[0], u64[1], n, pitch, out_dst);
+  SOR3_CK(c, cudaGetLastError());
+  if (!out_dev) SOR3_CK(c, cudaMemcpyAsync(u_out, d_u, ncube * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SlotState fin[2];
+  SOR3_CK(c, cudaMemcpyAsync(h_state, d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+  SOR3_CK(c, cudaStreamSynchronize(s));
+  fin[0] = h_state[0];
+  SOR3_CK(c, cudaMemcpy(&fin[1], d_state + 1, sizeof(SlotState), cudaMemcpyDeviceToHost));
+  float ms = 0.0f;
+  SOR3_CK(c, cudaEventElapsedTime(&ms, ev0, ev1));
+  if (fin[0].error || fin[1].error) {
+    c->set_error("device-side consistency check failed");
+    return SOR_ERR_INTERNAL;
+  }
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->iterations = fin[0].outer * inner;
+    res->converged = fin[0].converged;
+    res->outer_steps = fin[0].outer;
+    res->final_maxdelta = -1.0;
+    res->final_resid_rel = fin[0].last_rho;
+    res->latency_s = now_s() - t0;
+    res->device_s = ms * 1e-3;
+  }
+  return SOR_OK;
 }
 
 }  // namespace
@@ -1234,7 +1539,9 @@ sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const
   }
   std::ostringstream why;
   if (p->n < 1 || p->n > kMax3dN) why << "n must be in [1, " << kMax3dN << "]";
-  else if (p->precision != SOR_FP64 && p->precision != SOR_FP32) why << "3D solves run in FP64 or FP32";
+  else if (p->precision != SOR_FP64 && p->precision != SOR_FP32 && p->precision != SOR_FP32_REFINE)
+    why << "3D solves run in FP64, FP32 or FP32_REFINE";
+  else if (p->inner_sweeps < 0) why << "inner_sweeps must be >= 0";
   else if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) why << "unknown stop rule";
   else if (p->max_iters < 0 || p->check_every < 1) why << "max_iters >= 0 and check_every >= 1 required";
   else if (p->flags & ~SOR_FLAG_EXACT_ORDER) why << "unknown flags";
@@ -1245,6 +1552,7 @@ sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const
     c->set_error(why.str());
     return SOR_ERR_INVALID_ARG;
   }
+  if (p->precision == SOR_FP32_REFINE) return run3d_refine(c, p, u0, f, u_out, res);
   return p->precision == SOR_FP64 ? run3d<double>(c, p, u0, f, u_out, res) : run3d<float>(c, p, u0, f, u_out, res);
 }
 

@@ -213,6 +213,42 @@ def test_fp64_default_stops_like_oracle(ctx):
     assert np.max(np.abs(got - exact)) < 1e-11
 
 
+@pytest.mark.parametrize("n", [1, 3, 12, 33, 65])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_refine3d_bitwise(ctx, n, with_f):
+    """Defect correction on a cube (FP32 inner sweeps, FP64 residual and
+    correction): bit identical to the oracle, same correction count."""
+    capi = capi_mod()
+    u0 = wl.random_shell(n, 700 + n)
+    f = wl.gaussian_source3(n, 800 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    inner, cap = 7, 7 * 60
+    ref = oracle.refine3d(u0, w, f=f, inner_sweeps=inner, tol=1e-11, max_outer=cap // inner)
+    got, res = run3(ctx, u0, f, omega=w, tol=1e-11, max_iters=cap, inner_sweeps=inner,
+                    precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
+    assert res["iterations"] == ref["sweeps"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+def test_refine3d_cap_and_solution(ctx):
+    """The correction cap (max_iters / inner_sweeps) and a converged solve
+    against the DST-I solution the oracle is pinned to."""
+    capi = capi_mod()
+    n = 40
+    u0 = wl.random_shell(n, 21)
+    f = wl.gaussian_source3(n, 22)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine3d(u0, w, f=f, inner_sweeps=20, tol=1e-30, max_outer=3)
+    got, res = run3(ctx, u0, f, omega=w, tol=1e-30, max_iters=69, inner_sweeps=20, precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == 3 and not res["converged"] and res["iterations"] == 60
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
+    got, res = run3(ctx, u0, f, tol=1e-11, max_iters=20000, precision=capi.SOR_FP32_REFINE, device=False)
+    assert res["converged"] and res["final_resid_rel"] < 1e-11
+    assert pins.rel_err3(got, pins.dst_solve3(u0, f)) < 1e-9
+
+
 def test_bounded_wait_gives_up_and_context_survives(ctx):
     """The failure path of the data-flow kernels without a fault: their
     bounded device-side wait, run on a progress counter nothing advances,
@@ -238,8 +274,8 @@ def test_bounded_wait_gives_up_and_context_survives(ctx):
 def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_shell(4, 1)
-    for kw in (dict(precision=capi.SOR_FP32_REFINE), dict(stall_window=3), dict(omega=2.5),
-               dict(check_every=0), dict(flags=8)):
+    for kw in (dict(precision=7), dict(stall_window=3), dict(omega=2.5), dict(check_every=0), dict(flags=8),
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
         p = capi.make_params(4, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, out.ctypes.data)
