@@ -25,7 +25,7 @@ short:
   correction on a cube.
 * :func:`sor9_f64`, :func:`sor9_f32`, :func:`residual9` -- multi-colour SOR
   (Section 3.1 names it beside red-black SOR): four colours for the compact
-  9-point stencil.
+  9-point stencil; :func:`refine9` -- the defect correction with it.
 
 Parity status: every function is pinned by ``tests/test_oracle_pins.py`` and
 ``tests/test_oracle3d_pins.py`` and ``tests/test_oracle9_pins.py`` (dense
@@ -90,9 +90,10 @@ def _load():
             lib.oracle_sor9_f64.argtypes = lib.oracle_sor3d_f64.argtypes
             lib.oracle_sor9_f32.argtypes = lib.oracle_sor3d_f32.argtypes
             lib.oracle_residual9.argtypes = lib.oracle_residual3d.argtypes
+            lib.oracle_refine9.argtypes = lib.oracle_refine3d.argtypes
             for fn in (lib.oracle_sor_f64, lib.oracle_sor_f32, lib.oracle_residual, lib.oracle_refine,
                        lib.oracle_sor3d_f64, lib.oracle_sor3d_f32, lib.oracle_residual3d, lib.oracle_refine3d,
-                       lib.oracle_sor9_f64, lib.oracle_sor9_f32, lib.oracle_residual9):
+                       lib.oracle_sor9_f64, lib.oracle_sor9_f32, lib.oracle_residual9, lib.oracle_refine9):
                 fn.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -372,3 +373,24 @@ def residual9(u, *, f=None):
 def resid_rel9(u, *, f=None):
     _, rm, bm = residual9(u, f=f)
     return rm / bm if bm > 0 else rm
+
+
+def refine9(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, trace=False):
+    """FP64 defect correction around FP32 (or FP64) inner four-colour 9-point
+    SOR sweeps.  Returns a dict like :func:`refine`."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _grid(u0, n)
+    f = _src(f, n)
+    u = np.empty_like(u0)
+    ou, sw, cv = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    tr = np.zeros(max_outer + 1) if trace else None
+    rc = _load().oracle_refine9(n, float(omega), _ptr(u0), _ptr(f), int(inner_sweeps), int(bool(inner_f32)),
+                                float(tol), int(max_outer), _ptr(u), ctypes.byref(ou), ctypes.byref(sw),
+                                ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_refine9: bad arguments")
+    out = dict(u=u, outer_steps=ou.value, sweeps=sw.value, converged=bool(cv.value), final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: ou.value + 1].copy()
+    return out

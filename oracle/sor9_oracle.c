@@ -238,3 +238,65 @@ int oracle_residual9(int n, const double *u, const double *f, double *r, double 
   free(g);
   return 0;
 }
+
+/* Defect correction with the four-colour 9-point sweeps (the 2D
+ * oracle_refine carried to this stencil):
+ *   u <- u0; loop over outer steps:
+ *     r~ = (g + (4 s4 + sd)) - 20u (FP64), rho = max|r~|/max|b~|; stop if
+ *       rho < tol or when outer == max_outer;
+ *     d  <- 0 on the whole (n+2)^2 array (its ring stays 0);
+ *     inner_sweeps four-colour iterations on A d = r~ with right side
+ *       (float)r~ in FP32 (inner_f32 != 0, a = (float)(1 - w),
+ *       b = (float)(w / 20)) or r~ in FP64;
+ *     u_interior += (double)d.
+ * In exact arithmetic one outer step equals inner_sweeps plain iterations on
+ * u.  Outputs: outer steps done, total inner sweeps, final rho; trace
+ * (optional, length max_outer+1) receives rho per residual evaluation. */
+int oracle_refine9(int n, double omega, const double *u0, const double *f, int inner_sweeps, int inner_f32,
+                   double tol, int max_outer, double *u, int *outer_steps, int *sweeps, int *converged,
+                   double *final_resid_rel, double *trace) {
+  if (n < 1 || inner_sweeps < 1 || max_outer < 0 || !u0 || !u) return -1;
+  const int m = n + 2;
+  const size_t cells = (size_t)m * m;
+  if (u != u0) memcpy(u, u0, sizeof(double) * cells);
+  double *g = make_g9(n, f);
+  double *r = (double *)calloc(cells, sizeof(double));
+  double *d64 = (double *)calloc(cells, sizeof(double));
+  float *d32 = (float *)calloc(cells, sizeof(float));
+  float *r32 = (float *)calloc(cells, sizeof(float));
+  if ((f && !g) || !r || !d64 || !d32 || !r32) {
+    free(g); free(r); free(d64); free(d32); free(r32);
+    return -1;
+  }
+  const float a32 = (float)(1.0 - omega), b32 = (float)(omega / 20.0);
+  int outer = 0, conv = 0;
+  double rho = 0.0;
+  for (;;) {
+    double rm, bm;
+    residual9_f64(n, u, g, r, &rm, &bm);
+    rho = rel9(rm, bm);
+    if (trace) trace[outer] = rho;
+    if (rho < tol) { conv = 1; break; }
+    if (outer == max_outer) break;
+    if (inner_f32) {
+      for (size_t c = 0; c < cells; ++c) { d32[c] = 0.0f; r32[c] = (float)r[c]; }
+      for (int s = 0; s < inner_sweeps; ++s)
+        for (int colour = 0; colour < 4; ++colour) (void)phase9_f32(n, d32, r32, a32, b32, colour);
+      for (int i = 1; i <= n; ++i)
+        for (int j = 1; j <= n; ++j) AT(u, i, j, m) = AT(u, i, j, m) + (double)AT(d32, i, j, m);
+    } else {
+      memset(d64, 0, sizeof(double) * cells);
+      for (int s = 0; s < inner_sweeps; ++s)
+        for (int colour = 0; colour < 4; ++colour) (void)phase9_f64(n, d64, r, omega, colour);
+      for (int i = 1; i <= n; ++i)
+        for (int j = 1; j <= n; ++j) AT(u, i, j, m) = AT(u, i, j, m) + AT(d64, i, j, m);
+    }
+    ++outer;
+  }
+  free(g); free(r); free(d64); free(d32); free(r32);
+  if (outer_steps) *outer_steps = outer;
+  if (sweeps) *sweeps = outer * inner_sweeps;
+  if (converged) *converged = conv;
+  if (final_resid_rel) *final_resid_rel = rho;
+  return 0;
+}

@@ -139,3 +139,51 @@ def test_f32_within_its_rounding():
     a = oracle.sor9_f64(u0, w, f=f, max_iters=150, tol=0.0)["u"]
     b = oracle.sor9_f32(u0, w, f=f, max_iters=150, tol=0.0)["u"]
     assert 1e-9 < pins.rel_err(b, a) < 5e-5
+
+
+# --- defect correction with the 9-point sweeps ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("inner", [1, 3, 12])
+def test_refinement9_with_fp64_inner_equals_plain_sor(inner):
+    """u + delta_s = x* + M^s (u - x*): one outer step equals s plain
+    four-colour iterations (pinned to the multi-colour splitting)."""
+    n = 9
+    u0, f = _problem(n, 51)
+    w = oracle.omega_opt(n)
+    steps = 3
+    ref = oracle.refine9(u0, w, f=f, inner_sweeps=inner, inner_f32=False, tol=-1.0, max_outer=steps)
+    plain = oracle.sor9_f64(u0, w, f=f, max_iters=inner * steps, check_every=1000, tol=0.0)
+    assert ref["outer_steps"] == steps and ref["sweeps"] == inner * steps and not ref["converged"]
+    assert pins.rel_err(ref["u"], plain["u"]) < 1e-12
+
+
+def test_refinement9_fp32_inner_tracks_plain_sor():
+    n = 12
+    u0, f = _problem(n, 53)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine9(u0, w, f=f, inner_sweeps=5, inner_f32=True, tol=-1.0, max_outer=3)
+    plain = oracle.sor9_f64(u0, w, f=f, max_iters=15, check_every=1000, tol=0.0)
+    assert 0 < pins.rel_err(ref["u"], plain["u"]) < 1e-5
+
+
+def test_refinement9_reaches_tolerance_and_the_dst_solution():
+    n = 30
+    u0, f = _problem(n, 57)
+    w = oracle.omega_opt(n)
+    out = oracle.refine9(u0, w, f=f, inner_sweeps=20, inner_f32=True, tol=1e-12, max_outer=500, trace=True)
+    assert out["converged"] and out["final_resid_rel"] < 1e-12
+    assert oracle.resid_rel9(out["u"], f=f) == out["final_resid_rel"]
+    assert pins.rel_err(out["u"], pins.dst_solve9(u0, f)) < 1e-12 * 1e3
+    tr = out["trace"]
+    assert tr[-1] < 1e-12 and tr[-1] < 1e-8 * tr[0]
+
+
+def test_refinement9_caps_and_zero_steps():
+    n = 6
+    u0, f = _problem(n, 59)
+    w = oracle.omega_opt(n)
+    out = oracle.refine9(u0, w, f=f, inner_sweeps=4, tol=1e-30, max_outer=3)
+    assert out["outer_steps"] == 3 and out["sweeps"] == 12 and not out["converged"]
+    out0 = oracle.refine9(u0, w, f=f, inner_sweeps=4, tol=1e-30, max_outer=0)
+    assert out0["outer_steps"] == 0 and np.array_equal(out0["u"], u0)
+    assert out0["final_resid_rel"] == oracle.resid_rel9(u0, f=f)
