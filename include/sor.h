@@ -175,7 +175,13 @@ sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0,
  * multiply-adds (within 1e-12 of the exact order in the tested solves).  The
  * residual r~ = (6 h^2 f + (4 s4 + sd)) - 20 u is formed in FP64 and b~
  * weighs the ring's edge neighbours by 4 and its diagonal ones by 1.
- *   params: as for sor_solve with precision SOR_FP64 or SOR_FP32, flags 0 or
+ * SOR_FP32_REFINE runs the defect correction with these sweeps: per outer
+ * step the FP64 residual test (rho < tol), inner_sweeps FP32 four-colour
+ * iterations (exact order) on A d = (float)r~ from d = 0, then u += d in
+ * FP64; at most max_iters / inner_sweeps corrections (results equal the CPU
+ * oracle's bit for bit).
+ *   params: as for sor_solve with precision SOR_FP64, SOR_FP32 or
+ *           SOR_FP32_REFINE (inner_sweeps >= 0, 0 = 20), flags 0 or
  *           SOR_FLAG_EXACT_ORDER, stall_window 0 (else SOR_ERR_INVALID_ARG);
  *           omega <= 0 selects 2 / (1 + sin(pi / (N+1))).
  *   u0, f, u_out: as for sor_solve ((N+2)^2, N^2, (N+2)^2; host or device);

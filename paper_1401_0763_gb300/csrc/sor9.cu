@@ -27,6 +27,7 @@
 
 #include "sor_devfn.cuh"
 #include "sor_strips.cuh"
+#include "sor_bits.cuh"
 #include "sor_runtime.h"
 
 namespace sorgb {
@@ -44,6 +45,10 @@ struct Desc9 {
   float a32, b32;        // (float)(1 - w), (float)(w / 20)
   double a64, b64;       // 1 - w, w / 20
   double tol;
+  float* rhs32[4];       // defect correction, residual pass: r~ rounded to FP32, per quarter (else null)
+  SlotState* inner;      // defect correction, residual pass: the inner solve's state (skipped once converged)
+  double* ucorr[4];      // defect correction, inner sweeps: u, corrected by the final d (else null)
+  SlotState* outer;      // defect correction, inner sweeps: the outer state (counts corrections)
 };
 
 // Natural (N+2)^2 <-> quarters; interior cells also get 6 h^2 f and
@@ -253,7 +258,28 @@ __device__ __forceinline__ void finalize9(const Desc9& d, SlotState* st, int k, 
 // phase beats the data-flow schedule, whose per-item claims, waits and
 // fences sit on the critical path of every phase.  The last tile of the
 // phase of colour 3 closes the iteration.
-template <typename T, int C>
+// u += (double)d over the interior cells of quarter C in rows [a0, a1) (this
+// lane's columns), d just written by this lane.
+template <int C>
+__device__ __forceinline__ void correct9_rows(const Desc9& d, const float* __restrict__ D, int q0, int a0, int a1) {
+  double* U = d.ucorr[C];
+  const int pitch = d.pitch, blim = (d.n + (C & 1)) >> 1;
+  for (int r = a0; r < a1; ++r) {
+    double u[4];
+    float dv[4];
+    load4(U + e9(r, q0, pitch), u);
+    load4(D + e9(r, q0, pitch), dv);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if ((q0 + v) <= blim) u[v] = __dadd_rn(u[v], widen_f32(dv[v]));  // the widening is exact
+    store4(U + e9(r, q0, pitch), u);
+  }
+}
+
+// CORRECT (the inner sweeps of the defect correction, FP32): the phase of the
+// last iteration also adds the quarter's final d to u, and the last tile of
+// colour 3 counts the correction.
+template <typename T, int C, bool CORRECT = false>
 __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ dp, SlotState* st,
                                                      const Tile* __restrict__ tiles, int ntiles) {
   __shared__ unsigned long long red[kWarpsY];
@@ -287,6 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ d
       (void)sweep9_rows<T, C, false, true>(d, q0, a0, a1, lane);
     else
       (void)sweep9_rows<T, C, false, false>(d, q0, a0, a1, lane);
+    if (CORRECT && kk == d.max_iters) correct9_rows<C>(d, (const float*)d.x[C], q0, a0, a1);
     if (measure) block_max_to(dm, &st->dmax_bits, red);
     if (C == 3) {
       __threadfence();
@@ -296,6 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ d
         if (prev == (unsigned)d.tiles - 1u) {
           __threadfence();
           finalize9(d, st, kk, measure);
+          if (CORRECT && kk == d.max_iters) d.outer->outer += 1;
         }
       }
       __syncthreads();
@@ -401,8 +429,9 @@ __global__ void __launch_bounds__(kThreads) k_9_flow(const Desc9* __restrict__ d
   }
 }
 
-// Residual rows of quarter C: max |(g + (4 s4 + sd)) - 20 u| in FP64.
-template <typename T, int C>
+// Residual rows of quarter C: max |(g + (4 s4 + sd)) - 20 u| in FP64; WRITE
+// (the defect correction): r~ rounded to FP32 into rhs32[C].
+template <typename T, int C, bool WRITE>
 __device__ __forceinline__ unsigned long long resid9_rows(const Desc9& d, int q0, int a0, int a1, int lane) {
   constexpr int PI = C >> 1, PJ = C & 1;
   unsigned long long rm = 0;
@@ -428,6 +457,7 @@ __device__ __forceinline__ unsigned long long resid9_rows(const Desc9& d, int q0
     we_of<T, PJ>(w1, Q1 + (size_t)r * pitch, q0, lane, W, E);
     we_of<T, PJ>(n3, Q3 + (size_t)(r - PI) * pitch, q0, lane, NW, NE);
     we_of<T, PJ>(s3, Q3 + (size_t)(r + 1 - PI) * pitch, q0, lane, SW, SE);
+    float r32[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const double s4 =
@@ -436,13 +466,19 @@ __device__ __forceinline__ unsigned long long resid9_rows(const Desc9& d, int q0
           __dadd_rn(__dadd_rn((double)NW[v], (double)NE[v]), __dadd_rn((double)SW[v], (double)SE[v]));
       const double res = __dadd_rn(__dadd_rn(gv[v], __dadd_rn(__dmul_rn(4.0, s4), sd)),
                                    -__dmul_rn(20.0, (double)own[v]));
-      if ((q0 + v) <= blim) rm = umax64(rm, abs_bits(res));
+      const bool in = (q0 + v) <= blim;
+      if (in) rm = umax64(rm, abs_bits(res));
+      r32[v] = in ? narrow_f64(res) : 0.0f;  // round to nearest even, on the integer units
     }
+    if (WRITE) store4(d.rhs32[C] + e9(r, q0, pitch), r32);
   }
   return rm;
 }
 
-template <typename T, bool CHECK>
+// ROLE kResidCheck: the residual stop on iterations that are multiples of K;
+// kResidRefine: the defect correction's test after every correction, with r~
+// rounded to FP32 into rhs32; kResidFinal: only rho is recorded.
+template <typename T, int ROLE>
 __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ dp, SlotState* st,
                                                      const Tile* __restrict__ tiles, int ntiles) {
   __shared__ unsigned long long red[kWarpsY];
@@ -454,7 +490,7 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
     if (threadIdx.x == 0) {
       const int it = *((volatile int*)&st->iters);
       int skip = 0;
-      if (CHECK)
+      if (ROLE == kResidCheck)
         skip = *((volatile int*)&st->converged) || it == 0 || (it % d.K) != 0 ||
                it == *((volatile int*)&st->checked_iter);
       ctl[0] = skip;
@@ -468,10 +504,11 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
     const int rpw = (tl.nrows + kWarpsY - 1) / kWarpsY;
     const int a0 = tl.row0 + wy * rpw;
     const int a1 = min(a0 + rpw, tl.row0 + tl.nrows);
-    unsigned long long rm = resid9_rows<T, 0>(d, q0, a0, a1, lane);
-    rm = umax64(rm, resid9_rows<T, 1>(d, q0, a0, a1, lane));
-    rm = umax64(rm, resid9_rows<T, 2>(d, q0, a0, a1, lane));
-    rm = umax64(rm, resid9_rows<T, 3>(d, q0, a0, a1, lane));
+    constexpr bool W = ROLE == kResidRefine;
+    unsigned long long rm = resid9_rows<T, 0, W>(d, q0, a0, a1, lane);
+    rm = umax64(rm, resid9_rows<T, 1, W>(d, q0, a0, a1, lane));
+    rm = umax64(rm, resid9_rows<T, 2, W>(d, q0, a0, a1, lane));
+    rm = umax64(rm, resid9_rows<T, 3, W>(d, q0, a0, a1, lane));
     block_max_to(rm, &st->rmax_bits, red);
     __threadfence();
     __syncthreads();
@@ -484,12 +521,17 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
         const double bmax = bits_to_double(*((volatile unsigned long long*)&st->bmax_bits));
         const double rho = bmax > 0.0 ? __ddiv_rn(rmax, bmax) : rmax;
         st->last_rho = rho;
-        if (CHECK) {
+        if (ROLE == kResidCheck) {
           st->checked_iter = it;
           if (rho < d.tol) {
             st->done = 1;
             st->converged = 1;
           }
+        }
+        if (ROLE == kResidRefine && rho < d.tol) {
+          st->done = 1;
+          st->converged = 1;
+          d.inner->done = 1;  // the inner sweeps of this step are skipped
         }
       }
     }
@@ -525,13 +567,13 @@ struct Buffers9 {
   }
 };
 
-template <typename T>
+template <typename T, bool CORRECT = false>
 void launch_sweep9(int colour, int grid, cudaStream_t s, const Desc9* d, SlotState* st, const Tile* t, int nt) {
   switch (colour) {
-    case 0: k_sweep9<T, 0><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
-    case 1: k_sweep9<T, 1><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
-    case 2: k_sweep9<T, 2><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
-    default: k_sweep9<T, 3><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
+    case 0: k_sweep9<T, 0, CORRECT><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
+    case 1: k_sweep9<T, 1, CORRECT><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
+    case 2: k_sweep9<T, 2, CORRECT><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
+    default: k_sweep9<T, 3, CORRECT><<<grid, kThreads, 0, s>>>(d, st, t, nt); break;
   }
 }
 
@@ -727,7 +769,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
       for (int it = 1; it <= Lc; ++it) {
         for (int col = 0; col < 4; ++col) launch_sweep9<T>(col, grid, s, d_desc, d_state, d_tiles, nt);
         if (stop == kStopResid && (first + it) % d.K == 0)
-          k_resid9<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+          k_resid9<T, kResidCheck><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
       }
       SOR9_CK(c, cudaGetLastError());
       return SOR_OK;
@@ -746,7 +788,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
                                            has_f, s)));
       done_it += Ls;
       if (stop == kStopResid && (first + done_it) % d.K == 0)
-        k_resid9<T, true><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+        k_resid9<T, kResidCheck><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
     }
     SOR9_CK(c, cudaGetLastError());
     return SOR_OK;
@@ -795,7 +837,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
     finished = h_state->done != 0;
   }
   SOR9_CK(c, cudaEventRecord(ev1, s));
-  k_resid9<T, false><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+  k_resid9<T, kResidFinal><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
   SOR9_CK(c, cudaGetLastError());
   double* out_dst = out_dev ? u_out : d_u;
   k_unpack9<T><<<pgrid, kWarpCols, 0, s>>>(x[0], x[1], x[2], x[3], n, pitch, out_dst);
@@ -821,6 +863,248 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
   return SOR_OK;
 }
 
+// Defect correction with the four-colour sweeps (SOR_FP32_REFINE): per outer
+// step the FP64 residual test, which also rounds r~ to FP32 as the right
+// side; inner_sweeps FP32 four-colour iterations on A d = r~ from d = 0 (a
+// launch per phase), whose last phase of each colour also adds d to u in
+// FP64.  One step is a graph replayed up to max_iters / inner times; once the
+// test passes, the device skips the queued sweeps and the host stops at its
+// next poll.
+sor_status run9_refine(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                       sor_result* res) {
+  const double t0 = now_s();
+  const int n = p->n, m = n + 2;
+  const Layout L = Layout::make(n);
+  const int pitch = L.pitch;
+  const int qrows = ((n + 1) >> 1) + 2;
+  const size_t qelems = (size_t)qrows * pitch;
+  const size_t nnat = (size_t)m * m, nf = (size_t)n * n;
+  const bool has_f = f != nullptr;
+  const bool in_dev = is_device_ptr(u0), f_dev = has_f && is_device_ptr(f), out_dev = is_device_ptr(u_out);
+  const double w = p->omega <= 0.0 ? sor_omega_opt(n) : p->omega;
+  const int inner = p->inner_sweeps > 0 ? p->inner_sweeps : 20;
+  const int max_outer = p->max_iters / inner;
+
+  std::vector<Tile> tiles;
+  const int arows = (n + 1) >> 1;
+  for (int r = 1; r <= arows; r += kTileRows)
+    for (int t = 0; t < L.col_tiles(); ++t)
+      tiles.push_back(Tile{0, r, 1 + t * kWarpCols, std::min(kTileRows, arows - r + 1)});
+  const int nt = (int)tiles.size();
+
+  const bool stage_u = !in_dev || !out_dev;
+  size_t bytes = 4 * qelems * (sizeof(double) + 2 * sizeof(float)) + 2 * sizeof(Desc9) + 3 * sizeof(SlotState) +
+                 sizeof(Tile) * nt + 1024;
+  if (has_f) bytes += 4 * qelems * sizeof(double);
+  if (stage_u) bytes += nnat * sizeof(double);
+  if (has_f && !f_dev) bytes += nf * sizeof(double);
+  Buffers9 B;
+  B.c = c;
+  sor_status rs = ctx_reserve(c, bytes, false, 0.0);
+  if (rs != SOR_OK) {
+    c->set_error("9-point solve does not fit the device-memory budget");
+    return rs;
+  }
+  B.reserved = bytes;
+  double* u64 = (double*)B.get(4 * qelems * sizeof(double));
+  float* dbuf = (float*)B.get(4 * qelems * sizeof(float));  // the correction, four quarters
+  float* rbuf = (float*)B.get(4 * qelems * sizeof(float));  // the rounded residual, four quarters
+  double* g64 = has_f ? (double*)B.get(4 * qelems * sizeof(double)) : nullptr;
+  Desc9* d_desc = (Desc9*)B.get(2 * sizeof(Desc9));                // [0] u, [1] d
+  SlotState* d_state = (SlotState*)B.get(3 * sizeof(SlotState));  // [0] outer, [1] inner, [2] inner at rest
+  Tile* d_tiles = (Tile*)B.get(sizeof(Tile) * nt);
+  double* d_u = stage_u ? (double*)B.get(nnat * sizeof(double)) : nullptr;
+  double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
+  if (!u64 || !dbuf || !rbuf || (has_f && !g64) || !d_desc || !d_state || !d_tiles || (stage_u && !d_u) ||
+      (has_f && !f_dev && !d_f)) {
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  cudaStream_t s = c->stream;
+
+  Desc9 du, dd;
+  std::memset(&du, 0, sizeof(du));
+  std::memset(&dd, 0, sizeof(dd));
+  for (int q = 0; q < 4; ++q) {
+    du.x[q] = u64 + q * qelems;
+    du.g[q] = has_f ? g64 + q * qelems : nullptr;
+    du.g64[q] = has_f ? g64 + q * qelems : nullptr;
+    du.rhs32[q] = rbuf + q * qelems;
+    dd.x[q] = dbuf + q * qelems;
+    dd.g[q] = rbuf + q * qelems;
+    dd.ucorr[q] = u64 + q * qelems;
+  }
+  du.n = dd.n = n;
+  du.pitch = dd.pitch = pitch;
+  du.tiles = dd.tiles = nt;
+  du.K = 1;
+  du.max_iters = 1 << 30;
+  du.stop = kStopResid;
+  du.tol = p->tol;
+  du.inner = d_state + 1;
+  dd.K = inner;
+  dd.max_iters = inner;  // one run of `inner` iterations; its change test never stops it
+  dd.stop = kStopDelta;
+  dd.tol = -1.0;
+  dd.a32 = (float)(1.0 - w);
+  dd.b32 = (float)(w / 20.0);
+  dd.a64 = 1.0 - w;
+  dd.b64 = w / 20.0;
+  dd.outer = d_state;
+  SlotState st[3];
+  std::memset(st, 0, sizeof(st));
+  for (auto& x : st) {
+    x.checked_iter = -1;
+    x.last_dmax = -1.0;
+    x.last_rho = -1.0;
+    x.best_rho = HUGE_VAL;
+  }
+  SOR9_CK(c, cudaMemsetAsync(u64, 0, 4 * qelems * sizeof(double), s));
+  if (has_f) SOR9_CK(c, cudaMemsetAsync(g64, 0, 4 * qelems * sizeof(double), s));
+  SOR9_CK(c, cudaMemsetAsync(dbuf, 0, 4 * qelems * sizeof(float), s));
+  SOR9_CK(c, cudaMemsetAsync(rbuf, 0, 4 * qelems * sizeof(float), s));
+  const Desc9 descs[2] = {du, dd};
+  SOR9_CK(c, cudaMemcpyAsync(d_desc, descs, sizeof(descs), cudaMemcpyHostToDevice, s));
+  SOR9_CK(c, cudaMemcpyAsync(d_state, st, sizeof(st), cudaMemcpyHostToDevice, s));
+  SOR9_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+  const double* u_src = u0;
+  if (!in_dev) {
+    SOR9_CK(c, cudaMemcpyAsync(d_u, u0, nnat * sizeof(double), cudaMemcpyHostToDevice, s));
+    u_src = d_u;
+  }
+  const double* f_src = f;
+  if (has_f && !f_dev) {
+    SOR9_CK(c, cudaMemcpyAsync(d_f, f, nf * sizeof(double), cudaMemcpyHostToDevice, s));
+    f_src = d_f;
+  }
+  const double h = 1.0 / (double)(n + 1);
+  const dim3 pgrid((m + kWarpCols - 1) / kWarpCols, m);
+  double* gq[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (has_f)
+    for (int q = 0; q < 4; ++q) gq[q] = g64 + q * qelems;
+  k_pack9<double><<<pgrid, kWarpCols, 0, s>>>(u_src, f_src, n, pitch, 6.0 * (h * h), u64, u64 + qelems,
+                                              u64 + 2 * qelems, u64 + 3 * qelems, gq[0], gq[1], gq[2], gq[3],
+                                              nullptr, nullptr, nullptr, nullptr, d_state);
+  SOR9_CK(c, cudaGetLastError());
+
+  const int grid = std::min(nt, c->sm_count * 8);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SOR9_CK(c, cudaEventCreate(&ev0));
+  if (cudaEventCreate(&ev1) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ev0);
+    c->set_error("event creation failed");
+    return SOR_ERR_CUDA;
+  }
+  SlotState* h_state = nullptr;  // [0], [1]: the outer state after alternate batches
+  if (cudaMallocHost(&h_state, 2 * sizeof(SlotState)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    c->set_error("pinned allocation failed");
+    return SOR_ERR_OOM;
+  }
+  cudaEvent_t pev[2] = {nullptr, nullptr};
+  struct Cleanup {
+    cudaEvent_t a, b;
+    SlotState* hs;
+    cudaGraphExec_t g;
+    cudaEvent_t* pe;
+    ~Cleanup() {
+      if (g) cudaGraphExecDestroy(g);
+      for (int k = 0; k < 2; ++k)
+        if (pe[k]) cudaEventDestroy(pe[k]);
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaFreeHost(hs);
+    }
+  } cl{ev0, ev1, h_state, nullptr, pev};
+  for (int k = 0; k < 2; ++k) SOR9_CK(c, cudaEventCreateWithFlags(&pev[k], cudaEventDisableTiming));
+
+  // one outer step: inner state back to rest, d = 0, the residual test (and
+  // right side), the inner sweeps (the last phase of each colour corrects u)
+  auto enqueue_step = [&]() -> sor_status {
+    SOR9_CK(c, cudaMemcpyAsync(d_state + 1, d_state + 2, sizeof(SlotState), cudaMemcpyDeviceToDevice, s));
+    SOR9_CK(c, cudaMemsetAsync(dbuf, 0, 4 * qelems * sizeof(float), s));
+    k_resid9<double, kResidRefine><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+    for (int it = 0; it < inner; ++it)
+      for (int col = 0; col < 4; ++col) launch_sweep9<float, true>(col, grid, s, d_desc + 1, d_state + 1, d_tiles, nt);
+    SOR9_CK(c, cudaGetLastError());
+    return SOR_OK;
+  };
+  const bool use_graphs = c->opt_graphs.load() != 0;
+  if (use_graphs && max_outer > 0) {
+    cudaGraph_t gr = nullptr;
+    SOR9_CK(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const sor_status es = enqueue_step();
+    const cudaError_t ce = cudaStreamEndCapture(s, &gr);
+    if (es != SOR_OK) {
+      if (gr) cudaGraphDestroy(gr);
+      return es;
+    }
+    SOR9_CK(c, ce);
+    const cudaError_t ie = cudaGraphInstantiate(&cl.g, gr, 0);
+    cudaGraphDestroy(gr);
+    SOR9_CK(c, ie);
+  }
+  SOR9_CK(c, cudaEventRecord(ev0, s));
+  // batches of about a millisecond of steps; the host reads the state after
+  // batch b while batch b+1 runs (steps queued past convergence only repeat
+  // the residual test)
+  const double step_s = (double)n * n * inner / 3.0e11 + 20e-6;
+  const int per_poll = (int)std::max(1.0, std::min(32.0, std::floor(1e-3 / step_s)));
+  int planned = 0, batch = 0;
+  while (planned < max_outer) {
+    const int kk = std::min(per_poll, max_outer - planned);
+    for (int j = 0; j < kk; ++j) {
+      if (use_graphs) {
+        SOR9_CK(c, cudaGraphLaunch(cl.g, s));
+      } else {
+        const sor_status es = enqueue_step();
+        if (es != SOR_OK) return es;
+      }
+    }
+    planned += kk;
+    SOR9_CK(c, cudaMemcpyAsync(h_state + (batch & 1), d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR9_CK(c, cudaEventRecord(pev[batch & 1], s));
+    if (batch > 0) {
+      SOR9_CK(c, cudaEventSynchronize(pev[(batch - 1) & 1]));
+      const SlotState& prev = h_state[(batch - 1) & 1];
+      if (prev.converged || prev.error) break;
+    }
+    ++batch;
+  }
+  // the test after the last correction (a no-op repeat once converged)
+  k_resid9<double, kResidRefine><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+  SOR9_CK(c, cudaGetLastError());
+  SOR9_CK(c, cudaEventRecord(ev1, s));
+  double* out_dst = out_dev ? u_out : d_u;
+  k_unpack9<double><<<pgrid, kWarpCols, 0, s>>>(u64, u64 + qelems, u64 + 2 * qelems, u64 + 3 * qelems, n, pitch,
+                                                out_dst);
+  SOR9_CK(c, cudaGetLastError());
+  if (!out_dev) SOR9_CK(c, cudaMemcpyAsync(u_out, d_u, nnat * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SOR9_CK(c, cudaMemcpyAsync(h_state, d_state, 2 * sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+  SOR9_CK(c, cudaStreamSynchronize(s));
+  const SlotState fin = h_state[0], fin_inner = h_state[1];
+  float ms = 0.0f;
+  SOR9_CK(c, cudaEventElapsedTime(&ms, ev0, ev1));
+  if (fin.error || fin_inner.error) {
+    c->set_error("device-side consistency check failed");
+    return SOR_ERR_INTERNAL;
+  }
+  if (res) {
+    std::memset(res, 0, sizeof(*res));
+    res->iterations = fin.outer * inner;
+    res->converged = fin.converged;
+    res->outer_steps = fin.outer;
+    res->final_maxdelta = -1.0;
+    res->final_resid_rel = fin.last_rho;
+    res->latency_s = now_s() - t0;
+    res->device_s = ms * 1e-3;
+  }
+  return SOR_OK;
+}
+
 }  // namespace
 
 sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
@@ -832,7 +1116,9 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
   }
   std::ostringstream why;
   if (p->n < 1 || p->n > kMax9N) why << "n must be in [1, " << kMax9N << "]";
-  else if (p->precision != SOR_FP64 && p->precision != SOR_FP32) why << "9-point solves run in FP64 or FP32";
+  else if (p->precision != SOR_FP64 && p->precision != SOR_FP32 && p->precision != SOR_FP32_REFINE)
+    why << "9-point solves run in FP64, FP32 or FP32_REFINE";
+  else if (p->inner_sweeps < 0) why << "inner_sweeps must be >= 0";
   else if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) why << "unknown stop rule";
   else if (p->max_iters < 0 || p->check_every < 1) why << "max_iters >= 0 and check_every >= 1 required";
   else if (p->flags & ~SOR_FLAG_EXACT_ORDER) why << "unknown flags";
@@ -843,6 +1129,7 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
     c->set_error(why.str());
     return SOR_ERR_INVALID_ARG;
   }
+  if (p->precision == SOR_FP32_REFINE) return run9_refine(c, p, u0, f, u_out, res);
   return p->precision == SOR_FP64 ? run9<double>(c, p, u0, f, u_out, res) : run9<float>(c, p, u0, f, u_out, res);
 }
 

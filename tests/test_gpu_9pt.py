@@ -156,6 +156,40 @@ def test_quartic_harmonic_and_dst(ctx):
     assert pins.rel_err(got, pins.dst_solve9(u0, f)) < 1e-10
 
 
+@pytest.mark.parametrize("n", [1, 2, 7, 37, 129, 300])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_refine9_bitwise(ctx, n, with_f):
+    """Defect correction with FP32 four-colour inner sweeps, FP64 residual
+    and correction: bit identical to the oracle, same correction count."""
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 1100 + n)
+    f = wl.gaussian_source(n, 1200 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    inner, cap = 6, 6 * 80
+    ref = oracle.refine9(u0, w, f=f, inner_sweeps=inner, tol=1e-11, max_outer=cap // inner)
+    got, res = run9(ctx, u0, f, omega=w, tol=1e-11, max_iters=cap, inner_sweeps=inner,
+                    precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
+    assert res["iterations"] == ref["sweeps"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+def test_refine9_cap_and_solution(ctx):
+    capi = capi_mod()
+    n = 90
+    u0 = wl.random_edges(n, 31)
+    f = wl.gaussian_source(n, 32)
+    w = oracle.omega_opt(n)
+    ref = oracle.refine9(u0, w, f=f, inner_sweeps=20, tol=1e-30, max_outer=4)
+    got, res = run9(ctx, u0, f, omega=w, tol=1e-30, max_iters=99, inner_sweeps=20, precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == 4 and not res["converged"] and res["iterations"] == 80
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
+    got, res = run9(ctx, u0, f, tol=1e-11, max_iters=40000, precision=capi.SOR_FP32_REFINE, device=False)
+    assert res["converged"] and res["final_resid_rel"] < 1e-11
+    assert pins.rel_err(got, pins.dst_solve9(u0, f)) < 1e-8
+
+
 def test_host_and_device_pointers_agree(ctx):
     capi = capi_mod()
     n = 45
@@ -184,8 +218,8 @@ def test_full_size_plate_bitwise(ctx):
 def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_edges(6, 1)
-    for kw in (dict(precision=capi.SOR_FP32_REFINE), dict(stall_window=2), dict(omega=2.0),
-               dict(check_every=0), dict(flags=4)):
+    for kw in (dict(precision=7), dict(stall_window=2), dict(omega=2.0), dict(check_every=0), dict(flags=4),
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
         p = capi.make_params(6, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve9_raw(p, u0.ctypes.data, None, out.ctypes.data)
