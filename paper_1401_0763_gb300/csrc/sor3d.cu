@@ -1099,7 +1099,9 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   // at every tested iteration (a multiple of K or the cap), one flow launch
   // each; on the FP64 default path chunks also stay within the scale cap and
   // take their phase constants from a device table per chunk length
-  const long long lcap = fast ? lmax : (1LL << 30);
+  // (the claim counter numbers 2 L x strips items in 32 bits: L is capped
+  // to keep that below 2^30)
+  const long long lcap = std::min<long long>(fast ? lmax : (1LL << 30), std::max(1LL, (1LL << 29) / nst));
   auto plan_chunks = [&](long long first, int Lc) {
     std::vector<int> out;
     int done_it = 0;

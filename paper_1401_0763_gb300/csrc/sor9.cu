@@ -778,7 +778,9 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
     while (done_it < Lc) {
       const long long at = first + done_it;
       const long long next_m = std::min<long long>((at / d.K + 1) * d.K, p->max_iters);
-      const int Ls = (int)std::min<long long>(next_m - at, (long long)(Lc - done_it));
+      // the claim counter numbers 4 L x strips items in 32 bits: L stays below 2^28 / strips
+      const int Ls = (int)std::min<long long>({next_m - at, (long long)(Lc - done_it),
+                                               std::max(1LL, (1LL << 28) / std::max(1, nst))});
       SOR9_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
       if (fast)
         SOR9_CK(c, (launch_9_flow<double, true>(d_desc, d_state, d_strips, nst, ct, flow_grid, 4 * Ls, d_progress,
