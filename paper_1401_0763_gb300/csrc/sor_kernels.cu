@@ -1370,7 +1370,7 @@ __device__ __forceinline__ unsigned long long resid_cells(const double (&own)[4]
     const double r = __dsub_rn(__dadd_rn(gv[v], nb), times4(own[v]));
     const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
     const bool in = (q0 + v) <= qlim;
-    if (in) rm = umax64(rm, rb & 0x7fffffffffffffffull);
+    if (in) rm = umax64(rm, abs_bits(r));
     if (ROLE == kResidRefine) rv[v] = in ? narrow_f64(__longlong_as_double((long long)rb)) : 0.0f;
   }
   if (ROLE == kResidRefine) {
@@ -1381,6 +1381,43 @@ __device__ __forceinline__ unsigned long long resid_cells(const double (&own)[4]
       for (int v = 0; v < 4; ++v)
         if ((q0 + v) <= qlim) R[v] = rv[v];
     }
+  }
+  return rm;
+}
+
+// Both colours of row i (the own colour c0 = 0 has parity S0 = i & 1, c0 = 1
+// the other), so that each colour's neighbour arrangement is fixed at
+// compile time: as a runtime branch the compiler evaluated both
+// arrangements' W + E, one more FP64 addition per cell.
+template <typename T, int ROLE, int S0>
+__device__ __forceinline__ unsigned long long resid_row(const T* X0, const T* X1, const double* G0, const double* G1,
+                                                        float* R0, float* R1, int i, int q0, int pitch, int n,
+                                                        int lane) {
+  unsigned long long rm = 0;
+#pragma unroll
+  for (int c0 = 0; c0 < 2; ++c0) {
+    const T* Xs = c0 ? X1 : X0;  // own colour
+    const T* Xo = c0 ? X0 : X1;  // other colour
+    double own[4], nm[4], nc[4], np[4], gv[4];
+    load_u4(Xs, eidx(i, q0, pitch), own);
+    load_u4(Xo, eidx(i - 1, q0, pitch), nm);
+    load_u4(Xo, eidx(i, q0, pitch), nc);
+    load_u4(Xo, eidx(i + 1, q0, pitch), np);
+    if (G0) {
+      load4((c0 ? G1 : G0) + eidx(i, q0, pitch), gv);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) gv[v] = 0.0;
+    }
+    double left = __shfl_up_sync(0xffffffffu, nc[3], 1);
+    double right = __shfl_down_sync(0xffffffffu, nc[0], 1);
+    if (lane == 0) left = as_f64(Xo[eidx(i, q0 - 1, pitch)]);
+    if (lane == 31) right = as_f64(Xo[eidx(i, q0 + kVec, pitch)]);
+    float* R = (ROLE == kResidRefine) ? (c0 ? R1 : R0) + eidx(i, q0, pitch) : nullptr;
+    if (c0 == 0)
+      rm = umax64(rm, resid_cells<ROLE, S0>(own, nm, nc, np, gv, left, right, q0, n, R));
+    else
+      rm = umax64(rm, resid_cells<ROLE, 1 - S0>(own, nm, nc, np, gv, left, right, q0, n, R));
   }
   return rm;
 }
@@ -1441,33 +1478,16 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
     const int i0 = tl.row0 + wy * rows_per_warp;
     const int i1 = min(i0 + rows_per_warp, tl.row0 + tl.nrows);
     unsigned long long rm = 0;
-    for (int i = i0; i < i1; ++i) {
-#pragma unroll
-      for (int c0 = 0; c0 < 2; ++c0) {
-        const T* Xs = c0 ? X1 : X0;  // own colour
-        const T* Xo = c0 ? X0 : X1;  // other colour
-        double own[4], nm[4], nc[4], np[4], gv[4];
-        load_u4(Xs, eidx(i, q0, pitch), own);
-        load_u4(Xo, eidx(i - 1, q0, pitch), nm);
-        load_u4(Xo, eidx(i, q0, pitch), nc);
-        load_u4(Xo, eidx(i + 1, q0, pitch), np);
-        if (G0) {
-          load4((c0 ? G1 : G0) + eidx(i, q0, pitch), gv);
-        } else {
-#pragma unroll
-          for (int v = 0; v < 4; ++v) gv[v] = 0.0;
-        }
-        double left = __shfl_up_sync(0xffffffffu, nc[3], 1);
-        double right = __shfl_down_sync(0xffffffffu, nc[0], 1);
-        if (lane == 0) left = as_f64(Xo[eidx(i, q0 - 1, pitch)]);
-        if (lane == 31) right = as_f64(Xo[eidx(i, q0 + kVec, pitch)]);
-        float* R = (ROLE == kResidRefine) ? (c0 ? R1 : R0) + eidx(i, q0, pitch) : nullptr;
-        if (((i + c0) & 1) == 0)
-          rm = umax64(rm, resid_cells<ROLE, 0>(own, nm, nc, np, gv, left, right, q0, n, R));
-        else
-          rm = umax64(rm, resid_cells<ROLE, 1>(own, nm, nc, np, gv, left, right, q0, n, R));
-      }
+    int i = i0;
+    if (i < i1 && (i & 1)) {
+      rm = umax64(rm, resid_row<T, ROLE, 1>(X0, X1, G0, G1, R0, R1, i, q0, pitch, n, lane));
+      ++i;
     }
+    for (; i + 1 < i1; i += 2) {  // an even row, then an odd one
+      rm = umax64(rm, resid_row<T, ROLE, 0>(X0, X1, G0, G1, R0, R1, i, q0, pitch, n, lane));
+      rm = umax64(rm, resid_row<T, ROLE, 1>(X0, X1, G0, G1, R0, R1, i + 1, q0, pitch, n, lane));
+    }
+    if (i < i1) rm = umax64(rm, resid_row<T, ROLE, 0>(X0, X1, G0, G1, R0, R1, i, q0, pitch, n, lane));
     block_max_to(rm, &st->rmax_bits, red);
     __threadfence();
     __syncthreads();
