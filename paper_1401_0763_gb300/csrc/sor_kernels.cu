@@ -327,10 +327,37 @@ struct FastPhase {
 };
 
 // Register state of one warp walking down a strip of rows: the neighbour-colour
-// rows i-1 and i, and the lower-right pair sums of the previous row.
+// rows i-1 and i, the lower-right pair sums of the previous row, and the
+// strip-edge pairs of the coming parity-1 rows (below).
 struct FastWalk {
   double om[4], oc[4], dlp[4];
+  double edge;  // lane r: the edge pair of the r-th parity-1 row of the current group
+  int ek;       // parity-1 rows of the group already taken
 };
+
+// In a parity-1 row, lane 0's upper-left pair N + W = O[i-1][col0] +
+// O[i][col0-1] reaches one column left of the strip, past what the previous
+// row formed.  Formed row by row it cost a whole warp instruction on the FP64
+// pipe (predicating it to one lane costs the same), 1 of 25 per row pair.  So
+// the pairs of 32 parity-1 rows i, i+2, ... are formed together, lane r taking
+// row i + 2r, and each row takes its value by a shuffle.
+__device__ __forceinline__ void fast_edges(FastWalk& w, const double* __restrict__ O, int pitch, int col0, int i,
+                                           int i1, int lane) {
+  const int r = i + 2 * lane;
+  double e = 0.0;
+  if (r < i1) e = __dadd_rn(O[eidx(r - 1, col0, pitch)], O[eidx(r, col0 - 1, pitch)]);
+  w.edge = e;
+  w.ek = 0;
+}
+// The edge pair of parity-1 row i (rows taken in order; a new group at every
+// 32nd).
+__device__ __forceinline__ double fast_edge(FastWalk& w, const double* __restrict__ O, int pitch, int q0, int i,
+                                            int i1, int lane) {
+  if (w.ek == 32) fast_edges(w, O, pitch, q0 - lane * kVec, i, i1, lane);
+  const double e = __shfl_sync(0xffffffffu, w.edge, w.ek);
+  ++w.ek;
+  return e;
+}
 
 // Rows are staged through shared memory by asynchronous copies issued
 // kFastAhead rows ahead (a per-warp pipeline), so the loads' latency leaves
@@ -428,7 +455,7 @@ template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
 __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (&oc)[4], const double (&dlp)[4],
                                            const double (&op)[4], const FastIn& in, int n, int q0, int lane,
                                            const FastPhase& ph, double (&nv)[4], double (&DL)[4],
-                                           unsigned long long& dm) {
+                                           unsigned long long& dm, double e0) {
   double left = __shfl_up_sync(0xffffffffu, oc[3], 1);
   double right = __shfl_down_sync(0xffffffffu, oc[0], 1);
   if (lane == 0) left = in.el;
@@ -452,7 +479,7 @@ __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (
     for (int v = 0; v < 4; ++v) DU[v] = dlp[v];
   } else {  // previous row had s = 0: one column to the left
     double d0 = __shfl_up_sync(0xffffffffu, dlp[3], 1);
-    if (lane == 0) d0 = __dadd_rn(om[0], left);
+    if (lane == 0) d0 = e0;  // om[0] + left, formed with the strip's other edge pairs
     DU[0] = d0; DU[1] = dlp[0]; DU[2] = dlp[1]; DU[3] = dlp[2];
   }
   const int qlim = (n + S) >> 1;
@@ -485,7 +512,8 @@ __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage
   FastIn a;
   fast_read<HAS_G>(stages + b, lane, a);
   double nv[4], DL[4];
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm);
+  const double e0 = (S == 1 && !FIRST) ? fast_edge(w, O, pitch, q0, i, i1, lane) : 0.0;
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm, e0);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   store4(X + eidx(i, q0, pitch), nv);
@@ -511,8 +539,9 @@ __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage
   fast_read<HAS_G>(stages + b, lane, a);
   fast_read<HAS_G>(stages + wrap_stage(b + 1), lane, c);
   double nva[4], DLa[4], nvc[4], DLc[4];
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm);
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm);
+  const double e0 = fast_edge(w, O, pitch, q0, S == 1 ? i : i + 1, i1, lane);  // the pair's parity-1 row
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm, e0);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm, e0);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead + 1), i + kFastAhead + 1, i + kFastAhead + 1 < i1, O, X, G,
@@ -556,6 +585,8 @@ __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages
   load4(O + eidx(i0, q0, pitch), w.oc);
 #pragma unroll
   for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
+  // the edge pairs of the first 32 parity-1 rows after the first row
+  fast_edges(w, O, pitch, q0 - lane * kVec, ((i0 + 1 + colour) & 1) ? i0 + 1 : i0 + 2, i1, lane);
   unsigned long long dm = 0;
   if (i0 < i1) {
     if (((i0 + colour) & 1) == 0)
