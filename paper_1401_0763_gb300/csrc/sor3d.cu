@@ -399,7 +399,29 @@ __device__ __forceinline__ void f3_issue(Stage3<HAS_G>* st, int k, int i, bool v
 
 struct Walk3 {
   double om[4], oc[4], dlp[4];
+  double edge;  // lane r: the strip-edge pair of the r-th parity-1 row of the current group
+  int ek;       // parity-1 rows of the group already taken
 };
+
+// Lane 0's upper-left pair in a parity-1 row, O[k][i-1][col0] +
+// O[k][i][col0-1], reaches past the strip; formed row by row it costs a whole
+// warp instruction on the FP64 pipe.  The pairs of 32 parity-1 rows i,
+// i+2, ... are formed together (lane r: row i + 2r) and taken by shuffles.
+__device__ __forceinline__ void f3_edges(Walk3& w, const double* __restrict__ O, int k, int m, int pitch, int col0,
+                                         int i, int i1, int lane) {
+  const int r = i + 2 * lane;
+  double e = 0.0;
+  if (r < i1) e = __dadd_rn(O[e3(k, r - 1, col0, m, pitch)], O[e3(k, r, col0 - 1, m, pitch)]);
+  w.edge = e;
+  w.ek = 0;
+}
+__device__ __forceinline__ double f3_edge(Walk3& w, const double* __restrict__ O, int k, int m, int pitch, int q0,
+                                          int i, int i1, int lane) {
+  if (w.ek == 32) f3_edges(w, O, k, m, pitch, q0 - lane * kVec, i, i1, lane);
+  const double e = __shfl_sync(0xffffffffu, w.edge, w.ek);
+  ++w.ek;
+  return e;
+}
 
 // One row i of plane k (parity S = (i + k + colour) & 1 fixed at compile
 // time; FIRST: no previous row, form the upper-left pairs directly).
@@ -440,7 +462,8 @@ __device__ __forceinline__ void f3_row(Walk3& w, int k, int i, int i0, int i1, S
     for (int v = 0; v < 4; ++v) DU[v] = w.dlp[v];
   } else {
     double d0 = __shfl_up_sync(0xffffffffu, w.dlp[3], 1);
-    if (lane == 0) d0 = __dadd_rn(w.om[0], left);
+    const double e0 = f3_edge(w, O, k, m, pitch, q0, i, i1, lane);  // om[0] + left, formed with the others
+    if (lane == 0) d0 = e0;
     DU[0] = d0; DU[1] = w.dlp[0]; DU[2] = w.dlp[1]; DU[3] = w.dlp[2];
   }
   const int qlim = (n + S) >> 1;
@@ -648,6 +671,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
     for (int v = 0; v < 4; ++v) w.dlp[v] = 0.0;
     unsigned long long dm = 0;
     const int s0 = (i0 + k + colour) & 1;
+    // the edge pairs of the first 32 parity-1 rows after the first row
+    f3_edges(w, O, k, m, pitch, tl.col0, s0 ? i0 + 2 : i0 + 1, i1, lane);
     const bool unit = ph.beta == 1.0;
     if (measure) {  // the last iteration of the chunk: unscaled, change measured
       if (s0 == 0) f3_rows<false, HAS_G, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
