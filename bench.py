@@ -35,7 +35,7 @@ HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once 
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fast_chain launch (50 iterations) on this workload
 # (ncu capture of the current kernel, profiles/k_fast_chain_plate4096.md)
-FAST64_DRAM_BYTES_PER_LAUNCH = 18.805e9
+FAST64_DRAM_BYTES_PER_LAUNCH = 18.6435e9
 
 
 def dist_env():
