@@ -230,6 +230,20 @@ def test_fp64_full_size_sampled(ctx):
     assert res["final_maxdelta"] == pytest.approx(ref["final_maxdelta"], rel=1e-9)
 
 
+def test_fp64_long_strips(ctx):
+    """8194^2 with a source: 32 column tiles, so the strips are about 144 rows
+    long and the strip-edge pairs are formed in several groups of 32 rows;
+    everything compared with the oracle after 20 iterations."""
+    n = 8192
+    u0 = wl.random_edges(n, 3)
+    f = wl.gaussian_source(n, 4) * 10
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=20, check_every=10, tol=-1.0)
+    got, res = run(ctx, u0, f, omega=w, tol=-1.0, max_iters=20, check_every=10)
+    assert res["iterations"] == 20
+    assert pins.rel_err(got, ref["u"]) <= TOL64
+
+
 @pytest.mark.parametrize("n,omega,K,iters,with_f", [
     (256, None, 1, 40, False),     # chunk of one iteration: every phase unscaled
     (256, None, 50, 1000, False),  # the benchmark's check interval
