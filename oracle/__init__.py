@@ -81,7 +81,8 @@ def _load():
             lib.oracle_refine.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
             lib.oracle_sor3d_f64.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _dp]
+                                             ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _dp, _dp,
+                                             _dp]
             lib.oracle_sor3d_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual3d.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -231,10 +232,11 @@ def _src3(f, n):
     return f
 
 
-def sor3d_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):
+def sor3d_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, stall_window=0,
+              trace=False):
     """Plain FP64 red-black SOR on an (n+2)^3 cube, 7-point stencil (index
-    order [k, i, j] = plane, row, column).  Returns a dict like
-    :func:`sor_f64`."""
+    order [k, i, j] = plane, row, column; stall_window as for
+    :func:`sor_f64`).  Returns a dict like :func:`sor_f64`."""
     n = int(np.asarray(u0).shape[0]) - 2
     u0 = _cube(u0, n)
     f = _src3(f, n)
@@ -243,8 +245,8 @@ def sor3d_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, sto
     md, rr = ctypes.c_double(0), ctypes.c_double(0)
     tr = np.zeros(max(max_iters, 1)) if trace else None
     rc = _load().oracle_sor3d_f64(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
-                                  int(stop_mode), _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md),
-                                  ctypes.byref(rr), _ptr(tr))
+                                  int(stop_mode), int(stall_window), _ptr(u), ctypes.byref(it), ctypes.byref(cv),
+                                  ctypes.byref(md), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_sor3d_f64: bad arguments")
     out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
@@ -315,9 +317,11 @@ def refine3d(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, m
     return out
 
 
-def sor9_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, trace=False):
+def sor9_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0, stall_window=0,
+             trace=False):
     """Four-colour SOR on the 9-point stencil, FP64 (colour 2(i&1) + (j&1),
-    colours updated 0, 1, 2, 3).  Returns a dict like :func:`sor_f64`."""
+    colours updated 0, 1, 2, 3; stall_window as for :func:`sor_f64`).
+    Returns a dict like :func:`sor_f64`."""
     n = int(np.asarray(u0).shape[0]) - 2
     u0 = _grid(u0, n)
     f = _src(f, n)
@@ -326,8 +330,8 @@ def sor9_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop
     md, rr = ctypes.c_double(0), ctypes.c_double(0)
     tr = np.zeros(max(max_iters, 1)) if trace else None
     rc = _load().oracle_sor9_f64(n, float(omega), _ptr(u0), _ptr(f), int(max_iters), int(check_every), float(tol),
-                                 int(stop_mode), _ptr(u), ctypes.byref(it), ctypes.byref(cv), ctypes.byref(md),
-                                 ctypes.byref(rr), _ptr(tr))
+                                 int(stop_mode), int(stall_window), _ptr(u), ctypes.byref(it), ctypes.byref(cv),
+                                 ctypes.byref(md), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_sor9_f64: bad arguments")
     out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,

@@ -139,16 +139,16 @@ static double rel3(double rmax, double bmax) { return bmax > 0.0 ? rmax / bmax :
  *   max_iters) receives m_k for every iteration.  Returns 0, or -1 on bad
  *   arguments / allocation failure. */
 int oracle_sor3d_f64(int n, double omega, const double *u0, const double *f, int max_iters, int check_every,
-                     double tol, int stop_mode, double *u, int *iterations, int *converged, double *final_maxdelta,
+                     double tol, int stop_mode, int stall_window, double *u, int *iterations, int *converged, double *final_maxdelta,
                      double *final_resid_rel, double *trace) {
-  if (n < 1 || max_iters < 0 || check_every < 1 || !u0 || !u) return -1;
+  if (n < 1 || max_iters < 0 || check_every < 1 || stall_window < 0 || !u0 || !u) return -1;
   const int m = n + 2;
   const size_t cells = (size_t)m * m * m;
   if (u != u0) memcpy(u, u0, sizeof(double) * cells);
   double *g = make_g3(n, f);
   if (f && !g) return -1;
-  int it = 0, conv = 0;
-  double mk = 0.0, rho = -1.0;
+  int it = 0, conv = 0, run = 0;
+  double mk = 0.0, rho = -1.0, best = HUGE_VAL;
   for (int k = 1; k <= max_iters; ++k) {
     const double dr = phase3_f64(n, u, g, omega, 0); /* red   */
     const double db = phase3_f64(n, u, g, omega, 1); /* black */
@@ -163,6 +163,12 @@ int oracle_sor3d_f64(int n, double omega, const double *u0, const double *f, int
         residual3_f64(n, u, g, NULL, &rm, &bm);
         rho = rel3(rm, bm);
         if (rho < tol) { conv = 1; break; }
+        /* the stall rule of the 2D oracle: a plateau at the attainable
+         * floor, stall_window tests without a new smallest rho within a
+         * factor 4 of it, ends the run unconverged */
+        if (rho < best) { best = rho; run = 0; }
+        else if (rho < 4.0 * best) { ++run; if (stall_window > 0 && run >= stall_window) break; }
+        else run = 0;
       }
     }
   }

@@ -231,3 +231,39 @@ def test_refinement3d_caps_and_zero_steps():
     out0 = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=0)
     assert out0["outer_steps"] == 0 and np.array_equal(out0["u"], u0)
     assert out0["final_resid_rel"] == oracle.resid_rel3d(u0, f=f)
+
+
+# --- the stall rule on cubes (as on the plate: for tolerances below the FP64 floor) --------------------------------
+
+def _stall_stop(rhos, window):
+    """The rule as defined (c17): the index of the residual test at which a run
+    of `window` tests without a new minimum, all within 4x of it, ends."""
+    best, run = np.inf, 0
+    for j, r in enumerate(rhos):
+        if r < best:
+            best, run = r, 0
+        elif r < 4.0 * best:
+            run += 1
+            if run >= window:
+                return j
+        else:
+            run = 0
+    return None
+
+
+def test_stall_rule_on_cubes_matches_its_definition():
+    """Residuals of independent runs of 5j iterations fed to the rule give
+    the test at which the oracle's run with the rule stops unconverged."""
+    n = 6
+    u0, f = _random_cube(n, 61)
+    w = oracle.omega_opt(n)
+    K, window = 5, 6
+    rhos = [oracle.resid_rel3d(oracle.sor3d_f64(u0, w, f=f, max_iters=K * (j + 1), check_every=10 ** 6,
+                                                tol=0.0)["u"], f=f) for j in range(120)]
+    j = _stall_stop(rhos, window)
+    assert j is not None
+    out = oracle.sor3d_f64(u0, w, f=f, max_iters=K * 120, check_every=K, tol=1e-30, stop_mode=1,
+                           stall_window=window)
+    assert not out["converged"] and out["iterations"] == K * (j + 1)
+    off = oracle.sor3d_f64(u0, w, f=f, max_iters=K * 120, check_every=K, tol=1e-30, stop_mode=1, stall_window=0)
+    assert off["iterations"] == K * 120

@@ -187,3 +187,32 @@ def test_refinement9_caps_and_zero_steps():
     out0 = oracle.refine9(u0, w, f=f, inner_sweeps=4, tol=1e-30, max_outer=0)
     assert out0["outer_steps"] == 0 and np.array_equal(out0["u"], u0)
     assert out0["final_resid_rel"] == oracle.resid_rel9(u0, f=f)
+
+
+# --- the stall rule with the 9-point stencil ---------------------------------------------------------------------
+
+def test_stall_rule_9pt_matches_its_definition():
+    """Residuals of independent runs of 4j iterations fed to the rule (c17)
+    give the test at which the oracle's run with the rule stops."""
+    n = 10
+    u0, f = _problem(n, 63)
+    w = oracle.omega_opt(n)
+    K, window = 4, 6
+    rhos = [oracle.resid_rel9(oracle.sor9_f64(u0, w, f=f, max_iters=K * (j + 1), check_every=10 ** 6,
+                                              tol=0.0)["u"], f=f) for j in range(150)]
+    best, run, stop = np.inf, 0, None
+    for j, r in enumerate(rhos):
+        if r < best:
+            best, run = r, 0
+        elif r < 4.0 * best:
+            run += 1
+            if run >= window:
+                stop = j
+                break
+        else:
+            run = 0
+    assert stop is not None
+    out = oracle.sor9_f64(u0, w, f=f, max_iters=K * 150, check_every=K, tol=1e-30, stop_mode=1, stall_window=window)
+    assert not out["converged"] and out["iterations"] == K * (stop + 1)
+    off = oracle.sor9_f64(u0, w, f=f, max_iters=K * 150, check_every=K, tol=1e-30, stop_mode=1, stall_window=0)
+    assert off["iterations"] == K * 150
