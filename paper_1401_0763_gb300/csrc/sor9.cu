@@ -45,6 +45,7 @@ struct Desc9 {
   float a32, b32;        // (float)(1 - w), (float)(w / 20)
   double a64, b64;       // 1 - w, w / 20
   double tol;
+  int stall;             // residual stop: stall window (0 = off), the 2D rule
   float* rhs32[4];       // defect correction, residual pass: r~ rounded to FP32, per quarter (else null)
   SlotState* inner;      // defect correction, residual pass: the inner solve's state (skipped once converged)
   double* ucorr[4];      // defect correction, inner sweeps: u, corrected by the final d (else null)
@@ -526,6 +527,14 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
           if (rho < d.tol) {
             st->done = 1;
             st->converged = 1;
+          } else if (rho < st->best_rho) {
+            st->best_rho = rho;
+            st->stall_run = 0;
+          } else if (rho < 4.0 * st->best_rho) {  // a plateau near the smallest residual so far
+            st->stall_run += 1;
+            if (d.stall > 0 && st->stall_run >= d.stall) st->done = 1;  // the floor: tol is out of reach
+          } else {
+            st->stall_run = 0;  // far above it: still the early growth, not a plateau
           }
         }
         if (ROLE == kResidRefine && rho < d.tol) {
@@ -697,6 +706,7 @@ sor_status run9(Ctx* c, const sor_params* p, const double* u0, const double* f, 
   d.a32 = (float)(1.0 - w);
   d.b32 = (float)(w / 20.0);
   d.tol = p->tol;
+  d.stall = p->stall_window;
   SlotState st;
   std::memset(&st, 0, sizeof(st));
   st.checked_iter = -1;
@@ -1124,7 +1134,9 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
   else if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) why << "unknown stop rule";
   else if (p->max_iters < 0 || p->check_every < 1) why << "max_iters >= 0 and check_every >= 1 required";
   else if (p->flags & ~SOR_FLAG_EXACT_ORDER) why << "unknown flags";
-  else if (p->stall_window != 0) why << "stall_window is not supported on the 9-point stencil";
+  else if (p->stall_window < 0) why << "stall_window must be >= 0";
+  else if (p->stall_window != 0 && p->precision == SOR_FP32_REFINE)
+    why << "stall_window is not supported with FP32_REFINE on the 9-point stencil";
   else if (std::isnan(p->tol) || std::isnan(p->omega)) why << "tol and omega must not be NaN";
   else if (p->omega > 0.0 && !(p->omega < 2.0)) why << "omega must be in (0, 2)";
   if (!why.str().empty()) {

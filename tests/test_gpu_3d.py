@@ -249,6 +249,27 @@ def test_refine3d_cap_and_solution(ctx):
     assert pins.rel_err3(got, pins.dst_solve3(u0, f)) < 1e-9
 
 
+def test_stall_window_bitwise_and_default(ctx):
+    """A tolerance below the FP64 floor with the stall rule: the exact-order
+    path stops where the oracle does (same test, same bits); the default path
+    also stops on the plateau, unconverged, long before the cap."""
+    capi = capi_mod()
+    n = 10
+    u0 = wl.random_shell(n, 91)
+    f = wl.gaussian_source3(n, 92) * 50
+    w = oracle.omega_opt(n)
+    kw = dict(omega=w, tol=1e-30, max_iters=3000, check_every=5, stall_window=6)
+    ref = oracle.sor3d_f64(u0, w, f=f, stop_mode=1, **{k: v for k, v in kw.items() if k != "omega"})
+    assert not ref["converged"] and ref["iterations"] < 3000
+    got, res = run3(ctx, u0, f, precision=capi.SOR_FP64, stop=capi.SOR_STOP_RESID_REL,
+                    flags=capi.SOR_FLAG_EXACT_ORDER, **kw)
+    assert res["iterations"] == ref["iterations"] and not res["converged"]
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
+    got, res = run3(ctx, u0, f, precision=capi.SOR_FP64, stop=capi.SOR_STOP_RESID_REL, **kw)
+    assert not res["converged"] and res["iterations"] < 3000
+    assert res["final_resid_rel"] < 100 * ref["final_resid_rel"]
+
+
 def test_bounded_wait_gives_up_and_context_survives(ctx):
     """The failure path of the data-flow kernels without a fault: their
     bounded device-side wait, run on a progress counter nothing advances,
@@ -274,8 +295,9 @@ def test_bounded_wait_gives_up_and_context_survives(ctx):
 def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_shell(4, 1)
-    for kw in (dict(precision=7), dict(stall_window=3), dict(omega=2.5), dict(check_every=0), dict(flags=8),
-               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
+    for kw in (dict(precision=7), dict(stall_window=-1), dict(omega=2.5), dict(check_every=0), dict(flags=8),
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1),
+               dict(precision=capi.SOR_FP32_REFINE, stall_window=3)):
         p = capi.make_params(4, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, out.ctypes.data)

@@ -190,6 +190,26 @@ def test_refine9_cap_and_solution(ctx):
     assert pins.rel_err(got, pins.dst_solve9(u0, f)) < 1e-8
 
 
+def test_stall_window_bitwise_and_default(ctx):
+    """A tolerance below the FP64 floor with the stall rule: the exact-order
+    path stops where the oracle does; the default path stops on the plateau,
+    unconverged, long before the cap."""
+    capi = capi_mod()
+    n = 24
+    u0 = wl.random_edges(n, 93)
+    f = wl.gaussian_source(n, 94) * 50
+    w = oracle.omega_opt(n)
+    kw = dict(omega=w, tol=1e-30, max_iters=4000, check_every=4, stall_window=6)
+    ref = oracle.sor9_f64(u0, w, f=f, stop_mode=1, **{k: v for k, v in kw.items() if k != "omega"})
+    assert not ref["converged"] and ref["iterations"] < 4000
+    got, res = run9(ctx, u0, f, precision=capi.SOR_FP64, stop=capi.SOR_STOP_RESID_REL, flags=EXACT, **kw)
+    assert res["iterations"] == ref["iterations"] and not res["converged"]
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
+    got, res = run9(ctx, u0, f, precision=capi.SOR_FP64, stop=capi.SOR_STOP_RESID_REL, **kw)
+    assert not res["converged"] and res["iterations"] < 4000
+    assert res["final_resid_rel"] < 100 * ref["final_resid_rel"]
+
+
 def test_host_and_device_pointers_agree(ctx):
     capi = capi_mod()
     n = 45
@@ -218,8 +238,9 @@ def test_full_size_plate_bitwise(ctx):
 def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_edges(6, 1)
-    for kw in (dict(precision=7), dict(stall_window=2), dict(omega=2.0), dict(check_every=0), dict(flags=4),
-               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
+    for kw in (dict(precision=7), dict(stall_window=-2), dict(omega=2.0), dict(check_every=0), dict(flags=4),
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1),
+               dict(precision=capi.SOR_FP32_REFINE, stall_window=2)):
         p = capi.make_params(6, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve9_raw(p, u0.ctypes.data, None, out.ctypes.data)
