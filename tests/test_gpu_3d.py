@@ -97,6 +97,23 @@ def test_two_column_tiles_ragged(ctx):
     assert pins.rel_err3(got, ref["u"]) <= TOL64
 
 
+def test_three_column_tiles_large_cube(ctx):
+    """n = 513: 257 packed columns per row (three column tiles, the last one
+    ragged), 16 row bands per plane; exact order bitwise and the
+    default path within 1e-12 after 4 iterations (change measured at 2, 4)."""
+    capi = capi_mod()
+    n = 513
+    u0 = wl.random_shell(n, 17)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f64(u0, w, max_iters=4, check_every=2, tol=0.0)
+    got, res = run3(ctx, u0, omega=w, max_iters=4, check_every=2, tol=0.0, precision=capi.SOR_FP64,
+                    flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert res["iterations"] == 4 and np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+    got, res = run3(ctx, u0, omega=w, max_iters=4, check_every=2, tol=0.0, precision=capi.SOR_FP64)
+    assert res["iterations"] == 4 and pins.rel_err3(got, ref["u"]) <= TOL64
+
+
 def test_residual_stop_matches(ctx):
     capi = capi_mod()
     n = 24
