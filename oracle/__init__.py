@@ -87,7 +87,8 @@ def _load():
                                              ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual3d.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
             lib.oracle_refine3d.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
-                                            ctypes.c_double, ctypes.c_int, _dp, _ip, _ip, _ip, _dp, _dp]
+                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _ip, _dp,
+                                            _dp]
             lib.oracle_sor9_f64.argtypes = lib.oracle_sor3d_f64.argtypes
             lib.oracle_sor9_f32.argtypes = lib.oracle_sor3d_f32.argtypes
             lib.oracle_residual9.argtypes = lib.oracle_residual3d.argtypes
@@ -296,7 +297,8 @@ def resid_rel3d(u, *, f=None):
     return rm / bm if bm > 0 else rm
 
 
-def refine3d(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, trace=False):
+def refine3d(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, stall_window=0,
+             trace=False):
     """FP64 defect correction on a cube around FP32 (or FP64) inner red-black
     SOR sweeps (7-point stencil).  Returns a dict like :func:`refine`."""
     n = int(np.asarray(u0).shape[0]) - 2
@@ -307,8 +309,8 @@ def refine3d(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, m
     rr = ctypes.c_double(0)
     tr = np.zeros(max_outer + 1) if trace else None
     rc = _load().oracle_refine3d(n, float(omega), _ptr(u0), _ptr(f), int(inner_sweeps), int(bool(inner_f32)),
-                                 float(tol), int(max_outer), _ptr(u), ctypes.byref(ou), ctypes.byref(sw),
-                                 ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
+                                 float(tol), int(max_outer), int(stall_window), _ptr(u), ctypes.byref(ou),
+                                 ctypes.byref(sw), ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_refine3d: bad arguments")
     out = dict(u=u, outer_steps=ou.value, sweeps=sw.value, converged=bool(cv.value), final_resid_rel=rr.value)
@@ -379,7 +381,8 @@ def resid_rel9(u, *, f=None):
     return rm / bm if bm > 0 else rm
 
 
-def refine9(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, trace=False):
+def refine9(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, max_outer=10000, stall_window=0,
+             trace=False):
     """FP64 defect correction around FP32 (or FP64) inner four-colour 9-point
     SOR sweeps.  Returns a dict like :func:`refine`."""
     n = int(np.asarray(u0).shape[0]) - 2
@@ -390,8 +393,8 @@ def refine9(u0, omega, *, f=None, inner_sweeps=20, inner_f32=True, tol=1e-10, ma
     rr = ctypes.c_double(0)
     tr = np.zeros(max_outer + 1) if trace else None
     rc = _load().oracle_refine9(n, float(omega), _ptr(u0), _ptr(f), int(inner_sweeps), int(bool(inner_f32)),
-                                float(tol), int(max_outer), _ptr(u), ctypes.byref(ou), ctypes.byref(sw),
-                                ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
+                                float(tol), int(max_outer), int(stall_window), _ptr(u), ctypes.byref(ou),
+                                ctypes.byref(sw), ctypes.byref(cv), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_refine9: bad arguments")
     out = dict(u=u, outer_steps=ou.value, sweeps=sw.value, converged=bool(cv.value), final_resid_rel=rr.value)

@@ -259,9 +259,9 @@ int oracle_residual9(int n, const double *u, const double *f, double *r, double 
  * u.  Outputs: outer steps done, total inner sweeps, final rho; trace
  * (optional, length max_outer+1) receives rho per residual evaluation. */
 int oracle_refine9(int n, double omega, const double *u0, const double *f, int inner_sweeps, int inner_f32,
-                   double tol, int max_outer, double *u, int *outer_steps, int *sweeps, int *converged,
+                   double tol, int max_outer, int stall_window, double *u, int *outer_steps, int *sweeps, int *converged,
                    double *final_resid_rel, double *trace) {
-  if (n < 1 || inner_sweeps < 1 || max_outer < 0 || !u0 || !u) return -1;
+  if (n < 1 || inner_sweeps < 1 || max_outer < 0 || stall_window < 0 || !u0 || !u) return -1;
   const int m = n + 2;
   const size_t cells = (size_t)m * m;
   if (u != u0) memcpy(u, u0, sizeof(double) * cells);
@@ -275,8 +275,8 @@ int oracle_refine9(int n, double omega, const double *u0, const double *f, int i
     return -1;
   }
   const float a32 = (float)(1.0 - omega), b32 = (float)(omega / 20.0);
-  int outer = 0, conv = 0;
-  double rho = 0.0;
+  int outer = 0, conv = 0, run = 0;
+  double rho = 0.0, best = HUGE_VAL;
   for (;;) {
     double rm, bm;
     residual9_f64(n, u, g, r, &rm, &bm);
@@ -284,6 +284,10 @@ int oracle_refine9(int n, double omega, const double *u0, const double *f, int i
     if (trace) trace[outer] = rho;
     if (rho < tol) { conv = 1; break; }
     if (outer == max_outer) break;
+    /* the stall rule, as in the plain solve */
+    if (rho < best) { best = rho; run = 0; }
+    else if (rho < 4.0 * best) { ++run; if (stall_window > 0 && run >= stall_window) break; }
+    else run = 0;
     if (inner_f32) {
       for (size_t c = 0; c < cells; ++c) { d32[c] = 0.0f; r32[c] = (float)r[c]; }
       for (int s = 0; s < inner_sweeps; ++s)

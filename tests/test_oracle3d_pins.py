@@ -267,3 +267,18 @@ def test_stall_rule_on_cubes_matches_its_definition():
     assert not out["converged"] and out["iterations"] == K * (j + 1)
     off = oracle.sor3d_f64(u0, w, f=f, max_iters=K * 120, check_every=K, tol=1e-30, stop_mode=1, stall_window=0)
     assert off["iterations"] == K * 120
+
+
+def test_refinement3d_stall_rule_matches_its_definition():
+    """The defect correction's residual trace without the rule, fed to the
+    rule as defined, gives the correction count at which the run with the
+    rule stops unconverged."""
+    n = 6
+    u0, f = _random_cube(n, 67)
+    w = oracle.omega_opt(n)
+    full = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=200, trace=True)
+    j = _stall_stop(full["trace"][:200], 5)
+    assert j is not None
+    out = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=200, stall_window=5)
+    assert not out["converged"] and out["outer_steps"] == j
+    assert oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=200)["outer_steps"] == 200

@@ -216,3 +216,25 @@ def test_stall_rule_9pt_matches_its_definition():
     assert not out["converged"] and out["iterations"] == K * (stop + 1)
     off = oracle.sor9_f64(u0, w, f=f, max_iters=K * 150, check_every=K, tol=1e-30, stop_mode=1, stall_window=0)
     assert off["iterations"] == K * 150
+
+
+def test_refinement9_stall_rule_matches_its_definition():
+    n = 10
+    u0, f = _problem(n, 69)
+    w = oracle.omega_opt(n)
+    full = oracle.refine9(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=300, trace=True)
+    best, run, stop = np.inf, 0, None
+    for j, r in enumerate(full["trace"][:300]):
+        if r < best:
+            best, run = r, 0
+        elif r < 4.0 * best:
+            run += 1
+            if run >= 5:
+                stop = j
+                break
+        else:
+            run = 0
+    assert stop is not None
+    out = oracle.refine9(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=300, stall_window=5)
+    assert not out["converged"] and out["outer_steps"] == stop
+    assert oracle.refine9(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=300)["outer_steps"] == 300
