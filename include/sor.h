@@ -152,8 +152,8 @@ sor_status sor_solve(sor_ctx *ctx, const sor_params *params, const double *u0, c
  *           2 / (1 + sin(pi / (N+1))); stop, tol, max_iters, check_every as
  *           for sor_solve; precision SOR_FP64, SOR_FP32 or SOR_FP32_REFINE
  *           (inner_sweeps >= 0, 0 = 20); flags 0 or SOR_FLAG_EXACT_ORDER;
- *           stall_window >= 0 as for sor_solve (0 with SOR_FP32_REFINE).
- *           Anything else returns SOR_ERR_INVALID_ARG.
+ *           stall_window >= 0 as for sor_solve.  Anything else returns
+ *           SOR_ERR_INVALID_ARG.
  *   u0:    (N+2)^3 array indexed [k][i][j] (plane, row, column), its outer
  *          shell the Dirichlet data.  Host or device memory.
  *   f:     N^3 interior source of -Laplace(u) = f ([k][i][j]), or NULL.
@@ -183,8 +183,8 @@ sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0,
  * oracle's bit for bit).
  *   params: as for sor_solve with precision SOR_FP64, SOR_FP32 or
  *           SOR_FP32_REFINE (inner_sweeps >= 0, 0 = 20), flags 0 or
- *           SOR_FLAG_EXACT_ORDER, stall_window >= 0 as for sor_solve (0 with
- *           SOR_FP32_REFINE; else SOR_ERR_INVALID_ARG);
+ *           SOR_FLAG_EXACT_ORDER, stall_window >= 0 as for sor_solve (else
+ *           SOR_ERR_INVALID_ARG);
  *           omega <= 0 selects 2 / (1 + sin(pi / (N+1))).
  *   u0, f, u_out: as for sor_solve ((N+2)^2, N^2, (N+2)^2; host or device);
  *          the 9-point stencil also reads the ring's corners.

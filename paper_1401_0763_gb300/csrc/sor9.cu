@@ -537,10 +537,23 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
             st->stall_run = 0;  // far above it: still the early growth, not a plateau
           }
         }
-        if (ROLE == kResidRefine && rho < d.tol) {
-          st->done = 1;
-          st->converged = 1;
-          d.inner->done = 1;  // the inner sweeps of this step are skipped
+        if (ROLE == kResidRefine) {
+          if (rho < d.tol) {
+            st->done = 1;
+            st->converged = 1;
+            d.inner->done = 1;  // the inner sweeps of this step are skipped
+          } else if (rho < st->best_rho) {
+            st->best_rho = rho;
+            st->stall_run = 0;
+          } else if (rho < 4.0 * st->best_rho) {  // the stall rule, as in the plain solve
+            st->stall_run += 1;
+            if (d.stall > 0 && st->stall_run >= d.stall) {
+              st->done = 1;
+              d.inner->done = 1;
+            }
+          } else {
+            st->stall_run = 0;
+          }
         }
       }
     }
@@ -953,6 +966,7 @@ sor_status run9_refine(Ctx* c, const sor_params* p, const double* u0, const doub
   du.max_iters = 1 << 30;
   du.stop = kStopResid;
   du.tol = p->tol;
+  du.stall = p->stall_window;
   du.inner = d_state + 1;
   dd.K = inner;
   dd.max_iters = inner;  // one run of `inner` iterations; its change test never stops it
@@ -1082,7 +1096,7 @@ sor_status run9_refine(Ctx* c, const sor_params* p, const double* u0, const doub
     if (batch > 0) {
       SOR9_CK(c, cudaEventSynchronize(pev[(batch - 1) & 1]));
       const SlotState& prev = h_state[(batch - 1) & 1];
-      if (prev.converged || prev.error) break;
+      if (prev.done || prev.error) break;  // converged, or stalled at the floor
     }
     ++batch;
   }
@@ -1135,8 +1149,6 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
   else if (p->max_iters < 0 || p->check_every < 1) why << "max_iters >= 0 and check_every >= 1 required";
   else if (p->flags & ~SOR_FLAG_EXACT_ORDER) why << "unknown flags";
   else if (p->stall_window < 0) why << "stall_window must be >= 0";
-  else if (p->stall_window != 0 && p->precision == SOR_FP32_REFINE)
-    why << "stall_window is not supported with FP32_REFINE on the 9-point stencil";
   else if (std::isnan(p->tol) || std::isnan(p->omega)) why << "tol and omega must not be NaN";
   else if (p->omega > 0.0 && !(p->omega < 2.0)) why << "omega must be in (0, 2)";
   if (!why.str().empty()) {

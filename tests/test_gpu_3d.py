@@ -313,8 +313,7 @@ def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_shell(4, 1)
     for kw in (dict(precision=7), dict(stall_window=-1), dict(omega=2.5), dict(check_every=0), dict(flags=8),
-               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1),
-               dict(precision=capi.SOR_FP32_REFINE, stall_window=3)):
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
         p = capi.make_params(4, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, out.ctypes.data)
@@ -322,3 +321,19 @@ def test_invalid_arguments(ctx):
     p = capi.make_params(0)
     st, _ = ctx.solve3d_raw(p, u0.ctypes.data, None, u0.ctypes.data)
     assert st == capi.SOR_ERR_INVALID_ARG
+
+
+def test_refine3d_stall_window_bitwise(ctx):
+    """The defect correction with the stall rule below the FP64 floor: the
+    same correction count and bits as the oracle, unconverged."""
+    capi = capi_mod()
+    n = 8
+    u0 = wl.random_shell(n, 71)
+    f = wl.gaussian_source3(n, 72) * 50
+    w = oracle.omega_opt(n)
+    ref = oracle.refine3d(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=400, stall_window=5)
+    assert not ref["converged"] and ref["outer_steps"] < 400
+    got, res = run3(ctx, u0, f, omega=w, tol=1e-30, max_iters=1200, inner_sweeps=3, stall_window=5,
+                    precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == ref["outer_steps"] and not res["converged"]
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]

@@ -239,9 +239,24 @@ def test_invalid_arguments(ctx):
     capi = capi_mod()
     u0 = wl.random_edges(6, 1)
     for kw in (dict(precision=7), dict(stall_window=-2), dict(omega=2.0), dict(check_every=0), dict(flags=4),
-               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1),
-               dict(precision=capi.SOR_FP32_REFINE, stall_window=2)):
+               dict(precision=capi.SOR_FP32_REFINE, inner_sweeps=-1)):
         p = capi.make_params(6, **kw)
         out = np.empty_like(u0)
         st, _ = ctx.solve9_raw(p, u0.ctypes.data, None, out.ctypes.data)
         assert st == capi.SOR_ERR_INVALID_ARG, kw
+
+
+def test_refine9_stall_window_bitwise(ctx):
+    """The defect correction with the stall rule below the FP64 floor: the
+    same correction count and bits as the oracle, unconverged."""
+    capi = capi_mod()
+    n = 20
+    u0 = wl.random_edges(n, 73)
+    f = wl.gaussian_source(n, 74) * 50
+    w = oracle.omega_opt(n)
+    ref = oracle.refine9(u0, w, f=f, inner_sweeps=3, tol=1e-30, max_outer=400, stall_window=5)
+    assert not ref["converged"] and ref["outer_steps"] < 400
+    got, res = run9(ctx, u0, f, omega=w, tol=1e-30, max_iters=1200, inner_sweeps=3, stall_window=5,
+                    precision=capi.SOR_FP32_REFINE)
+    assert res["outer_steps"] == ref["outer_steps"] and not res["converged"]
+    assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
