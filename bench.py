@@ -306,7 +306,7 @@ def run_ours(args, ws, rank, local):
 
 
 # ---------------------------------------------------------------------------------------------------------------
-# other workloads (one JSON line each; not the driver's default line)
+# other workloads (one JSON line each, selected with --workload; the default line is above)
 # ---------------------------------------------------------------------------------------------------------------
 
 def _pct(xs, q):
