@@ -320,7 +320,7 @@ sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s) {
 static constexpr int kInflight = 3;
 
 // Iterations fused per tile pass for the FP32 sweeps: the SOR_OPT_TEMPORAL_DEPTH
-// option, 0 = the default depth 4; depths the kernel is not built for round
+// option, 0 = the default depth 6; depths the kernel is not built for round
 // down to the next built one.
 int resolve_tdepth(Ctx* c, const Plan& p) {
   if (p.kind == kPlain64) return 1;
