@@ -451,7 +451,7 @@ __device__ __forceinline__ void fast_read(const FastStage<HAS_G>* st, int lane, 
 // FIRST: no previous row, form the upper-left pairs directly.  Ring values
 // arrive already at the phase's scale.  Pure register work: the caller loads
 // and stores, so two rows can be scheduled together.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST, bool FULL>
 __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (&oc)[4], const double (&dlp)[4],
                                            const double (&op)[4], const FastIn& in, int n, int q0, int lane,
                                            const FastPhase& ph, double (&nv)[4], double (&DL)[4],
@@ -492,7 +492,7 @@ __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (
     else
       t2 = HAS_G ? __fma_rn(ph.gamma, in.g[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
     const double nu = __fma_rn(ph.alpha, in.own[v], t2);
-    const bool inside = (q0 + v) <= qlim;
+    const bool inside = FULL || (q0 + v) <= qlim;
     // cells past the interior (the ring cell, padding) keep their value; the
     // whole vector is written back, so no other lane's or warp's cell is touched
     nv[v] = inside ? nu : in.own[v];
@@ -503,7 +503,7 @@ __device__ __forceinline__ void fast_cells(const double (&om)[4], const double (
 __device__ __forceinline__ int wrap_stage(int b) { return b >= kFastStages ? b - kFastStages : b; }
 
 // One row i in buffer b.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL, int S, bool FIRST>
 __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
                                            const double* __restrict__ O, double* __restrict__ X,
                                            const double* __restrict__ G, int pitch, int n, int q0, int lane,
@@ -513,7 +513,7 @@ __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage
   fast_read<HAS_G>(stages + b, lane, a);
   double nv[4], DL[4];
   const double e0 = (S == 1 && !FIRST) ? fast_edge(w, O, pitch, q0, i, i1, lane) : 0.0;
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, FIRST>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm, e0);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, FIRST, FULL>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nv, DL, dm, e0);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   store4(X + eidx(i, q0, pitch), nv);
@@ -529,7 +529,7 @@ __device__ __forceinline__ void fast_step1(FastWalk& w, int i, int& b, FastStage
 // Rows i (parity S) and i + 1 (parity 1 - S); both rows' arithmetic is
 // independent enough to be interleaved, which doubles the FP64 work in flight
 // per warp.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL, int S>
 __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage<HAS_G>* stages, int i1,
                                            const double* __restrict__ O, double* __restrict__ X,
                                            const double* __restrict__ G, int pitch, int n, int q0, int lane,
@@ -540,8 +540,10 @@ __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage
   fast_read<HAS_G>(stages + wrap_stage(b + 1), lane, c);
   double nva[4], DLa[4], nvc[4], DLc[4];
   const double e0 = fast_edge(w, O, pitch, q0, S == 1 ? i : i + 1, i1, lane);  // the pair's parity-1 row
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, false>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm, e0);
-  fast_cells<UNIT_BETA, HAS_G, MEASURE, 1 - S, false>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm, e0);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, S, false, FULL>(w.om, w.oc, w.dlp, a.op, a, n, q0, lane, ph, nva, DLa, dm,
+                                                        e0);
+  fast_cells<UNIT_BETA, HAS_G, MEASURE, 1 - S, false, FULL>(w.oc, a.op, DLa, c.op, c, n, q0, lane, ph, nvc, DLc, dm,
+                                                            e0);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead), i + kFastAhead, i + kFastAhead < i1, O, X, G, pitch, q0,
                     lane);
   fast_issue<HAS_G>(stages + wrap_stage(b + kFastAhead + 1), i + kFastAhead + 1, i + kFastAhead + 1 < i1, O, X, G,
@@ -559,21 +561,22 @@ __device__ __forceinline__ void fast_step2(FastWalk& w, int i, int& b, FastStage
 
 // Rows [i0, i1) of one strip: the first row, then pairs (whose first row has
 // the parity of i0 + 1, fixed at compile time) and an odd row left over.
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S0>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL, int S0>
 __device__ __forceinline__ void fast_rows(FastWalk& w, FastStage<HAS_G>* stages, const double* __restrict__ O,
                                           double* __restrict__ X, const double* __restrict__ G, int pitch, int n,
                                           int q0, int i0, int i1, int lane, const FastPhase& ph,
                                           unsigned long long& dm) {
   int i = i0, b = 0;
-  fast_step1<UNIT_BETA, HAS_G, MEASURE, S0, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
+  fast_step1<UNIT_BETA, HAS_G, MEASURE, FULL, S0, true>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
   ++i;
   for (; i + 1 < i1; i += 2)
-    fast_step2<UNIT_BETA, HAS_G, MEASURE, 1 - S0>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
-  if (i < i1) fast_step1<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane,
-                                                                  ph, dm);
+    fast_step2<UNIT_BETA, HAS_G, MEASURE, FULL, 1 - S0>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph, dm);
+  if (i < i1)
+    fast_step1<UNIT_BETA, HAS_G, MEASURE, FULL, 1 - S0, false>(w, i, b, stages, i1, O, X, G, pitch, n, q0, lane, ph,
+                                                               dm);
 }
 
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL = false>
 __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages, const double* __restrict__ O,
                                                         double* __restrict__ X, const double* __restrict__ G,
                                                         int pitch, int n, int colour, int q0, int i0, int i1,
@@ -590,9 +593,9 @@ __device__ __forceinline__ unsigned long long fast_walk(FastStage<HAS_G>* stages
   unsigned long long dm = 0;
   if (i0 < i1) {
     if (((i0 + colour) & 1) == 0)
-      fast_rows<UNIT_BETA, HAS_G, MEASURE, 0>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
+      fast_rows<UNIT_BETA, HAS_G, MEASURE, FULL, 0>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
     else
-      fast_rows<UNIT_BETA, HAS_G, MEASURE, 1>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
+      fast_rows<UNIT_BETA, HAS_G, MEASURE, FULL, 1>(w, stages, O, X, G, pitch, n, q0, i0, i1, lane, ph, dm);
   }
   cp_async_wait<0>();  // no copy may still target the stages when the warp moves on
   return dm;
@@ -777,6 +780,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_fast_chain(const SlotDesc* __re
   const int pitch = sd.pitch, n = sd.n;
   const int q0 = tl.col0 + lane * kVec;
   const int i0 = tl.row0, i1 = tl.row0 + tl.nrows;
+  // every packed column of the strip is interior in rows of both parities:
+  // no cell needs the interior mask
+  const bool full = tl.col0 + kWarpCols - 1 <= (n >> 1);
   int measure_last = 0;
   for (int p = 0; p < nphases; ++p) {
     const int colour = p & 1;
@@ -808,6 +814,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_fast_chain(const SlotDesc* __re
       dm = warp_max64(dm);
       if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
       measure_last = 1;
+    } else if (unit && full) {
+      (void)fast_walk<true, HAS_G, false, true>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
     } else if (unit) {
       (void)fast_walk<true, HAS_G, false>(stages, O, X, G, pitch, n, colour, q0, i0, i1, lane, ph);
     } else {
