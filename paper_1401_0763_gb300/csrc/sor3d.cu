@@ -446,8 +446,9 @@ __device__ __forceinline__ double f3_edge(Walk3& w, const double* __restrict__ O
 }
 
 // One row i of plane k (parity S = (i + k + colour) & 1 fixed at compile
-// time; FIRST: no previous row, form the upper-left pairs directly).
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S, bool FIRST>
+// time; FIRST: no previous row, form the upper-left pairs directly; FULL:
+// every cell of the strip is interior, no mask).
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL, int S, bool FIRST>
 __device__ __forceinline__ void f3_row(Walk3& w, int k, int i, int i0, int i1, Stage3<HAS_G>* stages,
                                        const double* O, double* X, const double* G, int n, int m, int pitch, int q0,
                                        int lane, const Phase3& ph, unsigned long long& dm) {
@@ -499,7 +500,7 @@ __device__ __forceinline__ void f3_row(Walk3& w, int k, int i, int i0, int i1, S
     else
       t2 = HAS_G ? __fma_rn(ph.gamma, gv[v], __dmul_rn(ph.beta, sum)) : __dmul_rn(ph.beta, sum);
     const double nu = __fma_rn(ph.alpha, own[v], t2);
-    const bool inside = (q0 + v) <= qlim;
+    const bool inside = FULL || (q0 + v) <= qlim;
     nv[v] = inside ? nu : own[v];  // cells past the interior keep their value
     if (MEASURE && inside) dm = umax64(dm, abs_bits(__fma_rn(-ph.dscale, own[v], nu)));
   }
@@ -512,19 +513,23 @@ __device__ __forceinline__ void f3_row(Walk3& w, int k, int i, int i0, int i1, S
   }
 }
 
-template <bool UNIT_BETA, bool HAS_G, bool MEASURE, int S0>
+template <bool UNIT_BETA, bool HAS_G, bool MEASURE, bool FULL, int S0>
 __device__ __forceinline__ void f3_rows(Walk3& w, int k, int i0, int i1, Stage3<HAS_G>* stages, const double* O,
                                         double* X, const double* G, int n, int m, int pitch, int q0, int lane,
                                         const Phase3& ph, unsigned long long& dm) {
   int i = i0;
-  f3_row<UNIT_BETA, HAS_G, MEASURE, S0, true>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+  f3_row<UNIT_BETA, HAS_G, MEASURE, FULL, S0, true>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph,
+                                                    dm);
   ++i;
   for (; i + 1 < i1; i += 2) {
-    f3_row<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-    f3_row<UNIT_BETA, HAS_G, MEASURE, S0, false>(w, k, i + 1, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    f3_row<UNIT_BETA, HAS_G, MEASURE, FULL, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane,
+                                                           ph, dm);
+    f3_row<UNIT_BETA, HAS_G, MEASURE, FULL, S0, false>(w, k, i + 1, i0, i1, stages, O, X, G, n, m, pitch, q0, lane,
+                                                       ph, dm);
   }
   if (i < i1)
-    f3_row<UNIT_BETA, HAS_G, MEASURE, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    f3_row<UNIT_BETA, HAS_G, MEASURE, FULL, 1 - S0, false>(w, k, i, i0, i1, stages, O, X, G, n, m, pitch, q0, lane,
+                                                           ph, dm);
 }
 
 // Saved unscaled shell of one colour array: planes 0 and N+1 (m rows of pitch
@@ -697,14 +702,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
     f3_edges(w, O, k, m, pitch, tl.col0, s0 ? i0 + 2 : i0 + 1, i1, lane);
     const bool unit = ph.beta == 1.0;
     if (measure) {  // the last iteration of the chunk: unscaled, change measured
-      if (s0 == 0) f3_rows<false, HAS_G, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-      else f3_rows<false, HAS_G, true, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      if (s0 == 0) f3_rows<false, HAS_G, true, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<false, HAS_G, true, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+    } else if (unit && tl.col0 + kWarpCols - 1 <= (n >> 1)) {  // every column of the strip interior in both parities
+      if (s0 == 0) f3_rows<true, HAS_G, false, true, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<true, HAS_G, false, true, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
     } else if (unit) {
-      if (s0 == 0) f3_rows<true, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-      else f3_rows<true, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      if (s0 == 0) f3_rows<true, HAS_G, false, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<true, HAS_G, false, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
     } else {
-      if (s0 == 0) f3_rows<false, HAS_G, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
-      else f3_rows<false, HAS_G, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      if (s0 == 0) f3_rows<false, HAS_G, false, false, 0>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
+      else f3_rows<false, HAS_G, false, false, 1>(w, k, i0, i1, stages, O, X, G, n, m, pitch, q0, lane, ph, dm);
     }
     c3_wait<0>();
     f3_shell(d, colour ? shell1 : shell0, X, colour, k, i0, i1, tl.col0, q0, lane, ph.nscale);
