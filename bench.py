@@ -34,8 +34,9 @@ FP64_FLOPS_PER_LUP = 6.0    # (1-w)u + (w/4)(N+S+W+E): 3 adds, 2 multiplies, 1 a
 HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once per iteration
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_fast_chain launch (50 iterations) on this workload
-# (ncu capture of the current kernel, profiles/k_fast_chain_plate4096.md)
-FAST64_DRAM_BYTES_PER_LAUNCH = 18.6435e9
+# (profiles/k_fast_chain_plate4096.md).  Taken before strips with only interior columns stopped masking
+# their cells, a change to no load or store; reported as the last capture, `traffic` null until re-taken.
+FAST64_DRAM_BYTES_PER_LAUNCH_LAST = 18.6435e9
 
 
 def dist_env():
@@ -280,10 +281,12 @@ def run_ours(args, ws, rank, local):
                        "l2": "inputs larger than L2 (134 MB natural in + 136 MB colour-split state + 134 MB out; "
                              "no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": FAST64_DRAM_BYTES_PER_LAUNCH,
+                         "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": None,
+                         "traffic_last_capture": FAST64_DRAM_BYTES_PER_LAUNCH_LAST,
                          "traffic_unit": "bytes per launch of 50 iterations (dram read + write)",
                          "traffic_source": "ncu capture of k_fast_chain on this workload "
-                                           "(profiles/k_fast_chain_plate4096.md)",
+                                           "(profiles/k_fast_chain_plate4096.md), taken before the interior-mask "
+                                           "skip of all-interior strips (no load or store changed)",
                          "traffic_algorithmic": 16.0 * N * N * CHECK,
                          "kernel": "k_fast_chain<false> (a chunk of 50 iterations per launch; "
                                    "achieved from the per-phase CUDA-event time)",
