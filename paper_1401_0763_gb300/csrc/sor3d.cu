@@ -65,7 +65,7 @@ __global__ void k_pack3d(const double* __restrict__ u0, const double* __restrict
   const int qw = (n + 1) / 2 + 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y, k = blockIdx.z;
-  unsigned long long bb = 0;
+  unsigned long long bb = 0, ub = 0, gb = 0;
   if (q < qw) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -75,9 +75,11 @@ __global__ void k_pack3d(const double* __restrict__ u0, const double* __restrict
       const size_t nat = ((size_t)k * m + i) * m + j;
       const size_t e = e3(k, i, q, m, pitch);
       (c ? x1 : x0)[e] = (T)u0[nat];
+      ub = umax64(ub, abs_bits(u0[nat]));
       const bool interior = i >= 1 && i <= n && j >= 1 && j <= n && k >= 1 && k <= n;
       double gc = 0.0;
       if (interior && f) gc = __dmul_rn(h2, f[((size_t)(k - 1) * n + (i - 1)) * n + (j - 1)]);
+      gb = umax64(gb, abs_bits(gc));
       T* gg = c ? g1 : g0;
       if (gg) gg[e] = (T)gc;
       double* g6 = c ? g64_1 : g64_0;
@@ -96,6 +98,8 @@ __global__ void k_pack3d(const double* __restrict__ u0, const double* __restrict
     }
   }
   block_max_to(bb, &st->bmax_bits, red);
+  block_max_to(ub, &st->umax_bits, red);  // magnitudes that bound the rescaled phases' chunk length
+  block_max_to(gb, &st->gmax_bits, red);
 }
 
 template <typename T>
@@ -998,7 +1002,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   const int stop = p->stop == SOR_STOP_MAXDELTA ? kStopDelta : kStopResid;
   // FP64 default: the rescaled phases with shared pair sums (within 1e-12 of
   // the exact order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
-  const bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
+  bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
   if (fast) SOR3_CK(c, fast3_prepare());
   const int bps = fast ? fast3_blocks_per_sm(has_f) : exact3_blocks_per_sm<T>(has_f);
   if (bps < 1) {
@@ -1121,6 +1125,23 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
                                           sizeof(T) == 4 ? g64[0] : nullptr, sizeof(T) == 4 ? g64[1] : nullptr,
                                           d_state);
   SOR3_CK(c, cudaGetLastError());
+  int lrun = lmax;  // chunk cap of the rescaled phases for these inputs
+  if (fast) {
+    // input magnitudes bound the rescaled phases' chunk length; inputs they
+    // cannot carry take the exact-order phases (the same strips and grid:
+    // the exact flow kernel needs no co-residency)
+    SlotState hs;
+    SOR3_CK(c, cudaMemcpyAsync(&hs, d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR3_CK(c, cudaStreamSynchronize(s));
+    double umax = 0.0, gmax = 0.0;
+    std::memcpy(&umax, &hs.umax_bits, sizeof(double));
+    std::memcpy(&gmax, &hs.gmax_bits, sizeof(double));
+    const int cap = rescaled_lcap(umax, gmax, n, 3, w);
+    if (cap == 0)
+      fast = false;
+    else
+      lrun = std::min(lmax, cap);
+  }
   if (fast) {  // unscaled copy of both colours' shells, for the per-phase rewrite
     const int sb = (int)std::min<size_t>((shell_elems + 255) / 256, (size_t)c->sm_count * 8);
     k_shell_save3<<<dim3(sb, 2), 256, 0, s>>>(d_desc, d_shell0, d_shell1);
@@ -1157,7 +1178,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   // take their phase constants from a device table per chunk length
   // (the claim counter numbers 2 L x strips items in 32 bits: L is capped
   // to keep that below 2^30)
-  const long long lcap = std::min<long long>(fast ? lmax : (1LL << 30), std::max(1LL, (1LL << 29) / nst));
+  const long long lcap = std::min<long long>(fast ? lrun : (1LL << 30), std::max(1LL, (1LL << 29) / nst));
   auto plan_chunks = [&](long long first, int Lc) {
     std::vector<int> out;
     int done_it = 0;

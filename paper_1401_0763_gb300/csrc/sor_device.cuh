@@ -95,6 +95,8 @@ struct SlotState {
   double best_rho;               // smallest rho so far (+inf before the first test)
   double last_dmax;              // m_k of the last iteration that measured it (-1 if none)
   double last_rho;               // relative residual of the last residual pass (-1 if none)
+  unsigned long long umax_bits;  // max |u0| over the whole array (ring and interior), set at pack time
+  unsigned long long gmax_bits;  // max |h^2 f| over the interior, set at pack time
 };
 
 // A tile of work: slot index, first row, first packed column, row count.

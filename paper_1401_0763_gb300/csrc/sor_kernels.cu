@@ -38,7 +38,9 @@ void count_kernel_launches(int k) { t_launches += (unsigned long long)k; }
 
 // Thread (i, q) moves the natural cells j = 2q-1 and j = 2q of row i (one of
 // each colour) into the colour arrays; interior cells also receive h^2 f and
-// contribute |b~| = |h^2 f + (ring neighbours)| to ||b~||_inf.
+// contribute |b~| = |h^2 f + (ring neighbours)| to ||b~||_inf.  The largest
+// |u0| and |h^2 f| are reduced as well: they bound the values the rescaled
+// FP64 phases carry, whose chunk length the host derives from them.
 template <typename T>
 __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__ f, int n, int pitch, double h2,
                        T* x00, T* x01, T* x10, T* x11, T* g0, T* g1, double* g64_0, double* g64_1,
@@ -48,7 +50,7 @@ __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__
   const int qw = (n + 1) / 2 + 2;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
-  unsigned long long bb = 0;
+  unsigned long long bb = 0, ub = 0, gb = 0;
   if (q < qw) {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -56,6 +58,7 @@ __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__
       if (j < 0 || j >= m) continue;
       const int c = (i + j) & 1;
       const double v = u0[(size_t)i * m + j];
+      ub = umax64(ub, abs_bits(v));
       const size_t e = eidx(i, q, pitch);
       T* xa = c ? x01 : x00;
       T* xb = c ? x11 : x10;
@@ -68,6 +71,7 @@ __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__
       const bool interior = (i >= 1 && i <= n && j >= 1 && j <= n);
       double gij = 0.0;
       if (interior && f) gij = __dmul_rn(h2, f[(size_t)(i - 1) * n + (j - 1)]);
+      gb = umax64(gb, abs_bits(gij));
       T* gg = c ? g1 : g0;
       if (gg) gg[e] = (T)gij;
       double* g6 = c ? g64_1 : g64_0;
@@ -84,6 +88,8 @@ __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__
     }
   }
   block_max_to(bb, &st->bmax_bits, red);
+  block_max_to(ub, &st->umax_bits, red);
+  block_max_to(gb, &st->gmax_bits, red);
 }
 
 // Inverse of k_pack for the iterate in colour arrays c0 / c1 (type T).

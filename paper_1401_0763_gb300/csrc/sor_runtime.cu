@@ -377,9 +377,10 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
   if (p.kind == kPlain64) w->d_ring = (double*)ctx_dev_alloc(c, 2 * ring_elems * sizeof(double));
-  if (p.kind == kPlain64 && !p.exact) {
+  if (p.kind == kPlain64) {
     // chunk launches: cooperative, so the strip table's warps must all be
-    // resident at once in the chain kernel's own occupancy
+    // resident at once in the chain kernel's own occupancy (allocated for
+    // exact-order solves too: a later default solve reuses the workspace)
     w->d_progress = (unsigned*)ctx_dev_alloc(c, std::max<size_t>(1, ft.size()) * sizeof(unsigned));
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
@@ -392,7 +393,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
        w->d_nat_u &&
        (!p.has_f || w->d_nat_f) && (p.kind != kPlain64 || w->d_ring) &&
-       (p.kind != kPlain64 || p.exact || w->d_progress);
+       (p.kind != kPlain64 || w->d_progress);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
     cudaGetLastError();
     free_workspace(c, w.get());
@@ -531,6 +532,35 @@ static int fast_lmax(double omega) {
   return std::max(1, std::min(L, 256));
 }
 
+// Inside a chunk of L iterations the rescaled phases store each colour at a
+// scale of at most (c / omega)^(2L - 2), c = 4 (plate) or 6 (cube); the last
+// iteration of a chunk runs unscaled, so L = 1 carries no scale at all.  The
+// stored values are the iterates times that scale.  Bound on the iterates:
+//  * the discrete solution satisfies |u*| <= max|ring| + max|f| / 8 (maximum
+//    principle with the comparison function sum_d (x_d - 1/2)^2 / (2 dims),
+//    which the 5- and 7-point stencils differentiate exactly), and max|f| =
+//    max|h^2 f| (n + 1)^2, so M = umax + gmax max(1, (n + 1)^2 / 8) bounds
+//    both |u*| and |u0|;
+//  * every single-cell SOR update with 0 < omega < 2 lowers the energy
+//    norm of the error (the Ostrowski-Reich argument), so at any point of
+//    the iteration |e|_inf <= |e|_2 <= sqrt(kappa) n^(dims/2) |e0|_inf with
+//    sqrt(kappa) < n + 1: |u| <= M + 2M (n + 1)^(1 + dims/2);
+//  * neighbour sums and coefficient products add at most a few more bits.
+// The cap keeps log2 of the largest stored value below 1020.
+int rescaled_lcap(double umax, double gmax, int n, int dims, double omega) {
+  const double c = dims == 3 ? 6.0 : 4.0;
+  const double M = umax + gmax * std::max(1.0, (double)(n + 1) * (n + 1) / 8.0);
+  if (!std::isfinite(M) || !(M > 0.0)) return 0;
+  const double mbits = std::log2(M);
+  if (mbits < -960.0) return 0;
+  const double growth = std::log2(3.0) + (1.0 + 0.5 * dims) * std::log2((double)n + 1.0);
+  const double room = 1020.0 - (mbits + growth + 6.0);  // 6: sums of up to 7 terms, (1 - w) (c / w)^2 products
+  if (room < 0.0) return 0;
+  const double per_iter = 2.0 * std::log2(c / omega);  // scale bits per iteration
+  const double L = per_iter > 0.0 ? 1.0 + std::floor(room / per_iter) : 256.0;
+  return (int)std::max(1.0, std::min(L, 256.0));
+}
+
 // Iterations in the next chunk of a plain solve that has planned k0 so far.
 // The rescaled FP64 phases must end a chunk wherever |change| is measured
 // (multiples of K and the cap), since only chunk ends hold unscaled values.
@@ -543,7 +573,8 @@ static int next_chunk(Ctx* c, const Plan& p, long long k0, int L) {
   if (p.kind == kPlain64 && !p.exact) {
     const long long to_check = p.K - (k0 % p.K);
     const long long to_cap = (long long)p.max_iters - k0;
-    long long Lc = std::min<long long>(fast_lmax(p.omega), std::min(to_check, to_cap));
+    const int lmax = p.lcap > 0 ? std::min(p.lcap, fast_lmax(p.omega)) : fast_lmax(p.omega);
+    long long Lc = std::min<long long>(lmax, std::min(to_check, to_cap));
     (void)c;
     (void)L;
     return (int)std::max<long long>(1, Lc);
@@ -824,9 +855,10 @@ sor_status solve_blocking(Ctx* c, const Plan& plan_in, const double* u0, const d
   return solve_locked(c, p, u0, f, u_out, res, t0);
 }
 
-static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,
+static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const double* f, double* u_out,
                                sor_result* res, double t0) {
   cudaStream_t s = c->stream;
+  Plan p = plan;  // the FP64 default path may turn exact-order once the input magnitudes are known
   SolveWorkspace* w = nullptr;
   sor_status rs = get_workspace(c, p, &w);
   if (rs != SOR_OK) return rs;
@@ -886,6 +918,25 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
   }
   pa.state = w->d_state;
   SOR_CK(c, launch_pack(pa, s));
+  // small plain grids: the whole solve in one cluster launch (exact order)
+  const bool small = p.kind == kPlain64 ? p.n <= 384 : p.n <= 768;
+  const bool cluster = !(p.kind != kRefine && p.max_iters == 0) && p.kind != kRefine && small &&
+                       c->opt_cluster.load() && cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch);
+  if (p.kind == kPlain64 && !p.exact && !cluster) {
+    // the rescaled phases need the input magnitudes to bound their chunk
+    // length; inputs they cannot carry take the exact-order phases
+    SOR_CK(c, cudaMemcpyAsync(&w->h_state[0], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
+    SOR_CK(c, cudaStreamSynchronize(s));
+    double umax = 0.0, gmax = 0.0;
+    std::memcpy(&umax, &w->h_state[0].umax_bits, sizeof(double));
+    std::memcpy(&gmax, &w->h_state[0].gmax_bits, sizeof(double));
+    p.lcap = rescaled_lcap(umax, gmax, p.n, 2, p.omega);
+    if (p.lcap == 0) {
+      p.exact = true;
+      w->slot.desc.sweep_tiles = w->n_sweep_tiles;
+      SOR_CK(c, cudaMemcpyAsync(w->d_desc, &w->slot.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
+    }
+  }
   if (p.kind == kPlain64 && !p.exact) SOR_CK(c, launch_ring_save(w->d_desc, s));  // ring kept for the rescaled phases
 
   // chunks, polled with a lag of kInflight - 1 so the device never idles
@@ -915,10 +966,7 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
     last_iters = hs.iters;
     return SOR_OK;
   };
-  // small plain grids: the whole solve in one cluster launch
-  const bool small = p.kind == kPlain64 ? p.n <= 384 : p.n <= 768;
-  if (!finished && p.kind != kRefine && small && c->opt_cluster.load() &&
-      cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch)) {
+  if (cluster) {
     const int k = slot_i;
     if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
     SOR_CK(c, launch_cluster_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, w->d_desc, w->d_state, 0, s));

@@ -59,6 +59,7 @@ struct Plan {
   bool has_f = false;
   int tdepth = 1;  // FP32 sweeps: iterations fused per tile pass (1 = one launch per colour phase)
   int stall = 0;   // residual tests without a new minimum that end the solve (0 = never)
+  int lcap = 0;    // FP64 default path: longest chunk the input magnitudes allow (0 = not yet known)
   double omega = 0.0;
   double tol = 0.0;
 };
@@ -206,6 +207,9 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
 // Runs the flow kernels' bounded device-side wait on a counter preset to 0
 // (nothing advances it: the wait gives up after `polls` polls) or 1.
 sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out);
+// FP64 lane operations per second of the whole GPU on independent chains of
+// FMAs (kind 0) or additions (kind 1) (sor_probe.cu).
+sor_status diag_fp64_rate(Ctx* c, int kind, double* ops_per_s);
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res);
 
@@ -215,5 +219,12 @@ void batch_shutdown(Ctx* c);
 
 double now_s();
 bool is_device_ptr(const void* p);
+
+// Longest chunk of the rescaled FP64 phases that the inputs allow: umax =
+// max |u0| (whole array), gmax = max |h^2 f|, n the interior side, dims 2
+// (plate, scale factor 4 / omega per half iteration) or 3 (cube, 6 / omega).
+// 0: the magnitudes leave no room even unscaled (or are not finite, zero or
+// below 2^-960): the solve must take the exact-order phases.
+int rescaled_lcap(double umax, double gmax, int n, int dims, double omega);
 
 }  // namespace sorgb

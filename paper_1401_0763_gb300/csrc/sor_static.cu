@@ -101,6 +101,30 @@ sor_status static_plan(const sor_params* p, bool has_f, Plan* out) {
     }                                  \
   } while (0)
 
+// Failure after work was queued on the stream: wait for that work before the
+// caller's lock on the scratch is dropped, so the next call cannot overwrite
+// the scratch while it is still being read.
+#define SOR_SCK_Q(expr, s)             \
+  do {                                 \
+    if ((expr) != cudaSuccess) {       \
+      cudaGetLastError();              \
+      cudaStreamSynchronize(s);        \
+      cudaGetLastError();              \
+      return SOR_ERR_CUDA;             \
+    }                                  \
+  } while (0)
+
+// Device memory of the current device (the header requires inputs and
+// outputs there): a pointer on another GPU, or host memory, is refused.
+bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 constexpr int kStaticChunk = 32;  // iterations between polls of the solve state
 
 }  // namespace
@@ -115,9 +139,9 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   Plan plan;
   sor_status rs = static_plan(params, f != nullptr, &plan);
   if (rs != SOR_OK) return rs;
-  if (!is_device_ptr(u0) || !is_device_ptr(u_out) || (f && !is_device_ptr(f))) return SOR_ERR_INVALID_ARG;
   int dev = -1;
   SOR_SCK(cudaGetDevice(&dev));
+  if (!on_device(u0, dev) || !on_device(u_out, dev) || (f && !on_device(f, dev))) return SOR_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_static_mu);
   unsigned char* base = nullptr;
   SOR_SCK(static_scratch(dev, &base));
@@ -155,6 +179,9 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   d.a32 = (float)d.a64;
   d.b32 = (float)d.b64;
   d.tol = plan.tol;
+  // the scratch was sized with a copy of Layout::make's pitch rule: refuse
+  // to run if the two ever disagree
+  if (E * sizeof(double) > kArrayBytes || L.row_tiles() * L.col_tiles() > kStaticMaxTiles) return SOR_ERR_INTERNAL;
   Tile tiles[kStaticMaxTiles];
   int nt = 0;
   for (int r = 0; r < L.row_tiles(); ++r)
@@ -173,15 +200,15 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   // The scratch keeps whatever the previous call left: clear the arrays this
   // call reads before it writes them (padding included), then upload the
   // descriptor, the zeroed state and the tile table.
-  SOR_SCK(cudaMemsetAsync(arr[0], 0, E * sizeof(double), s));
-  SOR_SCK(cudaMemsetAsync(arr[1], 0, E * sizeof(double), s));
+  SOR_SCK_Q(cudaMemsetAsync(arr[0], 0, E * sizeof(double), s), s);
+  SOR_SCK_Q(cudaMemsetAsync(arr[1], 0, E * sizeof(double), s), s);
   if (plan.has_f) {
-    SOR_SCK(cudaMemsetAsync(arr[2], 0, E * sizeof(double), s));
-    SOR_SCK(cudaMemsetAsync(arr[3], 0, E * sizeof(double), s));
+    SOR_SCK_Q(cudaMemsetAsync(arr[2], 0, E * sizeof(double), s), s);
+    SOR_SCK_Q(cudaMemsetAsync(arr[3], 0, E * sizeof(double), s), s);
   }
-  SOR_SCK(cudaMemcpyAsync(d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-  SOR_SCK(cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
-  SOR_SCK(cudaMemcpyAsync(d_tiles, tiles, sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
+  SOR_SCK_Q(cudaMemcpyAsync(d_desc, &d, sizeof(d), cudaMemcpyHostToDevice, s), s);
+  SOR_SCK_Q(cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s), s);
+  SOR_SCK_Q(cudaMemcpyAsync(d_tiles, tiles, sizeof(Tile) * nt, cudaMemcpyHostToDevice, s), s);
 
   PackArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -199,7 +226,7 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
     pa.g[1] = arr[3];
   }
   pa.state = d_state;
-  SOR_SCK(launch_pack(pa, s));
+  SOR_SCK_Q(launch_pack(pa, s), s);
 
   SlotState hs;
   long long planned = 0;
@@ -207,19 +234,21 @@ extern "C" sor_status sor_solve_static(const sor_params* params, const double* u
   while (!finished && planned < plan.max_iters) {
     const int Lc = (int)std::min<long long>(kStaticChunk, plan.max_iters - planned);
     for (int it = 0; it < Lc; ++it) {
-      SOR_SCK(launch_sweep(kSweepPlain64, d_desc, d_state, d_tiles, nt, 0, 0, 0, s));
-      SOR_SCK(launch_sweep(kSweepPlain64, d_desc, d_state, d_tiles, nt, 0, 1, 0, s));
-      if (plan.stop == kStopResid) SOR_SCK(launch_resid(kResidCheck64, d_desc, d_state, d_tiles, nt, 0, 0, s));
+      SOR_SCK_Q(launch_sweep(kSweepPlain64, d_desc, d_state, d_tiles, nt, 0, 0, 0, s), s);
+      SOR_SCK_Q(launch_sweep(kSweepPlain64, d_desc, d_state, d_tiles, nt, 0, 1, 0, s), s);
+      // residual tests fall on multiples of K only (as in sor_solve)
+      if (plan.stop == kStopResid && (planned + it + 1) % plan.K == 0)
+        SOR_SCK_Q(launch_resid(kResidCheck64, d_desc, d_state, d_tiles, nt, 0, 0, s), s);
     }
     planned += Lc;
-    SOR_SCK(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    SOR_SCK(cudaStreamSynchronize(s));
+    SOR_SCK_Q(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s), s);
+    SOR_SCK_Q(cudaStreamSynchronize(s), s);
     finished = hs.done != 0;
   }
-  SOR_SCK(launch_resid(kResidFinal64, d_desc, d_state, d_tiles, nt, 0, 0, s));
-  SOR_SCK(launch_unpack(arr[0], arr[1], false, plan.n, L.pitch, u_out, s));
-  SOR_SCK(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s));
-  SOR_SCK(cudaStreamSynchronize(s));
+  SOR_SCK_Q(launch_resid(kResidFinal64, d_desc, d_state, d_tiles, nt, 0, 0, s), s);
+  SOR_SCK_Q(launch_unpack(arr[0], arr[1], false, plan.n, L.pitch, u_out, s), s);
+  SOR_SCK_Q(cudaMemcpyAsync(&hs, d_state, sizeof(hs), cudaMemcpyDeviceToHost, s), s);
+  SOR_SCK_Q(cudaStreamSynchronize(s), s);
   if (hs.error) return SOR_ERR_INTERNAL;
   if (res) {
     std::memset(res, 0, sizeof(*res));
