@@ -32,11 +32,12 @@ WORKLOAD = "paper-sized plain sweep: 4098x4098 array (4096^2 interior), random u
            "interior 0, f=0, w_opt, 1000 iterations, max|change| every 50"
 FP64_FLOPS_PER_LUP = 6.0    # (1-w)u + (w/4)(N+S+W+E): 3 adds, 2 multiplies, 1 add
 HBM_BYTES_PER_LUP = {"f64": 16.0, "f32": 8.0}  # read + write of each cell once per iteration
-NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_fast_chain launch (50 iterations) on this workload
-# (profiles/k_fast_chain_plate4096.md).  Taken before strips with only interior columns stopped masking
-# their cells, a change to no load or store; reported as the last capture, `traffic` null until re-taken.
-FAST64_DRAM_BYTES_PER_LAUNCH_LAST = 18.6435e9
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate: 152 SMs x 2 lanes/clk x 2.07 GHz x 2 flops
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_fast_chain launch (50 iterations) on this workload,
+# from the ncu capture of the current kernel (None: no capture of the current kernel yet)
+FAST64_DRAM_BYTES_PER_LAUNCH = 11405769728 + 6608791552
+# the same counters for one k_sweep_tb<6,0> launch (6 fused iterations) on the FP32 plate, per update
+TB32_DRAM_BYTES_PER_UPDATE = (68465664 + 22038272) / (6.0 * 4096 * 4096)
 
 
 def dist_env():
@@ -134,6 +135,22 @@ def oracle_sample(n_iters: int):
     return (N * N * n_iters) / dt / 1e9, dt
 
 
+def allcore_sample(n_iters: int):
+    """Time the threaded CPU twin of the oracle (bitwise equal to it) on every
+    host core, same plate."""
+    import cpu_baseline
+    import oracle
+    from paper_1401_0763_gb300 import workloads as wl
+    u0 = wl.random_edges(N, 0)
+    cpu_baseline.build()
+    w = oracle.omega_opt(N)
+    cores = cpu_baseline.host_cores()
+    t0 = time.perf_counter()
+    r = cpu_baseline.sor_f64_mt(u0, w, max_iters=n_iters, check_every=CHECK, tol=-1.0, threads=cores)
+    dt = time.perf_counter() - t0
+    return (N * N * n_iters) / dt / 1e9, dt, r["threads"]
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
@@ -225,6 +242,10 @@ def run_ours(args, ws, rank, local):
     peaks, peaks_src = measured_peaks()
     check = {"iterations": res["iterations"], "final_maxdelta": res["final_maxdelta"],
              "final_resid_rel": res["final_resid_rel"]}
+    # the FP64 peak, measured now on this GPU: independent FMA chains (2 flops each) and addition chains
+    fma_rate = ctx.diag_fp64_rate(0)
+    add_rate = ctx.diag_fp64_rate(1)
+    fp64_peak_tflops = 2.0 * fma_rate / 1e12
 
     # ---- FP32 storage, same plate (secondary line item) -----------------------------------------------------
     for _ in range(max(1, args.warmup // 2)):
@@ -240,9 +261,14 @@ def run_ours(args, ws, rank, local):
     ms32 = e0.elapsed_time(e1)
     st32 = ctx.stats()
     per32 = st32["sweep_ms"] / max(1, st32["timed_launches"])
+    # algorithmic bytes: 8 B per update of an unfused iteration (read + write each cell once); the fused
+    # kernel moves fewer DRAM bytes (state in L2 at this size; see dram_bytes_per_update)
     fp32 = {"value": lups_rank / (ms32 * 1e-3) / 1e9, "unit": "GLUP/s", "ms_per_step": ms32 / args.steps,
-            "sweep_hbm_gbs": lups_per_launch * HBM_BYTES_PER_LUP["f32"] / (per32 * 1e-3) / 1e9}
-    fp32["sweep_hbm_frac"] = fp32["sweep_hbm_gbs"] / peaks["hbm_gbs"]
+            "algorithmic_gbs": lups_per_launch * HBM_BYTES_PER_LUP["f32"] / (per32 * 1e-3) / 1e9,
+            "algorithmic_bytes_per_update": HBM_BYTES_PER_LUP["f32"],
+            "dram_bytes_per_update": TB32_DRAM_BYTES_PER_UPDATE,
+            "note": "the 68 MB FP32 state fits in L2: algorithmic_gbs is not an HBM measurement"}
+    fp32["algorithmic_over_hbm_peak"] = fp32["algorithmic_gbs"] / peaks["hbm_gbs"]
 
     # ---- end to end: pinned host buffers, copies inside the timed region ------------------------------------
     h_u0 = torch.from_numpy(u0_np).pin_memory()
@@ -266,9 +292,15 @@ def run_ours(args, ws, rank, local):
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N=1 only) ------------------------------------
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import cpu_baseline
         v, dt = oracle_sample(args.cpu_iters)
+        va, dta, threads = allcore_sample(args.allcore_iters)
         cpu = {"value": v, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
-               "sample": f"4096^2 plate, {args.cpu_iters} iterations ({dt:.1f} s, single thread)"}
+               "sample": f"4096^2 plate, {args.cpu_iters} iterations ({dt:.1f} s, single thread)",
+               "host_cores": cpu_baseline.host_cores(), "os_cpu_count": os.cpu_count(),
+               "allcore": {"value": va, "unit": "GLUP/s", "cores": threads,
+                           "kind": "threaded red-black twin of the oracle (bitwise equal to it)",
+                           "sample": f"4096^2 plate, {args.allcore_iters} iterations ({dta:.1f} s)"}}
 
     ctx.close()
     if rank == 0:
@@ -280,18 +312,17 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD, "n": N, "iterations": ITERS, "check_every": CHECK,
                        "l2": "inputs larger than L2 (134 MB natural in + 136 MB colour-split state + 134 MB out; "
                              "no flush)", "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                         "frac": fp64_tflops / NOMINAL_FP64_TFLOPS, "traffic": None,
-                         "traffic_last_capture": FAST64_DRAM_BYTES_PER_LAUNCH_LAST,
-                         "traffic_unit": "bytes per launch of 50 iterations (dram read + write)",
-                         "traffic_source": "ncu capture of k_fast_chain on this workload "
-                                           "(profiles/k_fast_chain_plate4096.md), taken before the interior-mask "
-                                           "skip of all-interior strips (no load or store changed)",
+            "roofline": {"bound": "alu", "achieved": fp64_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                         "frac": fp64_tflops / fp64_peak_tflops,
+                         "traffic": FAST64_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_unit": "bytes per launch of 50 iterations (dram read + write, ncu)",
                          "traffic_algorithmic": 16.0 * N * N * CHECK,
                          "kernel": "k_fast_chain<false> (a chunk of 50 iterations per launch; "
                                    "achieved from the per-phase CUDA-event time)",
-                         "peak_source": "nominal GB300 FP64 rate: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz x 2 flops; "
-                                        "a probe of independent FP64 chains reached 5.29e11 operations/s",
+                         "peak_source": "measured on this GPU by sor_diag_fp64_rate: independent FP64 FMA chains, "
+                                        "2 flops per FMA (of measured)",
+                         "fp64_fma_ops_per_s": fma_rate, "fp64_add_ops_per_s": add_rate,
+                         "nominal_peak": NOMINAL_FP64_TFLOPS, "frac_of_nominal": fp64_tflops / NOMINAL_FP64_TFLOPS,
                          "hbm_gbs": hbm_gbs_fp64, "hbm_frac": hbm_gbs_fp64 / peaks["hbm_gbs"],
                          "hbm_peak_source": peaks_src},
             "fp32": fp32,
@@ -348,7 +379,6 @@ def workload_poisson4096(args, ctx, capi, wl):
     import torch
     cases = [(4096, 1e-7), (4096, 1e-8), (1024, 1e-10)]
     detail = {}
-    exact_cache = {}
     for n, tol in cases:
         u0_np, f_np = wl.poisson_problem(n, args.seed)
         u0 = torch.from_numpy(u0_np).cuda()
@@ -371,11 +401,6 @@ def workload_poisson4096(args, ctx, capi, wl):
             rec = {"time_to_solution_s": dt, "sweeps": res["iterations"], "outer_steps": res["outer_steps"],
                    "final_resid_rel": res["final_resid_rel"], "converged": res["converged"],
                    "glups": float(n) * n * res["iterations"] / dt / 1e9}
-            if args.check:
-                from tests import pins  # the DST-I exact discrete solution (test-side mathematics)
-                if n not in exact_cache:
-                    exact_cache[n] = pins.dst_solve(u0_np, f_np)
-                rec["rel_err_vs_exact"] = pins.rel_err(out.cpu().numpy(), exact_cache[n])
             detail[key][name] = rec
         r, p = detail[key]["fp32_refine"], detail[key]["fp64_plain"]
         detail[key]["speedup_refine_vs_plain"] = p["time_to_solution_s"] / r["time_to_solution_s"]
@@ -763,7 +788,23 @@ def workload_ninepoint4096(args, ctx, capi, wl):
                        "l2": "4 quarter arrays of 34 MB FP64 (134 MB in all), above the 129 MB L2"}}
 
 
-WORKLOADS = {"paper": workload_paper, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
+def workload_fp64rate(args, ctx, capi, wl):
+    """The FP64 peak of this GPU as sor_diag_fp64_rate measures it (independent chains of FP64 FMAs and of
+    additions on a full-occupancy grid, CUDA-event timed), repeated `steps` times, next to the nominal rate."""
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    fma = [ctx.diag_fp64_rate(0) for _ in range(max(1, args.steps))]
+    add = [ctx.diag_fp64_rate(1) for _ in range(max(1, args.steps))]
+    nominal = props.multi_processor_count * 2 * 2.07e9
+    return {"metric": "FP64 lane operations per second (independent chains, whole GPU)",
+            "value": max(fma), "unit": "ops/s", "higher_is_better": True, "dtype": "f64",
+            "detail": {"fma_ops_per_s": fma, "add_ops_per_s": add, "fma_tflops": 2.0 * max(fma) / 1e12,
+                       "nominal_ops_per_s": nominal, "fma_frac_of_nominal": max(fma) / nominal,
+                       "add_frac_of_nominal": max(add) / nominal, "sms": props.multi_processor_count},
+            "config": {"workload": "8 blocks x 256 threads per SM, 8 chains per thread, 16384 steps per chain"}}
+
+
+WORKLOADS = {"paper": workload_paper, "fp64rate": workload_fp64rate, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
              "serve": workload_serve, "cube256": workload_cube256, "ninepoint4096": workload_ninepoint4096,
              "cubepoisson": workload_cubepoisson, "ninepoisson": workload_ninepoisson,
              "plate16384": workload_plate16384}
@@ -793,6 +834,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=150)
+    ap.add_argument("--allcore-iters", type=int, default=200, help="iterations of the all-core CPU sample")
     ap.add_argument("--ref-iters", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tdepth", type=int, default=0, help="FP32 iterations fused per tile pass (0 = library default)")
@@ -802,7 +844,6 @@ def main():
     ap.add_argument("--count", type=int, default=0, help="batch512 / serve: number of grids or requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate per second")
     ap.add_argument("--fp64-sample", type=int, default=16, help="serve: requests timed one at a time in FP64")
-    ap.add_argument("--check", action="store_true", help="poisson4096: error against the exact DST solution")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

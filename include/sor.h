@@ -204,6 +204,18 @@ sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, 
  * Returns SOR_ERR_INVALID_ARG for arguments out of range. */
 sor_status sor_diag_flow_wait(sor_ctx *ctx, int polls, int preset, int *timed_out);
 
+/* Measured FP64 rate of the context's GPU: the peak that bounds the FP64
+ * colour phases (Eq. 1 evaluated in FP64, Section 3.1) on GB300, whose HBM
+ * could feed them faster than its FP64 units compute.  A full-occupancy
+ * grid runs independent chains of FP64 fused multiply-adds (kind 0) or
+ * additions (kind 1) on the context's stream, timed with CUDA events (one
+ * warm-up launch, then one timed launch of about 70 ms); *ops_per_s receives
+ * the FP64 lane operations per second of the whole GPU (an FMA counts once;
+ * its flops are twice that).  Blocks until done; allocates and frees a
+ * 2.5 MB output buffer.  SOR_ERR_INVALID_ARG for another kind or a NULL
+ * output. */
+sor_status sor_diag_fp64_rate(sor_ctx *ctx, int kind, double *ops_per_s);
+
 /* Non-blocking submission to the context's continuous-batching scheduler.
  * u0 and f are copied before the call returns.  u_out must stay valid until
  * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.
@@ -287,7 +299,8 @@ double sor_omega_opt(int32_t n);
  *           (the SOR_FLAG_EXACT_ORDER path of sor_solve, whose results it
  *           equals bit for bit) whatever the flag says.
  *   u0, f, u_out: DEVICE pointers on the current device (f may be NULL);
- *           host pointers return SOR_ERR_INVALID_ARG.
+ *           host pointers and pointers on another device return
+ *           SOR_ERR_INVALID_ARG.
  *   res:    optional; device_s is 0 (no events are created).
  *   cuda_stream: stream for the work (NULL = the legacy default stream).
  * The first call on a device looks up the array's device address with that
@@ -295,7 +308,7 @@ double sor_omega_opt(int32_t n);
  * shares the one array and it keeps the previous call's contents, so each call
  * clears what it reads first.  Calls that overlapped on the GPU would race on
  * the array: the library serialises callers and each call returns only after
- * its work on the stream has finished.  Allocates nothing: no cudaMalloc,
+ * its work on the stream has finished, on error returns too.  Allocates nothing: no cudaMalloc,
  * cudaFree or allocating library call. */
 sor_status sor_solve_static(const sor_params *params, const double *u0, const double *f, double *u_out,
                             sor_result *res, void *cuda_stream);

@@ -50,7 +50,7 @@ SOR_OPT_FAST_CHAIN = 8
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
             "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d",
-            "sor_solve9", "sor_diag_flow_wait")
+            "sor_solve9", "sor_diag_flow_wait", "sor_diag_fp64_rate")
 
 
 class sor_params(ctypes.Structure):
@@ -126,6 +126,7 @@ def load(build_if_missing: bool = False):
         lib.sor_status_string.restype = ctypes.c_char_p
         lib.sor_solve_static.argtypes = [P(sor_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          P(sor_result), ctypes.c_void_p]
+        lib.sor_diag_fp64_rate.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp]
         lib.sor_omega_opt.argtypes = [ctypes.c_int32]
         lib.sor_omega_opt.restype = ctypes.c_double
         for name in EXPORTED:
@@ -291,6 +292,14 @@ class Context:
         st = self._lib.sor_diag_flow_wait(self._h, ctypes.c_int32(polls), ctypes.c_int32(preset),
                                           ctypes.byref(out))
         self._check(st, "sor_diag_flow_wait")
+        return out.value
+
+    def diag_fp64_rate(self, kind: int = 0) -> float:
+        """sor_diag_fp64_rate: measured FP64 lane operations per second
+        (kind 0: FMA chains, 1: addition chains)."""
+        out = ctypes.c_double(0.0)
+        st = self._lib.sor_diag_fp64_rate(self._h, ctypes.c_int32(kind), ctypes.byref(out))
+        self._check(st, "sor_diag_fp64_rate")
         return out.value
 
     def solve9_raw(self, params: sor_params, u0_ptr, f_ptr, out_ptr):

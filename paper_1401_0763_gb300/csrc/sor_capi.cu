@@ -177,6 +177,15 @@ sor_status sor_diag_flow_wait(sor_ctx* h, int polls, int preset, int* timed_out)
   return diag_flow_wait(c, polls, preset, timed_out);
 }
 
+sor_status sor_diag_fp64_rate(sor_ctx* h, int kind, double* ops_per_s) {
+  if (!h) return SOR_ERR_INVALID_ARG;
+  Ctx* c = &h->impl;
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return SOR_ERR_CUDA;
+  std::lock_guard<std::mutex> g(c->solve_mu);
+  return diag_fp64_rate(c, kind, ops_per_s);
+}
+
 sor_status sor_batch_submit(sor_ctx* h, const sor_params* params, const double* u0, const double* f, double* u_out,
                             uint64_t* ticket) {
   if (!h) return SOR_ERR_INVALID_ARG;

@@ -66,6 +66,7 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.sor_solve3d(None, None, None, None, None, None) == capi.SOR_ERR_INVALID_ARG
     assert lib.sor_solve9(None, None, None, None, None, None) == capi.SOR_ERR_INVALID_ARG
     assert lib.sor_diag_flow_wait(None, 10, 0, None) == capi.SOR_ERR_INVALID_ARG
+    assert lib.sor_diag_fp64_rate(None, 0, None) == capi.SOR_ERR_INVALID_ARG
     assert lib.sor_destroy(None) == capi.SOR_ERR_INVALID_ARG
     assert lib.sor_poll(None, 1, None) == capi.SOR_ERR_INVALID_ARG
     h = ctypes.c_void_p()
