@@ -243,16 +243,25 @@ typedef enum {
   SOR_OPT_TIMING = 1,          /* 1: time the sweep kernels with CUDA events (sor_get_stats) */
   SOR_OPT_GRAPHS = 2,          /* 1 (default): replay launch sequences as CUDA graphs */
   SOR_OPT_CHUNK = 3,           /* iterations per launched chunk between convergence polls (0 = auto) */
-  SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per tile pass (0 = autotuned when
-                                  SOR_OPT_AUTOTUNE is 1, else 6; supported: 1, 2, 3, 4, 6, 8) */
-  SOR_OPT_AUTOTUNE = 5,        /* 1: time candidate kernel configurations on first use of a size */
+  SOR_OPT_TEMPORAL_DEPTH = 4,  /* FP32 sweeps: iterations fused per launch (0 = autotuned when
+                                  SOR_OPT_AUTOTUNE is 1, else 6 with the tile kernels, 4 with the
+                                  wavefront kernels; supported: 1 (unfused), tile 2, 3, 4, 6, 8,
+                                  wavefront 2 .. 5; others round down) */
+  SOR_OPT_AUTOTUNE = 5,        /* 1: on the first FP32 or defect-correction solve of a size bucket,
+                                  time the fused-sweep kernel family, depth and rows per tile, and
+                                  the corrections per graph, and keep the fastest (results are the
+                                  same bit for bit whichever is chosen) */
   SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
   SOR_OPT_CLUSTER = 7,         /* 1 (default): plain solves of grids small enough for one thread-block
                                   cluster (N <= 384 in FP64, N <= 768 in FP32) run all their iterations
                                   in a single launch, exact operation order; 0: never */
-  SOR_OPT_FAST_CHAIN = 8       /* 1 (default): the FP64 default path runs each chunk of iterations in one
+  SOR_OPT_FAST_CHAIN = 8,      /* 1 (default): the FP64 default path runs each chunk of iterations in one
                                   cooperative launch with neighbour-to-neighbour progress counters; 0: one
                                   launch per colour phase.  Results are identical either way */
+  SOR_OPT_FUSED_KERNEL = 9     /* FP32 sweeps: 0 (default) = chosen by grid size (tile kernels up to
+                                  N = 6144, wavefront kernels above) or by the autotuner; 1 = tile
+                                  kernels (a shared-memory tile pass per launch); 2 = wavefront kernels
+                                  (a register wavefront per warp).  Results are identical either way */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsorgb.so")
 SOURCES = ["sor_kernels.cu", "sor_cluster.cu", "sor_runtime.cu", "sor_batch.cu", "sor_capi.cu", "sor_static.cu",
-           "sor3d.cu", "sor9.cu", "sor_probe.cu"]
+           "sor3d.cu", "sor9.cu", "sor_probe.cu", "sor_wf.cu", "sor_tile.cu"]
 HEADERS = ["sor_device.cuh", "sor_devfn.cuh", "sor_bits.cuh", "sor_strips.cuh", "sor_kernels.h", "sor_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

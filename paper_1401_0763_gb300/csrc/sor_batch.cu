@@ -35,6 +35,7 @@ namespace sorgb {
   } while (0)
 
 static constexpr int kPlainStepIters = 16;  // iterations per scheduler step for plain slots
+static constexpr int kBatchSegRows = 64;    // output rows per fused-sweep tile (many slots fill the GPU)
 
 struct Batcher {
   Ctx* c = nullptr;
@@ -62,15 +63,14 @@ struct Batcher {
   int nt_refine = 0, nt_p64 = 0, nt_p32 = 0, nt_reftb = 0;
   size_t off_p64 = 0, off_p32 = 0, off_reftb = 0;
   int max_inner = 1;
-  bool uniform_inner = true;  // every refine slot runs the same number of inner sweeps
-  int tdepth = 1;             // fused iterations of the refine sweeps this step (1 = unfused)
+  int tdepth = 0;             // fused iterations of the refine sweeps (1 = unfused; 0 = not chosen yet),
+                              // fixed for the scheduler's lifetime so every slot's buffers stay consistent
+  int fkind = 0;              // kernel family of the fused refine sweeps (FusedKind)
   size_t live_tiles = 0;      // tiles in the table at the last rebuild
   size_t dead_tiles = 0;      // of those, tiles of slots finished since
-  int dbuf_in = 0;            // buffer holding the corrections the next residual pass applies
   bool any_resid_stop = false;
   uint64_t version = 0;       // bumps when the active set changes
   uint64_t graph_version = ~0ull;
-  int graph_dbuf = -1;
   int graph_steps = 0;
   cudaGraphExec_t graph = nullptr;
   size_t reserved_tables = 0;
@@ -125,18 +125,7 @@ static sor_status rebuild_tiles(Batcher* b) {
   std::vector<Tile> ref, p64, p32, reftb;
   b->max_inner = 1;
   b->any_resid_stop = false;
-  int inner0 = -1;
-  b->uniform_inner = true;
-  for (size_t s = 0; s < b->slots.size(); ++s) {
-    Request* r = b->slots[s].get();
-    if (r && r->plan.kind == kRefine) {
-      if (inner0 < 0) inner0 = r->plan.inner;
-      if (r->plan.inner != inner0) b->uniform_inner = false;
-    }
-  }
-  Plan probe;
-  probe.kind = kRefine;
-  const int T = b->uniform_inner ? resolve_tdepth(b->c, probe) : 1;
+  const int T = b->tdepth;  // chosen when the first slot was activated
   for (size_t s = 0; s < b->slots.size(); ++s) {
     Request* r = b->slots[s].get();
     if (!r) continue;
@@ -144,7 +133,9 @@ static sor_status rebuild_tiles(Batcher* b) {
     const size_t before = ref.size() + p64.size() + p32.size() + reftb.size();
     if (r->plan.kind == kRefine) {
       build_tiles(L, (int)s, &ref, nullptr);
-      if (T > 1) build_tiles(L, (int)s, &reftb, nullptr, kTbRows, tb_out_cols(T));
+      if (T > 1)
+        build_tiles(L, (int)s, &reftb, nullptr, fused_out_rows(b->fkind, L.n, T, b->c->sm_count, kBatchSegRows),
+                    fused_out_cols(b->fkind, T));
       b->max_inner = std::max(b->max_inner, r->plan.inner);
     } else if (r->plan.kind == kPlain64) {
       build_tiles(L, (int)s, &p64, nullptr);
@@ -173,7 +164,6 @@ static sor_status rebuild_tiles(Batcher* b) {
   b->off_p64 = ref.size();
   b->off_p32 = ref.size() + p64.size();
   b->off_reftb = ref.size() + p64.size() + p32.size();
-  b->tdepth = T;
   Ctx* c = b->c;
   if (!all.empty())
     SOR_BCK(cudaMemcpyAsync(b->d_tiles, all.data(), sizeof(Tile) * all.size(), cudaMemcpyHostToDevice, b->stream));
@@ -182,18 +172,19 @@ static sor_status rebuild_tiles(Batcher* b) {
 }
 
 // The launches of one scheduler step over every active slot.
-static sor_status enqueue_step(Batcher* b, int dbuf_in) {
+static sor_status enqueue_step(Batcher* b) {
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
   if (b->nt_refine) {
-    // residual pass: applies the corrections of the previous step, tests, writes r~
-    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, dbuf_in, s));
+    // residual pass: applies the corrections of the previous step (each slot's
+    // from the buffer its own inner sweep count ends in), tests, writes r~
+    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, kDbufPerSlot, s));
     if (b->tdepth > 1) {
       const Tile* t = b->d_tiles + b->off_reftb;
       for (int j = 0, sw = 0; sw < b->max_inner; ++j, sw += b->tdepth) {
         const int nt = std::min(b->tdepth, b->max_inner - sw);
-        SOR_BCK(launch_sweep_tb(true, b->tdepth, b->d_desc, b->d_state, t, b->nt_reftb, 0, nt, (j % 2 == 0) ? 1 : 0,
-                                sw, s));
+        SOR_BCK(launch_fused(b->fkind, true, b->tdepth, b->d_desc, b->d_state, t, b->nt_reftb, 0, nt,
+                             (j % 2 == 0) ? 1 : 0, sw, s));
       }
     } else {
       for (int sw = 0; sw < b->max_inner; ++sw) {
@@ -217,16 +208,6 @@ static sor_status enqueue_step(Batcher* b, int dbuf_in) {
   return SOR_OK;
 }
 
-// Buffer the next residual pass reads the corrections from, after a step
-// whose sweeps ran with depth b->tdepth.
-static int step_dbuf_out(const Batcher* b) {
-  Plan q;
-  q.kind = kRefine;
-  q.inner = b->max_inner;
-  q.tdepth = b->tdepth;
-  return refine_dbuf(q);
-}
-
 // Steps replayed per host round trip: with little work active a step is a few
 // short launches, so several of them go into one graph (slots that finish
 // mid-way skip the rest on the device) and the host polls less often.
@@ -245,15 +226,14 @@ static sor_status run_step(Batcher* b, int* steps_out) {
   Ctx* c = b->c;
   const int m = steps_per_round(b);
   *steps_out = m;
-  const int dbuf_next = step_dbuf_out(b);
   if (!c->opt_graphs.load()) {
     for (int k = 0; k < m; ++k) {
-      sor_status rs = enqueue_step(b, k == 0 ? b->dbuf_in : dbuf_next);
+      sor_status rs = enqueue_step(b);
       if (rs != SOR_OK) return rs;
     }
     return SOR_OK;
   }
-  if (b->graph_version != b->version || !b->graph || b->graph_dbuf != b->dbuf_in || b->graph_steps != m) {
+  if (b->graph_version != b->version || !b->graph || b->graph_steps != m) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -261,7 +241,7 @@ static sor_status run_step(Batcher* b, int* steps_out) {
     cudaGraph_t g = nullptr;
     SOR_BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     sor_status rs = SOR_OK;
-    for (int k = 0; k < m && rs == SOR_OK; ++k) rs = enqueue_step(b, k == 0 ? b->dbuf_in : dbuf_next);
+    for (int k = 0; k < m && rs == SOR_OK; ++k) rs = enqueue_step(b);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rs != SOR_OK) {
       if (g) cudaGraphDestroy(g);
@@ -272,7 +252,6 @@ static sor_status run_step(Batcher* b, int* steps_out) {
     cudaGraphDestroy(g);
     SOR_BCK(e);
     b->graph_version = b->version;
-    b->graph_dbuf = b->dbuf_in;
     b->graph_steps = m;
   }
   SOR_BCK(cudaGraphLaunch(b->graph, b->stream));
@@ -304,7 +283,38 @@ static sor_status activate(Batcher* b, Request* r, int s) {
   SOR_BCK(cudaMemcpyAsync(r->d_stage, r->u0.data(), nu * 8, cudaMemcpyHostToDevice, b->stream));
   if (p.has_f)
     SOR_BCK(cudaMemcpyAsync(r->d_stage + nu, r->f.data(), (size_t)p.n * p.n * 8, cudaMemcpyHostToDevice, b->stream));
+  if (b->tdepth == 0) {
+    // the fused refine sweeps, chosen once (outside any capture) for the
+    // whole scheduler: the size rule of sor_solve for this first request, or
+    // the autotuner's choice for its size bucket if one was made
+    Plan probe = p;
+    resolve_fused(c, &probe);
+    if (c->opt_autotune.load() && c->opt_tdepth.load() == 0 && c->opt_fused_kernel.load() == 0) {
+      std::lock_guard<std::mutex> g(c->tune_mu);
+      std::ostringstream key;
+      int nb = 16;
+      while (nb < p.n) nb <<= 1;
+      key << nb << " " << 1;
+      auto it = c->tuned.find(key.str());
+      if (it != c->tuned.end()) {
+        probe.fkind = it->second.fkind;
+        probe.tdepth = it->second.tdepth;
+      }
+    }
+    if (probe.tdepth > 1 && fused_prepare(probe.fkind, probe.tdepth) != cudaSuccess) {
+      cudaGetLastError();
+      c->set_error("fused FP32 sweep kernel does not fit");
+      return SOR_ERR_CUDA;
+    }
+    b->fkind = probe.fkind;
+    b->tdepth = std::max(1, probe.tdepth);
+  }
   fill_desc(p, &r->buf);
+  if (p.kind == kRefine) {
+    Plan q = p;
+    q.tdepth = b->tdepth;
+    r->buf.desc.dbuf = refine_dbuf(q);
+  }
   SlotState st0 = initial_state(p);
   SOR_BCK(cudaMemcpyAsync(b->d_desc + s, &r->buf.desc, sizeof(SlotDesc), cudaMemcpyHostToDevice, b->stream));
   SOR_BCK(cudaMemcpyAsync(b->d_state + s, &st0, sizeof(SlotState), cudaMemcpyHostToDevice, b->stream));
@@ -512,7 +522,6 @@ static void scheduler_main(Batcher* b) {
       NvtxRange nvtx("sor_step");
       int steps = 1;
       rs = run_step(b, &steps);
-      b->dbuf_in = step_dbuf_out(b);
     }
     if (rs == SOR_OK) {  // one copy of the whole state table
       cudaError_t e = cudaMemcpyAsync(b->h_state, b->d_state, sizeof(SlotState) * b->slots.size(),

@@ -228,6 +228,10 @@ sor_status sor_set_option(sor_ctx* h, int32_t option, int64_t value) {
     case SOR_OPT_BATCH_MAX_SLOTS: c->opt_max_slots = v; return SOR_OK;
     case SOR_OPT_CLUSTER: c->opt_cluster = v ? 1 : 0; return SOR_OK;
     case SOR_OPT_FAST_CHAIN: c->opt_fast_chain = v ? 1 : 0; return SOR_OK;
+    case SOR_OPT_FUSED_KERNEL:
+      if (v > 2) return SOR_ERR_INVALID_ARG;
+      c->opt_fused_kernel = v;
+      return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }
@@ -244,6 +248,7 @@ sor_status sor_get_option(sor_ctx* h, int32_t option, int64_t* value) {
     case SOR_OPT_BATCH_MAX_SLOTS: *value = c->opt_max_slots.load(); return SOR_OK;
     case SOR_OPT_CLUSTER: *value = c->opt_cluster.load(); return SOR_OK;
     case SOR_OPT_FAST_CHAIN: *value = c->opt_fast_chain.load(); return SOR_OK;
+    case SOR_OPT_FUSED_KERNEL: *value = c->opt_fused_kernel.load(); return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }

@@ -71,6 +71,22 @@ __device__ __forceinline__ void block_max_to(unsigned long long v, unsigned long
   __syncthreads();
 }
 
+// Plain-mode bookkeeping after the black phase of iteration k (Algorithm 1):
+// count the iteration, test the change on check iterations, stop at the cap.
+__device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st, int k, int measure) {
+  st->arrive = 0;
+  st->iters = k;
+  if (measure) {
+    const double mk = bits_to_double(atomicExch(&st->dmax_bits, 0ull));
+    st->last_dmax = mk;
+    if (sd.stop == kStopDelta && (k % sd.K) == 0 && mk < sd.tol) {
+      st->done = 1;
+      st->converged = 1;
+    }
+  }
+  if (k >= sd.max_iters) st->done = 1;
+}
+
 __device__ __forceinline__ size_t eidx(int i, int q, int pitch) { return (size_t)i * pitch + q + kOff; }
 
 // Data-flow scheduling of a chunk of colour phases (the cube and 9-point

@@ -24,8 +24,6 @@ constexpr int kWarpCols = 32 * kVec;   // 128 packed columns per warp / tile
 constexpr int kWarpsY = 4;             // warps per block, stacked in rows
 constexpr int kThreads = 32 * kWarpsY; // 128 threads per block
 constexpr int kTileRows = 32;          // rows per sweep tile (8 per warp)
-constexpr int kTbRows = 64;            // output rows of a temporally blocked FP32 tile
-constexpr int kTbThreads = 256;        // threads of a temporally blocked tile
 
 struct Layout {
   int n;      // interior side
@@ -70,6 +68,8 @@ struct SlotDesc {
   int resid_tiles;      // tiles of this slot in one residual launch
   int K, max_iters, stop, inner;
   int stall;            // residual tests without a new minimum that end the solve (0 = never)
+  int dbuf;             // refine: buffer of x holding the correction after a step's inner sweeps
+                        // (read by launches given kDbufPerSlot)
   float a32, b32;       // (float)(1 - w), (float)(w / 4)
   double a64, b64;      // 1 - w, w / 4
   double tol;

@@ -119,22 +119,6 @@ struct TileCtl {
   int skip, k, measure, xbuf;
 };
 
-// Plain-mode bookkeeping after the black phase of iteration k (Algorithm 1):
-// count the iteration, test the change on check iterations, stop at the cap.
-__device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st, int k, int measure) {
-  st->arrive = 0;
-  st->iters = k;
-  if (measure) {
-    const double mk = bits_to_double(atomicExch(&st->dmax_bits, 0ull));
-    st->last_dmax = mk;
-    if (sd.stop == kStopDelta && (k % sd.K) == 0 && mk < sd.tol) {
-      st->done = 1;
-      st->converged = 1;
-    }
-  }
-  if (k >= sd.max_iters) st->done = 1;
-}
-
 // Rows [i0, i1) of one warp's share of a tile for k_sweep (one colour phase,
 // exact operation order).  MEASURE: also return max |change| (as the bits of
 // a non-negative double); a compile-time flag so that no |change| work is
@@ -928,399 +912,6 @@ int fast_blocks_per_sm() {
 }
 
 // ------------------------------------------------------------------------------------------------
-// FP32 colour phases fused over several iterations per tile (temporal blocking)
-// ------------------------------------------------------------------------------------------------
-//
-// A tile of kTbRows output rows and OQ = 128 - 2*HQ output packed columns of
-// both colours is staged in shared memory together with a halo of HR = 2T
-// rows and HQ >= T+1 packed columns (a cell's value after t red-black
-// iterations depends on cells at most 2t rows and t packed columns away), so
-// every staged row is exactly 128 packed columns: one float4 per lane of a
-// warp.  T iterations -- red phase, black phase, each the exact update of
-// k_sweep -- then run on the staged copy: each warp walks a segment of rows
-// keeping the neighbour colour's rows i-1, i in registers, W/E neighbours come
-// by shuffles, and a cell update costs two shared-memory loads and one store.
-// After each phase the cells next to the staged border are stale, the stale
-// band growing inward by at most one row and one packed column per phase; the
-// centre tile stays exact and is written to the other buffer of the
-// ping-pong pair, so neighbouring tiles keep reading the previous iterate.
-// HBM traffic per cell: one read and one write per T iterations plus the
-// halo re-reads, most of which L2 serves.
-
-template <int T>
-struct TbGeom {
-  static constexpr int HR = 2 * T;                              // halo rows
-  static constexpr int HQ = T <= 3 ? 4 : (T <= 7 ? 8 : 12);     // halo packed columns (multiple of 4, >= T+1)
-  static constexpr int C = 128;                                 // staged packed columns
-  static constexpr int OQ = C - 2 * HQ;                         // output packed columns
-  static constexpr int R = kTbRows + 2 * HR;                    // staged rows
-  static constexpr size_t smem = 2ull * R * C * sizeof(float);
-};
-
-__device__ __forceinline__ void cp_async16(float* smem_dst, const float* gsrc, bool valid) {
-  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
-  const int n = valid ? 16 : 0;  // src-size 0 fills the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(valid ? gsrc : nullptr), "r"(n)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
-// Right-hand-side rows are fetched kTbGAhead rows ahead into a ring of
-// kTbGSlots row buffers per warp (one asynchronous-copy group per row).
-constexpr int kTbGAhead = 3;
-constexpr int kTbGSlots = 4;
-
-// Right-hand-side values of staged row r (global row i) for this lane, copied
-// asynchronously into the warp's buffer (nothing for rows or lanes without
-// interior cells); one commit per row either way.
-__device__ __forceinline__ void tb_g_issue(float* gslot, const float* __restrict__ Gc, int i, int qf, int n, int pitch,
-                                           int colour, int lane, bool valid) {
-  const int s = (i + colour) & 1;
-  if (valid && i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1))
-    cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-// One row r of a phase on the staged tile.  om / oc / op: the neighbour
-// colour's staged rows r-1, r, r+1 (this lane's 4 columns, in registers);
-// S = (i + colour) & 1 for the global row i, fixed at compile time, which
-// decides which single neighbour value comes from the next lane (S == 0: the
-// east one of the last cell; S == 1: the west one of the first cell).  m: this
-// lane's interior cells (unused when FULL); out_row / outc: the cells counted
-// by the max|change| of a measured phase.  Exact operation order of the oracle.
-template <bool LASTM, bool FULL, bool HAS_G, int S>
-__device__ __forceinline__ void tb_row(const float (&om)[4], const float (&oc)[4], const float (&op)[4],
-                                       float* __restrict__ own_p, const float* __restrict__ g_p, unsigned m,
-                                       bool out_row, unsigned outc, float a, float b, unsigned& dm32) {
-  float W[4], E[4];
-  if (S == 0) {
-    const float side = __shfl_down_sync(0xffffffffu, oc[0], 1);
-    W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
-    E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = side;
-  } else {
-    const float side = __shfl_up_sync(0xffffffffu, oc[3], 1);
-    W[0] = side; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
-    E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
-  }
-  float own[4], gv[4];
-  load4(own_p, own);
-  if (HAS_G) {
-    if (FULL || m) {
-      load4(g_p, gv);
-    } else {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
-    }
-  }
-  // Cells of staged columns 0 and C-1 see a wrong W or E (no staged
-  // neighbour); like every cell near the staged border they are stale, and
-  // the stale band never reaches the output tile.
-  float nv[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    float sum = radd(radd(om[v], op[v]), radd(W[v], E[v]));
-    if (HAS_G) sum = radd(sum, gv[v]);
-    const float nu = radd(rmul(a, own[v]), rmul(b, sum));
-    const bool in = FULL || ((m >> v) & 1u);
-    nv[v] = in ? nu : own[v];
-    if (LASTM && out_row && in && ((outc >> v) & 1u)) dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
-  }
-  store4(own_p, nv);
-}
-
-// Per-phase constants of one warp's rows.
-struct TbRows {
-  float* Sc;        // own colour, staged
-  const float* So;  // neighbour colour, staged
-  const float* Gc;  // right-hand side of the own colour (HAS_G)
-  float* gbuf;      // this warp's kTbGSlots right-hand-side row buffers
-  int base_r, qf, n, pitch, colour, lane, r0, out_lo, out_hi;
-  unsigned in0, in1, outc;
-  float a, b;
-};
-
-template <int C, bool LASTM, bool FULL, bool HAS_G, int S>
-__device__ __forceinline__ void tb_row_at(const TbRows& R, int r, int r1, const float (&om)[4], const float (&oc)[4],
-                                          const float (&op)[4], unsigned& dm32) {
-  const float* gp = nullptr;
-  if (HAS_G) {  // fetch row r + kTbGAhead's right-hand side, then wait for row r's
-    const int ra = r + kTbGAhead;
-    tb_g_issue(R.gbuf + ((ra - R.r0) & (kTbGSlots - 1)) * C, R.Gc, R.base_r + ra, R.qf, R.n, R.pitch, R.colour,
-               R.lane, ra < r1);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTbGAhead) : "memory");
-    gp = R.gbuf + ((r - R.r0) & (kTbGSlots - 1)) * C + 4 * R.lane;
-  }
-  const bool out_row = LASTM && r >= R.out_lo && r < R.out_hi;
-  tb_row<LASTM, FULL, HAS_G, S>(om, oc, op, R.Sc + r * C + 4 * R.lane, gp, S ? R.in1 : R.in0, out_row, R.outc, R.a,
-                                R.b, dm32);
-}
-
-// Rows [R.r0, r1) of the staged tile, the first with parity S0.  Bodies of
-// four rows cycle four register rows in place (rows r-1 .. r+4 pass through
-// X, Y, P, Q and leave X, Y holding r+3, r+4), so no row values are moved.
-template <int C, bool LASTM, bool FULL, bool HAS_G, int S0>
-__device__ __forceinline__ void tb_rows(const TbRows& R, int r1, unsigned& dm32) {
-  const float* So = R.So + 4 * R.lane;
-  int r = R.r0;
-  float X[4], Y[4], P[4], Q[4];
-  load4(So + (r - 1) * C, X);
-  load4(So + r * C, Y);
-  if (HAS_G)
-    for (int k = 0; k < kTbGAhead; ++k)
-      tb_g_issue(R.gbuf + k * C, R.Gc, R.base_r + r + k, R.qf, R.n, R.pitch, R.colour, R.lane, r + k < r1);
-  for (; r + 4 <= r1; r += 4) {
-    load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
-    load4(So + (r + 2) * C, Q);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
-    load4(So + (r + 3) * C, X);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
-    load4(So + (r + 4) * C, Y);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 3, r1, Q, X, Y, dm32);
-  }
-  if (r < r1) {
-    load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
-    if (r + 1 < r1) {
-      load4(So + (r + 2) * C, Q);
-      tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
-      if (r + 2 < r1) {
-        load4(So + (r + 3) * C, X);
-        tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
-      }
-    }
-  }
-  if (HAS_G) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the groups past r1 are empty
-}
-
-// One colour phase on the staged tile: rows [r0, r1) of the staged arrays for
-// this warp, clipped to global interior rows.  LASTM: this phase belongs to a
-// measured iteration, track max |change| over the tile's output cells.
-// FULL: every staged column of the tile is an interior packed column of both
-// colours (no ring or padding cell among them), so no cell needs masking.
-template <int T, bool LASTM, bool FULL, bool HAS_G>
-__device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
-                                         const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
-                                         int r1, int n, int pitch, int out_rows, int lane, float a, float b,
-                                         unsigned& dm32, float* gbuf /* [kTbGSlots][128] for this warp */) {
-  using Gm = TbGeom<T>;
-  r0 = max(r0, 1 - base_r);  // global rows 1 .. n only
-  r1 = min(r1, n + 1 - base_r);
-  if (r0 >= r1) return;
-  TbRows R;
-  R.Sc = Sc;
-  R.So = So;
-  R.Gc = Gc;
-  R.gbuf = gbuf;
-  R.base_r = base_r;
-  R.qf = base_q + 4 * lane;
-  R.n = n;
-  R.pitch = pitch;
-  R.colour = colour;
-  R.lane = lane;
-  R.r0 = r0;
-  R.out_lo = Gm::HR;
-  R.out_hi = Gm::HR + out_rows;
-  R.a = a;
-  R.b = b;
-  // this lane's interior cells for row parity 0 / 1 (bit v: packed column qf + v)
-  // and, for the measured phase, its cells inside the output columns
-  R.in0 = 0xF;
-  R.in1 = 0xF;
-  R.outc = 0;
-  if (!FULL) {
-    R.in0 = 0;
-    R.in1 = 0;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int q = R.qf + v;
-      R.in0 |= (unsigned)(q >= 1 && q <= (n >> 1)) << v;
-      R.in1 |= (unsigned)(q >= 1 && q <= ((n + 1) >> 1)) << v;
-    }
-  }
-  if (LASTM) {
-    const int col = 4 * lane;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) R.outc |= (unsigned)(col + v >= Gm::HQ && col + v < Gm::HQ + Gm::OQ) << v;
-  }
-  if (((base_r + r0 + colour) & 1) == 0)
-    tb_rows<Gm::C, LASTM, FULL, HAS_G, 0>(R, r1, dm32);
-  else
-    tb_rows<Gm::C, LASTM, FULL, HAS_G, 1>(R, r1, dm32);
-}
-
-// MODE 0: plain FP32 iterations on x (rhs g optional), source buffer from the
-//         slot state; the last iteration of the launch may be a measured one.
-// MODE 1: inner sweeps of defect correction on d with rhs r~; `src` is the
-//         buffer holding d (the first launch of a correction, sweep0 == 0,
-//         starts from d = 0 and reads nothing).
-template <int T, int MODE>
-__global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __restrict__ slots, SlotState* states,
-                                                            const Tile* __restrict__ tiles, int ntiles, int nt_req,
-                                                            int src_param, int sweep0) {
-  using Gm = TbGeom<T>;
-  constexpr int kWarps = kTbThreads / 32;
-  extern __shared__ __align__(16) float tb_smem[];
-  float* const S0 = tb_smem;
-  float* const S1 = tb_smem + Gm::R * Gm::C;
-  __shared__ unsigned long long red[kWarps];
-  __shared__ int ctl[5];  // skip, nt, k_end, measure, src
-  __shared__ __align__(16) float gbufs[kWarps][kTbGSlots][Gm::C];  // right-hand-side rows, a ring per warp
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const SlotDesc& sd = slots[tl.slot];
-    SlotState* st = states + tl.slot;
-    if (threadIdx.x == 0) {
-      int skip = *((volatile int*)&st->done);
-      int nt = 0, k_end = 0, measure = 0, src = 0;
-      if (MODE == 0) {
-        const int k0 = *((volatile int*)&st->iters);
-        nt = min(nt_req, sd.max_iters - k0);
-        k_end = k0 + nt;
-        measure = (k_end % sd.K) == 0 || k_end >= sd.max_iters;
-        src = *((volatile int*)&st->xbuf);
-        for (int j = k0 + 1; j < k_end && !skip; ++j)  // the host plan ends launches at measured iterations
-          if ((j % sd.K) == 0) {
-            st->error = 1;
-            st->done = 1;
-            skip = 1;
-          }
-        if (nt <= 0) skip = 1;
-      } else {
-        nt = min(nt_req, sd.inner - sweep0);
-        if (nt <= 0) skip = 1;
-        src = src_param;
-      }
-      ctl[0] = skip; ctl[1] = nt; ctl[2] = k_end; ctl[3] = measure; ctl[4] = src;
-    }
-    __syncthreads();
-    const int skip = ctl[0], nt = ctl[1], k_end = ctl[2], measure = ctl[3], src = ctl[4];
-    __syncthreads();
-    if (skip) continue;
-
-    const int pitch = sd.pitch, n = sd.n;
-    const int base_r = tl.row0 - Gm::HR;
-    const int base_q = tl.col0 - Gm::HQ;
-    const int base_e = base_q + kOff;  // element index of staged column 0 (a multiple of 4)
-    const bool zero_start = (MODE == 1) && sweep0 == 0;
-    // stage both colours: warp per row, lane per float4; rows outside the
-    // array and columns outside the row read as 0
-    for (int row = warp; row < 2 * Gm::R; row += kWarps) {
-      const int c = row >= Gm::R;
-      const int r = row - c * Gm::R;
-      const int i = base_r + r;
-      const int e = base_e + 4 * lane;
-      const bool valid = !zero_start && i >= 0 && i <= n + 1 && e >= 0 && e + 4 <= pitch;
-      const float* gp = valid ? (const float*)sd.x[src][c] + (size_t)i * pitch + e : nullptr;
-      cp_async16((c ? S1 : S0) + r * Gm::C + 4 * lane, gp, valid);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    const float a = sd.a32, b = sd.b32;
-    unsigned dm32 = 0;
-    const bool full = base_q >= 1 && base_q + Gm::C - 1 <= (n >> 1);
-    for (int it = 0; it < nt; ++it) {
-      const bool lastm = (MODE == 0) && measure && it == nt - 1;
-#pragma unroll 1
-      for (int c = 0; c < 2; ++c) {
-        // Phase p = 2it + c + 1 of 2nt: only rows within 2nt - p of the output
-        // rows can still reach them, so the updated band shrinks by one row
-        // at each end per phase (it starts at staged rows 1 .. R-2 when nt = T).
-        const int reach = 2 * nt - (2 * it + c + 1);
-        const int lo = Gm::HR - reach, hi = Gm::HR + tl.nrows + reach;
-        const int seg = (hi - lo + kWarps - 1) / kWarps;
-        const int r0 = lo + warp * seg;
-        const int r1 = min(r0 + seg, hi);
-        float* Sc = c ? S1 : S0;
-        const float* So = c ? S0 : S1;
-        const float* Gc = (const float*)sd.g[c];
-        float* gb = &gbufs[warp][0][0];
-#define TB_PHASE(LM, FL, HG) \
-  tb_phase<T, LM, FL, HG>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb)
-        if (Gc) {
-          if (full) {
-            if (lastm) TB_PHASE(true, true, true); else TB_PHASE(false, true, true);
-          } else {
-            if (lastm) TB_PHASE(true, false, true); else TB_PHASE(false, false, true);
-          }
-        } else {
-          if (full) {
-            if (lastm) TB_PHASE(true, true, false); else TB_PHASE(false, true, false);
-          } else {
-            if (lastm) TB_PHASE(true, false, false); else TB_PHASE(false, false, false);
-          }
-        }
-#undef TB_PHASE
-        __syncthreads();
-      }
-    }
-    // write the centre tile to the other buffer: warp per row, lane per float4
-    const int dst = src ^ 1;
-    for (int row = warp; row < 2 * kTbRows; row += kWarps) {
-      const int c = row >= kTbRows;
-      const int r = row - c * kTbRows;
-      if (r >= tl.nrows) continue;
-      const int col = 4 * lane;
-      if (col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
-      const int i = tl.row0 + r;
-      const int s = (i + c) & 1;
-      const int qlim = (n + s) >> 1;
-      const int qf = base_q + col;
-      if (qf > qlim) continue;
-      float v4[4];
-      load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4);
-      float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
-      if (qf + 3 <= qlim) {
-        store4(Xd, v4);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (qf + v <= qlim) Xd[v] = v4[v];
-      }
-    }
-    if (MODE == 0) {
-      if (measure) {
-        unsigned long long dm = warp_max64(abs_bits_of(__uint_as_float(dm32)));
-        if (lane == 0) red[warp] = dm;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          unsigned long long m = 0;
-          for (int k = 0; k < kWarps; ++k) m = umax64(m, red[k]);
-          if (m) atomicMax(&st->dmax_bits, m);
-        }
-      }
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(&st->arrive, 1u);
-        if (prev == (unsigned)sd.sweep_tiles - 1u) {
-          __threadfence();
-          st->xbuf = src ^ 1;
-          finalize_plain(sd, st, k_end, measure);
-        }
-      }
-    }
-    __syncthreads();  // the next tile reuses the staged arrays
-  }
-}
-
-int tb_out_cols(int T) {
-  switch (T) {
-    case 2: return TbGeom<2>::OQ;
-    case 3: return TbGeom<3>::OQ;
-    case 4: return TbGeom<4>::OQ;
-    case 6: return TbGeom<6>::OQ;
-    case 8: return TbGeom<8>::OQ;
-    default: return kWarpCols;
-  }
-}
-
-// ------------------------------------------------------------------------------------------------
 // residual pass (FP64), both colours per tile
 // ------------------------------------------------------------------------------------------------
 
@@ -1338,7 +929,8 @@ __device__ __forceinline__ void load_u4(const T* X, size_t e, double (&v)[4]) {
 }
 
 // Defect correction, first half of a correction step: u += (double)d over the
-// interior of every pending refine slot (d from buffer dbuf of x), in place.
+// interior of every pending refine slot (d from buffer dbuf of x, or the
+// slot's own SlotDesc::dbuf when dbuf is kDbufPerSlot), in place.
 // Elementwise, so the residual pass that follows reads corrected values
 // without recomputing them for each of a cell's four neighbours.
 __global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict__ slots, SlotState* states,
@@ -1368,7 +960,7 @@ __global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict
         const int qlim = (n + ((i + c) & 1)) >> 1;
         if (q0 > qlim) continue;
         double* U = sd.u[ubuf][c] + eidx(i, q0, pitch);
-        const float* D = (const float*)sd.x[dbuf][c] + eidx(i, q0, pitch);
+        const float* D = (const float*)sd.x[dbuf < 0 ? sd.dbuf : dbuf][c] + eidx(i, q0, pitch);
         double u[4];
         float d[4];
         load4(U, u);
@@ -1680,43 +1272,6 @@ cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const 
   return cudaGetLastError();
 }
 
-template <int T, int MODE>
-static cudaError_t launch_tb_t(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
-                               int nt, int src, int sweep0, cudaStream_t s) {
-  static bool attr_set = false;  // benign race: setting the attribute twice is harmless
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TbGeom<T>::smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (grid <= 0 || grid > ntiles) grid = ntiles;
-  t_launches += 1;
-  k_sweep_tb<T, MODE><<<grid, kTbThreads, TbGeom<T>::smem, s>>>(slots, states, tiles, ntiles, nt, src, sweep0);
-  return cudaGetLastError();
-}
-
-bool tb_depth_supported(int T) { return T == 2 || T == 3 || T == 4 || T == 6 || T == 8; }
-
-cudaError_t launch_sweep_tb(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                            int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-  if (nt < 1 || nt > T) return cudaErrorInvalidValue;
-  switch (T) {
-    case 2: return inner ? launch_tb_t<2, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tb_t<2, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 3: return inner ? launch_tb_t<3, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tb_t<3, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 4: return inner ? launch_tb_t<4, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tb_t<4, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 6: return inner ? launch_tb_t<6, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tb_t<6, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 8: return inner ? launch_tb_t<8, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tb_t<8, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int dbuf, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
@@ -1747,6 +1302,30 @@ cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* state
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// fused FP32 sweeps: the two kernel families behind one interface
+// ------------------------------------------------------------------------------------------------
+
+bool fused_depth_supported(int kind, int T) {
+  return kind == kFusedWave ? wave_depth_supported(T) : tile_depth_supported(T);
+}
+
+int fused_out_cols(int kind, int T) { return kind == kFusedWave ? wave_out_cols(T) : tile_out_cols(T); }
+
+int fused_out_rows(int kind, int n, int T, int sm_count, int seg) {
+  if (kind != kFusedWave) return tile_out_rows();
+  if (seg > 0) return seg < n ? seg : n;
+  return wave_seg_rows(n, T, sm_count);
+}
+
+cudaError_t fused_prepare(int kind, int T) { return kind == kFusedWave ? wave_prepare(T) : tile_prepare(T); }
+
+cudaError_t launch_fused(int kind, bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
+                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s) {
+  return kind == kFusedWave ? launch_sweep_wave(inner, T, slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
+                            : launch_sweep_tile(inner, T, slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
 }
 
 }  // namespace sorgb

@@ -7,6 +7,10 @@
 namespace sorgb {
 
 enum SweepKind : int { kSweepPlain64 = 0, kSweepPlain32 = 1, kSweepInner32 = 2 };
+// dbuf argument of launch_resid: each slot's own SlotDesc::dbuf (slots whose
+// inner sweep counts differ end their corrections in different buffers).
+constexpr int kDbufPerSlot = -1;
+
 enum ResidKind : int { kResidFinal64 = 0, kResidFinal32 = 1, kResidCheck64 = 2, kResidCheck32 = 3, kResidRefine64 = 4 };
 
 struct PackArgs {
@@ -57,17 +61,41 @@ void fast_phase_pack(const FastPhaseArgs& a, void* out);
 // ntiles counts warp strips (one warp each); grid <= 0: one warp per strip.
 cudaError_t launch_sweep_fast64(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
                                 int colour, const FastPhaseArgs& a, bool has_g, cudaStream_t s);
-// FP32 phases fused over nt <= T iterations per tile (temporal blocking);
-// tiles are kTbRows x tb_out_cols(T).  inner: correction sweeps of defect
-// correction (src = buffer holding d, sweep0 = index of the first sweep of
-// this launch within the correction); otherwise plain FP32 iterations
-// (buffer and iteration count from the slot state).  Writes buffer src ^ 1.
-bool tb_depth_supported(int T);
-// Output packed columns of a fused-iteration tile of depth T (tiles are
-// kTbRows rows by tb_out_cols(T) packed columns, starting at column 1).
-int tb_out_cols(int T);
-cudaError_t launch_sweep_tb(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                            int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+// FP32 phases fused over nt <= T iterations per launch (temporal blocking).
+// Two kernel families compute the same iterations bit for bit:
+//   kFusedTile (sor_tile.cu): T iterations per shared-memory tile pass, tiles
+//     of tile_out_rows() output rows; depths 2, 3, 4, 6, 8;
+//   kFusedWave (sor_wf.cu): a register wavefront per warp streaming down a
+//     segment of rows (wave_seg_rows by default); depths 2 .. 5.
+// Tiles are out_rows x fused_out_cols(kind, T) output packed columns starting
+// at column 1.  inner: correction sweeps of defect correction (src = buffer
+// holding d, sweep0 = index of the first sweep of this launch within the
+// correction); otherwise plain FP32 iterations (buffer and iteration count
+// from the slot state).  Writes buffer src ^ 1.
+enum FusedKind : int { kFusedTile = 0, kFusedWave = 1 };
+bool fused_depth_supported(int kind, int T);
+int fused_out_cols(int kind, int T);
+// Output rows per tile: the tile family's fixed height; for the wavefront
+// `seg` when positive, else its default for an n x n plate on sm_count SMs.
+int fused_out_rows(int kind, int n, int T, int sm_count, int seg);
+// Opts the kernels of depth T into their shared memory (call outside graph capture).
+cudaError_t fused_prepare(int kind, int T);
+cudaError_t launch_fused(int kind, bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
+                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+// the two families
+bool tile_depth_supported(int T);
+int tile_out_cols(int T);
+int tile_out_rows();
+cudaError_t tile_prepare(int T);
+cudaError_t launch_sweep_tile(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
+                              int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+bool wave_depth_supported(int T);
+int wave_out_cols(int T);
+int wave_warps_per_sm(int T);
+int wave_seg_rows(int n, int T, int sm_count);
+cudaError_t wave_prepare(int T);
+cudaError_t launch_sweep_wave(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
+                              int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
 // Whole plain solve of a small grid inside one thread-block cluster (one
 // launch runs every iteration and the stopping test); exact-order update.
 bool cluster_solve_fits(bool fp32, int n, int pitch);

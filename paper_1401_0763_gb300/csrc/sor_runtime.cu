@@ -319,22 +319,72 @@ sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s) {
 
 static constexpr int kInflight = 3;
 
-// Iterations fused per tile pass for the FP32 sweeps: the SOR_OPT_TEMPORAL_DEPTH
-// option, 0 = the default depth 6; depths the kernel is not built for round
-// down to the next built one.
-int resolve_tdepth(Ctx* c, const Plan& p) {
-  if (p.kind == kPlain64) return 1;
+// Fused FP32 sweep kernel of an FP32 or defect-correction plan: the family
+// from SOR_OPT_FUSED_KERNEL, by default the tile family while the plate's
+// FP32 state stays near the L2 size (n <= 6144; measured the faster there)
+// and the wavefront family above it; the depth from
+// SOR_OPT_TEMPORAL_DEPTH, by default 6 (tile) or 4 (wavefront), rounded down
+// to a depth the family is built for; rows per tile the family's default.
+static constexpr int kTileFamilyMaxN = 6144;
+
+void resolve_fused(Ctx* c, Plan* p) {
+  if (p->kind == kPlain64) {
+    p->tdepth = 1;
+    return;
+  }
+  const int opt = c->opt_fused_kernel.load();
+  const int fk = opt == 1 ? kFusedTile : opt == 2 ? kFusedWave : (p->n <= kTileFamilyMaxN ? kFusedTile : kFusedWave);
   int t = c->opt_tdepth.load();
-  if (t == 0) t = 6;  // fastest fused depth on 4096^2 FP32 sweeps (2, 3, 4, 6, 8 timed)
-  while (t > 1 && !tb_depth_supported(t)) --t;
-  return std::max(1, t);
+  if (t == 0) t = fk == kFusedWave ? 4 : 6;
+  while (t > 1 && !fused_depth_supported(fk, t)) --t;
+  p->fkind = fk;
+  p->tdepth = std::max(1, t);
+  p->tseg = 0;
+}
+
+// Most tiles a fused-sweep table of an n x n plate can have (wavefront
+// segments of 16 rows, the narrowest output columns).
+static size_t fused_tile_cap(int n) {
+  const Layout L = Layout::make(n);
+  const size_t cols = (L.qmax + 111) / 112 + 1;
+  return cols * ((size_t)(n + 15) / 16 + 1);
+}
+
+// The fused-sweep tile table of the workspace for the plan's kernel family,
+// depth and rows per tile, rebuilt when one of them changes (the graphs
+// cached for the old table are dropped with it).  The stream is idle between
+// solves, so the table is never rewritten under a running launch.
+static sor_status ensure_fused_tiles(Ctx* c, SolveWorkspace* w, const Plan& p) {
+  if (p.kind == kPlain64 || p.tdepth <= 1) return SOR_OK;
+  const int rows = fused_out_rows(p.fkind, p.n, p.tdepth, c->sm_count, p.tseg);
+  if (w->fkind == p.fkind && w->tdepth == p.tdepth && w->tseg_rows == rows) return SOR_OK;
+  if (fused_prepare(p.fkind, p.tdepth) != cudaSuccess) {
+    cudaGetLastError();
+    c->set_error("fused FP32 sweep kernel does not fit");
+    return SOR_ERR_CUDA;
+  }
+  std::vector<Tile> tt;
+  build_tiles(w->slot.L, 0, &tt, nullptr, rows, fused_out_cols(p.fkind, p.tdepth));
+  if (tt.size() > w->tb_cap) {
+    c->set_error("fused-sweep tile table larger than its reservation");
+    return SOR_ERR_INTERNAL;
+  }
+  SOR_CK(c, cudaMemcpyAsync(w->d_tb_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  for (auto& kv : w->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  w->graphs.clear();
+  w->fkind = p.fkind;
+  w->tdepth = p.tdepth;
+  w->tseg_rows = rows;
+  w->n_tb_tiles = (int)tt.size();
+  return SOR_OK;
 }
 
 static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   const bool pingpong = p.tdepth > 1;
-  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f && c->ws->tdepth == p.tdepth) {
+  if (c->ws && c->ws->n == p.n && c->ws->kind == p.kind && c->ws->has_f == p.has_f && c->ws->pingpong == pingpong) {
     *out = c->ws.get();
-    return SOR_OK;
+    return ensure_fused_tiles(c, c->ws.get(), p);
   }
   release_solve_workspace(c);
   auto w = std::make_unique<SolveWorkspace>();
@@ -342,16 +392,15 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->kind = p.kind;
   w->has_f = p.has_f;
   w->pingpong = pingpong;
-  w->tdepth = p.tdepth;
   const Layout L = Layout::make(p.n);
-  std::vector<Tile> st, rt, ft, tt;
+  std::vector<Tile> st, rt, ft;
   build_tiles(L, 0, &st, &rt, kTileRows);
   build_strips(L, 0, c->sm_count * fast_blocks_per_sm() * kWarpsY, &ft);
-  if (p.tdepth > 1) build_tiles(L, 0, &tt, nullptr, kTbRows, tb_out_cols(p.tdepth));
+  w->tb_cap = pingpong ? fused_tile_cap(p.n) : 1;
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
   const size_t small = sizeof(SlotDesc) + sizeof(SlotState) +
-                       (st.size() + rt.size() + ft.size() + tt.size()) * sizeof(Tile) +
+                       (st.size() + rt.size() + ft.size() + w->tb_cap) * sizeof(Tile) +
                        2 * (2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2)) * sizeof(double);  // saved ring
   const size_t total = slot_bytes(p, pingpong) + nat_u + nat_f + small + 4096;
   sor_status rs = ctx_reserve(c, total, false, 0.0);
@@ -372,7 +421,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_sweep_tiles = (Tile*)ctx_dev_alloc(c, st.size() * sizeof(Tile));
   w->d_resid_tiles = (Tile*)ctx_dev_alloc(c, rt.size() * sizeof(Tile));
   w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
-  w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, std::max<size_t>(1, tt.size()) * sizeof(Tile));
+  w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, w->tb_cap * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
@@ -413,9 +462,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->n_sweep_tiles = (int)st.size();
   w->n_resid_tiles = (int)rt.size();
   w->n_fast_tiles = (int)ft.size();
-  w->n_tb_tiles = (int)tt.size();
-  if (!tt.empty())
-    SOR_CK(c, cudaMemcpyAsync(w->d_tb_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  w->n_tb_tiles = 0;
   SOR_CK(c, cudaMemcpyAsync(w->d_sweep_tiles, st.data(), st.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_resid_tiles, rt.data(), rt.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   SOR_CK(c, cudaMemcpyAsync(w->d_fast_tiles, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
@@ -428,7 +475,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   }
   c->ws = std::move(w);
   *out = c->ws.get();
-  return SOR_OK;
+  return ensure_fused_tiles(c, c->ws.get(), p);
 }
 
 // Chunk length (iterations for plain kinds, corrections for refine) between
@@ -438,6 +485,7 @@ static int chunk_length(Ctx* c, const Plan& p) {
   const double cells = (double)p.n * (double)p.n;
   if (p.kind == kRefine) {
     if (opt > 0) return opt;
+    if (p.rchunk > 0) return p.rchunk;
     const double per_step = cells * p.inner;
     int k = (int)std::ceil(4.0e8 / std::max(per_step, 1.0));
     return std::max(1, std::min(k, 16));
@@ -467,7 +515,7 @@ static sor_status enqueue_plain_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, 
     // the residual is tested, so no launch spans a tested iteration
     for (int done = 0; done < L;) {
       const int nt = std::min(p.tdepth, L - done);
-      SOR_CK(c, launch_sweep_tb(false, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt, 0, 0,
+      SOR_CK(c, launch_fused(p.fkind, false, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt, 0, 0,
                                 s));
       done += nt;
     }
@@ -508,7 +556,7 @@ static sor_status enqueue_refine_chunk(Ctx* c, SolveWorkspace* w, const Plan& p,
       SOR_CK(c, launch_resid(kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, dbuf, s));
       for (int j = 0, sw = 0; sw < p.inner; ++j, sw += p.tdepth) {
         const int nt = std::min(p.tdepth, p.inner - sw);
-        SOR_CK(c, launch_sweep_tb(true, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt,
+        SOR_CK(c, launch_fused(p.fkind, true, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt,
                                   (j % 2 == 0) ? 1 : 0, sw, s));
       }
     }
@@ -704,7 +752,7 @@ static sor_status launch_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int L, 
   std::ostringstream key;
   key.precision(17);
   key << p.kind << ":" << p.exact << ":" << p.stop << ":" << p.K << ":" << p.inner << ":" << L << ":" << p.has_f
-      << ":" << p.omega << ":" << p.tdepth << ":" << chain;
+      << ":" << p.omega << ":" << p.tdepth << ":" << p.fkind << ":" << w->tseg_rows << ":" << chain;
   auto it = w->graphs.find(key.str());
   if (it == w->graphs.end()) {
     cudaGraph_t g = nullptr;
@@ -735,18 +783,31 @@ static sor_status solve_locked(Ctx* c, const Plan& p, const double* u0, const do
                                sor_result* res, double t0);
 
 // ------------------------------------------------------------------------------------------------
-// autotuner: iterations fused per tile pass of the FP32 sweeps
+// autotuner: the fused FP32 sweep kernel and the corrections per graph
 // ------------------------------------------------------------------------------------------------
 //
 // On the first FP32 or defect-correction solve of a size bucket (and source
-// presence), each candidate depth runs a short plain FP32 solve on the call's
-// own inputs with the sweep chunks timed by CUDA events; the fastest depth is
-// kept for the bucket.  Every depth gives bit-identical results, so the choice
-// affects time only.  SOR_AUTOTUNE_CACHE names an optional file holding the
-// choices across processes ("<n_bucket> <has_f> <depth>" per line).
+// presence) with SOR_OPT_AUTOTUNE, short solves on the call's own inputs time
+//  * the FP32 sweeps: unfused (one launch per colour phase), the tile family
+//    at depths 2, 3, 4, 6, 8, and the wavefront family at depths 2 .. 5 with
+//    rows per tile {its default, 32, 64, 128} -- a plain FP32 solve of 120
+//    iterations each, its sweep chunks timed with CUDA events;
+//  * for defect correction, with that kernel, the corrections replayed per
+//    graph between host polls (the residual test runs in every correction
+//    regardless; this sets how often the host looks): 1, 2, 4, 8, timed on a
+//    chain of 16 corrections.
+// Every candidate gives bit-identical results, so the choice affects time
+// only.  SOR_AUTOTUNE_CACHE names an optional file holding the choices across
+// processes ("<n_bucket> <has_f> <family> <depth> <rows> <chunk>" per line;
+// lines of three numbers, "<n_bucket> <has_f> <depth>", name a tile-family
+// depth).
 
-static const int kTuneDepths[] = {1, 2, 3, 4, 6, 8};
-static constexpr int kTuneIters = 48;  // a multiple of every candidate depth
+static const int kTuneTileDepths[] = {2, 3, 4, 6, 8};
+static const int kTuneWaveDepths[] = {2, 3, 4, 5};
+static const int kTuneWaveRows[] = {0, 32, 64, 128};
+static const int kTuneChunks[] = {1, 2, 4, 8};
+static constexpr int kTuneIters = 120;   // a multiple of every candidate depth
+static constexpr int kTuneCorrections = 16;
 
 static int n_bucket(int n) {
   int b = 16;
@@ -760,15 +821,35 @@ static std::string tune_key(int n, bool has_f) {
   return os.str();
 }
 
+static bool tune_valid(const TuneChoice& t) {
+  return (t.fkind == kFusedTile || t.fkind == kFusedWave) && (t.tdepth == 1 || fused_depth_supported(t.fkind, t.tdepth)) &&
+         t.tseg >= 0 && t.rchunk >= 0 && t.rchunk <= 64;
+}
+
 void load_tune_cache(Ctx* c) {
   const char* path = std::getenv("SOR_AUTOTUNE_CACHE");
   if (!path || !*path) return;
   FILE* fp = std::fopen(path, "r");
   if (!fp) return;
-  int nb = 0, hf = 0, d = 0;
+  char line[256];
   std::lock_guard<std::mutex> g(c->tune_mu);
-  while (std::fscanf(fp, "%d %d %d", &nb, &hf, &d) == 3)
-    if (tb_depth_supported(d) || d == 1) c->tuned[tune_key(nb, hf != 0)] = d;
+  while (std::fgets(line, sizeof(line), fp)) {
+    int v[6];
+    const int k = std::sscanf(line, "%d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]);
+    TuneChoice t;
+    if (k == 3) {
+      t.fkind = kFusedTile;
+      t.tdepth = v[2];
+    } else if (k == 6) {
+      t.fkind = v[2];
+      t.tdepth = v[3];
+      t.tseg = v[4];
+      t.rchunk = v[5];
+    } else {
+      continue;
+    }
+    if (tune_valid(t)) c->tuned[tune_key(v[0], v[1] != 0)] = t;
+  }
   std::fclose(fp);
 }
 
@@ -777,11 +858,32 @@ static void save_tune_cache(Ctx* c) {
   if (!path || !*path) return;
   FILE* fp = std::fopen(path, "w");
   if (!fp) return;
-  for (const auto& kv : c->tuned) std::fprintf(fp, "%s %d\n", kv.first.c_str(), kv.second);
+  for (const auto& kv : c->tuned)
+    std::fprintf(fp, "%s %d %d %d %d\n", kv.first.c_str(), kv.second.fkind, kv.second.tdepth, kv.second.tseg,
+                 kv.second.rchunk);
   std::fclose(fp);
 }
 
-static sor_status autotune_depth(Ctx* c, const Plan& p, const double* u0, const double* f, int* best_out) {
+// Sweep time of the plain FP32 tuning solve q (the second of two runs: the
+// first builds the tile table and the graphs); result into the workspace.
+static sor_status tune_sweeps(Ctx* c, const Plan& q, const double* u0, const double* f, double* ms) {
+  sor_status rs = SOR_OK;
+  for (int rep = 0; rep < 2 && rs == SOR_OK; ++rep) {
+    {
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.sweep_ms = 0.0;
+    }
+    SolveWorkspace* w = nullptr;
+    rs = get_workspace(c, q, &w);
+    if (rs != SOR_OK) break;
+    rs = solve_locked(c, q, u0, f, w->d_nat_u, nullptr, now_s());
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    *ms = c->stats.sweep_ms;
+  }
+  return rs;
+}
+
+static sor_status autotune(Ctx* c, const Plan& p, const double* u0, const double* f, TuneChoice* out) {
   Plan q = p;
   q.kind = kPlain32;
   q.stop = kStopDelta;
@@ -789,34 +891,64 @@ static sor_status autotune_depth(Ctx* c, const Plan& p, const double* u0, const 
   q.max_iters = kTuneIters;
   q.tol = -1.0;
   q.exact = false;
+  q.stall = 0;
+  q.rchunk = 0;
   const int saved_timing = c->opt_timing.exchange(1);
   sor_stats keep;
   {
     std::lock_guard<std::mutex> g(c->stats_mu);
     keep = c->stats;
   }
-  double best_ms = 1e300;
-  int best = 4;
-  sor_status rs = SOR_OK;
-  for (int d : kTuneDepths) {
-    q.tdepth = d;
-    double ms = 0.0;
-    for (int rep = 0; rep < 2 && rs == SOR_OK; ++rep) {  // the first run builds buffers and graphs
-      {
-        std::lock_guard<std::mutex> g(c->stats_mu);
-        c->stats.sweep_ms = 0.0;
-      }
-      SolveWorkspace* w = nullptr;
-      rs = get_workspace(c, q, &w);
-      if (rs != SOR_OK) break;
-      rs = solve_locked(c, q, u0, f, w->d_nat_u, nullptr, now_s());  // result into the workspace staging
-      std::lock_guard<std::mutex> g(c->stats_mu);
-      ms = c->stats.sweep_ms;
+  std::vector<TuneChoice> cand;
+  cand.push_back(TuneChoice{kFusedTile, 1, 0, 0});
+  for (int d : kTuneTileDepths) cand.push_back(TuneChoice{kFusedTile, d, 0, 0});
+  for (int d : kTuneWaveDepths) {
+    std::vector<int> seen;
+    for (int rows : kTuneWaveRows) {
+      const int eff = fused_out_rows(kFusedWave, p.n, d, c->sm_count, rows);
+      if (std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
+      seen.push_back(eff);
+      cand.push_back(TuneChoice{kFusedWave, d, rows, 0});
     }
+  }
+  double best_ms = 1e300;
+  TuneChoice best = cand[0];
+  sor_status rs = SOR_OK;
+  for (const TuneChoice& t : cand) {
+    q.fkind = t.fkind;
+    q.tdepth = t.tdepth;
+    q.tseg = t.tseg;
+    double ms = 0.0;
+    rs = tune_sweeps(c, q, u0, f, &ms);
     if (rs != SOR_OK) break;
     if (ms < best_ms) {
       best_ms = ms;
-      best = d;
+      best = t;
+    }
+  }
+  if (rs == SOR_OK && p.kind == kRefine) {
+    Plan r = p;
+    r.fkind = best.fkind;
+    r.tdepth = best.tdepth;
+    r.tseg = best.tseg;
+    r.tol = -1.0;  // never converges: a fixed chain of corrections
+    r.stall = 0;
+    r.max_iters = r.inner * kTuneCorrections;
+    double best_s = 1e300;
+    for (int chunk : kTuneChunks) {
+      r.rchunk = chunk;
+      sor_result res;
+      std::memset(&res, 0, sizeof(res));
+      for (int rep = 0; rep < 2 && rs == SOR_OK; ++rep) {  // the first run builds the graphs
+        SolveWorkspace* w = nullptr;
+        rs = get_workspace(c, r, &w);
+        if (rs == SOR_OK) rs = solve_locked(c, r, u0, f, w->d_nat_u, &res, now_s());
+      }
+      if (rs != SOR_OK) break;
+      if (res.device_s < best_s) {
+        best_s = res.device_s;
+        best.rchunk = chunk;
+      }
     }
   }
   c->opt_timing = saved_timing;
@@ -824,7 +956,7 @@ static sor_status autotune_depth(Ctx* c, const Plan& p, const double* u0, const 
     std::lock_guard<std::mutex> g(c->stats_mu);
     c->stats = keep;
   }
-  *best_out = best;
+  *out = best;
   return rs;
 }
 
@@ -834,23 +966,31 @@ sor_status solve_blocking(Ctx* c, const Plan& plan_in, const double* u0, const d
   const double t0 = now_s();
   std::lock_guard<std::mutex> lock(c->solve_mu);
   Plan p = plan_in;
-  p.tdepth = resolve_tdepth(c, p);
-  if (p.kind != kPlain64 && c->opt_tdepth.load() == 0 && c->opt_autotune.load()) {
+  resolve_fused(c, &p);
+  if (p.kind != kPlain64 && c->opt_tdepth.load() == 0 && c->opt_fused_kernel.load() == 0 &&
+      c->opt_autotune.load()) {
     const std::string key = tune_key(p.n, p.has_f || p.kind == kRefine);
-    int d = -1;
+    TuneChoice ch;
+    bool found = false;
     {
       std::lock_guard<std::mutex> g(c->tune_mu);
       auto it = c->tuned.find(key);
-      if (it != c->tuned.end()) d = it->second;
+      if (it != c->tuned.end()) {
+        ch = it->second;
+        found = true;
+      }
     }
-    if (d < 0) {
-      sor_status rs = autotune_depth(c, p, u0, f, &d);
+    if (!found) {
+      sor_status rs = autotune(c, p, u0, f, &ch);
       if (rs != SOR_OK) return rs;
       std::lock_guard<std::mutex> g(c->tune_mu);
-      c->tuned[key] = d;
+      c->tuned[key] = ch;
       save_tune_cache(c);
     }
-    p.tdepth = d;
+    p.fkind = ch.fkind;
+    p.tdepth = ch.tdepth;
+    p.tseg = ch.tseg;
+    p.rchunk = ch.rchunk;
   }
   return solve_locked(c, p, u0, f, u_out, res, t0);
 }

@@ -58,6 +58,9 @@ struct Plan {
   bool exact = false;
   bool has_f = false;
   int tdepth = 1;  // FP32 sweeps: iterations fused per tile pass (1 = one launch per colour phase)
+  int fkind = 0;   // FP32 sweeps: kernel family of the fused sweeps (FusedKind)
+  int tseg = 0;    // FP32 sweeps, wavefront family: output rows per tile (0 = its default)
+  int rchunk = 0;  // defect correction: corrections per graph between polls (0 = by grid size)
   int stall = 0;   // residual tests without a new minimum that end the solve (0 = never)
   int lcap = 0;    // FP64 default path: longest chunk the input magnitudes allow (0 = not yet known)
   double omega = 0.0;
@@ -79,7 +82,8 @@ struct SolveWorkspace {
   int n = -1, kind = -1;
   bool has_f = false;
   bool pingpong = false;
-  int tdepth = 1;
+  int fkind = -1, tdepth = 0, tseg_rows = 0;  // shape of the fused-sweep tile table (ensure_fused_tiles)
+  size_t tb_cap = 0;                          // tiles the table can hold
   SlotBuffers slot;
   SlotDesc* d_desc = nullptr;
   SlotState* d_state = nullptr;
@@ -127,6 +131,13 @@ struct Completed {
   sor_result res{};
 };
 
+// What the autotuner chose for a size bucket: the fused FP32 sweep kernel
+// (family, depth, rows per tile) and the corrections per defect-correction
+// graph.
+struct TuneChoice {
+  int fkind = 0, tdepth = 1, tseg = 0, rchunk = 0;
+};
+
 struct Batcher;
 struct BatcherDeleter {
   void operator()(Batcher* b) const;  // defined in sor_batch.cu
@@ -164,9 +175,10 @@ struct Ctx {
   std::atomic<int> opt_max_slots{0};
   std::atomic<int> opt_cluster{1};
   std::atomic<int> opt_fast_chain{1};
+  std::atomic<int> opt_fused_kernel{0};  // 0: by grid size, 1: tile family, 2: wavefront family
 
   std::mutex tune_mu;
-  std::map<std::string, int> tuned;  // autotuned FP32 depth per "<n bucket> <has source>"
+  std::map<std::string, TuneChoice> tuned;  // autotuned choices per "<n bucket> <has source>"
 
   std::unique_ptr<Batcher, BatcherDeleter> batcher;
   std::mutex batcher_mu;
@@ -193,7 +205,7 @@ void build_strips(const Layout& L, int slot, int warps, std::vector<Tile>* out);
 sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s);
 SlotState initial_state(const Plan& p);
 void release_solve_workspace(Ctx* c);
-int resolve_tdepth(Ctx* c, const Plan& p);
+void resolve_fused(Ctx* c, Plan* p);
 void load_tune_cache(Ctx* c);
 int refine_dbuf(const Plan& p);
 sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out,

@@ -94,11 +94,21 @@ def gaussian_source(n: int, seed: int, count: int = 8) -> np.ndarray:
     c = g.uniform(0.0, 1.0, size=(count, 2))
     h = 1.0 / (n + 1)
     xs = np.arange(1, n + 1, dtype=np.float64) * h
+    ex = [np.exp(-((xs - c[k, 0]) ** 2) / (2.0 * s[k] ** 2)) for k in range(count)]
+    ey = [np.exp(-((xs - c[k, 1]) ** 2) / (2.0 * s[k] ** 2)) for k in range(count)]
+    # f = sum over k of a_k * (ey_k outer ex_k), terms added in order k = 0, 1, ...,
+    # evaluated in blocks of rows that stay in cache (each element is rounded
+    # exactly as in the unblocked expression: outer product, scaling, sum)
     f = np.zeros((n, n))
-    for k in range(count):
-        ex = np.exp(-((xs - c[k, 0]) ** 2) / (2.0 * s[k] ** 2))
-        ey = np.exp(-((xs - c[k, 1]) ** 2) / (2.0 * s[k] ** 2))
-        f += a[k] * np.outer(ey, ex)
+    rows = max(1, (1 << 15) // max(1, n))
+    buf = np.empty((rows, n))
+    for i0 in range(0, n, rows):
+        i1 = min(n, i0 + rows)
+        fb, tb = f[i0:i1], buf[:i1 - i0]
+        for k in range(count):
+            np.multiply.outer(ey[k][i0:i1], ex[k], out=tb)
+            np.multiply(a[k], tb, out=tb)
+            np.add(fb, tb, out=fb)
     return f
 
 

@@ -132,3 +132,32 @@ def test_destroy_with_pending_work():
     with capi.Context(0) as again:
         out, res = again.solve(wl.heat_plate(16, 1.0), tol=1e-8)
         assert res["converged"]
+
+
+@pytest.mark.parametrize("family,depth", [(1, 2), (1, 6), (2, 2), (2, 3), (2, 5)])
+def test_mixed_inner_sweeps_share_the_fused_sweeps(family, depth):
+    """Slots with different inner sweep counts in one batch: the fused sweeps
+    run for the largest count, each slot stops at its own (the kernel takes
+    min(depth, inner - sweep) per slot) and its correction is read from the
+    buffer its own count ends in; every result equals the oracle's defect
+    correction with that slot's count, bit for bit."""
+    capi = capi_mod()
+    counts = [7, 20, 13, 1, 4, 20, 9]
+    with capi.Context(0) as ctx:
+        ctx.set_option(capi.SOR_OPT_FUSED_KERNEL, family)
+        ctx.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, depth)
+        jobs = []
+        for k, inner in enumerate(counts):
+            n = 60 + 37 * k
+            u0, f = wl.poisson_problem(n, 40 + k)
+            u0 = u0 + wl.random_edges(n, 50 + k)
+            w = oracle.omega_opt(n)
+            t, out = ctx.submit(u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-9, max_iters=60000,
+                                inner_sweeps=inner)
+            jobs.append((t, out, u0, f, w, inner))
+        for t, out, u0, f, w, inner in jobs:
+            st, res = ctx.wait(t, 300.0)
+            assert st == capi.SOR_OK, ctx.last_error()
+            ref = oracle.refine(u0, w, f=f, inner_sweeps=inner, tol=1e-9, max_outer=60000 // inner)
+            assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
+            assert np.array_equal(out, ref["u"]), inner

@@ -280,31 +280,41 @@ def test_fp64_rescaled_converges_like_oracle(ctx_mc):
         assert res["converged"] and abs(res["iterations"] - refr["iterations"]) <= K
 
 
+# fused FP32 sweep kernels: (family option, depth); family 1 = tile kernels,
+# 2 = wavefront kernels; depth 1 = unfused (one launch per colour phase)
+FUSED = [(1, 1), (1, 2), (1, 3), (1, 4), (1, 6), (1, 8), (2, 2), (2, 3), (2, 4), (2, 5)]
+FUSED_IDS = ["unfused" if d == 1 else ("tile%d" % d if k == 1 else "wave%d" % d) for k, d in FUSED]
+
+
 @pytest.fixture(scope="module")
 def ctx_depth():
-    """Contexts with each temporal depth of the FP32 sweeps (1 = unfused)."""
+    """Contexts with each fused-sweep kernel family and depth of the FP32 sweeps."""
     from paper_1401_0763_gb300 import _build, capi
     _build.build()
     made = {}
 
-    def get(depth):
-        if depth not in made:
+    def get(shape):
+        family, depth = shape if isinstance(shape, tuple) else (1, shape)
+        if (family, depth) not in made:
             c = capi.Context(0)
+            c.set_option(capi.SOR_OPT_FUSED_KERNEL, family)
             c.set_option(capi.SOR_OPT_TEMPORAL_DEPTH, depth)
             c.set_option(capi.SOR_OPT_CLUSTER, 0)  # keep small grids on the fused-iteration kernel
-            made[depth] = c
-        return made[depth]
+            made[(family, depth)] = c
+        return made[(family, depth)]
     yield get
     for c in made.values():
         c.close()
 
 
-@pytest.mark.parametrize("depth", [1, 2, 3, 4, 6, 8])
+@pytest.mark.parametrize("shape", FUSED, ids=FUSED_IDS)
 @pytest.mark.parametrize("n,K,iters,with_f", [(1, 1, 9, True), (2, 3, 17, False), (63, 5, 43, True),
-                                               (130, 50, 200, False), (257, 7, 61, True)])
-def test_fp32_fused_iterations_bitwise(ctx_depth, depth, n, K, iters, with_f):
+                                               (130, 50, 200, False), (257, 7, 61, True), (600, 13, 52, True),
+                                               (601, 10, 40, False)])
+def test_fp32_fused_iterations_bitwise(ctx_depth, shape, n, K, iters, with_f):
     capi = capi_mod()
-    ctx = ctx_depth(depth)
+    depth = shape[1]
+    ctx = ctx_depth(shape)
     u0 = wl.random_edges(n, n + depth)
     f = wl.gaussian_source(n, K) * 25 if with_f else None
     w = oracle.omega_opt(n)
@@ -315,10 +325,10 @@ def test_fp32_fused_iterations_bitwise(ctx_depth, depth, n, K, iters, with_f):
     assert res["final_maxdelta"] == ref["final_maxdelta"]
 
 
-@pytest.mark.parametrize("depth", [1, 3, 4, 8])
-def test_fp32_fused_converges_like_oracle(ctx_depth, depth):
+@pytest.mark.parametrize("shape", FUSED, ids=FUSED_IDS)
+def test_fp32_fused_converges_like_oracle(ctx_depth, shape):
     capi = capi_mod()
-    ctx = ctx_depth(depth)
+    ctx = ctx_depth(shape)
     n = 150
     u0 = wl.heat_plate(n, 100.0)
     w = oracle.omega_opt(n)
@@ -328,11 +338,12 @@ def test_fp32_fused_converges_like_oracle(ctx_depth, depth):
     assert np.array_equal(got, ref["u"])
 
 
-@pytest.mark.parametrize("depth", [1, 2, 4, 6, 8])
-@pytest.mark.parametrize("n,inner", [(2, 20), (63, 20), (200, 7), (129, 1)])
-def test_refine_fused_bitwise(ctx_depth, depth, n, inner):
+@pytest.mark.parametrize("shape", FUSED, ids=FUSED_IDS)
+@pytest.mark.parametrize("n,inner", [(2, 20), (63, 20), (200, 7), (129, 1), (600, 20)])
+def test_refine_fused_bitwise(ctx_depth, shape, n, inner):
     capi = capi_mod()
-    ctx = ctx_depth(depth)
+    depth = shape[1]
+    ctx = ctx_depth(shape)
     u0, f = wl.poisson_problem(n, n + depth)
     u0 = u0 + wl.random_edges(n, n)
     w = oracle.omega_opt(n)
@@ -343,10 +354,13 @@ def test_refine_fused_bitwise(ctx_depth, depth, n, inner):
     assert np.array_equal(got, ref["u"])
 
 
-def test_fp32_fused_full_size(ctx_depth):
-    """4098^2 FP32 plate at the default depth, 100 iterations, against the oracle."""
+@pytest.mark.parametrize("shape", [(1, 6), (2, 2), (2, 4)], ids=["tile6", "wave2", "wave4"])
+def test_fp32_fused_full_size(ctx_depth, shape):
+    """4098^2 FP32 plate, 100 iterations (a launch of fewer iterations than the
+    depth at the end of each tested chunk of 50 for depths that do not divide
+    it), against the oracle."""
     capi = capi_mod()
-    ctx = ctx_depth(4)
+    ctx = ctx_depth(shape)
     n = 4096
     u0 = wl.random_edges(n, 1)
     w = oracle.omega_opt(n)
@@ -376,9 +390,13 @@ def test_autotuner_picks_a_depth_and_keeps_results(tmp_path, monkeypatch):
         refr = oracle.refine(u0p, w, f=f, inner_sweeps=20, tol=1e-10, max_outer=1000)
         assert np.array_equal(got, refr["u"]) and res["outer_steps"] == refr["outer_steps"]
         assert ctx.stats()["solves"] == 2  # tuning runs are not counted
-    lines = [l.split() for l in cache.read_text().splitlines()]
-    assert {(int(a), int(b)) for a, b, _ in lines} == {(512, 0), (512, 1)}
-    assert all(int(d) in (1, 2, 3, 4, 6, 8) for _, _, d in lines)
+    lines = [[int(x) for x in l.split()] for l in cache.read_text().splitlines()]
+    assert {(a, b) for a, b, *_ in lines} == {(512, 0), (512, 1)}
+    for _, _, family, depth, rows, chunk in lines:
+        assert (family, depth) in [(0, 1)] + [(0, d) for d in (2, 3, 4, 6, 8)] + [(1, d) for d in (2, 3, 4, 5)]
+        assert rows in (0, 32, 64, 128) and chunk in (0, 1, 2, 4, 8)
+    refine_line = [l for l in lines if l[1] == 1][0]
+    assert refine_line[5] in (1, 2, 4, 8)  # the refine solve also tuned its corrections per graph
 
 
 @pytest.mark.parametrize("path", PATHS)

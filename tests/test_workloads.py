@@ -29,3 +29,24 @@ def test_heat_plate_edges():
     for e in ("north", "south", "west", "east"):
         u = wl.heat_plate(5, 100.0, e)
         assert u.sum() == 100.0 * 7
+
+
+def _gaussian_source_unblocked(n, seed, count=8):
+    """The Gaussian sum written term by term on whole arrays (the blocked
+    generator must give the same bits)."""
+    g = wl.rng(seed)
+    a = g.uniform(-1.0, 1.0, size=count)
+    s = g.uniform(0.02, 0.2, size=count)
+    c = g.uniform(0.0, 1.0, size=(count, 2))
+    xs = np.arange(1, n + 1, dtype=np.float64) * (1.0 / (n + 1))
+    f = np.zeros((n, n))
+    for k in range(count):
+        ex = np.exp(-((xs - c[k, 0]) ** 2) / (2.0 * s[k] ** 2))
+        ey = np.exp(-((xs - c[k, 1]) ** 2) / (2.0 * s[k] ** 2))
+        f += a[k] * np.outer(ey, ex)
+    return f
+
+
+def test_gaussian_source_blocked_equals_unblocked():
+    for n in (1, 7, 300, 4097):
+        assert np.array_equal(wl.gaussian_source(n, n), _gaussian_source_unblocked(n, n))
