@@ -216,6 +216,19 @@ sor_status sor_diag_flow_wait(sor_ctx *ctx, int polls, int preset, int *timed_ou
  * output. */
 sor_status sor_diag_fp64_rate(sor_ctx *ctx, int kind, double *ops_per_s);
 
+/* Diagnostic of the debug build's device-side index checks (no counterpart
+ * in the paper: a test aid).  A library compiled with SOR_DEBUG_BOUNDS
+ * checks, before a kernel touches a tile of a plate (pack, the colour-phase
+ * sweeps, the fused FP32 sweeps, the residual and correction passes), that
+ * the rows and columns it will read and write lie inside the slot's arrays;
+ * a tile that does not is skipped and the solve returns SOR_ERR_INTERNAL
+ * ("device-side index check failed") instead of touching memory outside
+ * them.  This call sends one index below a one-element range through the
+ * check (no memory is accessed at it) and sets *fired = 1 when the check
+ * refused it and recorded the error, 0 in release builds, where the checks
+ * are compiled away.  SOR_ERR_INVALID_ARG for a NULL output. */
+sor_status sor_diag_bounds(sor_ctx *ctx, int *fired);
+
 /* Non-blocking submission to the context's continuous-batching scheduler.
  * u0 and f are copied before the call returns.  u_out must stay valid until
  * sor_poll / sor_wait reports SOR_OK for the ticket; it is written then.
@@ -223,6 +236,21 @@ sor_status sor_diag_fp64_rate(sor_ctx *ctx, int kind, double *ops_per_s);
  * budget, and every admitted request is stepped together with the others. */
 sor_status sor_batch_submit(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f,
                             double *u_out, uint64_t *ticket);
+
+/* Non-blocking submission of a cube solve (the 3D 7-point red-black SOR of
+ * sor_solve3d, with the same parameters, FP64 / FP32 / FP32_REFINE) to the
+ * context's scheduler.  u0 ((N+2)^3) and f (N^3 or NULL) are copied before
+ * the call returns; u_out must stay valid until sor_poll / sor_wait report
+ * SOR_OK for the ticket.  Cube requests are solved whole, in arrival order,
+ * by up to four worker threads, each on its own CUDA stream, concurrently
+ * with the plates the scheduler steps and with each other; each waits for
+ * device memory under the context's budget (SOR_ERR_BUDGET at submit only
+ * when it needs more than the whole budget).  The result equals
+ * sor_solve3d's for the same arguments, bit for bit.  Tickets are shared with
+ * sor_batch_submit.  sor_destroy cancels queued cube requests and stops
+ * running ones at their next chunk boundary (SOR_ERR_CANCELLED). */
+sor_status sor_batch_submit3d(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f,
+                              double *u_out, uint64_t *ticket);
 
 /* SOR_NOT_READY while the ticket is queued or running; SOR_OK (and *res)
  * once u_out holds the result -- the ticket is then retired; the solve's own
@@ -252,16 +280,22 @@ typedef enum {
                                   the corrections per graph, and keep the fastest (results are the
                                   same bit for bit whichever is chosen) */
   SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
-  SOR_OPT_CLUSTER = 7,         /* 1 (default): plain solves of grids small enough for one thread-block
-                                  cluster (N <= 384 in FP64, N <= 768 in FP32) run all their iterations
-                                  in a single launch, exact operation order; 0: never */
+  SOR_OPT_CLUSTER = 7,         /* plain solves of small plates (N <= 384 in FP64, N <= 768 in FP32) in a
+                                  single launch, exact operation order: 1 (default) = on a cooperative
+                                  grid of many SMs when the stop test is max|change|, else in one
+                                  thread-block cluster; 2 = always the cluster; 0 = never */
   SOR_OPT_FAST_CHAIN = 8,      /* 1 (default): the FP64 default path runs each chunk of iterations in one
                                   cooperative launch with neighbour-to-neighbour progress counters; 0: one
                                   launch per colour phase.  Results are identical either way */
-  SOR_OPT_FUSED_KERNEL = 9     /* FP32 sweeps: 0 (default) = chosen by grid size (tile kernels up to
+  SOR_OPT_FUSED_KERNEL = 9,    /* FP32 sweeps: 0 (default) = chosen by grid size (tile kernels up to
                                   N = 6144, wavefront kernels above) or by the autotuner; 1 = tile
                                   kernels (a shared-memory tile pass per launch); 2 = wavefront kernels
                                   (a register wavefront per warp).  Results are identical either way */
+  SOR_OPT_BATCH_PLAIN_STEP = 10 /* iterations per scheduler step of plain (FP64 / FP32) batch slots:
+                                   0 (default) = tuned online over the scheduler's first rounds with
+                                   plain slots (8, 16, 32, 64 tried, the highest update rate kept);
+                                   > 0 = that many.  Results are identical either way: every slot
+                                   stops on the device at its own tested iteration */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);
@@ -279,6 +313,7 @@ typedef struct {
   uint64_t bytes_reserved;    /* device bytes currently held for solves */
   uint64_t bytes_peak;        /* high-water mark of bytes_reserved */
   uint64_t kernel_launches;   /* kernel launches of sor_solve calls, every kind (graph replays included) */
+  uint64_t batch_plain_step;  /* iterations per scheduler step of plain batch slots in use (0 = none yet) */
 } sor_stats;
 
 sor_status sor_get_stats(sor_ctx *ctx, sor_stats *out);

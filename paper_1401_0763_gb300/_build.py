@@ -16,8 +16,12 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsorgb.so")
+# debug variant: device-side index checks (SOR_DEBUG_BOUNDS) that turn an
+# access outside a slot's arrays into a solve error instead of a fault
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libsorgb.so")
 SOURCES = ["sor_kernels.cu", "sor_cluster.cu", "sor_runtime.cu", "sor_batch.cu", "sor_capi.cu", "sor_static.cu",
-           "sor3d.cu", "sor9.cu", "sor_probe.cu", "sor_wf.cu", "sor_tile.cu"]
+           "sor3d.cu", "sor9.cu", "sor_probe.cu", "sor_wf.cu", "sor_tile.cu", "sor_grid.cu"]
 HEADERS = ["sor_device.cuh", "sor_devfn.cuh", "sor_bits.cuh", "sor_strips.cuh", "sor_kernels.h", "sor_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -37,18 +41,21 @@ def _stamp() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     """Compile and link; returns the library path.  Skips work when the
-    library is newer than every source."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _stamp():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    library is newer than every source.  debug=True builds the variant with
+    device-side index checks into its own directory."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _stamp():
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     objs = []
+    extra = ["-DSOR_DEBUG_BOUNDS"] if debug else []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -58,13 +65,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

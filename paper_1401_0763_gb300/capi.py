@@ -47,11 +47,12 @@ SOR_OPT_BATCH_MAX_SLOTS = 6
 SOR_OPT_CLUSTER = 7
 SOR_OPT_FAST_CHAIN = 8
 SOR_OPT_FUSED_KERNEL = 9
+SOR_OPT_BATCH_PLAIN_STEP = 10
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
             "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d",
-            "sor_solve9", "sor_diag_flow_wait", "sor_diag_fp64_rate")
+            "sor_solve9", "sor_diag_flow_wait", "sor_diag_fp64_rate", "sor_diag_bounds", "sor_batch_submit3d")
 
 
 class sor_params(ctypes.Structure):
@@ -76,7 +77,8 @@ class sor_stats(ctypes.Structure):
                 ("sweep_launches", ctypes.c_uint64), ("lattice_updates", ctypes.c_uint64),
                 ("sweep_ms", ctypes.c_double), ("timed_launches", ctypes.c_uint64),
                 ("timed_updates", ctypes.c_uint64), ("bytes_reserved", ctypes.c_uint64),
-                ("bytes_peak", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+                ("bytes_peak", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("batch_plain_step", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,7 +92,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the debug variant (device-side index
+    checks) when SOR_DEBUG_BOUNDS=1 is set in the environment."""
+    return _build.LIB_DEBUG if os.environ.get("SOR_DEBUG_BOUNDS") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -99,7 +103,8 @@ def load(build_if_missing: bool = False):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build() if build_if_missing else _build.LIB
+        debug = os.environ.get("SOR_DEBUG_BOUNDS") == "1"
+        path = _build.build(debug=debug) if build_if_missing else library_path()
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with paper_1401_0763_gb300._build.build() "
                                "(the CUDA library is required; there is no CPU fallback)")
@@ -115,6 +120,7 @@ def load(build_if_missing: bool = False):
         lib.sor_solve9.argtypes = lib.sor_solve.argtypes
         lib.sor_batch_submit.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, P(ctypes.c_uint64)]
+        lib.sor_batch_submit3d.argtypes = lib.sor_batch_submit.argtypes
         lib.sor_poll.argtypes = [ctypes.c_void_p, ctypes.c_uint64, P(sor_result)]
         lib.sor_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double, P(sor_result)]
         lib.sor_destroy.argtypes = [ctypes.c_void_p]
@@ -128,6 +134,7 @@ def load(build_if_missing: bool = False):
         lib.sor_solve_static.argtypes = [P(sor_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          P(sor_result), ctypes.c_void_p]
         lib.sor_diag_fp64_rate.argtypes = [ctypes.c_void_p, ctypes.c_int32, dp]
+        lib.sor_diag_bounds.argtypes = [ctypes.c_void_p, P(ctypes.c_int32)]
         lib.sor_omega_opt.argtypes = [ctypes.c_int32]
         lib.sor_omega_opt.restype = ctypes.c_double
         for name in EXPORTED:
@@ -303,6 +310,14 @@ class Context:
         self._check(st, "sor_diag_fp64_rate")
         return out.value
 
+    def diag_bounds(self) -> int:
+        """sor_diag_bounds: 1 when the device-side index checks are compiled
+        in (debug build) and refuse an out-of-range index, else 0."""
+        out = ctypes.c_int32(-1)
+        st = self._lib.sor_diag_bounds(self._h, ctypes.byref(out))
+        self._check(st, "sor_diag_bounds")
+        return out.value
+
     def solve9_raw(self, params: sor_params, u0_ptr, f_ptr, out_ptr):
         """sor_solve9 on raw addresses; returns (status, result)."""
         res = sor_result()
@@ -338,6 +353,26 @@ class Context:
                                         ctypes.c_void_p(_ptr(f)) if f is not None else None,
                                         ctypes.c_void_p(_ptr(out)), ctypes.byref(t))
         self._check(st, "sor_batch_submit")
+        self._keep[t.value] = out
+        return t.value, out
+
+    def submit3d(self, u0, f=None, out=None, **kw):
+        """sor_batch_submit3d (a cube request); returns (ticket, out).  Keep
+        ``out`` alive until the ticket completes (this object also holds a
+        reference)."""
+        n = int(u0.shape[0]) - 2
+        if tuple(u0.shape) != (n + 2,) * 3:
+            raise ValueError("u0 must be (n+2, n+2, n+2)")
+        if f is not None and tuple(f.shape) != (n,) * 3:
+            raise ValueError("f must be (n, n, n)")
+        if out is None:
+            out = np.empty_like(u0) if isinstance(u0, np.ndarray) else u0.new_empty(u0.shape)
+        p = make_params(n, **kw)
+        t = ctypes.c_uint64()
+        st = self._lib.sor_batch_submit3d(self._h, ctypes.byref(p), ctypes.c_void_p(_ptr(u0)),
+                                          ctypes.c_void_p(_ptr(f)) if f is not None else None,
+                                          ctypes.c_void_p(_ptr(out)), ctypes.byref(t))
+        self._check(st, "sor_batch_submit3d")
         self._keep[t.value] = out
         return t.value, out
 

@@ -988,8 +988,12 @@ struct Buffers3 {
   }
 };
 
+// One cube solve on stream s (the context's stream for sor_solve3d, a worker's
+// own stream for batched cube requests).  wait_budget: wait for device memory
+// under the context's budget instead of failing (batched requests).
 template <typename T>
-sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out, sor_result* res) {
+sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out, sor_result* res,
+                 cudaStream_t s, bool wait_budget) {
   const double t0 = now_s();
   const int n = p->n, m = n + 2;
   const Layout L = Layout::make(n);
@@ -1034,7 +1038,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   if (has_f && !f_dev) bytes += nf * sizeof(double);
   Buffers3 B;
   B.c = c;
-  sor_status rs = ctx_reserve(c, bytes, false, 0.0);
+  sor_status rs = ctx_reserve(c, bytes, wait_budget, -1.0);
   if (rs != SOR_OK) {
     c->set_error("3D solve does not fit the device-memory budget");
     return rs;
@@ -1069,7 +1073,6 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
-  cudaStream_t s = c->stream;
 
   Desc3 d;
   std::memset(&d, 0, sizeof(d));
@@ -1242,6 +1245,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   long long planned = 0;
   bool finished = st.done != 0;
   while (!finished && planned < p->max_iters) {
+    if (c->closing.load()) return SOR_ERR_CANCELLED;  // the context is being destroyed
     int Lc = (int)std::min<long long>(chunk, p->max_iters - planned);
     if (d.K > chunk0)  // batches end at tested iterations: few distinct chunk lengths
       Lc = (int)std::min<long long>(Lc, std::min<long long>((planned / d.K + 1) * d.K, p->max_iters) - planned);
@@ -1323,7 +1327,7 @@ __global__ void k_flow_wait_probe(const unsigned* progress, int polls, int* time
 // inner times; once the test passes, the device skips the remaining sweeps
 // and corrections, and the host stops at its next poll.
 sor_status run3d_refine(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
-                        sor_result* res) {
+                        sor_result* res, cudaStream_t s, bool wait_budget) {
   const double t0 = now_s();
   const int n = p->n, m = n + 2;
   const Layout L = Layout::make(n);
@@ -1359,7 +1363,7 @@ sor_status run3d_refine(Ctx* c, const sor_params* p, const double* u0, const dou
   if (has_f && !f_dev) bytes += nf * sizeof(double);
   Buffers3 B;
   B.c = c;
-  sor_status rs = ctx_reserve(c, bytes, false, 0.0);
+  sor_status rs = ctx_reserve(c, bytes, wait_budget, -1.0);
   if (rs != SOR_OK) {
     c->set_error("3D solve does not fit the device-memory budget");
     return rs;
@@ -1385,7 +1389,6 @@ sor_status run3d_refine(Ctx* c, const sor_params* p, const double* u0, const dou
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
-  cudaStream_t s = c->stream;
   float* dcol[2] = {dbuf, dbuf + elems};
   float* rcol[2] = {rbuf, rbuf + elems};
 
@@ -1529,6 +1532,7 @@ sor_status run3d_refine(Ctx* c, const sor_params* p, const double* u0, const dou
   const int per_poll = (int)std::max(1.0, std::min(32.0, std::floor(1e-3 / step_s)));
   int planned = 0, batch = 0;
   while (planned < max_outer) {
+    if (c->closing.load()) return SOR_ERR_CANCELLED;  // the context is being destroyed
     const int kk = std::min(per_poll, max_outer - planned);
     for (int j = 0; j < kk; ++j) {
       if (use_graphs) {
@@ -1610,9 +1614,7 @@ sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out) {
   return SOR_OK;
 }
 
-sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
-                            sor_result* res) {
-  NvtxRange nvtx("sor_solve3d");
+sor_status check_params3d(Ctx* c, const sor_params* p, const double* u0, const double* u_out) {
   if (!p || !u0 || !u_out) {
     c->set_error("params, u0 and u_out must be non-NULL");
     return SOR_ERR_INVALID_ARG;
@@ -1632,8 +1634,38 @@ sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const
     c->set_error(why.str());
     return SOR_ERR_INVALID_ARG;
   }
-  if (p->precision == SOR_FP32_REFINE) return run3d_refine(c, p, u0, f, u_out, res);
-  return p->precision == SOR_FP64 ? run3d<double>(c, p, u0, f, u_out, res) : run3d<float>(c, p, u0, f, u_out, res);
+  return SOR_OK;
+}
+
+sor_status run_cube(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out, sor_result* res,
+                    cudaStream_t s, bool wait_budget) {
+  if (p->precision == SOR_FP32_REFINE) return run3d_refine(c, p, u0, f, u_out, res, s, wait_budget);
+  return p->precision == SOR_FP64 ? run3d<double>(c, p, u0, f, u_out, res, s, wait_budget)
+                                  : run3d<float>(c, p, u0, f, u_out, res, s, wait_budget);
+}
+
+// Device bytes a cube solve reserves at most (the sum run3d and run3d_refine
+// reserve, taken for the larger of the two and with every staging copy).
+size_t cube_bytes(const sor_params* p, bool has_f) {
+  const int n = p->n, m = n + 2;
+  const Layout L = Layout::make(n);
+  const size_t elems = (size_t)m * m * L.pitch;
+  const size_t ncube = (size_t)m * m * m, nf = (size_t)n * n * n;
+  size_t b = 4 * elems * sizeof(double);      // iterate or solution ping-pong pairs
+  b += 4 * elems * sizeof(float);              // correction pair and its right side
+  if (has_f) b += 2 * elems * sizeof(double) + nf * sizeof(double);
+  b += ncube * sizeof(double);                 // staging
+  b += 2 * 2 * ((size_t)m * L.pitch * 4 + (size_t)m * m * 4) * sizeof(double);  // shells
+  b += (size_t)64 << 20;                       // tile, strip and phase tables, counters
+  return b;
+}
+
+sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                            sor_result* res) {
+  NvtxRange nvtx("sor_solve3d");
+  const sor_status rs = check_params3d(c, p, u0, u_out);
+  if (rs != SOR_OK) return rs;
+  return run_cube(c, p, u0, f, u_out, res, c->stream, false);
 }
 
 }  // namespace sorgb

@@ -34,7 +34,12 @@ namespace sorgb {
     }                                                                                              \
   } while (0)
 
-static constexpr int kPlainStepIters = 16;  // iterations per scheduler step for plain slots
+// Iterations per scheduler step for plain slots: tried online in this order,
+// kPlainTrialRounds rounds each, and the one with the highest update rate is
+// kept (SOR_OPT_BATCH_PLAIN_STEP fixes it instead).
+static constexpr int kPlainStepCand[] = {8, 16, 32, 64};
+static constexpr int kPlainCands = 4;
+static constexpr int kPlainTrialRounds = 2;
 static constexpr int kBatchSegRows = 64;    // output rows per fused-sweep tile (many slots fill the GPU)
 
 struct Batcher {
@@ -72,9 +77,22 @@ struct Batcher {
   uint64_t version = 0;       // bumps when the active set changes
   uint64_t graph_version = ~0ull;
   int graph_steps = 0;
+  int graph_plain_step = 0;
+  int plain_step = 0;                       // tuned iterations per step of plain slots (0: trial running)
+  int plain_trial = 0;                      // trial rounds done
+  double plain_rate[kPlainCands] = {};      // plain lattice updates per second, summed per candidate
+  int plain_rounds[kPlainCands] = {};
   cudaGraphExec_t graph = nullptr;
   size_t reserved_tables = 0;
+
+  // cube requests: solved whole, each by one of up to kCubeWorkers threads on
+  // its own stream, concurrently with the plate steps and with each other
+  std::deque<std::unique_ptr<Request>> cube_queue;
+  std::vector<std::thread> cube_workers;
+  int cube_busy = 0;
 };
+
+static constexpr int kCubeWorkers = 4;
 
 static sor_status ensure_tables(Batcher* b, int cap, size_t ntiles) {
   Ctx* c = b->c;
@@ -172,6 +190,14 @@ static sor_status rebuild_tiles(Batcher* b) {
 }
 
 // The launches of one scheduler step over every active slot.
+// Iterations per scheduler step of plain slots this round.
+static int plain_step_len(const Batcher* b) {
+  const int opt = b->c->opt_plain_step.load();
+  if (opt > 0) return opt;
+  if (b->plain_step > 0) return b->plain_step;
+  return kPlainStepCand[std::min(kPlainCands - 1, b->plain_trial / kPlainTrialRounds)];
+}
+
 static sor_status enqueue_step(Batcher* b) {
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
@@ -198,7 +224,8 @@ static sor_status enqueue_step(Batcher* b) {
     if (!nt) continue;
     const Tile* t = b->d_tiles + (kind == 0 ? b->off_p64 : b->off_p32);
     const SweepKind sk = kind == 0 ? kSweepPlain64 : kSweepPlain32;
-    for (int it = 0; it < kPlainStepIters; ++it) {
+    const int iters = plain_step_len(b);
+    for (int it = 0; it < iters; ++it) {
       SOR_BCK(launch_sweep(sk, b->d_desc, b->d_state, t, nt, 0, 0, 0, s));
       SOR_BCK(launch_sweep(sk, b->d_desc, b->d_state, t, nt, 0, 1, 0, s));
       if (b->any_resid_stop)
@@ -216,7 +243,7 @@ static int steps_per_round(const Batcher* b) {
   for (const auto& r : b->slots)
     if (r) {
       cells += (double)r->plan.n * r->plan.n;
-      sweeps = std::max(sweeps, (double)(r->plan.kind == kRefine ? r->plan.inner : kPlainStepIters));
+      sweeps = std::max(sweeps, (double)(r->plan.kind == kRefine ? r->plan.inner : plain_step_len(b)));
     }
   const double step_s = cells * sweeps / 4.0e11 + 40e-6;  // rough cost of one step
   return (int)std::max(1.0, std::min(16.0, std::floor(400e-6 / step_s)));
@@ -233,7 +260,7 @@ static sor_status run_step(Batcher* b, int* steps_out) {
     }
     return SOR_OK;
   }
-  if (b->graph_version != b->version || !b->graph || b->graph_steps != m) {
+  if (b->graph_version != b->version || !b->graph || b->graph_steps != m || b->graph_plain_step != plain_step_len(b)) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);
       b->graph = nullptr;
@@ -253,6 +280,7 @@ static sor_status run_step(Batcher* b, int* steps_out) {
     SOR_BCK(e);
     b->graph_version = b->version;
     b->graph_steps = m;
+    b->graph_plain_step = plain_step_len(b);
   }
   SOR_BCK(cudaGraphLaunch(b->graph, b->stream));
   return SOR_OK;
@@ -493,6 +521,7 @@ static void scheduler_main(Batcher* b) {
       }
     }
     sor_status rs = SOR_OK;
+    std::vector<int> new_slots;  // slots activated this round (their host state copy is stale)
     for (auto& r : admitted) {
       int sidx = -1;
       for (size_t k = 0; k < b->slots.size(); ++k)
@@ -513,10 +542,27 @@ static void scheduler_main(Batcher* b) {
         continue;
       }
       b->slots[sidx] = std::move(r);
+      new_slots.push_back(sidx);
     }
     if (rs == SOR_OK && !admitted.empty()) {
       NvtxRange nvtx("sor_admit");
       rs = rebuild_tiles(b);
+    }
+    // online trial of the plain slots' step length: this round's update rate
+    std::vector<std::pair<int, int>> plain_before;  // (slot, iterations before the round)
+    int cand = -1;
+    double t_round = 0.0;
+    if (c->opt_plain_step.load() == 0 && b->plain_step == 0) {
+      for (size_t k = 0; k < b->slots.size(); ++k) {
+        const Request* r = b->slots[k].get();
+        if (!r || r->plan.kind == kRefine) continue;
+        const bool fresh = std::find(new_slots.begin(), new_slots.end(), (int)k) != new_slots.end();
+        plain_before.emplace_back((int)k, fresh ? 0 : b->h_state[k].iters);
+      }
+      if (!plain_before.empty()) {
+        cand = std::min(kPlainCands - 1, b->plain_trial / kPlainTrialRounds);
+        t_round = now_s();
+      }
     }
     if (rs == SOR_OK && active_count(b) > 0) {
       NvtxRange nvtx("sor_step");
@@ -537,6 +583,36 @@ static void scheduler_main(Batcher* b) {
         c->set_error(cudaGetErrorString(e));
         rs = SOR_ERR_CUDA;
       }
+    }
+    if (rs == SOR_OK && cand >= 0) {
+      double upd = 0.0;
+      for (const auto& pb : plain_before) {
+        const double nn = (double)b->slots[pb.first]->plan.n;
+        upd += (double)(b->h_state[pb.first].iters - pb.second) * nn * nn;
+      }
+      const double dt = now_s() - t_round;
+      if (dt > 0.0 && upd > 0.0) {
+        b->plain_rate[cand] += upd / dt;
+        b->plain_rounds[cand] += 1;
+        if (++b->plain_trial >= kPlainCands * kPlainTrialRounds) {
+          int best = 1;
+          double best_rate = -1.0;
+          for (int k = 0; k < kPlainCands; ++k)
+            if (b->plain_rounds[k] > 0 && b->plain_rate[k] / b->plain_rounds[k] > best_rate) {
+              best_rate = b->plain_rate[k] / b->plain_rounds[k];
+              best = k;
+            }
+          b->plain_step = kPlainStepCand[best];
+        }
+      }
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.batch_plain_step = (unsigned long long)plain_step_len(b);
+    } else if (rs == SOR_OK && c->opt_plain_step.load() > 0) {
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.batch_plain_step = (unsigned long long)c->opt_plain_step.load();
+    } else if (rs == SOR_OK && b->plain_step > 0) {
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.batch_plain_step = (unsigned long long)b->plain_step;
     }
     if (rs == SOR_OK) {
       std::vector<int> fin;
@@ -565,6 +641,43 @@ static void scheduler_main(Batcher* b) {
 }
 
 void BatcherDeleter::operator()(Batcher* b) const { delete b; }
+
+// A cube worker: takes cube requests in arrival order and solves each on its
+// own stream (the cube kernels of sor_solve3d), waiting for device memory under
+// the context's budget; results complete their tickets like plates do.
+static void cube_worker(Batcher* b) {
+  Ctx* c = b->c;
+  cudaSetDevice(c->device);
+  cudaStream_t s = nullptr;
+  const bool have_stream = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+  for (;;) {
+    std::unique_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> g(b->mu);
+      b->cv.wait(g, [&] { return b->stop || !b->cube_queue.empty(); });
+      if (b->stop) break;
+      r = std::move(b->cube_queue.front());
+      b->cube_queue.pop_front();
+      b->cube_busy += 1;
+    }
+    sor_result res;
+    std::memset(&res, 0, sizeof(res));
+    sor_status st = have_stream ? run_cube(c, &r->p3, r->u0.data(), r->f.empty() ? nullptr : r->f.data(), r->u_out,
+                                           &res, s, true)
+                                : SOR_ERR_CUDA;
+    res.latency_s = now_s() - r->t_submit;
+    {
+      std::lock_guard<std::mutex> g(c->stats_mu);
+      c->stats.batch_completed += 1;
+    }
+    {
+      std::lock_guard<std::mutex> g(b->mu);
+      b->cube_busy -= 1;
+    }
+    complete(b, r->ticket, st, res);
+  }
+  if (have_stream) cudaStreamDestroy(s);
+}
 
 static sor_status start_batcher(Ctx* c) {
   std::lock_guard<std::mutex> g(c->batcher_mu);
@@ -637,6 +750,65 @@ sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f
   return SOR_OK;
 }
 
+sor_status batch_submit3d(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                          uint64_t* ticket) {
+  NvtxRange nvtx("sor_batch_submit3d");
+  sor_status rs = check_params3d(c, p, u0, u_out);
+  if (rs != SOR_OK) return rs;
+  if (!ticket) {
+    c->set_error("ticket must be non-NULL");
+    return SOR_ERR_INVALID_ARG;
+  }
+  if (cube_bytes(p, f != nullptr) > c->budget) {
+    c->set_error("request needs more device memory than the whole budget");
+    return SOR_ERR_BUDGET;
+  }
+  rs = start_batcher(c);
+  if (rs != SOR_OK) return rs;
+  Batcher* b = c->batcher.get();
+  auto r = std::make_unique<Request>();
+  r->cube = true;
+  r->p3 = *p;
+  r->t_submit = now_s();
+  const size_t m = (size_t)p->n + 2, nu = m * m * m, nf = (size_t)p->n * p->n * p->n;
+  r->u0.resize(nu);
+  if (is_device_ptr(u0)) {
+    if (cudaMemcpy(r->u0.data(), u0, nu * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      c->set_error("copy of u0 failed");
+      return SOR_ERR_CUDA;
+    }
+  } else {
+    std::memcpy(r->u0.data(), u0, nu * 8);
+  }
+  if (f) {
+    r->f.resize(nf);
+    if (is_device_ptr(f)) {
+      if (cudaMemcpy(r->f.data(), f, nf * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        c->set_error("copy of f failed");
+        return SOR_ERR_CUDA;
+      }
+    } else {
+      std::memcpy(r->f.data(), f, nf * 8);
+    }
+  }
+  r->u_out = u_out;
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    r->ticket = b->next_ticket++;
+    *ticket = r->ticket;
+    b->pending.insert(r->ticket);
+    b->cube_queue.push_back(std::move(r));
+    // one more worker while every running one is busy, up to kCubeWorkers
+    if ((int)b->cube_workers.size() < kCubeWorkers &&
+        (int)b->cube_queue.size() + b->cube_busy > (int)b->cube_workers.size())
+      b->cube_workers.emplace_back(cube_worker, b);
+  }
+  b->cv.notify_all();
+  return SOR_OK;
+}
+
 sor_status batch_poll(Ctx* c, uint64_t ticket, double timeout_s, sor_result* res) {
   Batcher* b = nullptr;
   {
@@ -670,6 +842,7 @@ void batch_shutdown(Ctx* c) {
     b = std::move(c->batcher);
   }
   if (!b) return;
+  c->closing = true;  // waits for memory and running cube solves give up
   {
     std::lock_guard<std::mutex> g(b->mu);
     b->stop = true;
@@ -677,6 +850,12 @@ void batch_shutdown(Ctx* c) {
   b->cv.notify_all();
   c->mem_cv.notify_all();
   if (b->th.joinable()) b->th.join();
+  for (auto& t : b->cube_workers)
+    if (t.joinable()) t.join();
+  {
+    std::lock_guard<std::mutex> g(b->mu);
+    b->cube_queue.clear();
+  }
   {
     std::lock_guard<std::mutex> g(b->mu);
     b->queue.clear();  // queued requests hold no reservation yet

@@ -186,6 +186,15 @@ sor_status sor_diag_fp64_rate(sor_ctx* h, int kind, double* ops_per_s) {
   return diag_fp64_rate(c, kind, ops_per_s);
 }
 
+sor_status sor_diag_bounds(sor_ctx* h, int* fired) {
+  if (!h) return SOR_ERR_INVALID_ARG;
+  Ctx* c = &h->impl;
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return SOR_ERR_CUDA;
+  std::lock_guard<std::mutex> g(c->solve_mu);
+  return diag_bounds(c, fired);
+}
+
 sor_status sor_batch_submit(sor_ctx* h, const sor_params* params, const double* u0, const double* f, double* u_out,
                             uint64_t* ticket) {
   if (!h) return SOR_ERR_INVALID_ARG;
@@ -200,6 +209,15 @@ sor_status sor_batch_submit(sor_ctx* h, const sor_params* params, const double* 
   DeviceGuard dg(c->device);
   if (!dg.ok) return SOR_ERR_CUDA;
   return batch_submit(c, plan, u0, f, u_out, ticket);
+}
+
+sor_status sor_batch_submit3d(sor_ctx* h, const sor_params* params, const double* u0, const double* f,
+                              double* u_out, uint64_t* ticket) {
+  if (!h) return SOR_ERR_INVALID_ARG;
+  Ctx* c = &h->impl;
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return SOR_ERR_CUDA;
+  return batch_submit3d(c, params, u0, f, u_out, ticket);
 }
 
 sor_status sor_poll(sor_ctx* h, uint64_t ticket, sor_result* res) {
@@ -226,11 +244,18 @@ sor_status sor_set_option(sor_ctx* h, int32_t option, int64_t value) {
     case SOR_OPT_TEMPORAL_DEPTH: c->opt_tdepth = v; return SOR_OK;
     case SOR_OPT_AUTOTUNE: c->opt_autotune = v ? 1 : 0; return SOR_OK;
     case SOR_OPT_BATCH_MAX_SLOTS: c->opt_max_slots = v; return SOR_OK;
-    case SOR_OPT_CLUSTER: c->opt_cluster = v ? 1 : 0; return SOR_OK;
+    case SOR_OPT_CLUSTER:
+      if (v > 2) return SOR_ERR_INVALID_ARG;
+      c->opt_cluster = v;
+      return SOR_OK;
     case SOR_OPT_FAST_CHAIN: c->opt_fast_chain = v ? 1 : 0; return SOR_OK;
     case SOR_OPT_FUSED_KERNEL:
       if (v > 2) return SOR_ERR_INVALID_ARG;
       c->opt_fused_kernel = v;
+      return SOR_OK;
+    case SOR_OPT_BATCH_PLAIN_STEP:
+      if (v > 4096) return SOR_ERR_INVALID_ARG;
+      c->opt_plain_step = v;
       return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
@@ -249,6 +274,7 @@ sor_status sor_get_option(sor_ctx* h, int32_t option, int64_t* value) {
     case SOR_OPT_CLUSTER: *value = c->opt_cluster.load(); return SOR_OK;
     case SOR_OPT_FAST_CHAIN: *value = c->opt_fast_chain.load(); return SOR_OK;
     case SOR_OPT_FUSED_KERNEL: *value = c->opt_fused_kernel.load(); return SOR_OK;
+    case SOR_OPT_BATCH_PLAIN_STEP: *value = c->opt_plain_step.load(); return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }

@@ -87,6 +87,31 @@ __device__ __forceinline__ void finalize_plain(const SlotDesc& sd, SlotState* st
   if (k >= sd.max_iters) st->done = 1;
 }
 
+// Device-side index checks of the debug build (SOR_DEBUG_BOUNDS): the range
+// [lo, hi) must lie inside [0, limit); when it does not, the slot's error
+// word records kErrBounds (the solve then returns SOR_ERR_INTERNAL) and the
+// caller skips the access.  Release builds compile every check to `true`.
+__device__ __forceinline__ bool dbg_range(long long lo, long long hi, long long limit, SlotState* st) {
+#ifdef SOR_DEBUG_BOUNDS
+  if (lo >= 0 && lo <= hi && hi <= limit) return true;
+  if (st) atomicExch(&st->error, kErrBounds);
+  return false;
+#else
+  (void)lo;
+  (void)hi;
+  (void)limit;
+  (void)st;
+  return true;
+#endif
+}
+
+// Debug check of a tile that touches rows [r0, r1) and packed columns
+// [q0, q1) of the colour arrays of slot sd (element offset q + kOff in a row).
+__device__ __forceinline__ bool dbg_tile(const SlotDesc& sd, SlotState* st, int r0, int r1, int q0, int q1) {
+  return dbg_range(r0, r1, (long long)sd.n + 2, st) &&
+         dbg_range((long long)q0 + kOff, (long long)q1 + kOff, (long long)sd.pitch, st);
+}
+
 __device__ __forceinline__ size_t eidx(int i, int q, int pitch) { return (size_t)i * pitch + q + kOff; }
 
 // Data-flow scheduling of a chunk of colour phases (the cube and 9-point

@@ -99,6 +99,10 @@ struct SlotState {
   unsigned long long gmax_bits;  // max |h^2 f| over the interior, set at pack time
 };
 
+// SlotState::error values: 1 = a consistency check of the kernels failed;
+// kErrBounds = a device-side index check of the debug build refused an access.
+constexpr int kErrBounds = 2;
+
 // A tile of work: slot index, first row, first packed column, row count.
 struct Tile {
   int slot, row0, col0, nrows;

@@ -57,6 +57,9 @@ __global__ void k_pack(const double* __restrict__ u0, const double* __restrict__
       const int j = 2 * q - 1 + t;
       if (j < 0 || j >= m) continue;
       const int c = (i + j) & 1;
+      if (!dbg_range((long long)i * m + j, (long long)i * m + j + 1, (long long)m * m, st) ||
+          !dbg_range((long long)eidx(i, q, pitch), (long long)eidx(i, q, pitch) + 1, (long long)m * pitch, st))
+        continue;
       const double v = u0[(size_t)i * m + j];
       ub = umax64(ub, abs_bits(v));
       const size_t e = eidx(i, q, pitch);
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(const SlotDesc* __restrict__
       c.k = *((volatile int*)&st->iters) + 1;
       c.measure = (MODE == 0) && (((c.k % sd.K) == 0) || (c.k >= sd.max_iters));
       c.xbuf = (MODE == 0) ? *((volatile int*)&st->xbuf) : 0;
+      if (!dbg_tile(sd, st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1)) c.skip = 1;
       ctl = c;
     }
     __syncthreads();
@@ -653,6 +657,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_sweep_fast(const SlotDesc* __re
         st->done = 1;
         skip = 1;
       }
+      if (!skip && !dbg_tile(sd, st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1))
+        skip = 1;
     }
     skip = __shfl_sync(0xffffffffu, skip, 0);
     if (skip) continue;
@@ -759,6 +765,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_fast_chain(const SlotDesc* __re
     skip = *((volatile int*)&st->done);
     k0 = *((volatile int*)&st->iters);
     xbuf = *((volatile int*)&st->xbuf);
+    if (!skip && !dbg_tile(sd, st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1)) {
+      st->done = 1;  // the neighbours' bounded waits then end the launch with an error
+      skip = 1;
+    }
   }
   skip = __shfl_sync(0xffffffffu, skip, 0);
   if (skip) return;  // set only between launches: every warp sees the same value
@@ -944,6 +954,7 @@ __global__ void __launch_bounds__(kThreads) k_correct(const SlotDesc* __restrict
     if (threadIdx.x == 0) {
       ctl[0] = *((volatile int*)&st->done) || *((volatile int*)&st->checked_iter) < 0;  // nothing pending
       ctl[1] = *((volatile int*)&st->ubuf);
+      if (!dbg_tile(sd, st, tl.row0, tl.row0 + tl.nrows, tl.col0, tl.col0 + kWarpCols)) ctl[0] = 1;
     }
     __syncthreads();
     const int skip = ctl[0], ubuf = ctl[1];
@@ -1088,6 +1099,7 @@ __global__ void __launch_bounds__(kThreads) k_resid(const SlotDesc* __restrict__
         c.measure = *((volatile int*)&st->checked_iter) >= 0;  // a correction is pending after the first pass
       }
       c.xbuf = (ROLE == kResidRefine) ? *((volatile int*)&st->ubuf) : *((volatile int*)&st->xbuf);
+      if (!dbg_tile(sd, st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1)) c.skip = 1;
       ctl = c;
     }
     __syncthreads();

@@ -101,6 +101,13 @@ cudaError_t launch_sweep_wave(bool inner, int T, const SlotDesc* slots, SlotStat
 bool cluster_solve_fits(bool fp32, int n, int pitch);
 cudaError_t launch_cluster_solve(bool fp32, int n, int pitch, const SlotDesc* slots, SlotState* states, int slot,
                                  cudaStream_t s);
+// Whole plain solve of a small plate on a cooperative grid of many SMs, one
+// band of rows per block (sor_grid.cu); exact-order update, max|change| stop
+// only.  `sync` is grid_sync_bytes() of device memory (zeroed by the launch).
+bool grid_solve_fits(bool fp32, int n, int pitch, int sm_count);
+size_t grid_sync_bytes();
+cudaError_t launch_grid_solve(bool fp32, int n, int pitch, int sm_count, const SlotDesc* slots, SlotState* states,
+                              int slot, void* sync, cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int dbuf, cudaStream_t s);
 

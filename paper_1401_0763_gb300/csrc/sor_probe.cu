@@ -14,6 +14,7 @@
 
 #include <sstream>
 
+#include "sor_devfn.cuh"
 #include "sor_runtime.h"
 
 namespace sorgb {
@@ -88,6 +89,48 @@ sor_status diag_fp64_rate(Ctx* c, int kind, double* ops_per_s) {
   }
   const double ops = (double)blocks * kProbeThreads * (double)kProbeIters * kChains;
   *ops_per_s = ms > 0.0f ? ops / (ms * 1e-3) : 0.0;
+  return SOR_OK;
+}
+
+// One index through the debug build's check, an index below a one-element
+// range: the check must refuse it and record kErrBounds.  No memory is
+// accessed at that index in any build; release builds compile the check away
+// and report that it did not fire.
+__global__ void k_dbg_probe(SlotState* st, int* fired) { *fired = dbg_range(-1, 0, 1, st) ? 0 : 1; }
+
+sor_status diag_bounds(Ctx* c, int* fired) {
+  if (!fired) {
+    c->set_error("fired must be non-NULL");
+    return SOR_ERR_INVALID_ARG;
+  }
+  const size_t bytes = sizeof(SlotState) + 256;
+  unsigned char* buf = (unsigned char*)ctx_dev_alloc(c, bytes);
+  if (!buf) {
+    c->set_error("device allocation failed");
+    return SOR_ERR_OOM;
+  }
+  SlotState* st = (SlotState*)buf;
+  int* out = (int*)(buf + sizeof(SlotState) + 128);
+  SlotState hs;
+  int hf = -1;
+  cudaError_t e = cudaMemsetAsync(buf, 0, bytes, c->stream);
+  if (e == cudaSuccess) {
+    k_dbg_probe<<<1, 1, 0, c->stream>>>(st, out);
+    count_kernel_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, out, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  ctx_dev_free(c, buf);
+  if (e != cudaSuccess) {
+    c->set_error(cudaGetErrorString(e));
+    cudaGetLastError();
+    return SOR_ERR_CUDA;
+  }
+  if (hf != 0 && hf != 1) return SOR_ERR_INTERNAL;
+  if (hf == 1 && hs.error != kErrBounds) return SOR_ERR_INTERNAL;  // fired but recorded nothing
+  *fired = hf;
   return SOR_OK;
 }
 

@@ -104,12 +104,13 @@ sor_status ctx_reserve(Ctx* c, size_t bytes, bool wait, double timeout_s) {
   if (bytes > c->budget) return SOR_ERR_BUDGET;
   if (c->reserved + bytes > c->budget) {
     if (!wait) return SOR_ERR_BUDGET;
-    auto pred = [&] { return c->reserved + bytes <= c->budget; };
+    auto pred = [&] { return c->closing.load() || c->reserved + bytes <= c->budget; };
     if (timeout_s < 0) {
       c->mem_cv.wait(g, pred);
     } else if (!c->mem_cv.wait_for(g, std::chrono::duration<double>(timeout_s), pred)) {
       return SOR_ERR_BUDGET;
     }
+    if (c->closing.load()) return SOR_ERR_CANCELLED;
   }
   c->reserved += bytes;
   c->peak = std::max(c->peak, c->reserved);
@@ -281,6 +282,7 @@ static void free_workspace(Ctx* c, SolveWorkspace* w) {
   ctx_dev_free(c, w->d_nat_f);
   ctx_dev_free(c, w->d_ring);
   ctx_dev_free(c, w->d_progress);
+  ctx_dev_free(c, w->d_gridsync);
   for (auto& kv : w->chain_phases) ctx_dev_free(c, kv.second);
   w->chain_phases.clear();
   if (w->h_state) cudaFreeHost(w->h_state);
@@ -423,6 +425,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
   w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, w->tb_cap * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
+  w->d_gridsync = ctx_dev_alloc(c, grid_sync_bytes());
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
   if (p.kind == kPlain64) w->d_ring = (double*)ctx_dev_alloc(c, 2 * ring_elems * sizeof(double));
@@ -440,7 +443,7 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
       w->chain_grid = c->sm_count * bps;
   }
   ok = w->d_desc && w->d_state && w->d_sweep_tiles && w->d_resid_tiles && w->d_fast_tiles && w->d_tb_tiles &&
-       w->d_nat_u &&
+       w->d_nat_u && w->d_gridsync &&
        (!p.has_f || w->d_nat_f) && (p.kind != kPlain64 || w->d_ring) &&
        (p.kind != kPlain64 || w->d_progress);
   if (!ok || cudaMallocHost(&w->h_state, sizeof(SlotState) * kInflight) != cudaSuccess) {
@@ -1058,11 +1061,15 @@ static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const
   }
   pa.state = w->d_state;
   SOR_CK(c, launch_pack(pa, s));
-  // small plain grids: the whole solve in one cluster launch (exact order)
+  // small plain plates: the whole solve in one launch, on a cooperative grid
+  // (max|change| stop) or in one thread-block cluster (exact order either way)
   const bool small = p.kind == kPlain64 ? p.n <= 384 : p.n <= 768;
-  const bool cluster = !(p.kind != kRefine && p.max_iters == 0) && p.kind != kRefine && small &&
-                       c->opt_cluster.load() && cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch);
-  if (p.kind == kPlain64 && !p.exact && !cluster) {
+  const int small_opt = c->opt_cluster.load();
+  const bool one_launch = !(p.kind != kRefine && p.max_iters == 0) && p.kind != kRefine && small && small_opt != 0;
+  const bool grid = one_launch && small_opt == 1 && p.stop == kStopDelta &&
+                    grid_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch, c->sm_count);
+  const bool cluster = one_launch && !grid && cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch);
+  if (p.kind == kPlain64 && !p.exact && !cluster && !grid) {
     // the rescaled phases need the input magnitudes to bound their chunk
     // length; inputs they cannot carry take the exact-order phases
     SOR_CK(c, cudaMemcpyAsync(&w->h_state[0], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
@@ -1106,10 +1113,14 @@ static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const
     last_iters = hs.iters;
     return SOR_OK;
   };
-  if (cluster) {
+  if (cluster || grid) {
     const int k = slot_i;
     if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
-    SOR_CK(c, launch_cluster_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, w->d_desc, w->d_state, 0, s));
+    if (grid)
+      SOR_CK(c, launch_grid_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, c->sm_count, w->d_desc, w->d_state, 0,
+                                  w->d_gridsync, s));
+    else
+      SOR_CK(c, launch_cluster_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, w->d_desc, w->d_state, 0, s));
     if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].second, s));
     SOR_CK(c, cudaMemcpyAsync(&w->h_state[k], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
     SOR_CK(c, cudaEventRecord(w->poll_events[k], s));
@@ -1167,7 +1178,7 @@ static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const
   float dev_ms = 0.f;
   SOR_CK(c, cudaEventElapsedTime(&dev_ms, w->ev0, w->ev1));
   if (fin.error) {
-    c->set_error("device-side consistency check failed");
+    c->set_error(fin.error == kErrBounds ? "device-side index check failed" : "device-side consistency check failed");
     return SOR_ERR_INTERNAL;
   }
   if (res) {

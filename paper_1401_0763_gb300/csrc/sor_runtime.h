@@ -96,6 +96,7 @@ struct SolveWorkspace {
   double* d_nat_f = nullptr;  // n^2 staging
   double* d_ring = nullptr;   // FP64: unscaled Dirichlet ring cells of both colours (SlotDesc::ring)
   unsigned* d_progress = nullptr;  // FP64 chunk launches: phases completed per strip
+  void* d_gridsync = nullptr;      // small plates solved on a cooperative grid: barrier state
   int fast_ct = 0;                 // column tiles of the strip table (strips are rows x fast_ct)
   int chain_grid = 0;              // blocks of a chunk launch (0: chunk launches unavailable)
   std::map<std::string, void*> chain_phases;  // packed phase records per chunk length and omega
@@ -114,6 +115,8 @@ struct Request {
   uint64_t ticket = 0;
   Plan plan;
   std::vector<double> u0, f;  // host copies of the inputs
+  bool cube = false;          // a cube (sor_batch_submit3d): solved whole by a cube worker
+  sor_params p3{};            // its parameters
   double* u_out = nullptr;
   bool out_on_device = false;
   double t_submit = 0.0;
@@ -155,6 +158,7 @@ struct Ctx {
 
   std::mutex mem_mu;
   std::condition_variable mem_cv;
+  std::atomic<bool> closing{false};  // sor_destroy has begun: waits for memory give up
   size_t reserved = 0, peak = 0;
 
   std::mutex solve_mu;  // serialises sor_solve callers
@@ -176,6 +180,7 @@ struct Ctx {
   std::atomic<int> opt_cluster{1};
   std::atomic<int> opt_fast_chain{1};
   std::atomic<int> opt_fused_kernel{0};  // 0: by grid size, 1: tile family, 2: wavefront family
+  std::atomic<int> opt_plain_step{0};    // batch plain slots: iterations per step (0: tuned online)
 
   std::mutex tune_mu;
   std::map<std::string, TuneChoice> tuned;  // autotuned choices per "<n bucket> <has source>"
@@ -222,8 +227,19 @@ sor_status diag_flow_wait(Ctx* c, int polls, int preset, int* timed_out);
 // FP64 lane operations per second of the whole GPU on independent chains of
 // FMAs (kind 0) or additions (kind 1) (sor_probe.cu).
 sor_status diag_fp64_rate(Ctx* c, int kind, double* ops_per_s);
+// Whether the device-side index checks are compiled in and fire (sor_probe.cu).
+sor_status diag_bounds(Ctx* c, int* fired);
 sor_status solve3d_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                             sor_result* res);
+// The parts of a cube solve the batch scheduler uses (sor3d.cu): argument
+// checks, the solve on a given stream (optionally waiting for budget), and an
+// upper bound of the device bytes it reserves.
+sor_status check_params3d(Ctx* c, const sor_params* p, const double* u0, const double* u_out);
+sor_status run_cube(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out, sor_result* res,
+                    cudaStream_t s, bool wait_budget);
+size_t cube_bytes(const sor_params* p, bool has_f);
+sor_status batch_submit3d(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
+                          uint64_t* ticket);
 
 sor_status batch_submit(Ctx* c, const Plan& p, const double* u0, const double* f, double* u_out, uint64_t* ticket);
 sor_status batch_poll(Ctx* c, uint64_t ticket, double timeout_s, sor_result* res);

@@ -284,6 +284,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
         if (nt <= 0) skip = 1;
         src = src_param;
       }
+      // the output rows and columns of the tile lie inside the slot's arrays
+      if (!skip && !dbg_tile(sd, st, tl.row0, tl.row0 + tl.nrows, tl.col0, tl.col0 + Gm::OQ)) skip = 1;
       ctl[0] = skip; ctl[1] = nt; ctl[2] = k_end; ctl[3] = measure; ctl[4] = src;
     }
     __syncthreads();

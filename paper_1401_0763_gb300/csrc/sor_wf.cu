@@ -339,6 +339,8 @@ __global__ void __launch_bounds__(kWfThreads, WfGeom<T>::kMinBlocks)
         src = src_param;
       }
       if (nt <= 0) skip = 1;
+      // the output rows and columns of the tile lie inside the slot's arrays
+      if (!skip && !dbg_tile(sd, st, tl.row0, tl.row0 + tl.nrows, tl.col0, tl.col0 + 128 - 2 * hq)) skip = 1;
     }
     skip = __shfl_sync(0xffffffffu, skip, 0);
     if (skip) continue;

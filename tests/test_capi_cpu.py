@@ -78,3 +78,12 @@ def test_null_arguments_rejected_without_device(lib):
         assert st == capi.SOR_OK
         lib.sor_destroy(h)
     del P
+
+
+def test_debug_build_exports_the_same_symbols():
+    """The debug variant (device-side index checks) builds for sm_103a and
+    exports every function the header declares."""
+    lib = _build.build(debug=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (sor_\w+)", out))
+    assert set(declared_functions()) <= exported

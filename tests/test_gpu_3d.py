@@ -337,3 +337,65 @@ def test_refine3d_stall_window_bitwise(ctx):
                     precision=capi.SOR_FP32_REFINE)
     assert res["outer_steps"] == ref["outer_steps"] and not res["converged"]
     assert np.array_equal(got, ref["u"]) and res["final_resid_rel"] == ref["final_resid_rel"]
+
+
+@pytest.mark.parametrize("budget_mb", [0, 200])
+def test_cube_requests_in_the_batch_scheduler(budget_mb):
+    """Cube requests through sor_batch_submit3d, mixed with plates: cubes run
+    whole on worker streams beside the scheduler's plate steps; each result
+    equals the lone sor_solve3d (sor_solve for the plates) bit for bit.  A
+    200 MB budget makes cube requests wait for each other's memory."""
+    capi = capi_mod()
+    cubes = [
+        (30, None, dict(precision=capi.SOR_FP64, tol=1e-9, max_iters=400, check_every=5)),
+        (41, None, dict(precision=capi.SOR_FP64, tol=1e-9, max_iters=300, check_every=7,
+                        flags=capi.SOR_FLAG_EXACT_ORDER)),
+        (25, None, dict(precision=capi.SOR_FP32, tol=1e-4, max_iters=200, check_every=10)),
+        (33, True, dict(precision=capi.SOR_FP32_REFINE, tol=1e-10, max_iters=20000)),
+        (19, True, dict(precision=capi.SOR_FP64, tol=1e-8, max_iters=2000, check_every=4,
+                        stop=capi.SOR_STOP_RESID_REL)),
+    ]
+    jobs = []
+    for k, (n, with_f, kw) in enumerate(cubes):
+        u0 = wl.random_shell(n, 500 + k)
+        f = wl.gaussian_source3(n, 600 + k) if with_f else None
+        jobs.append((u0, f, dict(kw, omega=oracle.omega_opt(n))))
+    plates = []
+    for k, n in enumerate((70, 130)):
+        u0, f = wl.poisson_problem(n, 700 + k)
+        plates.append((u0, f, dict(precision=capi.SOR_FP32_REFINE, omega=oracle.omega_opt(n), tol=1e-9,
+                                   max_iters=50000)))
+    with capi.Context(0) as solo:
+        alone = [solo.solve3d(u0, f, **kw) for u0, f, kw in jobs]
+        alone_p = [solo.solve(u0, f, **kw) for u0, f, kw in plates]
+    with capi.Context(0, budget_bytes=budget_mb << 20) as ctx:
+        t3 = [ctx.submit3d(u0, f, **kw) for u0, f, kw in jobs]
+        t2 = [ctx.submit(u0, f, **kw) for u0, f, kw in plates]
+        for (t, out), (ref, rres) in zip(t3, alone):
+            st, res = ctx.wait(t, 300.0)
+            assert st == capi.SOR_OK, ctx.last_error()
+            assert res["iterations"] == rres["iterations"] and res["converged"] == rres["converged"]
+            assert np.array_equal(out, ref)
+        for (t, out), (ref, rres) in zip(t2, alone_p):
+            st, res = ctx.wait(t, 300.0)
+            assert st == capi.SOR_OK, ctx.last_error()
+            assert np.array_equal(out, ref)
+        assert ctx.stats()["batch_completed"] == len(jobs) + len(plates)
+        if budget_mb:
+            assert ctx.stats()["bytes_peak"] <= budget_mb << 20
+
+
+def test_cube_requests_cancelled_by_destroy():
+    """Closing the context with cube requests queued and running returns
+    promptly (running solves stop at their next chunk) and the device stays
+    usable."""
+    capi = capi_mod()
+    ctx = capi.Context(0)
+    n = 200
+    u0 = wl.random_shell(n, 1)
+    for _ in range(6):
+        ctx.submit3d(u0, precision=capi.SOR_FP64, tol=0.0, max_iters=100000, check_every=50)
+    ctx.close()
+    with capi.Context(0) as again:
+        out, res = again.solve3d(wl.random_shell(10, 2), tol=1e-8, max_iters=500)
+        assert res["converged"]

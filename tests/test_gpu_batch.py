@@ -161,3 +161,35 @@ def test_mixed_inner_sweeps_share_the_fused_sweeps(family, depth):
             ref = oracle.refine(u0, w, f=f, inner_sweeps=inner, tol=1e-9, max_outer=60000 // inner)
             assert res["outer_steps"] == ref["outer_steps"] and bool(res["converged"]) == ref["converged"]
             assert np.array_equal(out, ref["u"]), inner
+
+
+@pytest.mark.parametrize("step", [0, 5, 64])
+def test_plain_step_length_changes_no_result(step):
+    """Plain (FP64 exact-order and FP32) batch slots step a number of
+    iterations per scheduler round that is tuned online (step 0: 8, 16, 32, 64
+    tried, the fastest kept) or fixed by SOR_OPT_BATCH_PLAIN_STEP; every slot
+    stops on the device at its own tested iteration, so results equal the
+    lone solves bit for bit whatever the length."""
+    capi = capi_mod()
+    reqs = []
+    for k in range(12):
+        n = 50 + 23 * k
+        if k % 2:
+            reqs.append((wl.heat_plate(n, 100.0), dict(precision=capi.SOR_FP64, omega=oracle.omega_opt(n), tol=1e-7,
+                                                       max_iters=4000, check_every=3,
+                                                       flags=capi.SOR_FLAG_EXACT_ORDER)))
+        else:
+            reqs.append((wl.random_edges(n, k), dict(precision=capi.SOR_FP32, omega=oracle.omega_opt(n), tol=1e-3,
+                                                     max_iters=3000, check_every=10)))
+    with capi.Context(0) as solo:
+        alone = [solo.solve(u0, None, **kw) for u0, kw in reqs]
+    with capi.Context(0) as ctx:
+        ctx.set_option(capi.SOR_OPT_BATCH_PLAIN_STEP, step)
+        tickets = [ctx.submit(u0, None, **kw) for u0, kw in reqs]
+        for (t, out), (ref, rres) in zip(tickets, alone):
+            st, res = ctx.wait(t, 300.0)
+            assert st == capi.SOR_OK, ctx.last_error()
+            assert res["iterations"] == rres["iterations"] and res["converged"] == rres["converged"]
+            assert np.array_equal(out, ref)
+        used = ctx.stats()["batch_plain_step"]
+        assert used == step if step else used in (8, 16, 32, 64)

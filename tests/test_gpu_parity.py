@@ -24,12 +24,15 @@ TOL64 = 1e-12
 
 @pytest.fixture(scope="module")
 def ctxs():
-    """Two contexts: the default one (small plain grids solved inside one
-    thread-block cluster) and one with that path switched off, so the
+    """Three contexts: the default one (small plain plates solved in one
+    launch on a cooperative grid of many SMs, or in one thread-block cluster
+    when the stop test is the residual), one that always takes the cluster
+    for them, and one with the one-launch paths switched off, so the chunked
     multi-CTA kernels are exercised at every size."""
     from paper_1401_0763_gb300 import _build, capi
     _build.build()
-    made = {"cluster": capi.Context(0), "multi": capi.Context(0)}
+    made = {"grid": capi.Context(0), "cluster": capi.Context(0), "multi": capi.Context(0)}
+    made["cluster"].set_option(capi.SOR_OPT_CLUSTER, 2)
     made["multi"].set_option(capi.SOR_OPT_CLUSTER, 0)
     yield made
     for c in made.values():
@@ -38,7 +41,7 @@ def ctxs():
 
 @pytest.fixture(scope="module")
 def ctx(ctxs):
-    return ctxs["cluster"]
+    return ctxs["grid"]
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +49,7 @@ def ctx_mc(ctxs):
     return ctxs["multi"]
 
 
-PATHS = ["cluster", "multi"]
+PATHS = ["grid", "cluster", "multi"]
 
 
 def capi_mod():
