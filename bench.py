@@ -355,9 +355,10 @@ def workload_plate256(args, ctx, capi, wl):
     u0 = np.ascontiguousarray(wl.heat_plate(n, 100.0))
     out = np.empty_like(u0)
     lines = {}
-    # the default (one launch on a cooperative grid of many SMs), the same in one thread-block cluster, and
-    # the chunked multi-CTA path; all three evaluate the update in the exact order of the oracle here
-    for name, small in (("fp64", 1), ("fp64_cluster", 2), ("fp64_chunked", 0)):
+    # the default (one launch on a cooperative grid of many SMs, bands exchanging edge rows point to point and
+    # the stop test decided behind the sweeps), the same grid with a grid-wide barrier per colour phase, one
+    # thread-block cluster, and the chunked multi-CTA path; all evaluate the update in the oracle's exact order
+    for name, small in (("fp64", 1), ("fp64_gridbar", 3), ("fp64_cluster", 2), ("fp64_chunked", 0)):
         ctx.set_option(capi.SOR_OPT_CLUSTER, small)
         kw = dict(omega=capi.sor_omega_opt(n), tol=1e-8, max_iters=5000, check_every=1,
                   flags=capi.SOR_FLAG_EXACT_ORDER)

@@ -282,8 +282,11 @@ typedef enum {
   SOR_OPT_BATCH_MAX_SLOTS = 6, /* cap on concurrently admitted batch requests (0 = no cap) */
   SOR_OPT_CLUSTER = 7,         /* plain solves of small plates (N <= 384 in FP64, N <= 768 in FP32) in a
                                   single launch, exact operation order: 1 (default) = on a cooperative
-                                  grid of many SMs when the stop test is max|change|, else in one
-                                  thread-block cluster; 2 = always the cluster; 0 = never */
+                                  grid of many SMs when the stop test is max|change| (neighbouring bands
+                                  exchange edge rows point to point, the stop test is decided behind the
+                                  sweeps), else in one thread-block cluster; 3 = the same grid with a
+                                  grid-wide barrier per colour phase; 2 = always the cluster; 0 = never.
+                                  Results are identical in every form */
   SOR_OPT_FAST_CHAIN = 8,      /* 1 (default): the FP64 default path runs each chunk of iterations in one
                                   cooperative launch with neighbour-to-neighbour progress counters; 0: one
                                   launch per colour phase.  Results are identical either way */

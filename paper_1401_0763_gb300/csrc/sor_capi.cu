@@ -245,7 +245,7 @@ sor_status sor_set_option(sor_ctx* h, int32_t option, int64_t value) {
     case SOR_OPT_AUTOTUNE: c->opt_autotune = v ? 1 : 0; return SOR_OK;
     case SOR_OPT_BATCH_MAX_SLOTS: c->opt_max_slots = v; return SOR_OK;
     case SOR_OPT_CLUSTER:
-      if (v > 2) return SOR_ERR_INVALID_ARG;
+      if (v < 0 || v > 3) return SOR_ERR_INVALID_ARG;
       c->opt_cluster = v;
       return SOR_OK;
     case SOR_OPT_FAST_CHAIN: c->opt_fast_chain = v ? 1 : 0; return SOR_OK;

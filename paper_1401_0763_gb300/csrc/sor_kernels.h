@@ -101,6 +101,9 @@ cudaError_t launch_sweep_wave(bool inner, int T, const SlotDesc* slots, SlotStat
 bool cluster_solve_fits(bool fp32, int n, int pitch);
 cudaError_t launch_cluster_solve(bool fp32, int n, int pitch, const SlotDesc* slots, SlotState* states, int slot,
                                  cudaStream_t s);
+// Largest plates solved in one launch (grid or cluster) by default.
+constexpr int kGridMaxN64 = 384;
+constexpr int kGridMaxN32 = 768;
 // Whole plain solve of a small plate on a cooperative grid of many SMs, one
 // band of rows per block (sor_grid.cu); exact-order update, max|change| stop
 // only.  `sync` is grid_sync_bytes() of device memory (zeroed by the launch).
@@ -108,6 +111,14 @@ bool grid_solve_fits(bool fp32, int n, int pitch, int sm_count);
 size_t grid_sync_bytes();
 cudaError_t launch_grid_solve(bool fp32, int n, int pitch, int sm_count, const SlotDesc* slots, SlotState* states,
                               int slot, void* sync, cudaStream_t s);
+// The same solves without grid barriers: tagged edge-row exchanges between
+// neighbouring bands and a stop test that an extra block decides behind the
+// sweeps (sor_grid.cu).  `sync` holds grid_flow_sync_bytes() (zeroed by the
+// launch); 0 bytes or a false fit: the plate does not fit this form.
+bool grid_flow_fits(bool fp32, int n, int pitch, int sm_count);
+size_t grid_flow_sync_bytes(bool fp32, int n, int pitch, int sm_count);
+cudaError_t launch_grid_flow(bool fp32, int n, int pitch, int sm_count, const SlotDesc* slots, SlotState* states,
+                             int slot, void* sync, size_t sync_bytes, cudaStream_t s);
 cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles,
                          int grid, int dbuf, cudaStream_t s);
 

@@ -401,7 +401,12 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->tb_cap = pingpong ? fused_tile_cap(p.n) : 1;
   const size_t nat_u = (size_t)(p.n + 2) * (p.n + 2) * 8;
   const size_t nat_f = p.has_f ? (size_t)p.n * p.n * 8 : 0;
-  const size_t small = sizeof(SlotDesc) + sizeof(SlotState) +
+  // barrier state of the grid solver, or the exchange and decision words of
+  // its barrier-free form for the plain plates small enough for it
+  size_t gsync = grid_sync_bytes();
+  if ((p.kind == kPlain64 && p.n <= kGridMaxN64) || (p.kind == kPlain32 && p.n <= kGridMaxN32))
+    gsync = std::max(gsync, grid_flow_sync_bytes(p.kind == kPlain32, p.n, L.pitch, c->sm_count));
+  const size_t small = gsync + sizeof(SlotDesc) + sizeof(SlotState) +
                        (st.size() + rt.size() + ft.size() + w->tb_cap) * sizeof(Tile) +
                        2 * (2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2)) * sizeof(double);  // saved ring
   const size_t total = slot_bytes(p, pingpong) + nat_u + nat_f + small + 4096;
@@ -425,7 +430,8 @@ static sor_status get_workspace(Ctx* c, const Plan& p, SolveWorkspace** out) {
   w->d_fast_tiles = (Tile*)ctx_dev_alloc(c, ft.size() * sizeof(Tile));
   w->d_tb_tiles = (Tile*)ctx_dev_alloc(c, w->tb_cap * sizeof(Tile));
   w->d_nat_u = (double*)ctx_dev_alloc(c, nat_u);
-  w->d_gridsync = ctx_dev_alloc(c, grid_sync_bytes());
+  w->d_gridsync = ctx_dev_alloc(c, gsync);
+  w->gridsync_bytes = gsync;
   if (p.has_f) w->d_nat_f = (double*)ctx_dev_alloc(c, nat_f);
   const size_t ring_elems = 2 * (size_t)L.pitch + 2 * (size_t)(p.n + 2);  // per colour
   if (p.kind == kPlain64) w->d_ring = (double*)ctx_dev_alloc(c, 2 * ring_elems * sizeof(double));
@@ -1063,13 +1069,17 @@ static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const
   SOR_CK(c, launch_pack(pa, s));
   // small plain plates: the whole solve in one launch, on a cooperative grid
   // (max|change| stop) or in one thread-block cluster (exact order either way)
-  const bool small = p.kind == kPlain64 ? p.n <= 384 : p.n <= 768;
+  const bool small = p.kind == kPlain64 ? p.n <= kGridMaxN64 : p.n <= kGridMaxN32;
   const int small_opt = c->opt_cluster.load();
   const bool one_launch = !(p.kind != kRefine && p.max_iters == 0) && p.kind != kRefine && small && small_opt != 0;
-  const bool grid = one_launch && small_opt == 1 && p.stop == kStopDelta &&
-                    grid_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch, c->sm_count);
-  const bool cluster = one_launch && !grid && cluster_solve_fits(p.kind == kPlain32, p.n, w->slot.L.pitch);
-  if (p.kind == kPlain64 && !p.exact && !cluster && !grid) {
+  const bool fp32 = p.kind == kPlain32;
+  const bool flow = one_launch && small_opt == 1 && p.stop == kStopDelta &&
+                    grid_flow_fits(fp32, p.n, w->slot.L.pitch, c->sm_count) &&
+                    grid_flow_sync_bytes(fp32, p.n, w->slot.L.pitch, c->sm_count) <= w->gridsync_bytes;
+  const bool grid = one_launch && !flow && (small_opt == 1 || small_opt == 3) && p.stop == kStopDelta &&
+                    grid_solve_fits(fp32, p.n, w->slot.L.pitch, c->sm_count);
+  const bool cluster = one_launch && !flow && !grid && cluster_solve_fits(fp32, p.n, w->slot.L.pitch);
+  if (p.kind == kPlain64 && !p.exact && !cluster && !grid && !flow) {
     // the rescaled phases need the input magnitudes to bound their chunk
     // length; inputs they cannot carry take the exact-order phases
     SOR_CK(c, cudaMemcpyAsync(&w->h_state[0], w->d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));
@@ -1113,10 +1123,13 @@ static sor_status solve_locked(Ctx* c, const Plan& plan, const double* u0, const
     last_iters = hs.iters;
     return SOR_OK;
   };
-  if (cluster || grid) {
+  if (cluster || grid || flow) {
     const int k = slot_i;
     if (timing) SOR_CK(c, cudaEventRecord(w->chunk_events[k].first, s));
-    if (grid)
+    if (flow)
+      SOR_CK(c, launch_grid_flow(fp32, p.n, w->slot.L.pitch, c->sm_count, w->d_desc, w->d_state, 0, w->d_gridsync,
+                                 w->gridsync_bytes, s));
+    else if (grid)
       SOR_CK(c, launch_grid_solve(p.kind == kPlain32, p.n, w->slot.L.pitch, c->sm_count, w->d_desc, w->d_state, 0,
                                   w->d_gridsync, s));
     else

@@ -97,6 +97,7 @@ struct SolveWorkspace {
   double* d_ring = nullptr;   // FP64: unscaled Dirichlet ring cells of both colours (SlotDesc::ring)
   unsigned* d_progress = nullptr;  // FP64 chunk launches: phases completed per strip
   void* d_gridsync = nullptr;      // small plates solved on a cooperative grid: barrier state
+  size_t gridsync_bytes = 0;       // its size (the barrier-free form needs the larger one)
   int fast_ct = 0;                 // column tiles of the strip table (strips are rows x fast_ct)
   int chain_grid = 0;              // blocks of a chunk launch (0: chunk launches unavailable)
   std::map<std::string, void*> chain_phases;  // packed phase records per chunk length and omega

@@ -57,32 +57,28 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Right-hand-side rows are fetched kTbGAhead rows ahead into a ring of
-// kTbGSlots row buffers per warp (one asynchronous-copy group per row).
-constexpr int kTbGAhead = 3;
-constexpr int kTbGSlots = 4;
-
-// Right-hand-side values of staged row r (global row i) for this lane, copied
-// asynchronously into the warp's buffer (nothing for rows or lanes without
-// interior cells); one commit per row either way.
-__device__ __forceinline__ void tb_g_issue(float* gslot, const float* __restrict__ Gc, int i, int qf, int n, int pitch,
-                                           int colour, int lane, bool valid) {
-  const int s = (i + colour) & 1;
-  if (valid && i >= 1 && i <= n && qf >= 1 && qf <= ((n + s) >> 1))
-    cp_async16(gslot + 4 * lane, Gc + (size_t)i * pitch + qf + kOff, true);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
+// Right-hand-side values of this lane's 4 cells of one row, read from global
+// memory four rows before their use (the right-hand side is read-only for
+// the launch and each lane uses only the values it loads, so they go straight
+// to registers); nothing is loaded for rows outside the phase's rows or lanes
+// without interior cells of that row parity, whose cells are masked.
+__device__ __forceinline__ void tb_g_load(float (&g)[4], const float* gp, bool ok) {
+  float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (ok) v = __ldg(reinterpret_cast<const float4*>(gp));
+  g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
 }
 
 // One row r of a phase on the staged tile.  om / oc / op: the neighbour
 // colour's staged rows r-1, r, r+1 (this lane's 4 columns, in registers);
 // S = (i + colour) & 1 for the global row i, fixed at compile time, which
 // decides which single neighbour value comes from the next lane (S == 0: the
-// east one of the last cell; S == 1: the west one of the first cell).  m: this
-// lane's interior cells (unused when FULL); out_row / outc: the cells counted
-// by the max|change| of a measured phase.  Exact operation order of the oracle.
+// east one of the last cell; S == 1: the west one of the first cell).  gv:
+// the row's right-hand side (HAS_G).  m: this lane's interior cells (unused
+// when FULL); out_row / outc: the cells counted by the max|change| of a
+// measured phase.  Exact operation order of the oracle.
 template <bool LASTM, bool FULL, bool HAS_G, int S>
 __device__ __forceinline__ void tb_row(const float (&om)[4], const float (&oc)[4], const float (&op)[4],
-                                       float* __restrict__ own_p, const float* __restrict__ g_p, unsigned m,
+                                       float* __restrict__ own_p, const float (&gv)[4], unsigned m,
                                        bool out_row, unsigned outc, float a, float b, unsigned& dm32) {
   float W[4], E[4];
   if (S == 0) {
@@ -94,16 +90,8 @@ __device__ __forceinline__ void tb_row(const float (&om)[4], const float (&oc)[4
     W[0] = side; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
     E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
   }
-  float own[4], gv[4];
+  float own[4];
   load4(own_p, own);
-  if (HAS_G) {
-    if (FULL || m) {
-      load4(g_p, gv);
-    } else {
-#pragma unroll
-      for (int v = 0; v < 4; ++v) gv[v] = 0.0f;
-    }
-  }
   // Cells of staged columns 0 and C-1 see a wrong W or E (no staged
   // neighbour); like every cell near the staged border they are stale, and
   // the stale band never reaches the output tile.
@@ -124,65 +112,68 @@ __device__ __forceinline__ void tb_row(const float (&om)[4], const float (&oc)[4
 struct TbRows {
   float* Sc;        // own colour, staged
   const float* So;  // neighbour colour, staged
-  const float* Gc;  // right-hand side of the own colour (HAS_G)
-  float* gbuf;      // this warp's kTbGSlots right-hand-side row buffers
-  int base_r, qf, n, pitch, colour, lane, r0, out_lo, out_hi;
+  const float* Gc;  // right-hand side of the own colour at this lane's first cell of row r0 (HAS_G)
+  int qf, pitch, lane, r0, out_lo, out_hi;
   unsigned in0, in1, outc;
+  bool gok0, gok1;  // this lane has interior cells in rows of parity 0 / 1
   float a, b;
 };
 
+// Row r (parity S) with right-hand side gv, after which gv takes row r + 4's
+// (the next row of the same parity this lane handles), from gp_next.
 template <int C, bool LASTM, bool FULL, bool HAS_G, int S>
 __device__ __forceinline__ void tb_row_at(const TbRows& R, int r, int r1, const float (&om)[4], const float (&oc)[4],
-                                          const float (&op)[4], unsigned& dm32) {
-  const float* gp = nullptr;
-  if (HAS_G) {  // fetch row r + kTbGAhead's right-hand side, then wait for row r's
-    const int ra = r + kTbGAhead;
-    tb_g_issue(R.gbuf + ((ra - R.r0) & (kTbGSlots - 1)) * C, R.Gc, R.base_r + ra, R.qf, R.n, R.pitch, R.colour,
-               R.lane, ra < r1);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kTbGAhead) : "memory");
-    gp = R.gbuf + ((r - R.r0) & (kTbGSlots - 1)) * C + 4 * R.lane;
-  }
+                                          const float (&op)[4], float (&gv)[4], const float* gp_next,
+                                          unsigned& dm32) {
   const bool out_row = LASTM && r >= R.out_lo && r < R.out_hi;
-  tb_row<LASTM, FULL, HAS_G, S>(om, oc, op, R.Sc + r * C + 4 * R.lane, gp, S ? R.in1 : R.in0, out_row, R.outc, R.a,
+  tb_row<LASTM, FULL, HAS_G, S>(om, oc, op, R.Sc + r * C + 4 * R.lane, gv, S ? R.in1 : R.in0, out_row, R.outc, R.a,
                                 R.b, dm32);
+  if (HAS_G) tb_g_load(gv, gp_next, r + 4 < r1 && (S ? R.gok1 : R.gok0));
 }
 
 // Rows [R.r0, r1) of the staged tile, the first with parity S0.  Bodies of
 // four rows cycle four register rows in place (rows r-1 .. r+4 pass through
-// X, Y, P, Q and leave X, Y holding r+3, r+4), so no row values are moved.
+// X, Y, P, Q and leave X, Y holding r+3, r+4), so no row values are moved;
+// G0 .. G3 hold the right-hand side of rows r .. r+3, each refilled with the
+// row four below as soon as it has been used.
 template <int C, bool LASTM, bool FULL, bool HAS_G, int S0>
 __device__ __forceinline__ void tb_rows(const TbRows& R, int r1, unsigned& dm32) {
   const float* So = R.So + 4 * R.lane;
   int r = R.r0;
   float X[4], Y[4], P[4], Q[4];
+  float G0[4], G1[4], G2[4], G3[4];
+  const ptrdiff_t gs = R.pitch;
+  const float* gp = R.Gc;  // right-hand side of row r
   load4(So + (r - 1) * C, X);
   load4(So + r * C, Y);
-  if (HAS_G)
-    for (int k = 0; k < kTbGAhead; ++k)
-      tb_g_issue(R.gbuf + k * C, R.Gc, R.base_r + r + k, R.qf, R.n, R.pitch, R.colour, R.lane, r + k < r1);
-  for (; r + 4 <= r1; r += 4) {
-    load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
-    load4(So + (r + 2) * C, Q);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
-    load4(So + (r + 3) * C, X);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
-    load4(So + (r + 4) * C, Y);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 3, r1, Q, X, Y, dm32);
+  if (HAS_G) {
+    tb_g_load(G0, gp, S0 ? R.gok1 : R.gok0);
+    tb_g_load(G1, gp + gs, r + 1 < r1 && (S0 ? R.gok0 : R.gok1));
+    tb_g_load(G2, gp + 2 * gs, r + 2 < r1 && (S0 ? R.gok1 : R.gok0));
+    tb_g_load(G3, gp + 3 * gs, r + 3 < r1 && (S0 ? R.gok0 : R.gok1));
   }
-  if (r < r1) {
+  for (; r + 4 <= r1; r += 4, gp += 4 * gs) {
     load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, dm32);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, G0, gp + 4 * gs, dm32);
+    load4(So + (r + 2) * C, Q);
+    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, G1, gp + 5 * gs, dm32);
+    load4(So + (r + 3) * C, X);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, G2, gp + 6 * gs, dm32);
+    load4(So + (r + 4) * C, Y);
+    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 3, r1, Q, X, Y, G3, gp + 7 * gs, dm32);
+  }
+  if (r < r1) {  // the last rows' right-hand sides are in G0 .. G2 already; nothing further is loaded
+    load4(So + (r + 1) * C, P);
+    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, G0, gp, dm32);
     if (r + 1 < r1) {
       load4(So + (r + 2) * C, Q);
-      tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, dm32);
+      tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, G1, gp, dm32);
       if (r + 2 < r1) {
         load4(So + (r + 3) * C, X);
-        tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, dm32);
+        tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, G2, gp, dm32);
       }
     }
   }
-  if (HAS_G) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the groups past r1 are empty
 }
 
 // One colour phase on the staged tile: rows [r0, r1) of the staged arrays for
@@ -194,7 +185,7 @@ template <int T, bool LASTM, bool FULL, bool HAS_G>
 __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __restrict__ So,
                                          const float* __restrict__ Gc, int colour, int base_r, int base_q, int r0,
                                          int r1, int n, int pitch, int out_rows, int lane, float a, float b,
-                                         unsigned& dm32, float* gbuf /* [kTbGSlots][128] for this warp */) {
+                                         unsigned& dm32) {
   using Gm = TbGeom<T>;
   r0 = max(r0, 1 - base_r);  // global rows 1 .. n only
   r1 = min(r1, n + 1 - base_r);
@@ -202,13 +193,9 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
   TbRows R;
   R.Sc = Sc;
   R.So = So;
-  R.Gc = Gc;
-  R.gbuf = gbuf;
-  R.base_r = base_r;
   R.qf = base_q + 4 * lane;
-  R.n = n;
+  R.Gc = HAS_G ? Gc + (ptrdiff_t)(base_r + r0) * pitch + R.qf + kOff : nullptr;
   R.pitch = pitch;
-  R.colour = colour;
   R.lane = lane;
   R.r0 = r0;
   R.out_lo = Gm::HR;
@@ -230,6 +217,8 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
       R.in1 |= (unsigned)(q >= 1 && q <= ((n + 1) >> 1)) << v;
     }
   }
+  R.gok0 = R.in0 != 0;
+  R.gok1 = R.in1 != 0;
   if (LASTM) {
     const int col = 4 * lane;
 #pragma unroll
@@ -257,7 +246,6 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
   float* const S1 = tb_smem + Gm::R * Gm::C;
   __shared__ unsigned long long red[kWarps];
   __shared__ int ctl[5];  // skip, nt, k_end, measure, src
-  __shared__ __align__(16) float gbufs[kWarps][kTbGSlots][Gm::C];  // right-hand-side rows, a ring per warp
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
@@ -330,9 +318,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
         float* Sc = c ? S1 : S0;
         const float* So = c ? S0 : S1;
         const float* Gc = (const float*)sd.g[c];
-        float* gb = &gbufs[warp][0][0];
 #define TB_PHASE(LM, FL, HG) \
-  tb_phase<T, LM, FL, HG>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32, gb)
+  tb_phase<T, LM, FL, HG>(Sc, So, Gc, c, base_r, base_q, r0, r1, n, pitch, tl.nrows, lane, a, b, dm32)
         if (Gc) {
           if (full) {
             if (lastm) TB_PHASE(true, true, true); else TB_PHASE(false, true, true);

@@ -24,14 +24,18 @@ TOL64 = 1e-12
 
 @pytest.fixture(scope="module")
 def ctxs():
-    """Three contexts: the default one (small plain plates solved in one
-    launch on a cooperative grid of many SMs, or in one thread-block cluster
-    when the stop test is the residual), one that always takes the cluster
-    for them, and one with the one-launch paths switched off, so the chunked
-    multi-CTA kernels are exercised at every size."""
+    """Four contexts: the default one (small plain plates solved in one
+    launch on a cooperative grid of many SMs, with point-to-point exchanges
+    between bands and the stop test decided behind the sweeps; in one
+    thread-block cluster when the stop test is the residual), one whose grid
+    takes a grid-wide barrier per colour phase instead, one that always takes
+    the cluster, and one with the one-launch paths switched off, so the
+    chunked multi-CTA kernels are exercised at every size."""
     from paper_1401_0763_gb300 import _build, capi
     _build.build()
-    made = {"grid": capi.Context(0), "cluster": capi.Context(0), "multi": capi.Context(0)}
+    made = {"grid": capi.Context(0), "gridbar": capi.Context(0), "cluster": capi.Context(0),
+            "multi": capi.Context(0)}
+    made["gridbar"].set_option(capi.SOR_OPT_CLUSTER, 3)
     made["cluster"].set_option(capi.SOR_OPT_CLUSTER, 2)
     made["multi"].set_option(capi.SOR_OPT_CLUSTER, 0)
     yield made
@@ -49,7 +53,7 @@ def ctx_mc(ctxs):
     return ctxs["multi"]
 
 
-PATHS = ["grid", "cluster", "multi"]
+PATHS = ["grid", "gridbar", "cluster", "multi"]
 
 
 def capi_mod():
@@ -444,6 +448,39 @@ def test_cluster_path_converges_like_oracle(ctx, n, precision):
     assert res["converged"] == ref["converged"] and res["iterations"] == ref["iterations"]
     assert np.array_equal(got, ref["u"])
     assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 9, 130, 301, 384])
+@pytest.mark.parametrize("K,iters,tol", [(1, 400, 1e-6), (4, 203, 1e-30), (5, 3000, 1e-7), (1000, 57, 1e-9)])
+def test_grid_flow_stops_like_oracle(ctxs, n, K, iters, tol):
+    """The barrier-free grid decides the stop test behind the sweeps and rolls
+    each band back to its copy of the stop iteration: the iteration count,
+    the last max|change| and the solution equal the oracle's, whether the
+    solve stops early (K = 1 or 5), runs to a cap that is not a multiple of K,
+    or has no tested iteration before the cap (K = 1000)."""
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 11 * n + K)
+    f = wl.gaussian_source(n, n + K) * 10 if n % 3 == 1 else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=iters, check_every=K, tol=tol)
+    for path in ("grid", "gridbar"):
+        got, res = run(ctxs[path], u0, f, omega=w, tol=tol, max_iters=iters, check_every=K,
+                       flags=capi.SOR_FLAG_EXACT_ORDER)
+        assert res["iterations"] == ref["iterations"] and res["converged"] == ref["converged"], path
+        assert res["final_maxdelta"] == ref["final_maxdelta"], path
+        assert np.array_equal(got, ref["u"]), path
+
+
+@pytest.mark.parametrize("n", [3, 200, 768])
+def test_grid_flow_fp32_stops_like_oracle(ctx, n):
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 7 * n)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f32(u0, w, max_iters=1500, check_every=1, tol=5e-3)
+    got, res = run(ctx, u0, precision=capi.SOR_FP32, omega=w, tol=5e-3, max_iters=1500, check_every=1)
+    assert res["iterations"] == ref["iterations"] and res["converged"] == ref["converged"]
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+    assert np.array_equal(got, ref["u"])
 
 
 @pytest.fixture(scope="module")
