@@ -119,61 +119,126 @@ struct TbRows {
   float a, b;
 };
 
-// Row r (parity S) with right-hand side gv, after which gv takes row r + 4's
-// (the next row of the same parity this lane handles), from gp_next.
-template <int C, bool LASTM, bool FULL, bool HAS_G, int S>
+// Row r (parity S) with right-hand side gv, after which gv takes row
+// r + AHEAD's (a row of the same parity), from gp_next.
+template <int C, bool LASTM, bool FULL, bool HAS_G, int S, int AHEAD = 8>
 __device__ __forceinline__ void tb_row_at(const TbRows& R, int r, int r1, const float (&om)[4], const float (&oc)[4],
                                           const float (&op)[4], float (&gv)[4], const float* gp_next,
                                           unsigned& dm32) {
   const bool out_row = LASTM && r >= R.out_lo && r < R.out_hi;
   tb_row<LASTM, FULL, HAS_G, S>(om, oc, op, R.Sc + r * C + 4 * R.lane, gv, S ? R.in1 : R.in0, out_row, R.outc, R.a,
                                 R.b, dm32);
-  if (HAS_G) tb_g_load(gv, gp_next, r + 4 < r1 && (S ? R.gok1 : R.gok0));
+  if (HAS_G) tb_g_load(gv, gp_next, r + AHEAD < r1 && (S ? R.gok1 : R.gok0));
 }
 
-// Rows [R.r0, r1) of the staged tile, the first with parity S0.  Bodies of
-// four rows cycle four register rows in place (rows r-1 .. r+4 pass through
-// X, Y, P, Q and leave X, Y holding r+3, r+4), so no row values are moved;
-// G0 .. G3 hold the right-hand side of rows r .. r+3, each refilled with the
-// row four below as soon as it has been used.
-template <int C, bool LASTM, bool FULL, bool HAS_G, int S0>
-__device__ __forceinline__ void tb_rows(const TbRows& R, int r1, unsigned& dm32) {
+// Rows [R.r0, r1) of the staged tile, the first with parity S0, without a
+// right-hand side.  Bodies of four rows cycle four register rows in place
+// (rows r-1 .. r+4 pass through X, Y, P, Q and leave X, Y holding r+3, r+4),
+// so no row values are moved.
+template <int C, bool LASTM, bool FULL, int S0>
+__device__ __forceinline__ void tb_rows_plain(const TbRows& R, int r1, unsigned& dm32) {
   const float* So = R.So + 4 * R.lane;
   int r = R.r0;
-  float X[4], Y[4], P[4], Q[4];
-  float G0[4], G1[4], G2[4], G3[4];
-  const ptrdiff_t gs = R.pitch;
-  const float* gp = R.Gc;  // right-hand side of row r
+  float X[4], Y[4], P[4], Q[4], G[4];  // G: unused right-hand side
   load4(So + (r - 1) * C, X);
   load4(So + r * C, Y);
-  if (HAS_G) {
-    tb_g_load(G0, gp, S0 ? R.gok1 : R.gok0);
-    tb_g_load(G1, gp + gs, r + 1 < r1 && (S0 ? R.gok0 : R.gok1));
-    tb_g_load(G2, gp + 2 * gs, r + 2 < r1 && (S0 ? R.gok1 : R.gok0));
-    tb_g_load(G3, gp + 3 * gs, r + 3 < r1 && (S0 ? R.gok0 : R.gok1));
-  }
-  for (; r + 4 <= r1; r += 4, gp += 4 * gs) {
+  for (; r + 4 <= r1; r += 4) {
     load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, G0, gp + 4 * gs, dm32);
+    tb_row_at<C, LASTM, FULL, false, S0>(R, r, r1, X, Y, P, G, nullptr, dm32);
     load4(So + (r + 2) * C, Q);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, G1, gp + 5 * gs, dm32);
+    tb_row_at<C, LASTM, FULL, false, 1 - S0>(R, r + 1, r1, Y, P, Q, G, nullptr, dm32);
     load4(So + (r + 3) * C, X);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, G2, gp + 6 * gs, dm32);
+    tb_row_at<C, LASTM, FULL, false, S0>(R, r + 2, r1, P, Q, X, G, nullptr, dm32);
     load4(So + (r + 4) * C, Y);
-    tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 3, r1, Q, X, Y, G3, gp + 7 * gs, dm32);
+    tb_row_at<C, LASTM, FULL, false, 1 - S0>(R, r + 3, r1, Q, X, Y, G, nullptr, dm32);
   }
-  if (r < r1) {  // the last rows' right-hand sides are in G0 .. G2 already; nothing further is loaded
+  if (r < r1) {
     load4(So + (r + 1) * C, P);
-    tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r, r1, X, Y, P, G0, gp, dm32);
+    tb_row_at<C, LASTM, FULL, false, S0>(R, r, r1, X, Y, P, G, nullptr, dm32);
     if (r + 1 < r1) {
       load4(So + (r + 2) * C, Q);
-      tb_row_at<C, LASTM, FULL, HAS_G, 1 - S0>(R, r + 1, r1, Y, P, Q, G1, gp, dm32);
+      tb_row_at<C, LASTM, FULL, false, 1 - S0>(R, r + 1, r1, Y, P, Q, G, nullptr, dm32);
       if (r + 2 < r1) {
         load4(So + (r + 3) * C, X);
-        tb_row_at<C, LASTM, FULL, HAS_G, S0>(R, r + 2, r1, P, Q, X, G2, gp, dm32);
+        tb_row_at<C, LASTM, FULL, false, S0>(R, r + 2, r1, P, Q, X, G, nullptr, dm32);
       }
     }
   }
+}
+
+// The same with a right-hand side: bodies of eight rows (two turns of the
+// four register rows), G[j] holding the right-hand side of row r + j and
+// refilled with row r + j + 8 as soon as it has been used, so each load is
+// issued eight rows before its use.
+template <int C, bool LASTM, bool FULL, int S0>
+__device__ __forceinline__ void tb_rows_g(const TbRows& R, int r1, unsigned& dm32) {
+  const float* So = R.So + 4 * R.lane;
+  int r = R.r0;
+  float X[4], Y[4], P[4], Q[4];
+  float G[8][4];
+  const ptrdiff_t gs = R.pitch;
+  const float* gp = R.Gc;  // right-hand side of row r
+  const bool ok0 = S0 ? R.gok1 : R.gok0;  // rows of the parity of row r0 / of the other parity
+  const bool ok1 = S0 ? R.gok0 : R.gok1;
+  load4(So + (r - 1) * C, X);
+  load4(So + r * C, Y);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) tb_g_load(G[j], gp + j * gs, r + j < r1 && ((j & 1) ? ok1 : ok0));
+  for (; r + 8 <= r1; r += 8, gp += 8 * gs) {
+    load4(So + (r + 1) * C, P);
+    tb_row_at<C, LASTM, FULL, true, S0>(R, r, r1, X, Y, P, G[0], gp + 8 * gs, dm32);
+    load4(So + (r + 2) * C, Q);
+    tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 1, r1, Y, P, Q, G[1], gp + 9 * gs, dm32);
+    load4(So + (r + 3) * C, X);
+    tb_row_at<C, LASTM, FULL, true, S0>(R, r + 2, r1, P, Q, X, G[2], gp + 10 * gs, dm32);
+    load4(So + (r + 4) * C, Y);
+    tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 3, r1, Q, X, Y, G[3], gp + 11 * gs, dm32);
+    load4(So + (r + 5) * C, P);
+    tb_row_at<C, LASTM, FULL, true, S0>(R, r + 4, r1, X, Y, P, G[4], gp + 12 * gs, dm32);
+    load4(So + (r + 6) * C, Q);
+    tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 5, r1, Y, P, Q, G[5], gp + 13 * gs, dm32);
+    load4(So + (r + 7) * C, X);
+    tb_row_at<C, LASTM, FULL, true, S0>(R, r + 6, r1, P, Q, X, G[6], gp + 14 * gs, dm32);
+    load4(So + (r + 8) * C, Y);
+    tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 7, r1, Q, X, Y, G[7], gp + 15 * gs, dm32);
+  }
+  // at most seven rows left, their right-hand sides in G[0] .. G[6]; nothing further is loaded
+  if (r < r1) {
+    load4(So + (r + 1) * C, P);
+    tb_row_at<C, LASTM, FULL, true, S0>(R, r, r1, X, Y, P, G[0], gp, dm32);
+    if (r + 1 < r1) {
+      load4(So + (r + 2) * C, Q);
+      tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 1, r1, Y, P, Q, G[1], gp, dm32);
+      if (r + 2 < r1) {
+        load4(So + (r + 3) * C, X);
+        tb_row_at<C, LASTM, FULL, true, S0>(R, r + 2, r1, P, Q, X, G[2], gp, dm32);
+        if (r + 3 < r1) {
+          load4(So + (r + 4) * C, Y);
+          tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 3, r1, Q, X, Y, G[3], gp, dm32);
+          if (r + 4 < r1) {
+            load4(So + (r + 5) * C, P);
+            tb_row_at<C, LASTM, FULL, true, S0>(R, r + 4, r1, X, Y, P, G[4], gp, dm32);
+            if (r + 5 < r1) {
+              load4(So + (r + 6) * C, Q);
+              tb_row_at<C, LASTM, FULL, true, 1 - S0>(R, r + 5, r1, Y, P, Q, G[5], gp, dm32);
+              if (r + 6 < r1) {
+                load4(So + (r + 7) * C, X);
+                tb_row_at<C, LASTM, FULL, true, S0>(R, r + 6, r1, P, Q, X, G[6], gp, dm32);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int C, bool LASTM, bool FULL, bool HAS_G, int S0>
+__device__ __forceinline__ void tb_rows(const TbRows& R, int r1, unsigned& dm32) {
+  if (HAS_G)
+    tb_rows_g<C, LASTM, FULL, S0>(R, r1, dm32);
+  else
+    tb_rows_plain<C, LASTM, FULL, S0>(R, r1, dm32);
 }
 
 // One colour phase on the staged tile: rows [r0, r1) of the staged arrays for
