@@ -37,7 +37,8 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal rate: 152 SMs x 2 
 # from the ncu capture of the current kernel (None: no capture of the current kernel yet)
 FAST64_DRAM_BYTES_PER_LAUNCH = 11405769728 + 6608791552
 # the same counters for one k_sweep_tb<6,0> launch (6 fused iterations) on the FP32 plate, per update
-TB32_DRAM_BYTES_PER_UPDATE = (68465664 + 22038272) / (6.0 * 4096 * 4096)
+# (captured again after the kernel lost its unused 16 KB right-hand-side ring)
+TB32_DRAM_BYTES_PER_UPDATE = (68468992 + 21732096) / (6.0 * 4096 * 4096)
 
 
 def dist_env():
