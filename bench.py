@@ -706,8 +706,9 @@ def workload_cube256(args, ctx, capi, wl):
     """3D red-black SOR (7-point stencil, the paper's next step, Section 5): 258^3 cube, shell values
     i.i.d. U[0, 100], interior 0, f = 0, w_opt, 1000 iterations with max|change| every 50, device-resident
     inputs.  Lines: FP64 default (rescaled unknowns, shared pair sums, within 1e-12 of the oracle), FP64
-    exact order and FP32 (both bitwise equal to the oracle).  The oracle is timed on 10 iterations of the
-    same cube on one host core."""
+    exact order and FP32 (both bitwise equal to the oracle); FP32 at each cube depth (iterations fused per
+    blocked launch, 1 and 2; the default 0 = one data-flow launch per run of iterations).  The
+    oracle is timed on 10 iterations of the same cube on one host core."""
     import numpy as np
     import torch
 
@@ -718,8 +719,11 @@ def workload_cube256(args, ctx, capi, wl):
     out = torch.empty_like(u0)
     w = capi.sor_omega_opt(n)
     lines = {}
-    for name, prec, flags in (("fp64", capi.SOR_FP64, 0), ("fp64_exact", capi.SOR_FP64, capi.SOR_FLAG_EXACT_ORDER),
-                              ("fp32", capi.SOR_FP32, 0)):
+    for name, prec, flags, depth in (("fp64", capi.SOR_FP64, 0, 0),
+                                     ("fp64_exact", capi.SOR_FP64, capi.SOR_FLAG_EXACT_ORDER, 0),
+                                     ("fp32", capi.SOR_FP32, 0, 0), ("fp32_blocked1", capi.SOR_FP32, 0, 1),
+                                     ("fp32_blocked2", capi.SOR_FP32, 0, 2)):
+        ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, depth)
         kw = dict(precision=prec, omega=w, tol=0.0, max_iters=iters, check_every=50, flags=flags)
         for _ in range(args.warmup):
             ctx.solve3d(u0, out=out, **dict(kw, max_iters=100))
@@ -734,6 +738,7 @@ def workload_cube256(args, ctx, capi, wl):
         lup = float(n) ** 3 * iters
         lines[name] = {"glups": lup / float(np.median(dev)) / 1e9, "glups_call": lup / dt / 1e9,
                        "solve_s": dt, "iterations": res["iterations"]}
+    ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, 0)
     # FP64: 8 algorithmic flops per update ((1-w)u + (w/6)(sum of six neighbours): 5 adds, 2 multiplies,
     # 1 add); the default kernel issues 5 FP64 operations per update for them, the exact one 8
     for name, kern in (("fp64", "k_f3_flow"), ("fp64_exact", "k_3_flow<double>")):
@@ -745,7 +750,8 @@ def workload_cube256(args, ctx, capi, wl):
     hbm = float(peaks.get("hbm_gbs") or 6800.0)
     lines["fp32"]["roofline"] = {"bound": "hbm", "achieved": 8.0 * lines["fp32"]["glups"], "peak": hbm,
                                  "unit": "GB/s", "frac": 8.0 * lines["fp32"]["glups"] / hbm,
-                                 "kernel": "k_3_flow<float>", "peak_source": src}
+                                 "kernel": "k_3_flow<float>", "peak_source": src,
+                                 "note": "unfused-equivalent bytes; the 69 MB FP32 state is L2-resident"}
     cpu = None
     if not args.no_cpu_baseline:
         k = 10
@@ -758,6 +764,43 @@ def workload_cube256(args, ctx, capi, wl):
             "unit": "GLUP/s", "higher_is_better": True, "dtype": "f64", "detail": lines, "cpu_baseline": cpu,
             "config": {"workload": "258^3 cube, shell U[0,100], w_opt, 1000 iterations, max|change| every 50",
                        "l2": "colour-split FP64 state 2 x 85 MB, above the 129 MB L2"}}
+
+
+def workload_cube512(args, ctx, capi, wl):
+    """FP32 red-black SOR on a 514^3 cube (state 0.6 GB per buffer pair, far above L2), shell U[0, 100],
+    interior 0, f = 0, w_opt, 200 iterations with max|change| every 50, device-resident inputs, at each cube
+    depth (0 = default, one data-flow launch per run of iterations; 1 and 2 = blocked sweeps)."""
+    import numpy as np
+    import torch
+    n, iters = 512, 200
+    u0 = torch.from_numpy(wl.random_shell(n, args.seed)).cuda()
+    out = torch.empty_like(u0)
+    w = capi.sor_omega_opt(n)
+    lines = {}
+    for name, depth in (("fp32", 0), ("fp32_blocked1", 1), ("fp32_blocked2", 2)):
+        ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, depth)
+        kw = dict(precision=capi.SOR_FP32, omega=w, tol=0.0, max_iters=iters, check_every=50)
+        for _ in range(args.warmup):
+            ctx.solve3d(u0, out=out, **dict(kw, max_iters=50))
+        torch.cuda.synchronize()
+        dev = []
+        for _ in range(args.steps):
+            _, res = ctx.solve3d(u0, out=out, **kw)
+            dev.append(res["device_s"])
+        lup = float(n) ** 3 * iters
+        g = lup / float(np.median(dev)) / 1e9
+        lines[name] = {"glups": g, "device_s": float(np.median(dev)), "iterations": res["iterations"],
+                       "unfused_equiv_gbs": 8.0 * g}
+    ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, 0)
+    peaks, src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    return {"metric": "FP32 3D red-black SOR GLUP/s (514^3 cube, 7-point stencil)", "value": lines["fp32"]["glups"],
+            "unit": "GLUP/s", "higher_is_better": True, "dtype": "f32", "detail": lines,
+            "roofline": {"bound": "hbm", "achieved": 8.0 * lines["fp32"]["glups"], "peak": hbm, "unit": "GB/s",
+                         "frac": 8.0 * lines["fp32"]["glups"] / hbm, "kernel": "k_3_flow<float>",
+                         "peak_source": src, "note": "unfused-equivalent bytes (8 per update)"},
+            "config": {"workload": "514^3 cube, shell U[0,100], w_opt, 200 iterations, max|change| every 50",
+                       "l2": "FP32 colour arrays 2 x 0.3 GB per buffer pair, far above the 129 MB L2"}}
 
 
 def workload_cubepoisson(args, ctx, capi, wl):
@@ -936,7 +979,7 @@ def workload_fp64rate(args, ctx, capi, wl):
 WORKLOADS = {"paper": workload_paper, "fp64rate": workload_fp64rate, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
              "serve": workload_serve, "cube256": workload_cube256, "ninepoint4096": workload_ninepoint4096,
              "cubepoisson": workload_cubepoisson, "ninepoisson": workload_ninepoisson,
-             "plate16384": workload_plate16384}
+             "plate16384": workload_plate16384, "cube512": workload_cube512}
 
 
 def run_workload(args):

@@ -294,11 +294,17 @@ typedef enum {
                                   N = 6144, wavefront kernels above) or by the autotuner; 1 = tile
                                   kernels (a shared-memory tile pass per launch); 2 = wavefront kernels
                                   (a register wavefront per warp).  Results are identical either way */
-  SOR_OPT_BATCH_PLAIN_STEP = 10 /* iterations per scheduler step of plain (FP64 / FP32) batch slots:
+  SOR_OPT_BATCH_PLAIN_STEP = 10, /* iterations per scheduler step of plain (FP64 / FP32) batch slots:
                                    0 (default) = tuned online over the scheduler's first rounds with
                                    plain slots (8, 16, 32, 64 tried, the highest update rate kept);
                                    > 0 = that many.  Results are identical either way: every slot
                                    stops on the device at its own tested iteration */
+  SOR_OPT_CUBE_DEPTH = 11       /* FP32 sweeps on cubes (sor_solve3d, SOR_FP32): 0 (default) = one
+                                   data-flow launch per run of iterations, one colour phase at a time;
+                                   1 or 2 = that many iterations fused per blocked launch, each tile of
+                                   rows x packed columns x planes streamed through its planes with the
+                                   colour phases run as a wavefront in shared memory (slower on GB300 at
+                                   the sizes measured).  Results are identical */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);

@@ -40,7 +40,8 @@ __device__ __forceinline__ size_t e3(int k, int i, int q, int m, int pitch) {
 
 // Solve description in device memory (constant while the solve runs).
 struct Desc3 {
-  void* x[2];            // colour arrays (FP64 or FP32)
+  void* x[2];            // colour arrays (FP64 or FP32); with blocked FP32 sweeps, the current pair
+  void* xalt[2];         // blocked FP32 sweeps: the other pair (written by each launch, then made current)
   const void* g[2];      // h^2 f in the sweep type, or null
   const double* g64[2];  // h^2 f in FP64 for the residual, or null
   int n, m, pitch, K, max_iters, stop, tiles;
@@ -959,6 +960,334 @@ cudaError_t launch_3_flow(const Desc3* d, SlotState* st, const Tile* strips, int
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------------
+// FP32 iterations fused per tile, streamed through the planes (temporal blocking on cubes)
+// ------------------------------------------------------------------------------------------------
+//
+// The 2D tile family's temporal blocking carried to the cube.  A tile is a
+// block of TY rows x OQ packed columns over a run of up to TZ planes.  Its
+// block walks the planes in order; at step s it stages plane s + 2 (both
+// colours: TY + 2 HR rows x 128 packed columns, HR = 2T halo rows and HQ
+// halo packed columns each side) into a ring of 2T + 3 plane slots in shared
+// memory and runs phase p = 1 .. 2T (red first; the exact update of k_3_flow)
+// on plane s - p + 1, in place.  When phase p reaches plane z, phase p - 1
+// has already passed planes z - 1, z and z + 1, and phase p + 1 has not yet
+// touched z - 1, so every read sees the values of the right phase.  Phase p
+// covers only the rows and planes within 2T - p of the tile's output (a cell
+// after t iterations depends on cells at most 2t rows or planes and t packed
+// columns away), so the stale band that grows inward from the staged border
+// never reaches the output.  Finished planes go to the other buffer pair
+// (neighbouring tiles read their halos from the previous iterate), which the
+// last block then makes the current one by swapping the descriptor's
+// pointers.  Traffic per cell: one read and one write per T iterations, plus
+// the halo re-reads.
+//
+// Measured on GB300 it is slower than the per-phase data-flow kernel on
+// cubes up to 514^3 (depth 2: 121 and 181 GLUP/s on 258^3 and 514^3, depth
+// 1: 140 and 220, per phase: 462 and 423).  A plane's band of about 22 rows
+// per phase is spread over 16 warps, so a warp updates one or two rows and
+// reuses no row in registers: the launch executes about 166 instructions per
+// update with the issue slots 61 % busy, while the per-phase kernel is not
+// bound by memory traffic at these sizes.  It is kept behind
+// SOR_OPT_CUBE_DEPTH = 1 or 2; results are identical to the per-phase form.
+
+template <int TD>
+struct Tb3Geom {
+  static constexpr int HR = 2 * TD;                    // halo rows
+  static constexpr int HQ = TD <= 3 ? 4 : 8;           // halo packed columns (a multiple of 4, >= TD + 1)
+  static constexpr int C = 128;                        // staged packed columns
+  static constexpr int OQ = C - 2 * HQ;                // output packed columns
+  static constexpr int TY = 16;                        // output rows
+  static constexpr int RY = TY + 2 * HR;               // staged rows
+  static constexpr int TZ = 32;                        // output planes
+  static constexpr int NS = 2 * TD + 3;                // plane slots
+  static constexpr int THREADS = TD == 1 ? 256 : 512;  // one block per SM at depth >= 2
+  static constexpr size_t smem = (size_t)NS * 2 * RY * C * sizeof(float);
+};
+
+// One tile: output planes [k0, k0 + nz), rows [row0, row0 + nrows), packed
+// columns [col0, col0 + OQ).
+struct Tile3 {
+  int k0, nz, row0, nrows, col0;
+};
+
+__device__ __forceinline__ void tb3_cp16(float* sdst, const float* gsrc, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(valid ? gsrc : nullptr),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+// Row r of plane z, colour c, on the staged tile (this lane's 4 packed
+// columns).  Sc: own colour of plane z; So / Sd / Su: the other colour of
+// planes z, z - 1, z + 1.  out_cells: bit v set for cells of the tile's output
+// whose change is measured (0 when not measured).
+__device__ __forceinline__ void tb3_row(float* __restrict__ Sc, const float* __restrict__ So,
+                                        const float* __restrict__ Sd, const float* __restrict__ Su,
+                                        const float* __restrict__ Gp, int r, int S, int qf, int qlim, float a,
+                                        float b, unsigned out_cells, unsigned& dm32, int lane) {
+  constexpr int C = 128;
+  const int o = r * C + 4 * lane;
+  float own[4], om[4], oc[4], op[4], dn[4], up[4];
+  load4(Sc + o, own);
+  load4(So + o - C, om);
+  load4(So + o, oc);
+  load4(So + o + C, op);
+  load4(Sd + o, dn);
+  load4(Su + o, up);
+  float W[4], E[4];
+  if (S == 0) {
+    const float side = __shfl_down_sync(0xffffffffu, oc[0], 1);
+    W[0] = oc[0]; W[1] = oc[1]; W[2] = oc[2]; W[3] = oc[3];
+    E[0] = oc[1]; E[1] = oc[2]; E[2] = oc[3]; E[3] = side;
+  } else {
+    const float side = __shfl_up_sync(0xffffffffu, oc[3], 1);
+    W[0] = side; W[1] = oc[0]; W[2] = oc[1]; W[3] = oc[2];
+    E[0] = oc[0]; E[1] = oc[1]; E[2] = oc[2]; E[3] = oc[3];
+  }
+  float gv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (Gp) {
+    const float4 g4 = __ldg(reinterpret_cast<const float4*>(Gp));
+    gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+  }
+  // cells of staged columns 0 and 127 see a wrong W or E: like every cell
+  // near the staged border they are stale, and the stale band never reaches
+  // the output
+  float nv[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    float sum = radd(radd(radd(om[v], op[v]), radd(W[v], E[v])), radd(dn[v], up[v]));
+    if (Gp) sum = radd(sum, gv[v]);
+    const float nu = radd(rmul(a, own[v]), rmul(b, sum));
+    const bool in = qf + v >= 1 && qf + v <= qlim;
+    nv[v] = in ? nu : own[v];
+    if (in && ((out_cells >> v) & 1u)) dm32 = max(dm32, abs_bits32(radd(nu, -own[v])));
+  }
+  store4(Sc + o, nv);
+}
+
+template <int TD>
+__global__ void __launch_bounds__(Tb3Geom<TD>::THREADS) k_sweep3_tb(Desc3* dp, SlotState* st,
+                                                                    const Tile3* __restrict__ tiles, int ntiles,
+                                                                    int nt_req) {
+  using Gm = Tb3Geom<TD>;
+  constexpr int NW = Gm::THREADS / 32;
+  constexpr int C = Gm::C;
+  extern __shared__ __align__(16) float t3s[];
+  __shared__ unsigned long long red[NW];
+  __shared__ int ctl[4];  // skip, iterations, last iteration, measured
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = dp->n, m = dp->m, pitch = dp->pitch;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile3 tl = tiles[t];
+    if (threadIdx.x == 0) {
+      int skip = *((volatile int*)&st->done);
+      const int k0 = *((volatile int*)&st->iters);
+      const int nt = min(nt_req, dp->max_iters - k0);
+      const int k_end = k0 + nt;
+      const int measure = (k_end % dp->K) == 0 || k_end >= dp->max_iters;
+      for (int j = k0 + 1; j < k_end && !skip; ++j)  // the host plan ends launches at tested iterations
+        if ((j % dp->K) == 0) {
+          st->error = 1;
+          st->done = 1;
+          skip = 1;
+        }
+      if (nt <= 0) skip = 1;
+      ctl[0] = skip;
+      ctl[1] = nt;
+      ctl[2] = k_end;
+      ctl[3] = measure;
+    }
+    __syncthreads();
+    const int skip = ctl[0], nt = ctl[1], k_end = ctl[2], measure = ctl[3];
+    __syncthreads();
+    if (skip) continue;
+
+    const float* X0 = (const float*)dp->x[0];  // the current pair: staged from
+    const float* X1 = (const float*)dp->x[1];
+    float* Y0 = (float*)dp->xalt[0];  // the other pair: the tile's output goes here
+    float* Y1 = (float*)dp->xalt[1];
+    const float* G0 = (const float*)dp->g[0];
+    const float* G1 = (const float*)dp->g[1];
+    const float a = dp->a32, b = dp->b32;
+    const int base_r = tl.row0 - Gm::HR;
+    const int base_q = tl.col0 - Gm::HQ;
+    const int base_e = base_q + kOff;  // element of staged column 0 (a multiple of 4)
+    const int zlo = tl.k0, zhi = tl.k0 + tl.nz;  // output planes [zlo, zhi)
+    const int z_first = max(1, zlo - 2 * nt + 1);  // the first plane of phase 1 (the first step)
+    const int z_last = zhi - 1 + 2 * nt - 1;       // the step of phase 2nt on the last output plane
+    const int z_in = min(m - 1, zhi + 2 * nt - 1);  // the last plane staged
+    auto plane = [&](int z, int c) -> float* {
+      return t3s + ((size_t)((z + 8 * Gm::NS) % Gm::NS) * 2 + c) * Gm::RY * C;
+    };
+    // plane z of both colours into its slot, rows and columns outside the
+    // array reading as 0; one copy group per call
+    auto stage = [&](int z) {
+      if (z <= z_in) {
+        for (int idx = threadIdx.x; idx < 2 * Gm::RY * 32; idx += blockDim.x) {
+          const int c = idx / (Gm::RY * 32);
+          const int rr = (idx >> 5) - c * Gm::RY;
+          const int ln = idx & 31;
+          const int i = base_r + rr;
+          const int e = base_e + 4 * ln;
+          const bool valid = i >= 0 && i < m && e >= 0 && e + 4 <= pitch;
+          const float* gp = valid ? (c ? X1 : X0) + ((size_t)z * m + i) * pitch + e : nullptr;
+          tb3_cp16(plane(z, c) + rr * C + 4 * ln, gp, valid);
+        }
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    stage(z_first - 1);
+    stage(z_first);
+    stage(z_first + 1);
+    unsigned dm32 = 0;
+    for (int s = z_first; s <= z_last; ++s) {
+      stage(s + 2);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // plane s + 1 has arrived
+      __syncthreads();
+#pragma unroll 1
+      for (int p = 1; p <= 2 * nt; ++p) {
+        const int z = s - p + 1;
+        const int reach = 2 * nt - p;
+        const int c = (p - 1) & 1;
+        if (z >= max(1, zlo - reach) && z <= min(n, zhi - 1 + reach)) {
+          const bool lastm = measure && p >= 2 * nt - 1 && z >= zlo && z < zhi;
+          const int r_lo = max(Gm::HR - reach, 1 - base_r);
+          const int r_hi = min(Gm::HR + tl.nrows + reach, n + 1 - base_r);
+          float* Sc = plane(z, c);
+          const float* So = plane(z, c ^ 1);
+          const float* Sd = plane(z - 1, c ^ 1);
+          const float* Su = plane(z + 1, c ^ 1);
+          const float* Gc = c ? G1 : G0;
+          const int qf = base_q + 4 * lane;
+          unsigned outc = 0;
+          if (lastm)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              outc |= (unsigned)(4 * lane + v >= Gm::HQ && 4 * lane + v < Gm::HQ + Gm::OQ) << v;
+          for (int r = r_lo + warp; r < r_hi; r += NW) {
+            const int i = base_r + r;
+            const int S = (i + z + c) & 1;
+            const int qlim = (n + S) >> 1;
+            const float* Gp = (Gc && qf <= qlim && qf + 3 >= 1) ? Gc + ((size_t)z * m + i) * pitch + qf + kOff : nullptr;
+            const bool out_row = r >= Gm::HR && r < Gm::HR + tl.nrows;
+            tb3_row(Sc, So, Sd, Su, Gp, r, S, qf, qlim, a, b, out_row ? outc : 0u, dm32, lane);
+          }
+        }
+        __syncthreads();
+      }
+      // plane s - 2nt + 1 has had its last phase: its output rows and columns to the other pair
+      const int zo = s - 2 * nt + 1;
+      if (zo >= zlo && zo < zhi) {
+        for (int idx = threadIdx.x; idx < 2 * tl.nrows * 32; idx += blockDim.x) {
+          const int c = idx / (tl.nrows * 32);
+          const int rr = (idx >> 5) - c * tl.nrows;
+          const int col = 4 * (idx & 31);
+          if (col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
+          const int i = tl.row0 + rr;
+          const int qlim = (n + ((i + zo + c) & 1)) >> 1;
+          const int qf = base_q + col;
+          if (qf > qlim) continue;
+          float v4[4];
+          load4(plane(zo, c) + (Gm::HR + rr) * C + col, v4);
+          float* Yd = (c ? Y1 : Y0) + ((size_t)zo * m + i) * pitch + qf + kOff;
+          if (qf + 3 <= qlim) {
+            store4(Yd, v4);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (qf + v <= qlim) Yd[v] = v4[v];
+          }
+        }
+      }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the groups past the last plane are empty
+    if (measure) {
+      unsigned long long dm = warp_max64(abs_bits_of(__uint_as_float(dm32)));
+      if (lane == 0) red[warp] = dm;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned long long mm = 0;
+        for (int w = 0; w < NW; ++w) mm = umax64(mm, red[w]);
+        if (mm) atomicMax(&st->dmax_bits, mm);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned prev = atomicAdd(&st->arrive, 1u);
+      if (prev == (unsigned)ntiles - 1u) {  // every tile is written: the other pair becomes the current one
+        __threadfence();
+        void* t0 = dp->x[0];
+        void* t1 = dp->x[1];
+        dp->x[0] = dp->xalt[0];
+        dp->x[1] = dp->xalt[1];
+        dp->xalt[0] = t0;
+        dp->xalt[1] = t1;
+        finalize3(*dp, st, k_end, measure);
+      }
+    }
+    __syncthreads();  // the next tile reuses the plane slots
+  }
+}
+
+template <int TD>
+cudaError_t tb3_prepare() {
+  return cudaFuncSetAttribute(k_sweep3_tb<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tb3Geom<TD>::smem);
+}
+
+template <int TD>
+int tb3_blocks_per_sm() {
+  int nb = 0;
+  if (tb3_prepare<TD>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep3_tb<TD>, Tb3Geom<TD>::THREADS, Tb3Geom<TD>::smem) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+template <int TD>
+cudaError_t launch_sweep3_tb(Desc3* d, SlotState* st, const Tile3* tiles, int ntiles, int grid, int nt,
+                             cudaStream_t s) {
+  count_kernel_launches(1);
+  k_sweep3_tb<TD><<<grid, Tb3Geom<TD>::THREADS, Tb3Geom<TD>::smem, s>>>(d, st, tiles, ntiles, nt);
+  return cudaGetLastError();
+}
+
+// The tiles of a cube for depth TD.
+template <int TD>
+std::vector<Tile3> tb3_tiles(int n) {
+  using Gm = Tb3Geom<TD>;
+  std::vector<Tile3> out;
+  const int qmax = (n + 1) / 2;
+  for (int k0 = 1; k0 <= n; k0 += Gm::TZ)
+    for (int r0 = 1; r0 <= n; r0 += Gm::TY)
+      for (int q0 = 1; q0 <= qmax; q0 += Gm::OQ)
+        out.push_back(Tile3{k0, std::min(Gm::TZ, n - k0 + 1), r0, std::min(Gm::TY, n - r0 + 1), q0});
+  return out;
+}
+
+// Unpacks the descriptor's current pair (the blocked sweeps swap pairs on the device).
+template <typename T>
+__global__ void k_unpack3d_cur(const Desc3* __restrict__ dp, double* u) {
+  const int n = dp->n, pitch = dp->pitch, m = n + 2;
+  const T* x0 = (const T*)dp->x[0];
+  const T* x1 = (const T*)dp->x[1];
+  const int qw = (n + 1) / 2 + 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y, k = blockIdx.z;
+  if (q >= qw) return;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int j = 2 * q - 1 + t;
+    if (j < 0 || j >= m) continue;
+    const int c = (i + j + k) & 1;
+    u[((size_t)k * m + i) * m + j] = (double)(c ? x1 : x0)[e3(k, i, q, m, pitch)];
+  }
+}
+
 #define SOR3_CK(ctx, expr)                                                                    \
   do {                                                                                        \
     cudaError_t e_ = (expr);                                                                  \
@@ -1008,6 +1337,15 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   // the exact order); SOR_FLAG_EXACT_ORDER or FP32: the exact-order phases
   bool fast = sizeof(T) == 8 && !(p->flags & SOR_FLAG_EXACT_ORDER);
   if (fast) SOR3_CK(c, fast3_prepare());
+  // FP32: blocked sweeps of SOR_OPT_CUBE_DEPTH iterations per launch (0, the
+  // default: the per-phase flow kernel, faster here); same results either way
+  const int tbd = sizeof(T) == 4 ? c->opt_cube_depth.load() : 0;
+  const int tb_bps = tbd == 1 ? tb3_blocks_per_sm<1>() : tbd == 2 ? tb3_blocks_per_sm<2>() : 0;
+  const bool tb = tbd > 0 && tb_bps > 0;
+  std::vector<Tile3> tb_tiles;
+  if (tb) tb_tiles = tbd == 1 ? tb3_tiles<1>(n) : tb3_tiles<2>(n);
+  const int ntb = (int)tb_tiles.size();
+  const int tb_grid = std::max(1, std::min(ntb, c->sm_count * std::max(1, tb_bps)));
   const int bps = fast ? fast3_blocks_per_sm(has_f) : exact3_blocks_per_sm<T>(has_f);
   if (bps < 1) {
     c->set_error("3D phase kernel does not fit on an SM");
@@ -1033,6 +1371,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   bytes += sizeof(Tile) * nst + sizeof(unsigned) * (nst + 1);
   if (fast) bytes += 2 * shell_elems * sizeof(double) + sizeof(Phase3) * 2 * (size_t)lmax * kTables;
   if (has_f) bytes += 2 * elems * sizeof(T) + (sizeof(T) == 4 ? 2 * elems * sizeof(double) : 0);
+  if (tb) bytes += 2 * elems * sizeof(T) + sizeof(Tile3) * (size_t)ntb;
   const bool stage_u = !in_dev || !out_dev;
   if (stage_u) bytes += ncube * sizeof(double);
   if (has_f && !f_dev) bytes += nf * sizeof(double);
@@ -1068,7 +1407,10 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   double* d_shell1 = fast ? (double*)B.get(shell_elems * sizeof(double)) : nullptr;
   double* d_u = stage_u ? (double*)B.get(ncube * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
-  if (!x[0] || !x[1] || (has_f && (!g[0] || !g[1] || !g64[0] || !g64[1])) || !d_desc || !d_state || !d_tiles ||
+  T* xalt[2] = {tb ? (T*)B.get(elems * sizeof(T)) : nullptr, tb ? (T*)B.get(elems * sizeof(T)) : nullptr};
+  Tile3* d_tb = tb ? (Tile3*)B.get(sizeof(Tile3) * (size_t)ntb) : nullptr;
+  if ((tb && (!xalt[0] || !xalt[1] || !d_tb)) ||
+      !x[0] || !x[1] || (has_f && (!g[0] || !g[1] || !g64[0] || !g64[1])) || !d_desc || !d_state || !d_tiles ||
       (stage_u && !d_u) || (has_f && !f_dev && !d_f) || !d_strips || !d_progress || (fast && (!d_shell0 || !d_shell1 || !d_tables))) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
@@ -1078,6 +1420,8 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   std::memset(&d, 0, sizeof(d));
   d.x[0] = x[0];
   d.x[1] = x[1];
+  d.xalt[0] = xalt[0];
+  d.xalt[1] = xalt[1];
   d.g[0] = g[0];
   d.g[1] = g[1];
   d.g64[0] = g64[0];
@@ -1112,6 +1456,7 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   SOR3_CK(c, cudaMemcpyAsync(d_state, &st, sizeof(st), cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(Tile) * nt, cudaMemcpyHostToDevice, s));
   SOR3_CK(c, cudaMemcpyAsync(d_strips, strips.data(), sizeof(Tile) * nst, cudaMemcpyHostToDevice, s));
+  if (tb) SOR3_CK(c, cudaMemcpyAsync(d_tb, tb_tiles.data(), sizeof(Tile3) * ntb, cudaMemcpyHostToDevice, s));
   const double* u_src = u0;
   if (!in_dev) {
     SOR3_CK(c, cudaMemcpyAsync(d_u, u0, ncube * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1128,6 +1473,9 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
                                           sizeof(T) == 4 ? g64[0] : nullptr, sizeof(T) == 4 ? g64[1] : nullptr,
                                           d_state);
   SOR3_CK(c, cudaGetLastError());
+  if (tb)  // the other pair starts as a copy (its shell never changes; every launch rewrites the interior)
+    for (int k = 0; k < 2; ++k)
+      SOR3_CK(c, cudaMemcpyAsync(xalt[k], x[k], elems * sizeof(T), cudaMemcpyDeviceToDevice, s));
   int lrun = lmax;  // chunk cap of the rescaled phases for these inputs
   if (fast) {
     // input magnitudes bound the rescaled phases' chunk length; inputs they
@@ -1221,6 +1569,17 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   auto enqueue = [&](int first, int Lc) -> sor_status {
     int done_it = 0;
     for (int Ls : plan_chunks(first, Lc)) {
+      if (tb) {  // blocks of tbd iterations, the last one ending the chunk
+        for (int it = 0; it < Ls; it += tbd) {
+          const int nit = std::min(tbd, Ls - it);
+          SOR3_CK(c, tbd == 1 ? launch_sweep3_tb<1>(d_desc, d_state, d_tb, ntb, tb_grid, nit, s)
+                              : launch_sweep3_tb<2>(d_desc, d_state, d_tb, ntb, tb_grid, nit, s));
+        }
+        done_it += Ls;
+        if (stop == kStopResid && (first + done_it) % d.K == 0)
+          k_resid3d<T, kResidCheck><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
+        continue;
+      }
       SOR3_CK(c, cudaMemsetAsync(d_progress, 0, sizeof(unsigned) * (nst + 1), s));
       if (fast)
         SOR3_CK(c, launch_f3_flow(d_desc, d_state, d_strips, nst, bands, L.col_tiles(), flow_grid, d_shell0,
@@ -1288,7 +1647,10 @@ sor_status run3d(Ctx* c, const sor_params* p, const double* u0, const double* f,
   k_resid3d<T, kResidFinal><<<grid, kThreads, 0, s>>>(d_desc, d_state, d_tiles, nt);
   SOR3_CK(c, cudaGetLastError());
   double* out_dst = out_dev ? u_out : d_u;
-  k_unpack3d<T><<<pgrid, kWarpCols, 0, s>>>(x[0], x[1], n, pitch, out_dst);
+  if (tb)  // the current pair is the descriptor's (the blocked launches swap pairs on the device)
+    k_unpack3d_cur<T><<<pgrid, kWarpCols, 0, s>>>(d_desc, out_dst);
+  else
+    k_unpack3d<T><<<pgrid, kWarpCols, 0, s>>>(x[0], x[1], n, pitch, out_dst);
   SOR3_CK(c, cudaGetLastError());
   if (!out_dev) SOR3_CK(c, cudaMemcpyAsync(u_out, d_u, ncube * sizeof(double), cudaMemcpyDeviceToHost, s));
   SOR3_CK(c, cudaMemcpyAsync(h_state, d_state, sizeof(SlotState), cudaMemcpyDeviceToHost, s));

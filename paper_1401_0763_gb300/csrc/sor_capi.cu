@@ -257,6 +257,10 @@ sor_status sor_set_option(sor_ctx* h, int32_t option, int64_t value) {
       if (v > 4096) return SOR_ERR_INVALID_ARG;
       c->opt_plain_step = v;
       return SOR_OK;
+    case SOR_OPT_CUBE_DEPTH:
+      if (v < 0 || v > 2) return SOR_ERR_INVALID_ARG;
+      c->opt_cube_depth = v;
+      return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }
@@ -275,6 +279,7 @@ sor_status sor_get_option(sor_ctx* h, int32_t option, int64_t* value) {
     case SOR_OPT_FAST_CHAIN: *value = c->opt_fast_chain.load(); return SOR_OK;
     case SOR_OPT_FUSED_KERNEL: *value = c->opt_fused_kernel.load(); return SOR_OK;
     case SOR_OPT_BATCH_PLAIN_STEP: *value = c->opt_plain_step.load(); return SOR_OK;
+    case SOR_OPT_CUBE_DEPTH: *value = c->opt_cube_depth.load(); return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }

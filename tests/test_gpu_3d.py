@@ -399,3 +399,50 @@ def test_cube_requests_cancelled_by_destroy():
     with capi.Context(0) as again:
         out, res = again.solve3d(wl.random_shell(10, 2), tol=1e-8, max_iters=500)
         assert res["converged"]
+
+
+@pytest.mark.parametrize("depth", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 40, 65, 100])
+@pytest.mark.parametrize("with_f", [False, True])
+def test_fp32_blocked_sweeps_bitwise(depth, n, with_f):
+    """FP32 cube sweeps with SOR_OPT_CUBE_DEPTH iterations fused per launch
+    (each tile streamed through its planes, the phases a wavefront in shared
+    memory, output to the other buffer pair) or one data-flow launch per run
+    of iterations (depth 0): equal to the oracle bit for bit at every depth,
+    on ragged sizes, for runs to the cap that end in a launch shorter than the
+    depth (K = 7, 23 iterations) and for early stops (K = 3)."""
+    capi = capi_mod()
+    u0 = wl.random_shell(n, 900 + n)
+    f = wl.gaussian_source3(n, 950 + n) * 5 if with_f else None
+    w = oracle.omega_opt(n)
+    with capi.Context(0) as c:
+        c.set_option(capi.SOR_OPT_CUBE_DEPTH, depth)
+        ref = oracle.sor3d_f32(u0, w, f=f, max_iters=23, check_every=7, tol=-1.0)
+        got, res = run3(c, u0, f, omega=w, max_iters=23, check_every=7, tol=-1.0, precision=capi.SOR_FP32)
+        assert res["iterations"] == 23 and not res["converged"]
+        assert np.array_equal(got, ref["u"])
+        assert res["final_maxdelta"] == ref["final_maxdelta"]
+        ref = oracle.sor3d_f32(u0, w, f=f, max_iters=3000, check_every=3, tol=2e-2)
+        got, res = run3(c, u0, f, omega=w, max_iters=3000, check_every=3, tol=2e-2, precision=capi.SOR_FP32)
+        assert res["iterations"] == ref["iterations"] and res["converged"] == ref["converged"]
+        assert np.array_equal(got, ref["u"])
+        assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
+def test_fp32_blocked_sweeps_large_cube():
+    """A cube of several tiles in every direction, host and device buffers."""
+    capi = capi_mod()
+    n = 210
+    u0 = wl.random_shell(n, 77)
+    f = wl.gaussian_source3(n, 78) * 3
+    w = oracle.omega_opt(n)
+    ref = oracle.sor3d_f32(u0, w, f=f, max_iters=9, check_every=4, tol=-1.0)
+    with capi.Context(0) as c:
+        for depth in (1, 2):
+            c.set_option(capi.SOR_OPT_CUBE_DEPTH, depth)
+            for device in (True, False):
+                got, res = run3(c, u0, f, device=device, omega=w, max_iters=9, check_every=4, tol=-1.0,
+                                precision=capi.SOR_FP32)
+                assert res["iterations"] == 9
+                assert np.array_equal(got, ref["u"]), (depth, device)
+                assert res["final_maxdelta"] == ref["final_maxdelta"]
