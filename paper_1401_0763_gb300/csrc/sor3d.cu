@@ -38,6 +38,18 @@ __device__ __forceinline__ size_t e3(int k, int i, int q, int m, int pitch) {
   return ((size_t)k * (size_t)m + (size_t)i) * (size_t)pitch + (size_t)(q + kOff);
 }
 
+// Debug check (SOR_DEBUG_BOUNDS) of a work item that touches planes [k0, k1),
+// rows [i0, i1) and packed columns [q0, q1) of the colour arrays: on failure
+// the state records kErrBounds and stops; release builds compile it to true.
+__device__ __forceinline__ bool dbg_tile3(SlotState* st, int k0, int k1, int i0, int i1, int q0, int q1, int m,
+                                          int pitch) {
+  if (dbg_range(k0, k1, m, st) && dbg_range(i0, i1, m, st) &&
+      dbg_range((long long)q0 + kOff, (long long)q1 + kOff, pitch, st))
+    return true;
+  st->done = 1;
+  return false;
+}
+
 // Solve description in device memory (constant while the solve runs).
 struct Desc3 {
   void* x[2];            // colour arrays (FP64 or FP32); with blocked FP32 sweeps, the current pair
@@ -233,6 +245,10 @@ __global__ void __launch_bounds__(kThreads) k_resid3d(const Desc3* __restrict__ 
       if (ROLE == kResidCheck)
         skip = *((volatile int*)&st->converged) || it == 0 || (it % d.K) != 0 ||
                it == *((volatile int*)&st->checked_iter);
+      const int kt = tl.row0 / d.m, it0 = tl.row0 - kt * d.m;
+      if (!skip && !dbg_tile3(st, kt - 1, kt + 2, it0 - 1, it0 + tl.nrows + 1, tl.col0 - 1,
+                              tl.col0 + kWarpCols + 1, d.m, d.pitch))
+        skip = 1;
       ctl[0] = skip;
       ctl[1] = it;
     }
@@ -690,6 +706,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_f3_flow(const Desc3* __restrict
     }
     const Tile tl = strips[t];
     const int k = tl.row0 / m, i0 = tl.row0 - k * m, i1 = i0 + tl.nrows;
+    if (!dbg_tile3(st, k - 1, k + 2, i0 - 1, i1 + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1, m, pitch)) return;
     double* X = (double*)d.x[colour];
     const double* O = (const double*)d.x[colour ^ 1];
     const double* G = (const double*)d.g[colour];
@@ -815,6 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_3_flow(const Desc3* __restrict__ d
     }
     const Tile tl = strips[t];
     const int k = tl.row0 / m, i0 = tl.row0 - k * m, i1 = i0 + tl.nrows;
+    if (!dbg_tile3(st, k - 1, k + 2, i0 - 1, i1 + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1, m, pitch)) return;
     T* X = (T*)d.x[colour];
     const T* O = (const T*)d.x[colour ^ 1];
     const T* G = (const T*)d.g[colour];
@@ -1093,6 +1111,10 @@ __global__ void __launch_bounds__(Tb3Geom<TD>::THREADS) k_sweep3_tb(Desc3* dp, S
           skip = 1;
         }
       if (nt <= 0) skip = 1;
+      // the tile's output planes, rows and columns lie inside the arrays
+      if (!skip && !dbg_tile3(st, tl.k0, tl.k0 + tl.nz, tl.row0, tl.row0 + tl.nrows, tl.col0, tl.col0 + Gm::OQ,
+                              dp->m, dp->pitch))
+        skip = 1;
       ctl[0] = skip;
       ctl[1] = nt;
       ctl[2] = k_end;

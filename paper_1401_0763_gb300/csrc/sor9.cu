@@ -37,6 +37,17 @@ __device__ __forceinline__ size_t e9(int a, int b, int pitch) {
   return (size_t)a * (size_t)pitch + (size_t)(b + kOff);
 }
 
+// Debug check (SOR_DEBUG_BOUNDS) of a work item that touches quarter rows
+// [a0, a1) and columns [b0, b1) of the quarter arrays ((N+1)/2 + 2 rows): on
+// failure the state records kErrBounds and stops; release builds compile it
+// to true.
+__device__ __forceinline__ bool dbg_tile9(SlotState* st, int a0, int a1, int b0, int b1, int n, int pitch) {
+  if (dbg_range(a0, a1, ((n + 1) >> 1) + 2, st) && dbg_range((long long)b0 + kOff, (long long)b1 + kOff, pitch, st))
+    return true;
+  st->done = 1;
+  return false;
+}
+
 struct Desc9 {
   void* x[4];            // quarter arrays (FP64 or FP32)
   const void* g[4];      // 6 h^2 f per quarter in the sweep type, or null
@@ -295,6 +306,9 @@ __global__ void __launch_bounds__(kThreads) k_sweep9(const Desc9* __restrict__ d
       ctl[0] = *((volatile int*)&st->done);
       ctl[1] = kk;
       ctl[2] = ((kk % d.K) == 0) || (kk >= d.max_iters);
+      if (!ctl[0] && !dbg_tile9(st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1, d.n,
+                                d.pitch))
+        ctl[0] = 1;
     }
     __syncthreads();
     const int skip = ctl[0], kk = ctl[1], measure = ctl[2];
@@ -400,6 +414,8 @@ __global__ void __launch_bounds__(kThreads) k_9_flow(const Desc9* __restrict__ d
       }
     }
     const Tile tl = strips[t];
+    if (!dbg_tile9(st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1, d.n, d.pitch))
+      return;
     const int q0 = tl.col0 + lane * kVec;
     const int a0 = tl.row0;
     const int a1 = min(tl.row0 + tl.nrows, ((d.n + (C >> 1)) >> 1) + 1);
@@ -494,6 +510,9 @@ __global__ void __launch_bounds__(kThreads) k_resid9(const Desc9* __restrict__ d
       if (ROLE == kResidCheck)
         skip = *((volatile int*)&st->converged) || it == 0 || (it % d.K) != 0 ||
                it == *((volatile int*)&st->checked_iter);
+      if (!skip && !dbg_tile9(st, tl.row0 - 1, tl.row0 + tl.nrows + 1, tl.col0 - 1, tl.col0 + kWarpCols + 1, d.n,
+                             d.pitch))
+        skip = 1;
       ctl[0] = skip;
       ctl[1] = it;
     }

@@ -202,15 +202,19 @@ static sor_status enqueue_step(Batcher* b) {
   Ctx* c = b->c;
   cudaStream_t s = b->stream;
   if (b->nt_refine) {
-    // residual pass: applies the corrections of the previous step (each slot's
-    // from the buffer its own inner sweep count ends in), tests, writes r~
-    SOR_BCK(launch_resid(kResidRefine64, b->d_desc, b->d_state, b->d_tiles, b->nt_refine, 0, kDbufPerSlot, s));
+    // residual pass: tests, writes r~; before it, the corrections of the
+    // previous step (each slot's from the buffer its own inner sweep count
+    // ends in), unless the fused sweeps already applied them (each slot's
+    // last inner launch adds its d to u)
+    const bool fix = b->tdepth > 1 && fused_corrects(b->fkind);
+    SOR_BCK(launch_resid(fix ? kResidRefine64Fixed : kResidRefine64, b->d_desc, b->d_state, b->d_tiles,
+                         b->nt_refine, 0, kDbufPerSlot, s));
     if (b->tdepth > 1) {
       const Tile* t = b->d_tiles + b->off_reftb;
       for (int j = 0, sw = 0; sw < b->max_inner; ++j, sw += b->tdepth) {
         const int nt = std::min(b->tdepth, b->max_inner - sw);
         SOR_BCK(launch_fused(b->fkind, true, b->tdepth, b->d_desc, b->d_state, t, b->nt_reftb, 0, nt,
-                             (j % 2 == 0) ? 1 : 0, sw, s));
+                             (j % 2 == 0) ? 1 : 0, sw, s, fix));
       }
     } else {
       for (int sw = 0; sw < b->max_inner; ++sw) {

@@ -1289,7 +1289,8 @@ cudaError_t launch_resid(ResidKind kind, const SlotDesc* slots, SlotState* state
   if (ntiles <= 0) return cudaSuccess;
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   t_launches += kind == kResidRefine64 ? 2 : 1;
-  if (kind == kResidRefine64) {  // u += d first (nothing when no correction is pending)
+  if (kind == kResidRefine64Fixed) kind = kResidRefine64;  // the sweeps applied the correction
+  else if (kind == kResidRefine64) {  // u += d first (nothing when no correction is pending)
     k_correct<<<grid, kThreads, 0, s>>>(slots, states, tiles, ntiles, dbuf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1334,10 +1335,14 @@ int fused_out_rows(int kind, int n, int T, int sm_count, int seg) {
 
 cudaError_t fused_prepare(int kind, int T) { return kind == kFusedWave ? wave_prepare(T) : tile_prepare(T); }
 
+bool fused_corrects(int kind) { return kind != kFusedWave; }
+
 cudaError_t launch_fused(int kind, bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s) {
+                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s, bool correct) {
+  if (correct && !fused_corrects(kind)) return cudaErrorInvalidValue;
   return kind == kFusedWave ? launch_sweep_wave(inner, T, slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                            : launch_sweep_tile(inner, T, slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+                            : launch_sweep_tile(inner, T, slots, states, tiles, ntiles, grid, nt, src, sweep0, s,
+                                                correct);
 }
 
 }  // namespace sorgb

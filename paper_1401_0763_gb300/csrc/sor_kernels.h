@@ -11,7 +11,16 @@ enum SweepKind : int { kSweepPlain64 = 0, kSweepPlain32 = 1, kSweepInner32 = 2 }
 // inner sweep counts differ end their corrections in different buffers).
 constexpr int kDbufPerSlot = -1;
 
-enum ResidKind : int { kResidFinal64 = 0, kResidFinal32 = 1, kResidCheck64 = 2, kResidCheck32 = 3, kResidRefine64 = 4 };
+// kResidRefine64 applies the pending correction (k_correct) before the
+// residual; kResidRefine64Fixed omits it (the inner sweeps applied it).
+enum ResidKind : int {
+  kResidFinal64 = 0,
+  kResidFinal32 = 1,
+  kResidCheck64 = 2,
+  kResidCheck32 = 3,
+  kResidRefine64 = 4,
+  kResidRefine64Fixed = 5
+};
 
 struct PackArgs {
   const double* u0;  // natural (n+2)^2, device
@@ -80,15 +89,18 @@ int fused_out_cols(int kind, int T);
 int fused_out_rows(int kind, int n, int T, int sm_count, int seg);
 // Opts the kernels of depth T into their shared memory (call outside graph capture).
 cudaError_t fused_prepare(int kind, int T);
+// correct (inner sweeps, families with fused_corrects(kind)): the launch that
+// ends a slot's inner sweeps adds the final correction to u itself.
 cudaError_t launch_fused(int kind, bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+                         int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s, bool correct = false);
+bool fused_corrects(int kind);
 // the two families
 bool tile_depth_supported(int T);
 int tile_out_cols(int T);
 int tile_out_rows();
 cudaError_t tile_prepare(int T);
 cudaError_t launch_sweep_tile(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                              int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s);
+                              int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s, bool correct);
 bool wave_depth_supported(int T);
 int wave_out_cols(int T);
 int wave_warps_per_sm(int T);

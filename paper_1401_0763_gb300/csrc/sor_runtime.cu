@@ -560,13 +560,17 @@ int refine_dbuf(const Plan& p) {
 
 static sor_status enqueue_refine_chunk(Ctx* c, SolveWorkspace* w, const Plan& p, int C, cudaStream_t s) {
   if (p.tdepth > 1) {
+    // the tile family's last launch of each correction adds d to u itself,
+    // so the residual pass needs no correction pass before it
     const int dbuf = refine_dbuf(p);
+    const bool fix = fused_corrects(p.fkind);
     for (int step = 0; step < C; ++step) {
-      SOR_CK(c, launch_resid(kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles, w->n_resid_tiles, 0, dbuf, s));
+      SOR_CK(c, launch_resid(fix ? kResidRefine64Fixed : kResidRefine64, w->d_desc, w->d_state, w->d_resid_tiles,
+                             w->n_resid_tiles, 0, dbuf, s));
       for (int j = 0, sw = 0; sw < p.inner; ++j, sw += p.tdepth) {
         const int nt = std::min(p.tdepth, p.inner - sw);
         SOR_CK(c, launch_fused(p.fkind, true, p.tdepth, w->d_desc, w->d_state, w->d_tb_tiles, w->n_tb_tiles, 0, nt,
-                                  (j % 2 == 0) ? 1 : 0, sw, s));
+                               (j % 2 == 0) ? 1 : 0, sw, s, fix));
       }
     }
     return SOR_OK;

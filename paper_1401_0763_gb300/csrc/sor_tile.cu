@@ -7,6 +7,7 @@
 // faster of the two while a plate's FP32 state stays in L2.
 #include <cuda_runtime.h>
 
+#include "sor_bits.cuh"
 #include "sor_devfn.cuh"
 #include "sor_device.cuh"
 #include "sor_kernels.h"
@@ -299,18 +300,21 @@ __device__ __forceinline__ void tb_phase(float* __restrict__ Sc, const float* __
 //         slot state; the last iteration of the launch may be a measured one.
 // MODE 1: inner sweeps of defect correction on d with rhs r~; `src` is the
 //         buffer holding d (the first launch of a correction, sweep0 == 0,
-//         starts from d = 0 and reads nothing).
+//         starts from d = 0 and reads nothing).  corr: the launch that ends
+//         a slot's inner sweeps adds its final d to u (u += (double)d, the
+//         rounding of k_correct) instead of storing d, so no correction pass
+//         runs before the next residual.
 template <int T, int MODE>
 __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __restrict__ slots, SlotState* states,
                                                             const Tile* __restrict__ tiles, int ntiles, int nt_req,
-                                                            int src_param, int sweep0) {
+                                                            int src_param, int sweep0, int corr) {
   using Gm = TbGeom<T>;
   constexpr int kWarps = kTbThreads / 32;
   extern __shared__ __align__(16) float tb_smem[];
   float* const S0 = tb_smem;
   float* const S1 = tb_smem + Gm::R * Gm::C;
   __shared__ unsigned long long red[kWarps];
-  __shared__ int ctl[5];  // skip, nt, k_end, measure, src
+  __shared__ int ctl[7];  // skip, nt, k_end, measure, src, correct u here, u buffer
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
@@ -336,6 +340,8 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
         nt = min(nt_req, sd.inner - sweep0);
         if (nt <= 0) skip = 1;
         src = src_param;
+        ctl[5] = corr && sweep0 + nt >= sd.inner;  // this slot's inner sweeps end in this launch
+        ctl[6] = *((volatile int*)&st->ubuf);
       }
       // the output rows and columns of the tile lie inside the slot's arrays
       if (!skip && !dbg_tile(sd, st, tl.row0, tl.row0 + tl.nrows, tl.col0, tl.col0 + Gm::OQ)) skip = 1;
@@ -343,6 +349,7 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
     }
     __syncthreads();
     const int skip = ctl[0], nt = ctl[1], k_end = ctl[2], measure = ctl[3], src = ctl[4];
+    const int fix_u = MODE == 1 ? ctl[5] : 0, ubuf = MODE == 1 ? ctl[6] : 0;
     __syncthreads();
     if (skip) continue;
 
@@ -417,6 +424,21 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
       if (qf > qlim) continue;
       float v4[4];
       load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4);
+      if (MODE == 1 && fix_u) {  // the correction: u += (double)d over these cells
+        double* Ud = sd.u[ubuf][c] + (size_t)i * pitch + qf + kOff;
+        if (qf + 3 <= qlim) {
+          double u4[4];
+          load4(Ud, u4);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) u4[v] = __dadd_rn(u4[v], widen_f32(v4[v]));
+          store4(Ud, u4);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (qf + v <= qlim) Ud[v] = __dadd_rn(Ud[v], widen_f32(v4[v]));
+        }
+        continue;
+      }
       float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
       if (qf + 3 <= qlim) {
         store4(Xd, v4);
@@ -466,7 +488,7 @@ int tile_out_cols(int T) {
 
 template <int T, int MODE>
 static cudaError_t launch_tile_t(const SlotDesc* slots, SlotState* states, const Tile* tiles, int ntiles, int grid,
-                               int nt, int src, int sweep0, cudaStream_t s) {
+                               int nt, int src, int sweep0, int corr, cudaStream_t s) {
   static bool attr_set = false;  // benign race: setting the attribute twice is harmless
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_sweep_tb<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -476,27 +498,28 @@ static cudaError_t launch_tile_t(const SlotDesc* slots, SlotState* states, const
   }
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   count_kernel_launches(1);
-  k_sweep_tb<T, MODE><<<grid, kTbThreads, TbGeom<T>::smem, s>>>(slots, states, tiles, ntiles, nt, src, sweep0);
+  k_sweep_tb<T, MODE><<<grid, kTbThreads, TbGeom<T>::smem, s>>>(slots, states, tiles, ntiles, nt, src, sweep0, corr);
   return cudaGetLastError();
 }
 
 bool tile_depth_supported(int T) { return T == 2 || T == 3 || T == 4 || T == 6 || T == 8; }
 
 cudaError_t launch_sweep_tile(bool inner, int T, const SlotDesc* slots, SlotState* states, const Tile* tiles,
-                            int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s) {
+                            int ntiles, int grid, int nt, int src, int sweep0, cudaStream_t s, bool correct) {
   if (ntiles <= 0) return cudaSuccess;
   if (nt < 1 || nt > T) return cudaErrorInvalidValue;
+  const int corr = inner && correct ? 1 : 0;
   switch (T) {
-    case 2: return inner ? launch_tile_t<2, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tile_t<2, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 3: return inner ? launch_tile_t<3, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tile_t<3, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 4: return inner ? launch_tile_t<4, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tile_t<4, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 6: return inner ? launch_tile_t<6, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tile_t<6, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
-    case 8: return inner ? launch_tile_t<8, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s)
-                         : launch_tile_t<8, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, s);
+    case 2: return inner ? launch_tile_t<2, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s)
+                         : launch_tile_t<2, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s);
+    case 3: return inner ? launch_tile_t<3, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s)
+                         : launch_tile_t<3, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s);
+    case 4: return inner ? launch_tile_t<4, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s)
+                         : launch_tile_t<4, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s);
+    case 6: return inner ? launch_tile_t<6, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s)
+                         : launch_tile_t<6, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s);
+    case 8: return inner ? launch_tile_t<8, 1>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s)
+                         : launch_tile_t<8, 0>(slots, states, tiles, ntiles, grid, nt, src, sweep0, corr, s);
     default: return cudaErrorInvalidValue;
   }
 }

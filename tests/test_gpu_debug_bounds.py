@@ -9,7 +9,9 @@ debug build:
   outside its range (no memory is accessed at that index);
 * small grids on every plate path -- exact-order and default FP64, FP32
   sweeps of both fused families, defect correction, the batch scheduler --
-  run with no check firing and give the oracle's results.
+  and on the cube and 9-point paths (every precision, the cube's blocked
+  sweeps at both depths) run with no check firing and give the oracle's
+  results.
 The release library reports the checks compiled away.
 """
 import os
@@ -66,6 +68,44 @@ CHILD = textwrap.dedent("""
             assert st == capi.SOR_OK, ctx.last_error()
             ref = oracle.refine(u0, oracle.omega_opt(n), f=f, inner_sweeps=20, tol=1e-9, max_outer=2500)
             assert np.array_equal(out, ref["u"]), n
+        # cubes: FP64 default and exact order, FP32 per phase and blocked, defect correction
+        for n in (1, 6, 33):
+            u0 = wl.random_shell(n, n)
+            f = wl.gaussian_source3(n, n + 2) * 5
+            w = oracle.omega_opt(n)
+            ref = oracle.sor3d_f64(u0, w, f=f, max_iters=21, check_every=7, tol=-1.0)
+            got, res = ctx.solve3d(u0, f, omega=w, tol=-1.0, max_iters=21, check_every=7,
+                                   flags=capi.SOR_FLAG_EXACT_ORDER)
+            assert np.array_equal(got, ref["u"]), n
+            got, res = ctx.solve3d(u0, f, omega=w, tol=-1.0, max_iters=21, check_every=7)
+            assert np.max(np.abs(got - ref["u"])) <= 1e-12 * max(1.0, np.max(np.abs(ref["u"]))), n
+            ref32 = oracle.sor3d_f32(u0, w, f=f, max_iters=21, check_every=7, tol=-1.0)
+            for depth in (0, 1, 2):
+                ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, depth)
+                got, res = ctx.solve3d(u0, f, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=21,
+                                       check_every=7)
+                assert np.array_equal(got, ref32["u"]), (n, depth)
+            ctx.set_option(capi.SOR_OPT_CUBE_DEPTH, 0)
+            refr = oracle.refine3d(u0, w, f=f, inner_sweeps=20, tol=1e-9, max_outer=300)
+            got, res = ctx.solve3d(u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-9, max_iters=6000)
+            assert np.array_equal(got, refr["u"]), n
+        # 9-point plates: FP64 default and exact order, FP32, defect correction
+        for n in (1, 4, 77):
+            u0 = wl.random_edges(n, n + 5)
+            f = wl.gaussian_source(n, n + 6) * 5
+            w = oracle.omega_opt(n)
+            ref = oracle.sor9_f64(u0, w, f=f, max_iters=22, check_every=11, tol=-1.0)
+            got, res = ctx.solve9(u0, f, omega=w, tol=-1.0, max_iters=22, check_every=11,
+                                  flags=capi.SOR_FLAG_EXACT_ORDER)
+            assert np.array_equal(got, ref["u"]), n
+            got, res = ctx.solve9(u0, f, omega=w, tol=-1.0, max_iters=22, check_every=11)
+            assert np.max(np.abs(got - ref["u"])) <= 1e-12 * max(1.0, np.max(np.abs(ref["u"]))), n
+            ref32 = oracle.sor9_f32(u0, w, f=f, max_iters=22, check_every=11, tol=-1.0)
+            got, res = ctx.solve9(u0, f, precision=capi.SOR_FP32, omega=w, tol=-1.0, max_iters=22, check_every=11)
+            assert np.array_equal(got, ref32["u"]), n
+            refr = oracle.refine9(u0, w, f=f, inner_sweeps=20, tol=1e-9, max_outer=400)
+            got, res = ctx.solve9(u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-9, max_iters=8000)
+            assert np.array_equal(got, refr["u"]), n
     print("debug build checks passed")
 """) % ROOT
 
