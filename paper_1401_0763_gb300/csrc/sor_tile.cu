@@ -409,43 +409,77 @@ __global__ void __launch_bounds__(kTbThreads, 2) k_sweep_tb(const SlotDesc* __re
         __syncthreads();
       }
     }
-    // write the centre tile to the other buffer: warp per row, lane per float4
-    const int dst = src ^ 1;
-    for (int row = warp; row < 2 * kTbRows; row += kWarps) {
-      const int c = row >= kTbRows;
-      const int r = row - c * kTbRows;
-      if (r >= tl.nrows) continue;
-      const int col = 4 * lane;
-      if (col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
-      const int i = tl.row0 + r;
-      const int s = (i + c) & 1;
-      const int qlim = (n + s) >> 1;
-      const int qf = base_q + col;
-      if (qf > qlim) continue;
-      float v4[4];
-      load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4);
-      if (MODE == 1 && fix_u) {  // the correction: u += (double)d over these cells
-        double* Ud = sd.u[ubuf][c] + (size_t)i * pitch + qf + kOff;
-        if (qf + 3 <= qlim) {
-          double u4[4];
-          load4(Ud, u4);
+    // the correction ending a slot's inner sweeps: u += (double)d over the
+    // centre tile, the u vectors of kTbFixRows rows requested together before
+    // any is used (a row at a time, each thread waited for every load)
+    if (MODE == 1 && fix_u) {
+      constexpr int kTbFixRows = 2;
+      for (int row0 = warp; row0 < 2 * kTbRows; row0 += kWarps * kTbFixRows) {
+        double u4[kTbFixRows][4];
+        float v4[kTbFixRows][4];
+        double* Ud[kTbFixRows];
+        int cnt[kTbFixRows];  // interior cells of the vector: 4, 1 .. 3 at the row's end, 0 = none
 #pragma unroll
-          for (int v = 0; v < 4; ++v) u4[v] = __dadd_rn(u4[v], widen_f32(v4[v]));
-          store4(Ud, u4);
+        for (int j = 0; j < kTbFixRows; ++j) {
+          cnt[j] = 0;
+          Ud[j] = nullptr;
+          const int row = row0 + j * kWarps;
+          const int c = row >= kTbRows;
+          const int r = row - c * kTbRows;
+          const int col = 4 * lane;
+          if (row >= 2 * kTbRows || r >= tl.nrows || col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
+          const int i = tl.row0 + r;
+          const int qlim = (n + ((i + c) & 1)) >> 1;
+          const int qf = base_q + col;
+          if (qf > qlim) continue;
+          cnt[j] = min(4, qlim - qf + 1);
+          load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4[j]);
+          Ud[j] = sd.u[ubuf][c] + (size_t)i * pitch + qf + kOff;
+          if (cnt[j] == 4) {
+            load4(Ud[j], u4[j]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) u4[j][v] = v < cnt[j] ? Ud[j][v] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kTbFixRows; ++j) {
+          if (cnt[j] == 0) continue;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) u4[j][v] = __dadd_rn(u4[j][v], widen_f32(v4[j][v]));
+          if (cnt[j] == 4) {
+            store4(Ud[j], u4[j]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+              if (v < cnt[j]) Ud[j][v] = u4[j][v];
+          }
+        }
+      }
+    } else {
+      // write the centre tile to the other buffer: warp per row, lane per float4
+      const int dst = src ^ 1;
+      for (int row = warp; row < 2 * kTbRows; row += kWarps) {
+        const int c = row >= kTbRows;
+        const int r = row - c * kTbRows;
+        if (r >= tl.nrows) continue;
+        const int col = 4 * lane;
+        if (col < Gm::HQ || col >= Gm::HQ + Gm::OQ) continue;
+        const int i = tl.row0 + r;
+        const int s = (i + c) & 1;
+        const int qlim = (n + s) >> 1;
+        const int qf = base_q + col;
+        if (qf > qlim) continue;
+        float v4[4];
+        load4((c ? S1 : S0) + (Gm::HR + r) * Gm::C + col, v4);
+        float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
+        if (qf + 3 <= qlim) {
+          store4(Xd, v4);
         } else {
 #pragma unroll
           for (int v = 0; v < 4; ++v)
-            if (qf + v <= qlim) Ud[v] = __dadd_rn(Ud[v], widen_f32(v4[v]));
+            if (qf + v <= qlim) Xd[v] = v4[v];
         }
-        continue;
-      }
-      float* Xd = (float*)sd.x[dst][c] + (size_t)i * pitch + qf + kOff;
-      if (qf + 3 <= qlim) {
-        store4(Xd, v4);
-      } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-          if (qf + v <= qlim) Xd[v] = v4[v];
       }
     }
     if (MODE == 0) {
