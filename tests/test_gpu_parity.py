@@ -524,3 +524,29 @@ def test_kernel_launch_count(ctx_mc):
     ctx_mc.reset_stats()
     ctx_mc.solve(u0, omega=oracle.omega_opt(n), tol=-1.0, max_iters=1000, check_every=50)
     assert ctx_mc.stats()["kernel_launches"] == 2 + 20 + 2
+
+
+@pytest.mark.parametrize("with_f", [False, True])
+def test_residual_signed_zeros_bitwise(ctx, with_f):
+    """Inputs holding -0.0 (interior and one edge): the residual pass without a
+    source maps g + x to x with -0 turned into +0 on the integer units, which
+    must give the oracle's bits exactly, signs of zeros included, in the
+    residual stop and through the defect correction (where r~ feeds the
+    sweeps and u += d)."""
+    capi = capi_mod()
+    n = 37
+    u0 = np.full((n + 2, n + 2), -0.0)
+    u0[0, :] = 50.0
+    u0[:, 0] = -0.0
+    u0[5:9, 5:9] = 0.0
+    f = wl.gaussian_source(n, 3) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_f64(u0, w, f=f, max_iters=40, check_every=5, tol=-1.0, stop_mode=1)
+    got, res = run(ctx, u0, f, omega=w, tol=-1.0, max_iters=40, check_every=5, stop=capi.SOR_STOP_RESID_REL,
+                   flags=capi.SOR_FLAG_EXACT_ORDER)
+    assert np.array_equal(got.view(np.int64), ref["u"].view(np.int64))
+    assert res["final_resid_rel"] == ref["final_resid_rel"]
+    ref = oracle.refine(u0, w, f=f, inner_sweeps=20, tol=1e-9, max_outer=200)
+    got, res = run(ctx, u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-9, max_iters=4000)
+    assert res["outer_steps"] == ref["outer_steps"] and res["iterations"] == ref["sweeps"]
+    assert np.array_equal(got.view(np.int64), ref["u"].view(np.int64))
