@@ -291,7 +291,8 @@ typedef enum {
                                   cooperative launch with neighbour-to-neighbour progress counters; 0: one
                                   launch per colour phase.  Results are identical either way */
   SOR_OPT_FUSED_KERNEL = 9,    /* FP32 sweeps: 0 (default) = chosen by grid size (tile kernels up to
-                                  N = 6144, wavefront kernels above) or by the autotuner; 1 = tile
+                                  N = 6144 for SOR_FP32 and N = 12288 for the inner sweeps of
+                                  SOR_FP32_REFINE, wavefront kernels above) or by the autotuner; 1 = tile
                                   kernels (a shared-memory tile pass per launch); 2 = wavefront kernels
                                   (a register wavefront per warp).  Results are identical either way */
   SOR_OPT_BATCH_PLAIN_STEP = 10, /* iterations per scheduler step of plain (FP64 / FP32) batch slots:

@@ -322,12 +322,16 @@ sor_status zero_slot(Ctx* c, const Plan& p, SlotBuffers* b, cudaStream_t s) {
 static constexpr int kInflight = 3;
 
 // Fused FP32 sweep kernel of an FP32 or defect-correction plan: the family
-// from SOR_OPT_FUSED_KERNEL, by default the tile family while the plate's
-// FP32 state stays near the L2 size (n <= 6144; measured the faster there)
-// and the wavefront family above it; the depth from
+// from SOR_OPT_FUSED_KERNEL, by default the tile family up to a size and
+// the wavefront family above it, as measured on GB300: plain FP32 sweeps up
+// to n = 6144 (the FP32 state near the L2 size), the inner sweeps of defect
+// correction up to n = 12288 (they also read the right-hand side, and the
+// tile family folds the correction into its last launch: faster at 8192^2
+// by 10 %, slower at 16384^2 by 4 %); the depth from
 // SOR_OPT_TEMPORAL_DEPTH, by default 6 (tile) or 4 (wavefront), rounded down
 // to a depth the family is built for; rows per tile the family's default.
 static constexpr int kTileFamilyMaxN = 6144;
+static constexpr int kTileFamilyMaxNRefine = 12288;
 
 void resolve_fused(Ctx* c, Plan* p) {
   if (p->kind == kPlain64) {
@@ -335,7 +339,8 @@ void resolve_fused(Ctx* c, Plan* p) {
     return;
   }
   const int opt = c->opt_fused_kernel.load();
-  const int fk = opt == 1 ? kFusedTile : opt == 2 ? kFusedWave : (p->n <= kTileFamilyMaxN ? kFusedTile : kFusedWave);
+  const int tile_max = p->kind == kRefine ? kTileFamilyMaxNRefine : kTileFamilyMaxN;
+  const int fk = opt == 1 ? kFusedTile : opt == 2 ? kFusedWave : (p->n <= tile_max ? kFusedTile : kFusedWave);
   int t = c->opt_tdepth.load();
   if (t == 0) t = fk == kFusedWave ? 4 : 6;
   while (t > 1 && !fused_depth_supported(fk, t)) --t;
