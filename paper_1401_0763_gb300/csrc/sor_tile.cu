@@ -59,14 +59,16 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // Right-hand-side values of this lane's 4 cells of one row, read from global
-// memory four rows before their use (the right-hand side is read-only for
-// the launch and each lane uses only the values it loads, so they go straight
-// to registers); nothing is loaded for rows outside the phase's rows or lanes
-// without interior cells of that row parity, whose cells are masked.
+// memory rows before their use (the right-hand side is read-only for the
+// launch and each lane uses only the values it loads, so they go straight to
+// registers).  Nothing is loaded for rows past the phase's rows or lanes
+// without interior cells of that row parity; g then keeps stale values, which
+// only masked cells (whose result is discarded) or no row at all ever use.
 __device__ __forceinline__ void tb_g_load(float (&g)[4], const float* gp, bool ok) {
-  float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  if (ok) v = __ldg(reinterpret_cast<const float4*>(gp));
-  g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
+  if (ok) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(gp));
+    g[0] = v.x; g[1] = v.y; g[2] = v.z; g[3] = v.w;
+  }
 }
 
 // One row r of a phase on the staged tile.  om / oc / op: the neighbour
@@ -177,6 +179,10 @@ __device__ __forceinline__ void tb_rows_g(const TbRows& R, int r1, unsigned& dm3
   int r = R.r0;
   float X[4], Y[4], P[4], Q[4];
   float G[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) G[j][v] = 0.0f;  // once per phase: a load that is skipped leaves them
   const ptrdiff_t gs = R.pitch;
   const float* gp = R.Gc;  // right-hand side of row r
   const bool ok0 = S0 ? R.gok1 : R.gok0;  // rows of the parity of row r0 / of the other parity
