@@ -15,6 +15,10 @@ short:
   convergence test every K iterations, Section 2.1 / Section 3.3) with the
   cell update of Eq. 1 taken with the 5-point Gauss-Seidel value.
 * :func:`sor_f32` -- the same iteration in FP32 arithmetic and storage.
+* :func:`sor_block_f64` -- block two-colour SOR, the reading of the
+  block-parallel SOR that Section 3.1 names beside red-black SOR: blocks of
+  by x bx cells coloured like a checkerboard, colour 0 first, row-major order
+  inside a block.
 * :func:`residual` -- the scaled residual h^2 (f - A u) and its infinity
   norm relative to the right-hand side (boundary moved to the right).
 * :func:`refine` -- FP64 defect correction around FP32 (or FP64) inner
@@ -27,8 +31,9 @@ short:
   (Section 3.1 names it beside red-black SOR): four colours for the compact
   9-point stencil; :func:`refine9` -- the defect correction with it.
 
-Parity status: every function is pinned by ``tests/test_oracle_pins.py`` and
-``tests/test_oracle3d_pins.py`` and ``tests/test_oracle9_pins.py`` (dense
+Parity status: every function is pinned by ``tests/test_oracle_pins.py``,
+``tests/test_oracle_block_pins.py``, ``tests/test_oracle3d_pins.py`` and
+``tests/test_oracle9_pins.py`` (dense
 direct solves, the explicit SOR
 iteration matrix, closed-form harmonic and quadratic solutions, a DST-I fast
 Poisson solve, SOR convergence theory and superposition/symmetry invariants).
@@ -75,6 +80,9 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.oracle_sor_f64.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip, _dp, _dp, _dp]
+            lib.oracle_sor_block_f64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
+                                                 _ip, _ip, _dp, _dp, _dp]
             lib.oracle_sor_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -147,6 +155,31 @@ def sor_f64(u0, omega, *, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_
                                 ctypes.byref(md), ctypes.byref(rr), _ptr(tr))
     if rc != 0:
         raise ValueError("oracle_sor_f64: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
+               final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def sor_block_f64(u0, omega, *, by, bx, f=None, max_iters=5000, check_every=1, tol=1e-8, stop_mode=0,
+                  trace=False):
+    """Block two-colour SOR in FP64 (the reading of block-parallel SOR stated
+    in ``sor_oracle.c``): blocks of ``by`` x ``bx`` cells coloured (I + J) mod
+    2, colour 0 first, row-major order inside a block.  Same loop, stopping
+    test and result dict as :func:`sor_f64` (no stall rule)."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _grid(u0, n)
+    f = _src(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md, rr = ctypes.c_double(0), ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor_block_f64(n, int(by), int(bx), float(omega), _ptr(u0), _ptr(f), int(max_iters),
+                                      int(check_every), float(tol), int(stop_mode), _ptr(u), ctypes.byref(it),
+                                      ctypes.byref(cv), ctypes.byref(md), ctypes.byref(rr), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor_block_f64: bad arguments")
     out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
                final_resid_rel=rr.value)
     if trace:

@@ -302,3 +302,97 @@ int oracle_refine(int n, double omega, const double *u0, const double *f, int in
   if (final_resid_rel) *final_resid_rel = rho;
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * Block two-colour SOR (block-parallel SOR).
+ *
+ * Section 3.1 names block-parallel SOR beside red-black and multi-colour SOR
+ * as a parallel form of SOR, citing other work, and does not define it; the
+ * reading taken here:
+ *   - the interior is tiled into blocks of by rows x bx columns: block
+ *     (I, J) holds rows 1 + I*by .. min(n, (I+1)*by) and columns
+ *     1 + J*bx .. min(n, (J+1)*bx) (the last blocks of a row or column are
+ *     clipped at n);
+ *   - block (I, J) has colour (I + J) mod 2, so blocks of one colour touch
+ *     only at corners and the 5-point stencil couples a block only to itself
+ *     and to blocks of the other colour;
+ *   - one iteration updates every colour-0 block, then every colour-1 block;
+ *     inside a block the cells are updated one at a time in row-major order
+ *     with the update of Eq. 1 (the expression and rounding order of
+ *     phase_f64), each reading the newest value of every neighbour.
+ * The blocks of a colour are independent, so they may run in any order or
+ * at once (the parallelism of the method); they are taken here in row-major
+ * block order.  by = bx = 1 gives red-black SOR (colour (i + j) mod 2, red
+ * first); one block covering the interior gives SOR in natural row-major
+ * order.  Each interior cell is updated once per iteration, so the largest
+ * per-update change is again the difference between successive iterates.
+ * ------------------------------------------------------------------------- */
+static double block_phase_f64(int n, double *U, const double *g, double omega, int by, int bx, int colour) {
+  const int m = n + 2;
+  const double a = 1.0 - omega, b = omega / 4.0;
+  const int nbr = (n + by - 1) / by, nbc = (n + bx - 1) / bx;
+  double dmax = 0.0;
+  for (int I = 0; I < nbr; ++I) {
+    for (int J = 0; J < nbc; ++J) {
+      if ((I + J) % 2 != colour) continue;
+      const int ilast = (I + 1) * by < n ? (I + 1) * by : n;
+      const int jlast = (J + 1) * bx < n ? (J + 1) * bx : n;
+      for (int i = 1 + I * by; i <= ilast; ++i) {
+        for (int j = 1 + J * bx; j <= jlast; ++j) {
+          const double old = U[IDX(i, j, m)];
+          double s = (U[IDX(i - 1, j, m)] + U[IDX(i + 1, j, m)]) + (U[IDX(i, j - 1, m)] + U[IDX(i, j + 1, m)]);
+          if (g) s = s + g[IDX(i, j, m)];
+          const double nu = a * old + b * s;
+          U[IDX(i, j, m)] = nu;
+          const double d = fabs(nu - old);
+          if (d > dmax || d != d) dmax = d;
+        }
+      }
+    }
+  }
+  return dmax;
+}
+
+/* Block two-colour SOR in FP64 with the loop and stopping test of
+ * oracle_sor_f64 (test every K iterations, strict <; stop_mode 0 on the
+ * largest change, 1 on the scaled residual; no stall rule).  by, bx >= 1.
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_sor_block_f64(int n, int by, int bx, double omega, const double *u0, const double *f, int max_iters,
+                         int check_every, double tol, int stop_mode, double *u, int *iterations, int *converged,
+                         double *final_maxdelta, double *final_resid_rel, double *trace) {
+  if (n < 1 || by < 1 || bx < 1 || max_iters < 0 || check_every < 1 || !u0 || !u) return -1;
+  const int m = n + 2;
+  if (u != u0) memcpy(u, u0, sizeof(double) * (size_t)m * m);
+  double *g = make_g(n, f);
+  if (f && !g) return -1;
+  int it = 0, conv = 0;
+  double mk = 0.0, rho = -1.0;
+  for (int k = 1; k <= max_iters; ++k) {
+    const double d0 = block_phase_f64(n, u, g, omega, by, bx, 0);
+    const double d1 = block_phase_f64(n, u, g, omega, by, bx, 1);
+    mk = (d0 > d1 || d0 != d0) ? d0 : d1;
+    if (trace) trace[k - 1] = mk;
+    it = k;
+    if (k % check_every == 0) {
+      if (stop_mode == 0) {
+        if (mk < tol) { conv = 1; break; }
+      } else {
+        double rm, bm;
+        residual_f64(n, u, g, NULL, &rm, &bm);
+        rho = rel(rm, bm);
+        if (rho < tol) { conv = 1; break; }
+      }
+    }
+  }
+  {
+    double rm, bm;
+    residual_f64(n, u, g, NULL, &rm, &bm);
+    rho = rel(rm, bm);
+  }
+  free(g);
+  if (iterations) *iterations = it;
+  if (converged) *converged = conv;
+  if (final_maxdelta) *final_maxdelta = mk;
+  if (final_resid_rel) *final_resid_rel = rho;
+  return 0;
+}

@@ -99,6 +99,34 @@ def red_black_iteration(u0, omega, iters, f=None):
     return out
 
 
+def ordered_sor_iteration(u0, omega, iters, order, f=None):
+    """SOR with the unknowns updated in the given order (a permutation of the
+    natural row-major interior indices), written as the matrix splitting
+    x_{k+1} = (D - wL)^{-1}[((1-w)D + wU) x_k + w b] with L / U the strictly
+    lower / upper parts of A in that order.  Returns u_1..u_iters."""
+    n = u0.shape[0] - 2
+    A, b = dense_system(u0, f)
+    order = np.asarray(order)
+    P = A[np.ix_(order, order)]
+    bp = b[order]
+    D = np.diag(np.diag(P))
+    L = -np.tril(P, -1)
+    U = -np.triu(P, 1)
+    lhs = D - omega * L
+    M = np.linalg.solve(lhs, (1.0 - omega) * D + omega * U)
+    c = np.linalg.solve(lhs, omega * bp)
+    x = u0[1:-1, 1:-1].ravel()[order].copy()
+    out = []
+    for _ in range(iters):
+        x = M @ x + c
+        full = np.empty(n * n)
+        full[order] = x
+        u = u0.copy()
+        u[1:-1, 1:-1] = full.reshape(n, n)
+        out.append(u)
+    return out
+
+
 def young_rate(omega, n):
     """Asymptotic SOR convergence factor for a consistently ordered matrix
     with Jacobi spectral radius mu = cos(pi h), for omega <= omega_opt."""
