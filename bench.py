@@ -960,6 +960,61 @@ def workload_ninepoint4096(args, ctx, capi, wl):
                        "l2": "4 quarter arrays of 34 MB FP64 (134 MB in all), above the 129 MB L2"}}
 
 
+def workload_block4096(args, ctx, capi, wl):
+    """Block two-colour SOR (the block-parallel SOR of Section 3.1: blocks of by x bx cells coloured (I + J)
+    mod 2, colour 0 first, row-major order inside a block) on the 4098^2 plate of the default workload
+    (random edges U[0, 100], f = 0, w_opt), 1000 iterations with max|change| every 50, device-resident inputs,
+    FP64 in the exact order (bitwise equal to the oracle), for four block shapes.  The oracle is
+    timed on 10 iterations of the same plate on one host core."""
+    import numpy as np
+    import torch
+
+    import oracle
+    n, iters = 4096, 1000
+    u0_np = wl.random_edges(n, args.seed)
+    u0 = torch.from_numpy(u0_np).cuda()
+    out = torch.empty_like(u0)
+    w = capi.sor_omega_opt(n)
+    lines = {}
+    for by, bx in ((32, 64), (32, 128), (16, 128), (8, 256)):
+        kw = dict(block_rows=by, block_cols=bx, precision=capi.SOR_FP64, omega=w, tol=0.0, max_iters=iters,
+                  check_every=50)
+        for _ in range(args.warmup):
+            ctx.solve_block(u0, out=out, **dict(kw, max_iters=100))
+        torch.cuda.synchronize()
+        dev = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, res = ctx.solve_block(u0, out=out, **kw)
+            dev.append(res["device_s"])
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        lup = float(n) * n * iters
+        glups = lup / float(np.median(dev)) / 1e9
+        # 6 algorithmic FP64 flops per update (3 adds of the neighbours, 2 multiplies, 1 add), all issued
+        ach = 6.0 * glups / 1e3
+        lines[f"{by}x{bx}"] = {"glups": glups, "glups_call": lup / dt / 1e9, "solve_s": dt,
+                               "iterations": res["iterations"], "wavefront_lane_use": bx / (bx + by - 1.0),
+                               "roofline": {"bound": "alu", "achieved": ach, "peak": NOMINAL_FP64_TFLOPS,
+                                            "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
+                                            "kernel": "k_blk_phase<false,*>"}}
+    best = max(lines, key=lambda k: lines[k]["glups"])
+    cpu = None
+    if not args.no_cpu_baseline:
+        k = 10
+        t0 = time.perf_counter()
+        oracle.sor_block_f64(u0_np, w, by=32, bx=128, max_iters=k, check_every=50, tol=0.0)
+        ct = time.perf_counter() - t0
+        cpu = {"value": float(n) * n * k / ct / 1e9, "unit": "GLUP/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} iterations of the same 4098^2 plate, blocks of 32 x 128"}
+    return {"metric": "block two-colour SOR GLUP/s (4098^2 plate)", "value": lines[best]["glups"],
+            "unit": "GLUP/s", "higher_is_better": True, "dtype": "f64", "detail": lines, "best_shape": best,
+            "cpu_baseline": cpu,
+            "config": {"workload": "4098^2 plate, random edges U[0,100], w_opt, 1000 iterations, max|change| every "
+                                   "50, blocks of 32 x 64, 32 x 128, 16 x 128 and 8 x 256 cells",
+                       "l2": "one 134 MB FP64 array, above the 129 MB L2"}}
+
+
 def workload_fp64rate(args, ctx, capi, wl):
     """The FP64 peak of this GPU as sor_diag_fp64_rate measures it (independent chains of FP64 FMAs and of
     additions on a full-occupancy grid, CUDA-event timed), repeated `steps` times, next to the nominal rate."""
@@ -979,7 +1034,7 @@ def workload_fp64rate(args, ctx, capi, wl):
 WORKLOADS = {"paper": workload_paper, "fp64rate": workload_fp64rate, "plate256": workload_plate256, "poisson4096": workload_poisson4096, "batch512": workload_batch512,
              "serve": workload_serve, "cube256": workload_cube256, "ninepoint4096": workload_ninepoint4096,
              "cubepoisson": workload_cubepoisson, "ninepoisson": workload_ninepoisson,
-             "plate16384": workload_plate16384, "cube512": workload_cube512}
+             "plate16384": workload_plate16384, "cube512": workload_cube512, "block4096": workload_block4096}
 
 
 def run_workload(args):

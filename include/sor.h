@@ -192,6 +192,40 @@ sor_status sor_solve3d(sor_ctx *ctx, const sor_params *params, const double *u0,
 sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, const double *f, double *u_out,
                       sor_result *res);
 
+/* Blocking solve of one plate by block two-colour SOR, the reading taken
+ * here of the block-parallel SOR that Section 3.1 names beside red-black and
+ * multi-colour SOR (it gives no definition of its own):
+ *   - the interior is tiled into blocks of block_rows x block_cols cells,
+ *     block (I, J) holding rows 1 + I*block_rows .. and columns
+ *     1 + J*block_cols .. (the last blocks clipped at N);
+ *   - block (I, J) has colour (I + J) mod 2; an iteration updates every
+ *     colour-0 block, then every colour-1 block;
+ *   - inside a block the cells are updated one at a time in row-major order
+ *     with the update of Eq. 1 (5-point Gauss-Seidel value), each reading the
+ *     newest value of every neighbour:
+ *       U <- (1-w) U + (w/4) (((N + S) + (W + E)) + h^2 f),
+ *     every product and sum rounded on its own in that order (FP64).
+ * Blocks of one colour share no edge, so they are updated at once, one warp
+ * per block (the lanes take the block's rows as a wavefront, which reads the
+ * same values as the row-major order).  1 x 1 blocks are red-black SOR with
+ * red = (i + j) even first; one block covering the interior is SOR in
+ * natural order.  Results equal the CPU reference bit for bit.
+ *   params: n (1 <= N <= 60000), omega (<= 0 selects 2 / (1 + sin(pi / (N+1)))),
+ *           stop (SOR_STOP_MAXDELTA or SOR_STOP_RESID_REL, tested when the
+ *           iteration count is a multiple of check_every), tol, max_iters,
+ *           check_every as for sor_solve; precision must be SOR_FP64; flags
+ *           0 or SOR_FLAG_EXACT_ORDER (the same: the order is always exact);
+ *           stall_window must be 0.  Anything else returns SOR_ERR_INVALID_ARG.
+ *   block_rows: 1 .. 32; block_cols: >= 1 (else SOR_ERR_INVALID_ARG).
+ *   u0, f, u_out: as for sor_solve ((N+2)^2, N^2 or NULL, (N+2)^2; host or
+ *          device memory; u_out may equal u0).  A device u_out holds the
+ *          iterate during the solve.  res: optional (final_resid_rel is the
+ *          scaled residual of the returned iterate).
+ * Device memory counts against the context's budget (SOR_ERR_BUDGET when
+ * the solve does not fit). */
+sor_status sor_solve_block(sor_ctx *ctx, const sor_params *params, int32_t block_rows, int32_t block_cols,
+                           const double *u0, const double *f, double *u_out, sor_result *res);
+
 /* Diagnostic of the failure path of the data-flow kernels (sor_solve3d and
  * sor_solve9 in FP64).  Their device-side waits are bounded: a warp whose
  * neighbours do not report progress gives up after a fixed number of polls,

@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libsorgb.so")
 BUILD_DEBUG = os.path.join(PKG, "_build_debug")
 LIB_DEBUG = os.path.join(BUILD_DEBUG, "libsorgb.so")
 SOURCES = ["sor_kernels.cu", "sor_cluster.cu", "sor_runtime.cu", "sor_batch.cu", "sor_capi.cu", "sor_static.cu",
-           "sor3d.cu", "sor9.cu", "sor_probe.cu", "sor_wf.cu", "sor_tile.cu", "sor_grid.cu"]
+           "sor3d.cu", "sor9.cu", "sor_probe.cu", "sor_wf.cu", "sor_tile.cu", "sor_grid.cu", "sor_block.cu"]
 HEADERS = ["sor_device.cuh", "sor_devfn.cuh", "sor_bits.cuh", "sor_strips.cuh", "sor_kernels.h", "sor_runtime.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

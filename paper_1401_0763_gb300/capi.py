@@ -53,7 +53,8 @@ SOR_OPT_CUBE_DEPTH = 11
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",
             "sor_status_string", "sor_omega_opt", "sor_solve_static", "sor_solve3d",
-            "sor_solve9", "sor_diag_flow_wait", "sor_diag_fp64_rate", "sor_diag_bounds", "sor_batch_submit3d")
+            "sor_solve9", "sor_diag_flow_wait", "sor_diag_fp64_rate", "sor_diag_bounds", "sor_batch_submit3d",
+            "sor_solve_block")
 
 
 class sor_params(ctypes.Structure):
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = False):
         lib.sor_solve3d.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     P(sor_result)]
         lib.sor_solve9.argtypes = lib.sor_solve.argtypes
+        lib.sor_solve_block.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, P(sor_result)]
         lib.sor_batch_submit.argtypes = [ctypes.c_void_p, P(sor_params), ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, P(ctypes.c_uint64)]
         lib.sor_batch_submit3d.argtypes = lib.sor_batch_submit.argtypes
@@ -340,6 +343,31 @@ class Context:
         p = make_params(n, **kw)
         st, res = self.solve9_raw(p, _ptr(u0), _ptr(f), _ptr(out))
         self._check(st, "sor_solve9")
+        return out, res.as_dict()
+
+    def solve_block_raw(self, params: sor_params, block_rows: int, block_cols: int, u0_ptr, f_ptr, out_ptr):
+        """sor_solve_block on raw addresses; returns (status, result)."""
+        res = sor_result()
+        st = self._lib.sor_solve_block(self._h, ctypes.byref(params), int(block_rows), int(block_cols),
+                                       ctypes.c_void_p(u0_ptr), ctypes.c_void_p(f_ptr) if f_ptr else None,
+                                       ctypes.c_void_p(out_ptr), ctypes.byref(res))
+        return st, res
+
+    def solve_block(self, u0, f=None, out=None, *, block_rows: int, block_cols: int, **kw) -> tuple:
+        """Blocking block two-colour SOR solve (blocks of block_rows x
+        block_cols cells, colour (I + J) mod 2, row-major order inside a
+        block).  ``u0`` is (n+2, n+2), ``f`` is (n, n) or None.  Returns
+        (u_out, result dict)."""
+        n = int(u0.shape[0]) - 2
+        if tuple(u0.shape) != (n + 2, n + 2):
+            raise ValueError("u0 must be square (n+2, n+2)")
+        if f is not None and tuple(f.shape) != (n, n):
+            raise ValueError("f must be (n, n)")
+        if out is None:
+            out = np.empty_like(u0) if isinstance(u0, np.ndarray) else u0.new_empty(u0.shape)
+        p = make_params(n, **kw)
+        st, res = self.solve_block_raw(p, block_rows, block_cols, _ptr(u0), _ptr(f), _ptr(out))
+        self._check(st, "sor_solve_block")
         return out, res.as_dict()
 
     def submit(self, u0, f=None, out=None, **kw):

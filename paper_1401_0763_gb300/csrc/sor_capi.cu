@@ -168,6 +168,16 @@ sor_status sor_solve9(sor_ctx* h, const sor_params* params, const double* u0, co
   return solve9_blocking(c, params, u0, f, u_out, res);
 }
 
+sor_status sor_solve_block(sor_ctx* h, const sor_params* params, int32_t block_rows, int32_t block_cols,
+                           const double* u0, const double* f, double* u_out, sor_result* res) {
+  if (!h) return SOR_ERR_INVALID_ARG;
+  Ctx* c = &h->impl;
+  DeviceGuard dg(c->device);
+  if (!dg.ok) return SOR_ERR_CUDA;
+  std::lock_guard<std::mutex> g(c->solve_mu);
+  return solve_block_blocking(c, params, block_rows, block_cols, u0, f, u_out, res);
+}
+
 sor_status sor_diag_flow_wait(sor_ctx* h, int polls, int preset, int* timed_out) {
   if (!h) return SOR_ERR_INVALID_ARG;
   Ctx* c = &h->impl;

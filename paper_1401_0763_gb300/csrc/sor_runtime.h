@@ -222,6 +222,14 @@ sor_status solve_blocking(Ctx* c, const Plan& p, const double* u0, const double*
 sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const double* f, double* u_out,
                            sor_result* res);
 
+// Block two-colour SOR (sor_solve_block, sor_block.cu); the caller holds
+// solve_mu.  Blocks of by x bx cells, by <= kBlockMaxRows (a block's rows are
+// the lanes of one warp).
+constexpr int kBlockMaxN = 60000;
+constexpr int kBlockMaxRows = 32;
+sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, const double* u0, const double* f,
+                                double* u_out, sor_result* res);
+
 // 3D cube solve (sor_solve3d); the caller holds solve_mu.
 // Runs the flow kernels' bounded device-side wait on a counter preset to 0
 // (nothing advances it: the wait gives up after `polls` polls) or 1.
