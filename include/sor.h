@@ -334,12 +334,16 @@ typedef enum {
                                    plain slots (8, 16, 32, 64 tried, the highest update rate kept);
                                    > 0 = that many.  Results are identical either way: every slot
                                    stops on the device at its own tested iteration */
-  SOR_OPT_CUBE_DEPTH = 11       /* FP32 sweeps on cubes (sor_solve3d, SOR_FP32): 0 (default) = one
+  SOR_OPT_CUBE_DEPTH = 11,      /* FP32 sweeps on cubes (sor_solve3d, SOR_FP32): 0 (default) = one
                                    data-flow launch per run of iterations, one colour phase at a time;
                                    1 or 2 = that many iterations fused per blocked launch, each tile of
                                    rows x packed columns x planes streamed through its planes with the
                                    colour phases run as a wavefront in shared memory (slower on GB300 at
                                    the sizes measured).  Results are identical */
+  SOR_OPT_BLOCK_CHAIN = 12      /* sor_solve_block: blocks of one block row that a warp segment runs
+                                   back to back, its wavefront carried from one into the next so it
+                                   ramps up and down once per run: 0 (default) = enough blocks for
+                                   about 128 columns per run; k > 0 = k blocks.  Results are identical */
 } sor_option;
 
 sor_status sor_set_option(sor_ctx *ctx, int32_t option, int64_t value);

@@ -49,6 +49,7 @@ SOR_OPT_FAST_CHAIN = 8
 SOR_OPT_FUSED_KERNEL = 9
 SOR_OPT_BATCH_PLAIN_STEP = 10
 SOR_OPT_CUBE_DEPTH = 11
+SOR_OPT_BLOCK_CHAIN = 12
 
 EXPORTED = ("sor_create", "sor_solve", "sor_batch_submit", "sor_poll", "sor_wait", "sor_destroy",
             "sor_set_option", "sor_get_option", "sor_get_stats", "sor_reset_stats", "sor_last_error",

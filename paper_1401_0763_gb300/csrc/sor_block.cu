@@ -50,8 +50,13 @@
 namespace sorgb {
 namespace {
 
-constexpr int kBlkWarps = 4;  // method blocks (one per warp) per CTA
-constexpr int kBlkThreads = 32 * kBlkWarps;
+constexpr int kBlkThreads = 128;  // residual pass
+// A phase runs one warp per CTA: the warps share nothing, and a CTA per
+// warp lets the block scheduler even out the warps per SM (with 4-warp CTAs,
+// 512 CTAs on 152 SMs left some SMs a fourth CTA while the rest idled, 18 %
+// of the cycles in ncu).
+constexpr int kBlkPhaseWarps = 1;
+constexpr int kBlkPhaseThreads = 32 * kBlkPhaseWarps;
 
 #define SORB_CK(ctx, expr)                                                                    \
   do {                                                                                        \
@@ -75,102 +80,150 @@ __global__ void k_blk_source(const double* __restrict__ f, double* __restrict__ 
 
 constexpr int kBlkAhead = 4;  // steps between a load and its use
 
-// The values a lane needs at its column c (when 0 <= c < cols): its east
-// neighbour, the north / south neighbour when it holds the block's first /
-// last row, and the source.  Zero when the lane is idle at that column.
-template <bool HAS_G>
-__device__ __forceinline__ void blk_fetch(double& e, double& nn, double& ss, double& g, int c, bool live, bool top,
-                                          bool bottom, int cols, int j0, const double* __restrict__ Ur,
+// A warp segment's run: up to `chain` blocks of one block row of the phase's
+// colour (block columns J, J + 2, ...), done back to back.  Position v =
+// 0 .. total-1 walks the run's columns (block q covers v in [q*bx, q*bx +
+// cols_q); only the last block of a run can be narrower, and a run never
+// ends in an empty block).  Lane r updates position v at step r + v.
+struct BlkRun {
+  int i0, rows;  // the block row's first grid row and its rows
+  int jb;        // grid column of the run's first cell
+  int stride;    // grid columns from one block's first column to the next one's (2 bx)
+  int total;     // positions in the run (0: no run)
+};
+
+// What a lane needs at position v of its run: the column jv of the cell (0
+// when the lane is idle there, negated at a block's first column), its east
+// neighbour, the old value of the lane's next cell (the east neighbour inside
+// a block, the next block's first cell at a block's end), the north / south
+// neighbour when the lane holds the block's first / last row, the west
+// neighbour at a block's first column, and the source.  Every value read is
+// old: the lane's own later cells are updated only by the lane, after their
+// use, and the rows above and below the block row, the column left of a
+// block and the source are not written in the phase.
+// RUNS false (runs of one block): the next cell is always the east one and
+// the west neighbour of the first column is read once, before the walk.
+template <bool HAS_G, bool RUNS>
+__device__ __forceinline__ void blk_fetch(int& jv, double& e, double& nf, double& nn, double& ss, double& w0,
+                                          double& g, int v, int q, int c, const BlkRun& R, int bx, bool live,
+                                          bool top, bool bottom, const double* __restrict__ Ur,
                                           const double* __restrict__ Un, const double* __restrict__ Us,
                                           const double* __restrict__ Gr) {
-  const bool on = live && c >= 0 && c < cols;
-  const int j = j0 + c;
+  const bool on = live && v >= 0 && v < R.total;
+  const int j = R.jb + q * R.stride + c;
+  jv = on ? (c == 0 ? -j : j) : 0;
   e = on ? Ur[j + 1] : 0.0;
+  if (RUNS) {
+    const bool block_end = c + 1 == bx || v + 1 == R.total;
+    nf = (on && block_end && v + 1 < R.total) ? Ur[j + R.stride - bx + 1] : e;
+    w0 = (on && c == 0) ? Ur[j - 1] : 0.0;
+  } else {
+    nf = e;
+    w0 = 0.0;
+  }
   nn = (on && top) ? Un[j] : 0.0;
   ss = (on && bottom) ? Us[j] : 0.0;
   g = (HAS_G && on) ? __ldg(Gr + j) : 0.0;
 }
 
-// One colour phase: every block of colour `colour`.  Blocks of the colour
-// are numbered w = I * slots + k with J = 2k + ((I + colour) & 1), slots =
-// ceil(nbc / 2); a number whose J lies past the last block column is
-// skipped.  A warp is cut into 32 / SEG segments of SEG lanes (SEG the
-// smallest power of two >= by, passed as seg_log2), one block per segment,
-// so blocks of few rows still fill the warp and their wavefronts ramp up and
-// down in by - 1 steps, not 31; the shuffles stay inside a segment.
-// MEASURE: fold |change| into st->dmax_bits.
-template <bool HAS_G, bool MEASURE>
-__global__ void __launch_bounds__(kBlkThreads) k_blk_phase(double* __restrict__ U, const double* __restrict__ G,
-                                                           int n, int pitch, int by, int bx, int nbr, int slots,
-                                                           int seg_log2, int colour, double a, double b,
+// One colour phase: every block of colour `colour`.  A warp is cut into
+// 32 / SEG segments of SEG lanes (SEG the smallest power of two >= by,
+// passed as seg_log2); each segment takes runs of up to `chain` blocks of one
+// block row (numbered run = I * runs_per_row + h), so blocks of few rows
+// still fill the warp and a wavefront ramps up and down once per run rather
+// than once per block; the shuffles stay inside a segment.
+// RUNS false: runs of one block (chain == 1), with fewer values in flight
+// per lane (fewer registers: more warps per SM, measured faster for blocks
+// of 128 columns or more).  MEASURE: fold |change| into st->dmax_bits.
+template <bool HAS_G, bool MEASURE, bool RUNS>
+__global__ void __launch_bounds__(kBlkPhaseThreads) k_blk_phase(double* __restrict__ U, const double* __restrict__ G,
+                                                           int n, int pitch, int by, int bx, int nbr, int nbc,
+                                                           int chain, int seg_log2, int colour, double a, double b,
                                                            SlotState* st) {
   if (*((volatile int*)&st->done)) return;
   const int lane = threadIdx.x & 31;
   const int segw = 1 << seg_log2, per_warp = 32 >> seg_log2;
-  const int r = lane & (segw - 1);  // the lane's row in its block
-  const long long nblk = (long long)nbr * slots;
-  const long long tasks = (nblk + per_warp - 1) / per_warp;
+  const int r = lane & (segw - 1);  // the lane's row in its block row
+  const int slots = (nbc + 1) >> 1;
+  const int runs_per_row = (slots + chain - 1) / chain;
+  const long long nruns = (long long)nbr * runs_per_row;
+  const long long tasks = (nruns + per_warp - 1) / per_warp;
   unsigned long long dm = 0;
-  for (long long task = blockIdx.x * (long long)kBlkWarps + (threadIdx.x >> 5); task < tasks;
-       task += (long long)gridDim.x * kBlkWarps) {
-    const long long w = task * per_warp + (lane >> seg_log2);
-    int i0 = 1, j0 = 1, rows = 0, cols = 0;
-    if (w < nblk) {
-      const int I = (int)(w / slots);
-      const int J = 2 * (int)(w - (long long)I * slots) + ((I + colour) & 1);
+  for (long long task = blockIdx.x * (long long)kBlkPhaseWarps + (threadIdx.x >> 5); task < tasks;
+       task += (long long)gridDim.x * kBlkPhaseWarps) {
+    const long long run = task * per_warp + (lane >> seg_log2);
+    BlkRun R{1, 0, 1, 2 * bx, 0};
+    if (run < nruns) {
+      const int I = (int)(run / runs_per_row), h = (int)(run - (long long)I * runs_per_row);
+      const int J = ((I + colour) & 1) + 2 * h * chain;  // first block column of the run
       if ((long long)J * bx < n) {
-        i0 = 1 + I * by;
-        j0 = 1 + J * bx;
-        rows = min(by, n + 1 - i0);
-        cols = min(bx, n + 1 - j0);
-        // the block and the neighbours it reads: rows i0-1 .. i0+rows, columns j0-1 .. j0+cols
-        if (!dbg_range(i0 - 1, i0 + rows + 1, (long long)n + 2, st) ||
-            !dbg_range(j0 - 1, j0 + cols + 1, pitch, st))
-          rows = cols = 0;
+        // blocks J, J + 2, ... below nbc, at most `chain` of them
+        const int nq = min(chain, (nbc - J + 1) >> 1);
+        const int jlast0 = 1 + (J + 2 * (nq - 1)) * bx;  // first column of the run's last block
+        const int cols_last = min(bx, n + 1 - jlast0);
+        R.i0 = 1 + I * by;
+        R.rows = min(by, n + 1 - R.i0);
+        R.jb = 1 + J * bx;
+        R.total = (nq - 1) * bx + cols_last;
+        // the run's rows and columns with the neighbours it reads
+        if (!dbg_range(R.i0 - 1, R.i0 + R.rows + 1, (long long)n + 2, st) ||
+            !dbg_range(R.jb - 1, (long long)jlast0 + cols_last + 1, pitch, st))
+          R.rows = R.total = 0;
       }
     }
-    const bool live = r < rows;
-    const int i = i0 + (live ? r : 0);
+    const bool live = r < R.rows;
+    const int i = R.i0 + (live ? r : 0);
     double* __restrict__ Ur = U + (size_t)i * pitch;
     const double* __restrict__ Gr = HAS_G ? G + (size_t)i * pitch : nullptr;
-    const double* __restrict__ Un = U + (size_t)(i - 1) * pitch;  // north row (another block or the ring)
+    const double* __restrict__ Un = U + (size_t)(i - 1) * pitch;  // north row (another block row or the ring)
     const double* __restrict__ Us = U + (size_t)(i + 1) * pitch;  // south row
-    const bool top = r == 0, bottom = r == rows - 1;
-    double cur = live ? Ur[j0] : 0.0;          // old value of the cell the lane updates next
-    const double west0 = live ? Ur[j0 - 1] : 0.0;  // west neighbour of its first cell (old)
-    double last = 0.0;                         // the lane's most recent result
-    const int steps = __reduce_max_sync(0xffffffffu, (unsigned)max(cols + rows - 1, 0));
-    // Loads run kBlkAhead steps ahead of their use (all of them read old
-    // values: a lane's east cells are updated only by the lane itself, after
-    // their use; north / south rows of the first / last lane and the source
-    // are not written in the phase), so the per-step chain holds only the
-    // shuffles and the arithmetic.
-    double qe[kBlkAhead], qn[kBlkAhead], qs[kBlkAhead], qg[kBlkAhead];
+    const bool top = r == 0, bottom = r == R.rows - 1;
+    double cur = (live && R.total > 0) ? Ur[R.jb] : 0.0;  // old value of the cell the lane updates next
+    double last = 0.0;                                   // the lane's most recent result
+    const double west_first = (!RUNS && live && R.total > 0) ? Ur[R.jb - 1] : 0.0;
+    const int steps = __reduce_max_sync(0xffffffffu, (unsigned)max(R.total + R.rows - 1, 0));
+    // fetch position fv, block fq and column fc in it (a run of one block:
+    // fc = fv): loads run kBlkAhead steps ahead of their use
+    int fv = -r, fq = 0, fc = 0;
+    int jq[kBlkAhead];
+    double qe[kBlkAhead], qf[kBlkAhead], qn[kBlkAhead], qs[kBlkAhead], qw[kBlkAhead], qg[kBlkAhead];
 #pragma unroll
-    for (int d = 0; d < kBlkAhead; ++d)
-      blk_fetch<HAS_G>(qe[d], qn[d], qs[d], qg[d], d - r, live, top, bottom, cols, j0, Ur, Un, Us, Gr);
+    for (int d = 0; d < kBlkAhead; ++d) {
+      blk_fetch<HAS_G, RUNS>(jq[d], qe[d], qf[d], qn[d], qs[d], qw[d], qg[d], fv, RUNS ? fq : 0, RUNS ? fc : fv, R,
+                             bx, live, top, bottom, Ur, Un, Us, Gr);
+      if (++fv > 0 && RUNS && ++fc == bx) {
+        fc = 0;
+        ++fq;
+      }
+    }
     for (int t0 = 0; t0 < steps; t0 += kBlkAhead) {
 #pragma unroll
       for (int d = 0; d < kBlkAhead; ++d) {
-        const int c = t0 + d - r;
-        const bool act = live && c >= 0 && c < cols;
-        const double east = qe[d], north_m = qn[d], south_m = qs[d], gv = qg[d];
-        blk_fetch<HAS_G>(qe[d], qn[d], qs[d], qg[d], c + kBlkAhead, live, top, bottom, cols, j0, Ur, Un, Us, Gr);
-        // to the lane above: the old value of the cell below its current one
-        const double offer = (c == -1) ? cur : east;
+        const int v = t0 + d - r;
+        const int j = abs(jq[d]);
+        const bool first_col = jq[d] < 0;
+        const double east = qe[d], next = qf[d], north_m = qn[d], south_m = qs[d], west0 = qw[d], gv = qg[d];
+        blk_fetch<HAS_G, RUNS>(jq[d], qe[d], qf[d], qn[d], qs[d], qw[d], qg[d], fv, RUNS ? fq : 0,
+                               RUNS ? fc : fv, R, bx, live, top, bottom, Ur, Un, Us, Gr);
+        if (++fv > 0 && RUNS && ++fc == bx) {
+          fc = 0;
+          ++fq;
+        }
+        // to the lane above: the old value of the cell below its next one
+        const double offer = (v == -1) ? cur : next;
         const double below = __shfl_down_sync(0xffffffffu, offer, 1, segw);
         const double above = __shfl_up_sync(0xffffffffu, last, 1, segw);
-        if (act) {
+        if (j != 0) {
           const double north = top ? north_m : above;
           const double south = bottom ? south_m : below;
-          const double west = c == 0 ? west0 : last;
+          const double west = first_col ? (RUNS ? west0 : west_first) : last;
           double sum = __dadd_rn(__dadd_rn(north, south), __dadd_rn(west, east));
           if (HAS_G) sum = __dadd_rn(sum, gv);
           const double nu = __dadd_rn(__dmul_rn(a, cur), __dmul_rn(b, sum));
-          Ur[j0 + c] = nu;
+          Ur[j] = nu;
           if (MEASURE) dm = umax64(dm, abs_bits(__dadd_rn(nu, -cur)));
           last = nu;
-          cur = east;
+          cur = next;
         }
       }
     }
@@ -242,15 +295,25 @@ __global__ void k_blk_end(SlotState* st, int K, int max_iters, int stop, double 
   if (k >= max_iters) st->done = 1;
 }
 
+template <bool HAS_G, bool MEASURE>
+void launch_blk_phase2(int grid, cudaStream_t s, double* U, const double* G, int n, int pitch, int by, int bx,
+                       int nbr, int nbc, int chain, int seg_log2, int colour, double a, double b, SlotState* st) {
+  if (chain > 1)
+    k_blk_phase<HAS_G, MEASURE, true><<<grid, kBlkPhaseThreads, 0, s>>>(U, G, n, pitch, by, bx, nbr, nbc, chain,
+                                                                    seg_log2, colour, a, b, st);
+  else
+    k_blk_phase<HAS_G, MEASURE, false><<<grid, kBlkPhaseThreads, 0, s>>>(U, G, n, pitch, by, bx, nbr, nbc, 1, seg_log2,
+                                                                     colour, a, b, st);
+}
+
 template <bool HAS_G>
 void launch_blk_phase(bool measure, int grid, cudaStream_t s, double* U, const double* G, int n, int pitch, int by,
-                      int bx, int nbr, int slots, int seg_log2, int colour, double a, double b, SlotState* st) {
+                      int bx, int nbr, int nbc, int chain, int seg_log2, int colour, double a, double b,
+                      SlotState* st) {
   if (measure)
-    k_blk_phase<HAS_G, true><<<grid, kBlkThreads, 0, s>>>(U, G, n, pitch, by, bx, nbr, slots, seg_log2, colour, a, b,
-                                                           st);
+    launch_blk_phase2<HAS_G, true>(grid, s, U, G, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour, a, b, st);
   else
-    k_blk_phase<HAS_G, false><<<grid, kBlkThreads, 0, s>>>(U, G, n, pitch, by, bx, nbr, slots, seg_log2, colour, a,
-                                                            b, st);
+    launch_blk_phase2<HAS_G, false>(grid, s, U, G, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour, a, b, st);
 }
 
 struct BlkBuffers {
@@ -346,12 +409,24 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
   }
 
   const double a = 1.0 - w, b = w / 4.0;
-  int seg_log2 = 0;  // segments of 2^seg_log2 >= by lanes, one block each
+  int seg_log2 = 0;  // segments of 2^seg_log2 >= by lanes, one run of blocks each
   while ((1 << seg_log2) < by) ++seg_log2;
-  const long long nblk = (long long)nbr * slots;
-  const long long tasks = (nblk + (32 >> seg_log2) - 1) / (32 >> seg_log2);
-  const int grid = (int)std::max<long long>(1, std::min<long long>((tasks + kBlkWarps - 1) / kBlkWarps,
-                                                                   (long long)c->sm_count * 16));
+  // blocks per run: set by the option, else enough for about 128 columns
+  // when that raises the wavefront's busy lanes, L / (L + by - 1) for a run
+  // of L columns, by more than 15 % (measured on the 4098^2 plate: runs of
+  // several blocks cost about 8 % in bookkeeping, so 32 x 32 and 16 x 32
+  // blocks gain from them, 16 x 64 and 8 x 64 lose)
+  int chain = c->opt_block_chain.load();
+  if (chain <= 0) {
+    chain = std::max(1, 128 / bx);
+    const double one = (double)bx / (bx + by - 1), run = (double)(chain * bx) / (chain * bx + by - 1);
+    if (run < 1.15 * one) chain = 1;
+  }
+  chain = std::max(1, std::min(slots, chain));
+  const long long nruns = (long long)nbr * ((slots + chain - 1) / chain);
+  const long long tasks = (nruns + (32 >> seg_log2) - 1) / (32 >> seg_log2);
+  const int grid = (int)std::max<long long>(1, std::min<long long>((tasks + kBlkPhaseWarps - 1) / kBlkPhaseWarps,
+                                                                   (long long)c->sm_count * 64));
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   SORB_CK(c, cudaEventCreate(&ev0));
   if (cudaEventCreate(&ev1) != cudaSuccess) {
@@ -392,11 +467,11 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
       const bool measure = tested || k == p->max_iters;
       for (int colour = 0; colour < 2; ++colour) {
         if (has_f)
-          launch_blk_phase<true>(measure, grid, s, d_u, d_g, n, pitch, by, bx, nbr, slots, seg_log2, colour, a, b,
-                                 d_state);
+          launch_blk_phase<true>(measure, grid, s, d_u, d_g, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour,
+                                 a, b, d_state);
         else
-          launch_blk_phase<false>(measure, grid, s, d_u, nullptr, n, pitch, by, bx, nbr, slots, seg_log2, colour, a,
-                                  b, d_state);
+          launch_blk_phase<false>(measure, grid, s, d_u, nullptr, n, pitch, by, bx, nbr, nbc, chain, seg_log2,
+                                  colour, a, b, d_state);
       }
       if (stop == kStopResid && tested) {
         if (has_f)

@@ -271,6 +271,10 @@ sor_status sor_set_option(sor_ctx* h, int32_t option, int64_t value) {
       if (v < 0 || v > 2) return SOR_ERR_INVALID_ARG;
       c->opt_cube_depth = v;
       return SOR_OK;
+    case SOR_OPT_BLOCK_CHAIN:
+      if (v > (1 << 20)) return SOR_ERR_INVALID_ARG;
+      c->opt_block_chain = v;
+      return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }
@@ -290,6 +294,7 @@ sor_status sor_get_option(sor_ctx* h, int32_t option, int64_t* value) {
     case SOR_OPT_FUSED_KERNEL: *value = c->opt_fused_kernel.load(); return SOR_OK;
     case SOR_OPT_BATCH_PLAIN_STEP: *value = c->opt_plain_step.load(); return SOR_OK;
     case SOR_OPT_CUBE_DEPTH: *value = c->opt_cube_depth.load(); return SOR_OK;
+    case SOR_OPT_BLOCK_CHAIN: *value = c->opt_block_chain.load(); return SOR_OK;
     default: return SOR_ERR_INVALID_ARG;
   }
 }

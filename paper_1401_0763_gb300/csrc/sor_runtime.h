@@ -183,6 +183,7 @@ struct Ctx {
   std::atomic<int> opt_fused_kernel{0};  // 0: by grid size, 1: tile family, 2: wavefront family
   std::atomic<int> opt_plain_step{0};    // batch plain slots: iterations per step (0: tuned online)
   std::atomic<int> opt_cube_depth{0};    // FP32 cube sweeps: iterations per blocked launch (0: per-phase flow)
+  std::atomic<int> opt_block_chain{0};   // block SOR: blocks per warp-segment run (0: about 128 columns)
 
   std::mutex tune_mu;
   std::map<std::string, TuneChoice> tuned;  // autotuned choices per "<n bucket> <has source>"

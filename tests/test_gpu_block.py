@@ -65,6 +65,24 @@ def test_block_bitwise(ctx, n, by, bx, with_f):
     check_equal(got, res, ref)
 
 
+@pytest.mark.parametrize("chain", [1, 2, 3, 7, 1000])
+@pytest.mark.parametrize("n,by,bx", [(61, 4, 5), (100, 16, 9), (130, 32, 20), (97, 1, 3)])
+def test_block_runs_of_blocks_bitwise(ctx, chain, n, by, bx):
+    """SOR_OPT_BLOCK_CHAIN: a warp segment runs 1 .. many blocks of a block row back to back; the
+    results are those of the oracle whatever the run length."""
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 800 + n)
+    f = wl.gaussian_source(n, 810 + n)
+    ref = oracle.sor_block_f64(u0, 1.7, by=by, bx=bx, f=f, max_iters=25, check_every=5, tol=1e-12)
+    ctx.set_option(capi.SOR_OPT_BLOCK_CHAIN, chain)
+    try:
+        got, res = run_block(ctx, u0, f, block_rows=by, block_cols=bx, omega=1.7, max_iters=25, check_every=5,
+                             tol=1e-12)
+    finally:
+        ctx.set_option(capi.SOR_OPT_BLOCK_CHAIN, 0)
+    check_equal(got, res, ref)
+
+
 @pytest.mark.parametrize("n,by,bx", [(9, 1, 1), (20, 4, 6), (45, 32, 16)])
 def test_block_runs_to_convergence(ctx, n, by, bx):
     u0 = wl.heat_plate(n, 100.0)
