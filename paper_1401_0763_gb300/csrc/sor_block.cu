@@ -9,8 +9,9 @@
 // row-major order with the update of Eq. 1, each reading the newest value of
 // every neighbour.  Blocks of one colour touch only at corners, so the
 // 5-point stencil couples a block only to itself and to blocks of the other
-// colour: all blocks of a colour run at once, one warp (or a segment of one,
-// for blocks of 16 rows or fewer) each.
+// colour: all blocks of a colour can run at once.  Each goes to a warp (or a
+// segment of one, for blocks of 16 rows or fewer); a segment may take a run
+// of several blocks of its block row one after another (narrow blocks).
 //
 // Inside a block the row-major order is a chain (every cell reads its west
 // and north neighbours' new values), but it is the same chain as a wavefront:
