@@ -23,16 +23,17 @@
 // it bit for bit (the operations are rounded one at a time in the order of
 // the CPU reference: ((N + S) + (W + E)) [+ h^2 f], then (1-w) u + (w/4) s).
 //
-// Data flow of a step: a lane loads the east neighbour of its current cell
-// (which becomes its own old value at the next step); the north value comes
-// from lane r - 1 by a shuffle of its last result, the south value from lane
-// r + 1 by a shuffle of the value that lane loaded this step (its east
-// neighbour, one column behind, i.e. the old value of the cell below this
-// one), the west value is the lane's own last result.  Only the block's
-// first row, last row and first column read neighbours outside the block
-// (cells of other-colour blocks or the Dirichlet ring, unchanged during the
-// phase).  No cell is read from memory after a lane of the warp wrote it in
-// the phase, so the lanes need no barrier beyond the shuffles.
+// Data flow of a step: a lane has loaded (a few steps earlier) the east
+// neighbour of its current cell and the old value of its next cell (the
+// same cell inside a block; the next block's first cell at the end of a
+// block in a run); the north value comes from lane r - 1 by a shuffle of its
+// last result, the south value from lane r + 1 by a shuffle of that lane's
+// next-cell value (one column behind, i.e. the old value of the cell below
+// this one), the west value is the lane's own last result.  Only the
+// block's first row, last row and first column read neighbours outside the
+// block (cells of other-colour blocks or the Dirichlet ring, unchanged
+// during the phase).  No cell is read from memory after a lane of the warp
+// wrote it in the phase, so the lanes need no barrier beyond the shuffles.
 //
 // Storage is the natural (N+2)^2 row-major array: the method reads all four
 // neighbours of a cell from one array, and a block's rows are contiguous.
@@ -317,8 +318,12 @@ void launch_blk_phase(bool measure, int grid, cudaStream_t s, double* U, const d
     launch_blk_phase2<HAS_G, false>(grid, s, U, G, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour, a, b, st);
 }
 
+// The solve's device buffers; released when the solve returns, after the
+// work queued on its stream has finished (an early error return must not
+// free memory that queued kernels still use).
 struct BlkBuffers {
   Ctx* c = nullptr;
+  cudaStream_t s = nullptr;
   std::vector<void*> ptrs;
   size_t reserved = 0;
   void* get(size_t bytes) {
@@ -327,6 +332,7 @@ struct BlkBuffers {
     return p;
   }
   ~BlkBuffers() {
+    if (!ptrs.empty() && cudaStreamSynchronize(s) != cudaSuccess) cudaGetLastError();
     for (void* p : ptrs) ctx_dev_free(c, p);
     if (reserved) ctx_release(c, reserved);
   }
@@ -371,6 +377,7 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
   if (has_f) bytes += nnat * sizeof(double) + (f_dev ? 0 : nf * sizeof(double));
   BlkBuffers B;
   B.c = c;
+  B.s = c->stream;
   sor_status rs = ctx_reserve(c, bytes, false, 0.0);
   if (rs != SOR_OK) {
     c->set_error("block SOR solve does not fit the device-memory budget");
