@@ -9,9 +9,9 @@ debug build:
   outside its range (no memory is accessed at that index);
 * small grids on every plate path -- exact-order and default FP64, FP32
   sweeps of both fused families, defect correction, the batch scheduler --
-  and on the cube and 9-point paths (every precision, the cube's blocked
-  sweeps at both depths) run with no check firing and give the oracle's
-  results.
+  and on the cube, 9-point and block-SOR paths (every precision, the cube's
+  blocked sweeps at both depths, block runs of one and of several blocks) run
+  with no check firing and give the oracle's results.
 The release library reports the checks compiled away.
 """
 import os
@@ -106,6 +106,16 @@ CHILD = textwrap.dedent("""
             refr = oracle.refine9(u0, w, f=f, inner_sweeps=20, tol=1e-9, max_outer=400)
             got, res = ctx.solve9(u0, f, precision=capi.SOR_FP32_REFINE, omega=w, tol=1e-9, max_iters=8000)
             assert np.array_equal(got, refr["u"]), n
+        # block two-colour SOR: one-block runs and runs of several blocks
+        for n, by, bx, chain in ((1, 1, 1, 0), (5, 2, 3, 0), (70, 7, 5, 0), (70, 32, 20, 3), (45, 16, 128, 0)):
+            u0 = wl.random_edges(n, n + 9)
+            f = wl.gaussian_source(n, n + 10) * 5
+            ref = oracle.sor_block_f64(u0, 1.6, by=by, bx=bx, f=f, max_iters=12, check_every=4, tol=-1.0)
+            ctx.set_option(capi.SOR_OPT_BLOCK_CHAIN, chain)
+            got, res = ctx.solve_block(u0, f, block_rows=by, block_cols=bx, omega=1.6, tol=-1.0, max_iters=12,
+                                       check_every=4)
+            ctx.set_option(capi.SOR_OPT_BLOCK_CHAIN, 0)
+            assert np.array_equal(got, ref["u"]), (n, by, bx, chain)
     print("debug build checks passed")
 """) % ROOT
 
