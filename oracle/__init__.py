@@ -18,7 +18,7 @@ short:
 * :func:`sor_block_f64` -- block two-colour SOR, the reading of the
   block-parallel SOR that Section 3.1 names beside red-black SOR: blocks of
   by x bx cells coloured like a checkerboard, colour 0 first, row-major order
-  inside a block.
+  inside a block; :func:`sor_block_f32` -- the same in FP32.
 * :func:`residual` -- the scaled residual h^2 (f - A u) and its infinity
   norm relative to the right-hand side (boundary moved to the right).
 * :func:`refine` -- FP64 defect correction around FP32 (or FP64) inner
@@ -83,6 +83,9 @@ def _load():
             lib.oracle_sor_block_f64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
                                                  ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp,
                                                  _ip, _ip, _dp, _dp, _dp]
+            lib.oracle_sor_block_f32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                                 ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _ip, _ip, _dp,
+                                                 _dp]
             lib.oracle_sor_f32.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, _dp, _ip, _ip, _dp, _dp]
             lib.oracle_residual.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
@@ -182,6 +185,27 @@ def sor_block_f64(u0, omega, *, by, bx, f=None, max_iters=5000, check_every=1, t
         raise ValueError("oracle_sor_block_f64: bad arguments")
     out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value,
                final_resid_rel=rr.value)
+    if trace:
+        out["trace"] = tr[: it.value].copy()
+    return out
+
+
+def sor_block_f32(u0, omega, *, by, bx, f=None, max_iters=5000, check_every=1, tol=1e-8, trace=False):
+    """Block two-colour SOR in FP32 arithmetic and storage, with the
+    conventions of :func:`sor_f32` (stop on max|change|)."""
+    n = int(np.asarray(u0).shape[0]) - 2
+    u0 = _grid(u0, n)
+    f = _src(f, n)
+    u = np.empty_like(u0)
+    it, cv = ctypes.c_int(0), ctypes.c_int(0)
+    md = ctypes.c_double(0)
+    tr = np.zeros(max(max_iters, 1)) if trace else None
+    rc = _load().oracle_sor_block_f32(n, int(by), int(bx), float(omega), _ptr(u0), _ptr(f), int(max_iters),
+                                      int(check_every), float(tol), _ptr(u), ctypes.byref(it), ctypes.byref(cv),
+                                      ctypes.byref(md), _ptr(tr))
+    if rc != 0:
+        raise ValueError("oracle_sor_block_f32: bad arguments")
+    out = dict(u=u, iterations=it.value, converged=bool(cv.value), final_maxdelta=md.value)
     if trace:
         out["trace"] = tr[: it.value].copy()
     return out

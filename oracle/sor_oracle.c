@@ -396,3 +396,72 @@ int oracle_sor_block_f64(int n, int by, int bx, double omega, const double *u0, 
   if (final_resid_rel) *final_resid_rel = rho;
   return 0;
 }
+
+/* One colour phase of block two-colour SOR in FP32 arithmetic (the block
+ * order of block_phase_f64, the expression and rounding of phase_f32). */
+static float block_phase_f32(int n, float *U, const float *g, float a, float b, int by, int bx, int colour) {
+  const int m = n + 2;
+  const int nbr = (n + by - 1) / by, nbc = (n + bx - 1) / bx;
+  float dmax = 0.0f;
+  for (int I = 0; I < nbr; ++I) {
+    for (int J = 0; J < nbc; ++J) {
+      if ((I + J) % 2 != colour) continue;
+      const int ilast = (I + 1) * by < n ? (I + 1) * by : n;
+      const int jlast = (J + 1) * bx < n ? (J + 1) * bx : n;
+      for (int i = 1 + I * by; i <= ilast; ++i) {
+        for (int j = 1 + J * bx; j <= jlast; ++j) {
+          const float old = U[IDX(i, j, m)];
+          float s = (U[IDX(i - 1, j, m)] + U[IDX(i + 1, j, m)]) + (U[IDX(i, j - 1, m)] + U[IDX(i, j + 1, m)]);
+          if (g) s = s + g[IDX(i, j, m)];
+          const float nu = a * old + b * s;
+          U[IDX(i, j, m)] = nu;
+          const float d = fabsf(nu - old);
+          if (d > dmax || d != d) dmax = d;
+        }
+      }
+    }
+  }
+  return dmax;
+}
+
+/* Block two-colour SOR in FP32 arithmetic and storage, with the conventions
+ * of oracle_sor_f32 (u0 rounded to FP32 on entry, coefficients (float)(1-w)
+ * and (float)(w/4), the source rounded once as (float)(h^2 f), stop on
+ * max|change| only, the result widened to FP64 on exit). */
+int oracle_sor_block_f32(int n, int by, int bx, double omega, const double *u0, const double *f, int max_iters,
+                         int check_every, double tol, double *u, int *iterations, int *converged,
+                         double *final_maxdelta, double *trace) {
+  if (n < 1 || by < 1 || bx < 1 || max_iters < 0 || check_every < 1 || !u0 || !u) return -1;
+  const int m = n + 2;
+  const size_t cells = (size_t)m * m;
+  float *U = (float *)malloc(sizeof(float) * cells);
+  float *G = NULL;
+  if (!U) return -1;
+  for (size_t c = 0; c < cells; ++c) U[c] = (float)u0[c];
+  double *g = make_g(n, f);
+  if (f && !g) { free(U); return -1; }
+  if (g) {
+    G = (float *)malloc(sizeof(float) * cells);
+    if (!G) { free(U); free(g); return -1; }
+    for (size_t c = 0; c < cells; ++c) G[c] = (float)g[c];
+    free(g);
+  }
+  const float a = (float)(1.0 - omega), b = (float)(omega / 4.0);
+  int it = 0, conv = 0;
+  float mk = 0.0f;
+  for (int k = 1; k <= max_iters; ++k) {
+    const float d0 = block_phase_f32(n, U, G, a, b, by, bx, 0);
+    const float d1 = block_phase_f32(n, U, G, a, b, by, bx, 1);
+    mk = (d0 > d1 || d0 != d0) ? d0 : d1;
+    if (trace) trace[k - 1] = (double)mk;
+    it = k;
+    if (k % check_every == 0 && (double)mk < tol) { conv = 1; break; }
+  }
+  for (size_t c = 0; c < cells; ++c) u[c] = (double)U[c];
+  free(U);
+  free(G);
+  if (iterations) *iterations = it;
+  if (converged) *converged = conv;
+  if (final_maxdelta) *final_maxdelta = (double)mk;
+  return 0;
+}

@@ -159,3 +159,43 @@ def test_bad_arguments_rejected():
     for kw in (dict(by=0, bx=1), dict(by=1, bx=0)):
         with pytest.raises(ValueError):
             oracle.sor_block_f64(u0, 1.0, max_iters=1, **kw)
+
+
+# --- the FP32 form ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 4, 11])
+@pytest.mark.parametrize("with_f", [False, True])
+@pytest.mark.parametrize("K", [1, 3])
+def test_fp32_unit_blocks_are_red_black_fp32(n, with_f, K):
+    """1 x 1 blocks in FP32 are the FP32 red-black oracle (pinned on its own), bit for bit."""
+    u0 = wl.random_edges(n, seed=40 + n)
+    f = wl.rng(41 + n).uniform(-50, 50, size=(n, n)) if with_f else None
+    a = oracle.sor_f32(u0, 1.45, f=f, max_iters=300, check_every=K, tol=1e-4, trace=True)
+    b = oracle.sor_block_f32(u0, 1.45, by=1, bx=1, f=f, max_iters=300, check_every=K, tol=1e-4, trace=True)
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["trace"], b["trace"])
+    for key in ("iterations", "converged", "final_maxdelta"):
+        assert a[key] == b[key], key
+
+
+@pytest.mark.parametrize("by,bx", [(2, 3), (5, 5), (1, 7), (4, 2)])
+def test_fp32_tracks_fp64_within_single_precision(by, bx):
+    """The FP32 iterate stays within a few single-precision units (relative to the data) of the FP64 one
+    of the same block ordering, itself pinned to the ordered SOR splitting."""
+    n = 10
+    u0 = wl.random_edges(n, seed=50)
+    f = wl.rng(51).uniform(-100, 100, size=(n, n))
+    for k in (1, 5, 40):
+        a = oracle.sor_block_f64(u0, 1.5, by=by, bx=bx, f=f, max_iters=k, tol=-1.0)
+        b = oracle.sor_block_f32(u0, 1.5, by=by, bx=bx, f=f, max_iters=k, tol=-1.0)
+        scale = max(1.0, float(np.max(np.abs(a["u"]))))
+        assert float(np.max(np.abs(a["u"] - b["u"]))) <= 64 * 2.0 ** -24 * scale * k
+
+
+def test_fp32_converges_to_dense_solve_in_single_precision():
+    n = 12
+    u0 = wl.random_edges(n, seed=52)
+    f = wl.rng(53).uniform(-100, 100, size=(n, n))
+    out = oracle.sor_block_f32(u0, 1.5, by=3, bx=4, f=f, max_iters=5000, tol=1e-4)  # FP32 floor of the change: ~1e-5 at |u| ~ 100
+    assert out["converged"]
+    ref = pins.dense_solve(u0, f)
+    assert float(np.max(np.abs(out["u"] - ref))) <= 1e-4 * max(1.0, float(np.max(np.abs(ref))))
