@@ -964,7 +964,7 @@ def workload_block4096(args, ctx, capi, wl):
     """Block two-colour SOR (the block-parallel SOR of Section 3.1: blocks of by x bx cells coloured (I + J)
     mod 2, colour 0 first, row-major order inside a block) on the 4098^2 plate of the default workload
     (random edges U[0, 100], f = 0, w_opt), 1000 iterations with max|change| every 50, device-resident inputs,
-    FP64 in the exact order (bitwise equal to the oracle), for six block shapes.  The oracle is
+    FP64 in the exact order (bitwise equal to the oracle), for six block shapes, and in FP32 for two.  The oracle is
     timed on 10 iterations of the same plate on one host core."""
     import numpy as np
     import torch
@@ -1004,6 +1004,22 @@ def workload_block4096(args, ctx, capi, wl):
                                             "unit": "TFLOP/s", "frac": ach / NOMINAL_FP64_TFLOPS,
                                             "kernel": "k_blk_phase<false,*>"}}
     best = max(lines, key=lambda k: lines[k]["glups"])
+    # the same iterations in FP32 storage and arithmetic (bitwise equal to the FP32 oracle)
+    for by, bx in ((16, 128), (32, 128)):
+        kw = dict(block_rows=by, block_cols=bx, precision=capi.SOR_FP32, omega=w, tol=0.0, max_iters=iters,
+                  check_every=50)
+        for _ in range(args.warmup):
+            ctx.solve_block(u0, out=out, **dict(kw, max_iters=100))
+        torch.cuda.synchronize()
+        dev = []
+        for _ in range(args.steps):
+            _, res = ctx.solve_block(u0, out=out, **kw)
+            dev.append(res["device_s"])
+        lines[f"fp32_{by}x{bx}"] = {
+            "glups": float(n) * n * iters / float(np.median(dev)) / 1e9, "iterations": res["iterations"],
+            "hbm_gbs_unfused": 8.0 * float(n) * n * iters / float(np.median(dev)) / 1e9,
+            "note": "FP32 storage, blocks staged in shared memory; device time of the iterations (the rounding of "
+                    "u0 to FP32 and the widening of the result excluded)"}
     cpu = None
     if not args.no_cpu_baseline:
         k = 10

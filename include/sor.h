@@ -204,7 +204,9 @@ sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, 
  *     with the update of Eq. 1 (5-point Gauss-Seidel value), each reading the
  *     newest value of every neighbour:
  *       U <- (1-w) U + (w/4) (((N + S) + (W + E)) + h^2 f),
- *     every product and sum rounded on its own in that order (FP64).
+ *     every product and sum rounded on its own in that order, in FP64, or in
+ *     FP32 (precision SOR_FP32: u0 and h^2 f rounded once to FP32, the
+ *     coefficients (float)(1-w) and (float)(w/4), the result widened).
  * Blocks of one colour share no edge, so they are updated at once, one warp
  * per block (the lanes take the block's rows as a wavefront, which reads the
  * same values as the row-major order).  1 x 1 blocks are red-black SOR with
@@ -213,14 +215,18 @@ sor_status sor_solve9(sor_ctx *ctx, const sor_params *params, const double *u0, 
  *   params: n (1 <= N <= 60000), omega (<= 0 selects 2 / (1 + sin(pi / (N+1)))),
  *           stop (SOR_STOP_MAXDELTA or SOR_STOP_RESID_REL, tested when the
  *           iteration count is a multiple of check_every), tol, max_iters,
- *           check_every as for sor_solve; precision must be SOR_FP64; flags
- *           0 or SOR_FLAG_EXACT_ORDER (the same: the order is always exact);
- *           stall_window must be 0.  Anything else returns SOR_ERR_INVALID_ARG.
+ *           check_every as for sor_solve; precision SOR_FP64 or SOR_FP32 (FP32
+ *           stops on max|change| only, and stages each block with its halo
+ *           in shared memory: (32 / s) (block_rows + 2) (block_cols + 2)
+ *           floats, s the smallest power of two >= block_rows, at most
+ *           200 KB); flags 0 or SOR_FLAG_EXACT_ORDER (the same: the order is
+ *           always exact); stall_window must be 0.  Anything else returns
+ *           SOR_ERR_INVALID_ARG.
  *   block_rows: 1 .. 32; block_cols: >= 1 (else SOR_ERR_INVALID_ARG).
  *   u0, f, u_out: as for sor_solve ((N+2)^2, N^2 or NULL, (N+2)^2; host or
  *          device memory; u_out may equal u0).  A device u_out holds the
  *          iterate during the solve.  res: optional (final_resid_rel is the
- *          scaled residual of the returned iterate).
+ *          scaled residual of the returned iterate, in FP64).
  * Device memory counts against the context's budget (SOR_ERR_BUDGET when
  * the solve does not fit). */
 sor_status sor_solve_block(sor_ctx *ctx, const sor_params *params, int32_t block_rows, int32_t block_cols,

@@ -46,6 +46,7 @@
 #include <sstream>
 #include <vector>
 
+#include "sor_bits.cuh"
 #include "sor_devfn.cuh"
 #include "sor_runtime.h"
 
@@ -318,6 +319,158 @@ void launch_blk_phase(bool measure, int grid, cudaStream_t s, double* U, const d
     launch_blk_phase2<HAS_G, false>(grid, s, U, G, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour, a, b, st);
 }
 
+// FP32 phases (precision SOR_FP32) stage each block in shared memory.  An
+// FP32 step is short, so the FP64 kernel's loads from global memory (each
+// lane walking its own row; L1 hit rate near 30 % in FP32) stall every step;
+// here a warp segment copies its block with the surrounding halo, (rows + 2)
+// x (cols + 2) cells, into its tile, runs the wavefront there and writes the
+// block's cells back.  In the tile, lane r's cell of column c is (r + 1, c +
+// 1): its north neighbour (tile row r) was written by lane r - 1 one step
+// earlier, its south neighbour (tile row r + 2) is still old, its west one is
+// the lane's last result and its east one is still old, as in row-major
+// order; a __syncwarp after every step orders those writes and reads.  Tile
+// rows are ws floats, ws even, so the lanes of a step (addresses r (ws - 1)
+// apart) fall in different banks.  One-block runs only.
+constexpr int kBlkGAhead = 8;  // steps between a source load and its use
+
+// 4-byte asynchronous copy from global to shared memory.
+__device__ __forceinline__ void blk_cp_async4(float* smem_dst, const float* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(saddr), "l"(gsrc) : "memory");
+}
+
+template <bool HAS_G, bool MEASURE>
+__global__ void __launch_bounds__(kBlkPhaseThreads) k_blk_phase_s(float* __restrict__ U, const float* __restrict__ G,
+                                                                 int n, int pitch, int by, int bx, int nbr, int nbc,
+                                                                 int seg_log2, int ws, int colour, float a, float b,
+                                                                 SlotState* st) {
+  extern __shared__ float blk_tile[];
+  if (*((volatile int*)&st->done)) return;
+  const int lane = threadIdx.x & 31;
+  const int segw = 1 << seg_log2, per_warp = 32 >> seg_log2;
+  const int r = lane & (segw - 1), seg = lane >> seg_log2;
+  float* const tile = blk_tile + (size_t)seg * (by + 2) * ws;
+  const int slots = (nbc + 1) >> 1;
+  const long long nblk = (long long)nbr * slots;
+  const long long tasks = (nblk + per_warp - 1) / per_warp;
+  unsigned long long dm = 0;
+  for (long long task = blockIdx.x; task < tasks; task += gridDim.x) {
+    const long long w = task * per_warp + seg;
+    int i0 = 1, j0 = 1, rows = 0, cols = 0;
+    if (w < nblk) {
+      const int I = (int)(w / slots);
+      const int J = 2 * (int)(w - (long long)I * slots) + ((I + colour) & 1);
+      if ((long long)J * bx < n) {
+        i0 = 1 + I * by;
+        j0 = 1 + J * bx;
+        rows = min(by, n + 1 - i0);
+        cols = min(bx, n + 1 - j0);
+        if (!dbg_range(i0 - 1, i0 + rows + 1, (long long)n + 2, st) || !dbg_range(j0 - 1, j0 + cols + 1, pitch, st))
+          rows = cols = 0;
+      }
+    }
+    // stage rows i0-1 .. i0+rows and columns j0-1 .. j0+cols: asynchronous
+    // copies, all in flight together, then one wait
+    if (rows > 0)
+      for (int rr = 0; rr < rows + 2; ++rr) {
+        const float* __restrict__ src = U + (size_t)(i0 - 1 + rr) * pitch + (j0 - 1);
+        for (int cc = r; cc < cols + 2; cc += segw) blk_cp_async4(tile + rr * ws + cc, src + cc);
+      }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+    const bool live = r < rows;
+    float* const trow = tile + (r + 1) * ws;
+    const float* __restrict__ Gr = HAS_G ? G + (size_t)(i0 + (live ? r : 0)) * pitch + j0 : nullptr;
+    float cur = live ? trow[1] : 0.0f;  // old value of the cell the lane updates next
+    float last = 0.0f;                  // the lane's most recent result
+    const int steps = __reduce_max_sync(0xffffffffu, (unsigned)max(rows + cols - 1, 0));
+    float qg[kBlkGAhead];
+#pragma unroll
+    for (int d = 0; d < kBlkGAhead; ++d) {
+      const int c = d - r;
+      qg[d] = (HAS_G && live && c >= 0 && c < cols) ? __ldg(Gr + c) : 0.0f;
+    }
+    for (int t0 = 0; t0 < steps; t0 += kBlkGAhead) {
+#pragma unroll
+      for (int d = 0; d < kBlkGAhead; ++d) {
+        const int c = t0 + d - r;
+        const float gv = qg[d];
+        if (HAS_G) {
+          const int cf = c + kBlkGAhead;
+          qg[d] = (live && cf >= 0 && cf < cols) ? __ldg(Gr + cf) : 0.0f;
+        }
+        if (live && c >= 0 && c < cols) {
+          const float north = tile[r * ws + c + 1];
+          const float south = tile[(r + 2) * ws + c + 1];
+          const float west = c == 0 ? trow[0] : last;
+          const float east = trow[c + 2];
+          float sum = radd(radd(north, south), radd(west, east));
+          if (HAS_G) sum = radd(sum, gv);
+          const float nu = radd(rmul(a, cur), rmul(b, sum));
+          trow[c + 1] = nu;
+          if (MEASURE) dm = umax64(dm, abs_bits(widen_f32(radd(nu, -cur))));
+          last = nu;
+          cur = east;
+        }
+        __syncwarp();
+      }
+    }
+    // write the block's cells back
+    for (int rr = 0; rr < rows; ++rr) {
+      float* __restrict__ dst = U + (size_t)(i0 + rr) * pitch + j0;
+      for (int cc = r; cc < cols; cc += segw) dst[cc] = tile[(rr + 1) * ws + cc + 1];
+    }
+    __syncwarp();  // the next task stages over the tile
+  }
+  if (MEASURE) {
+    dm = warp_max64(dm);
+    if (lane == 0 && dm) atomicMax(&st->dmax_bits, dm);
+  }
+}
+
+void launch_blk_phase_s(bool measure, bool has_g, int grid, size_t smem, cudaStream_t s, float* U, const float* G,
+                        int n, int pitch, int by, int bx, int nbr, int nbc, int seg_log2, int ws, int colour, float a,
+                        float b, SlotState* st) {
+  if (has_g) {
+    if (measure)
+      k_blk_phase_s<true, true><<<grid, kBlkPhaseThreads, smem, s>>>(U, G, n, pitch, by, bx, nbr, nbc, seg_log2, ws,
+                                                                     colour, a, b, st);
+    else
+      k_blk_phase_s<true, false><<<grid, kBlkPhaseThreads, smem, s>>>(U, G, n, pitch, by, bx, nbr, nbc, seg_log2, ws,
+                                                                      colour, a, b, st);
+  } else {
+    if (measure)
+      k_blk_phase_s<false, true><<<grid, kBlkPhaseThreads, smem, s>>>(U, G, n, pitch, by, bx, nbr, nbc, seg_log2, ws,
+                                                                      colour, a, b, st);
+    else
+      k_blk_phase_s<false, false><<<grid, kBlkPhaseThreads, smem, s>>>(U, G, n, pitch, by, bx, nbr, nbc, seg_log2,
+                                                                       ws, colour, a, b, st);
+  }
+}
+
+cudaError_t blk_phase_s_allow(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  const int v = (int)smem;
+  for (cudaError_t x : {cudaFuncSetAttribute(k_blk_phase_s<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v),
+                        cudaFuncSetAttribute(k_blk_phase_s<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, v),
+                        cudaFuncSetAttribute(k_blk_phase_s<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v),
+                        cudaFuncSetAttribute(k_blk_phase_s<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             v)})
+    if (x != cudaSuccess) e = x;
+  return e;
+}
+
+// FP32 storage: the FP64 array rounded to nearest (every cell, the ring
+// included), and back (exact).
+__global__ void k_blk_narrow(const double* __restrict__ src, float* __restrict__ dst, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = __double2float_rn(src[t]);
+}
+__global__ void k_blk_widen(const float* __restrict__ src, double* __restrict__ dst, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = (double)src[t];
+}
+
 // The solve's device buffers; released when the solve returns, after the
 // work queued on its stream has finished (an early error return must not
 // free memory that queued kernels still use).
@@ -352,13 +505,22 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
   if (p->n < 1 || p->n > kBlockMaxN) why << "n must be in [1, " << kBlockMaxN << "]";
   else if (by < 1 || by > kBlockMaxRows) why << "block_rows must be in [1, " << kBlockMaxRows << "]";
   else if (bx < 1) why << "block_cols must be >= 1";
-  else if (p->precision != SOR_FP64) why << "block SOR runs in FP64";
+  else if (p->precision != SOR_FP64 && p->precision != SOR_FP32) why << "block SOR runs in FP64 or FP32";
   else if (p->stop != SOR_STOP_MAXDELTA && p->stop != SOR_STOP_RESID_REL) why << "unknown stop rule";
+  else if (p->precision == SOR_FP32 && p->stop != SOR_STOP_MAXDELTA) why << "FP32 block SOR stops on max|change|";
   else if (p->max_iters < 0 || p->check_every < 1) why << "max_iters >= 0 and check_every >= 1 required";
   else if (p->flags & ~SOR_FLAG_EXACT_ORDER) why << "unknown flags";
   else if (p->stall_window != 0) why << "block SOR has no stall rule: stall_window must be 0";
   else if (std::isnan(p->tol) || std::isnan(p->omega)) why << "tol and omega must not be NaN";
   else if (p->omega > 0.0 && !(p->omega < 2.0)) why << "omega must be in (0, 2)";
+  // FP32: a shared-memory tile of (by + 2) x ws floats per warp segment
+  int seg_log2 = 0;  // segments of 2^seg_log2 >= by lanes, one run of blocks each
+  while ((1 << seg_log2) < by) ++seg_log2;
+  const int ws = (bx + 2) % 2 == 0 ? bx + 2 : bx + 3;
+  const size_t tile_bytes = (size_t)(32 >> seg_log2) * (by + 2) * ws * sizeof(float);
+  if (why.str().empty() && p->precision == SOR_FP32 && tile_bytes > kBlockMaxTileBytes)
+    why << "FP32 block SOR stages each block in shared memory: (32 / s) x (block_rows + 2) x (block_cols + 2) floats, "
+           "s the smallest power of two >= block_rows, must stay within " << kBlockMaxTileBytes << " bytes";
   if (!why.str().empty()) {
     c->set_error(why.str());
     return SOR_ERR_INVALID_ARG;
@@ -375,6 +537,8 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
   size_t bytes = sizeof(SlotState) + 256;
   if (!out_dev) bytes += nnat * sizeof(double);
   if (has_f) bytes += nnat * sizeof(double) + (f_dev ? 0 : nf * sizeof(double));
+  const bool f32 = p->precision == SOR_FP32;  // FP32 storage and arithmetic in the phases
+  if (f32) bytes += (has_f ? 2 : 1) * nnat * sizeof(float);
   BlkBuffers B;
   B.c = c;
   B.s = c->stream;
@@ -388,7 +552,10 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
   double* d_g = has_f ? (double*)B.get(nnat * sizeof(double)) : nullptr;
   double* d_f = (has_f && !f_dev) ? (double*)B.get(nf * sizeof(double)) : nullptr;
   SlotState* d_state = (SlotState*)B.get(sizeof(SlotState));
-  if (!d_u || (has_f && !d_g) || (has_f && !f_dev && !d_f) || !d_state) {
+  float* d_u32 = f32 ? (float*)B.get(nnat * sizeof(float)) : nullptr;
+  float* d_g32 = (f32 && has_f) ? (float*)B.get(nnat * sizeof(float)) : nullptr;
+  if (!d_u || (has_f && !d_g) || (has_f && !f_dev && !d_f) || !d_state || (f32 && !d_u32) ||
+      (f32 && has_f && !d_g32)) {
     c->set_error("device allocation failed");
     return SOR_ERR_OOM;
   }
@@ -415,10 +582,15 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
     k_blk_source<<<fill_grid, 256, 0, s>>>(f_src, d_g, n, pitch, h * h);
     SORB_CK(c, cudaGetLastError());
   }
+  if (f32) {  // the FP32 iterate and source: each FP64 value rounded once
+    k_blk_narrow<<<fill_grid, 256, 0, s>>>(d_u, d_u32, (long long)nnat);
+    if (has_f) k_blk_narrow<<<fill_grid, 256, 0, s>>>(d_g, d_g32, (long long)nnat);
+    SORB_CK(c, cudaGetLastError());
+    SORB_CK(c, blk_phase_s_allow(tile_bytes));
+  }
 
   const double a = 1.0 - w, b = w / 4.0;
-  int seg_log2 = 0;  // segments of 2^seg_log2 >= by lanes, one run of blocks each
-  while ((1 << seg_log2) < by) ++seg_log2;
+  const float a32 = (float)a, b32 = (float)b;
   // blocks per run: set by the option, else enough for about 128 columns
   // when that raises the wavefront's busy lanes, L / (L + by - 1) for a run
   // of L columns, by more than 15 % (measured on the 4098^2 plate: runs of
@@ -430,7 +602,7 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
     const double one = (double)bx / (bx + by - 1), run = (double)(chain * bx) / (chain * bx + by - 1);
     if (run < 1.15 * one) chain = 1;
   }
-  chain = std::max(1, std::min(slots, chain));
+  chain = std::max(1, std::min(slots, f32 ? 1 : chain));  // the FP32 kernel runs one block per segment
   const long long nruns = (long long)nbr * ((slots + chain - 1) / chain);
   const long long tasks = (nruns + (32 >> seg_log2) - 1) / (32 >> seg_log2);
   const int grid = (int)std::max<long long>(1, std::min<long long>((tasks + kBlkPhaseWarps - 1) / kBlkPhaseWarps,
@@ -474,7 +646,10 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
       const bool tested = k % p->check_every == 0;
       const bool measure = tested || k == p->max_iters;
       for (int colour = 0; colour < 2; ++colour) {
-        if (has_f)
+        if (f32)
+          launch_blk_phase_s(measure, has_f, grid, tile_bytes, s, d_u32, d_g32, n, pitch, by, bx, nbr, nbc, seg_log2,
+                             ws, colour, a32, b32, d_state);
+        else if (has_f)
           launch_blk_phase<true>(measure, grid, s, d_u, d_g, n, pitch, by, bx, nbr, nbc, chain, seg_log2, colour,
                                  a, b, d_state);
         else
@@ -496,7 +671,11 @@ sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, con
     finished = h_state->done != 0 || h_state->error != 0;
   }
   SORB_CK(c, cudaEventRecord(ev1, s));
-  // residual of the final iterate
+  if (f32) {
+    k_blk_widen<<<fill_grid, 256, 0, s>>>(d_u32, d_u, (long long)nnat);
+    SORB_CK(c, cudaGetLastError());
+  }
+  // residual of the final iterate (in FP64, of the returned values)
   SORB_CK(c, cudaMemsetAsync(&d_state->rmax_bits, 0, 2 * sizeof(unsigned long long), s));
   if (has_f)
     k_blk_resid<true><<<fill_grid, kBlkThreads, 0, s>>>(d_u, d_g, n, pitch, d_state);

@@ -228,6 +228,7 @@ sor_status solve9_blocking(Ctx* c, const sor_params* p, const double* u0, const 
 // the lanes of one warp).
 constexpr int kBlockMaxN = 60000;
 constexpr int kBlockMaxRows = 32;
+constexpr size_t kBlockMaxTileBytes = 200 * 1024;  // FP32: shared-memory tiles of one warp's blocks
 sor_status solve_block_blocking(Ctx* c, const sor_params* p, int by, int bx, const double* u0, const double* f,
                                 double* u_out, sor_result* res);
 

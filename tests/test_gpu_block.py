@@ -7,7 +7,8 @@ stop decision, max|change| and final residual.  Sizes cover 1 x 1 blocks
 (red-black SOR), single blocks (natural order), ragged last blocks in both
 directions, blocks of 1 to 32 rows (one block per warp, or two to 32 blocks
 sharing a warp in segments of 16, 8, 4, 2 or 1 lanes), the degenerate
-grids n = 1, 2, 3, and the full 4098^2 plate of the benchmark."""
+grids n = 1, 2, 3, and the full 4098^2 plate of the benchmark, in FP64 and
+in FP32 (against the FP32 oracle)."""
 import numpy as np
 import pytest
 
@@ -83,6 +84,54 @@ def test_block_runs_of_blocks_bitwise(ctx, chain, n, by, bx):
     check_equal(got, res, ref)
 
 
+FP32_CASES = [(1, 1, 1), (3, 2, 2), (33, 7, 5), (100, 16, 128), (130, 32, 20), (257, 8, 64), (97, 1, 3),
+              (300, 32, 300), (170, 17, 3)]
+
+
+@pytest.mark.parametrize("n,by,bx", FP32_CASES)
+@pytest.mark.parametrize("with_f", [False, True])
+def test_block_fp32_bitwise(ctx, n, by, bx, with_f):
+    """FP32 storage and arithmetic (blocks staged in shared memory): equal to the FP32 oracle bit for bit
+    (the same roundings of u0, h^2 f and the coefficients); the final residual is the FP64 one of the
+    returned values."""
+    capi = capi_mod()
+    u0 = wl.random_edges(n, 900 + n)
+    f = wl.gaussian_source(n, 910 + n) if with_f else None
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_block_f32(u0, w, by=by, bx=bx, f=f, max_iters=60, check_every=4, tol=1e-5)
+    got, res = run_block(ctx, u0, f, block_rows=by, block_cols=bx, omega=w, max_iters=60, check_every=4, tol=1e-5,
+                         precision=capi.SOR_FP32)
+    assert res["iterations"] == ref["iterations"] and res["converged"] == ref["converged"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+    assert res["final_resid_rel"] == oracle.resid_rel(ref["u"], f=f)
+
+
+def test_block_fp32_host_buffers_and_convergence(ctx):
+    capi = capi_mod()
+    n = 45
+    u0 = wl.heat_plate(n, 100.0)
+    ref = oracle.sor_block_f32(u0, 1.6, by=16, bx=16, max_iters=5000, check_every=3, tol=1e-4)
+    assert ref["converged"]
+    got, res = run_block(ctx, u0, device=False, block_rows=16, block_cols=16, omega=1.6, max_iters=5000,
+                         check_every=3, tol=1e-4, precision=capi.SOR_FP32)
+    assert res["iterations"] == ref["iterations"] and res["converged"]
+    assert np.array_equal(got, ref["u"])
+
+
+def test_block_fp32_full_plate_bitwise(ctx):
+    capi = capi_mod()
+    n = 4096
+    u0 = wl.random_edges(n, 1)
+    w = oracle.omega_opt(n)
+    ref = oracle.sor_block_f32(u0, w, by=16, bx=128, max_iters=6, check_every=3, tol=-1.0)
+    got, res = run_block(ctx, u0, block_rows=16, block_cols=128, omega=w, max_iters=6, check_every=3, tol=-1.0,
+                         precision=capi.SOR_FP32)
+    assert res["iterations"] == ref["iterations"]
+    assert np.array_equal(got, ref["u"])
+    assert res["final_maxdelta"] == ref["final_maxdelta"]
+
+
 @pytest.mark.parametrize("n,by,bx", [(9, 1, 1), (20, 4, 6), (45, 32, 16)])
 def test_block_runs_to_convergence(ctx, n, by, bx):
     u0 = wl.heat_plate(n, 100.0)
@@ -136,7 +185,9 @@ def test_block_rejects_bad_arguments(ctx):
     n = 8
     u0 = torch.from_numpy(wl.heat_plate(n, 1.0)).cuda()
     for kw in (dict(block_rows=0, block_cols=4), dict(block_rows=33, block_cols=4), dict(block_rows=4, block_cols=0),
-               dict(block_rows=4, block_cols=4, precision=capi.SOR_FP32),
+               dict(block_rows=4, block_cols=4, precision=capi.SOR_FP32_REFINE),
+               dict(block_rows=4, block_cols=4, precision=capi.SOR_FP32, stop=capi.SOR_STOP_RESID_REL),
+               dict(block_rows=1, block_cols=4000, precision=capi.SOR_FP32),
                dict(block_rows=4, block_cols=4, stall_window=3), dict(block_rows=4, block_cols=4, omega=2.5)):
         with pytest.raises(RuntimeError):
             ctx.solve_block(u0, **kw)
